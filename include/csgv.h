@@ -1,0 +1,157 @@
+/*
+ * csgv.h -- C ABI of libcsgv.so, a B300 (sm_103a) implementation of the
+ * compressed segmentation volume brick codec of Piochowiak & Dachsbacher,
+ * "Fast Compressed Segmentation Volumes for Scientific Visualization"
+ * (IEEE TVCG 2023).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller
+ *     unless stated otherwise; *_host are host pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it unless stated otherwise.
+ *   - Volumes are uint32 labels, x fastest: element (x, y, z) at
+ *     x + dims[0] * (y + dims[1] * z).
+ *   - Return value: CSGV_OK or an error code; csgv_last_error() gives a
+ *     message for the calling thread.  No call throws, and no kernel traps:
+ *     corrupt data is reported through status words.
+ *
+ * Stream format (fixed readings of the paper, Sec. 3):
+ *   brick b = 2^N (N = 1..5), clamp-to-edge padding, brick id
+ *   bx + nbx * (by + nby * bz); per brick a palette of uint32 labels and two
+ *   rANS-coded nibble streams (interior: children on levels N-1..1; leaf:
+ *   children on level 0).  Nibble = op | stop << 3 with R_p=0 R_x=1 R_y=2
+ *   R_z=3 P_0=4 P_delta=5 P_a=6, a P_delta nibble followed by its delta.
+ *   rANS: 32-bit states, M = 4096, L = 2^16, 16-bit words; K =
+ *   clamp(n / S_min, 1, K_max) interleaved states; stream = K final states
+ *   (low half first) then renormalisation words in decode order.
+ */
+#ifndef CSGV_H
+#define CSGV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CSGV_API __attribute__((visibility("default")))
+#else
+#define CSGV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CSGV_OK = 0,
+    CSGV_PENDING = 1,          /* serve: ticket not finished yet */
+    CSGV_ERR_INVALID_ARG = 2,  /* bad argument (host-side check) */
+    CSGV_ERR_OOM = 3,          /* device or host allocation failed */
+    CSGV_ERR_CORRUPT = 4,      /* per-request status: stream does not follow the format */
+    CSGV_ERR_TIMEOUT = 5,      /* a bounded wait ran out */
+    CSGV_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+    CSGV_ERR_RANGE = 7         /* per-request status: brick id or LOD out of range */
+};
+
+/* Two static nibble frequency tables (Sec. 3.3): interior then leaf, each
+ * 16 entries summing to 4096, every entry >= 1. */
+typedef struct {
+    uint32_t freq[32];
+    uint64_t counts[32]; /* raw nibble counts of the prepass (diagnostic) */
+} csgv_freq_table;
+
+/* Encoder parameters (interleaving rule R10). */
+typedef struct {
+    uint32_t K_max; /* most interleaved rANS states per stream, 1..32 (default 32) */
+    uint32_t S_min; /* symbols per state before another state is added (default 256) */
+} csgv_config;
+
+typedef struct csgv_volume csgv_volume;
+
+typedef struct {
+    uint32_t N;             /* log2 brick size */
+    uint64_t dims[3];       /* volume size in voxels */
+    uint64_t grid[3];       /* bricks per axis */
+    uint64_t n_bricks;
+    uint32_t K_max, S_min;
+    uint32_t max_palette;   /* largest palette of any brick */
+    uint64_t palette_labels, int_words, leaf_words;
+    uint64_t compressed_bytes; /* palettes + streams + per-brick header (3 u64 offsets + 2 u32 counts) */
+    uint32_t freq[32];
+} csgv_volume_info;
+
+/* Message of the last error on this thread ("" if none). */
+CSGV_API const char *csgv_last_error(void);
+
+/*
+ * Frequency prepass (Sec. 3.3 and 3.4: "a quick prepass over a subset of
+ * bricks ... to determine the two frequency tables").  Runs the brick
+ * encoder in count-only mode over every brick whose id is a multiple of
+ * sample_stride, counts interior and leaf nibbles, and normalises each
+ * table to 4096 (f = 1 + floor(c * 4080 / total), remainder to the largest
+ * counts).  vol_dev: dims[0]*dims[1]*dims[2] labels.  b: 2..32, a power of
+ * two.  Synchronises `stream` (reads 32 counters back).
+ */
+CSGV_API int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, uint32_t sample_stride,
+                          csgv_freq_table *out, void *stream);
+
+/*
+ * Brick encoder (Alg. 2, Sec. 3.2-3.4) for every brick of the volume, then
+ * entropy coding and packing.  The library allocates the compressed arrays;
+ * the returned volume owns them until csgv_volume_destroy.  cfg may be NULL
+ * (defaults).  Synchronises `stream` (reads sizes back to allocate).
+ */
+CSGV_API int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
+                       const csgv_config *cfg, csgv_volume **out, void *stream);
+
+/*
+ * Batched decoding (Alg. 1, Sec. 4.1: "the decompression is executed in
+ * parallel for all required bricks").  Request r decodes brick
+ * brick_ids_dev[r] to level of detail lods_dev[r] (0 = full resolution,
+ * N = the single root label) into out_dev + out_offsets_dev[r]:
+ * (b >> lod)^3 labels, x fastest.  One persistent launch; warps take
+ * requests from a work counter.  status_dev[r] receives CSGV_OK,
+ * CSGV_ERR_CORRUPT or CSGV_ERR_RANGE.  All request arrays are device arrays
+ * of n entries owned by the caller.  Asynchronous; the return value covers
+ * argument and launch errors only.
+ */
+CSGV_API int csgv_decode_bricks(const csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
+                       uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream);
+
+/*
+ * Same results as csgv_decode_bricks, one kernel launch per request (the
+ * plain per-brick baseline).
+ */
+CSGV_API int csgv_decode_bricks_plain(const csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev,
+                             uint32_t n, uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev,
+                             void *stream);
+
+/* Sizes and tables of a volume (host call, no device work). */
+CSGV_API int csgv_volume_info_get(const csgv_volume *vol, csgv_volume_info *info);
+
+/*
+ * Copy the compressed arrays to host buffers sized from csgv_volume_info:
+ * offsets have n_bricks + 1 entries (palette offsets in labels, word offsets
+ * in 16-bit words), counts n_bricks entries.  Any pointer may be NULL to
+ * skip that array.  Synchronous.
+ */
+CSGV_API int csgv_volume_export(const csgv_volume *vol, uint64_t *pal_off_host, uint32_t *pal_host, uint64_t *int_off_host,
+                       uint16_t *int_words_host, uint64_t *leaf_off_host, uint16_t *leaf_words_host,
+                       uint32_t *n_int_sym_host, uint32_t *n_leaf_sym_host);
+
+/*
+ * Build a device volume from host arrays in the layout of csgv_volume_export
+ * (for example a stream written by another encoder, or loaded from disk).
+ * freq: 32 entries.  Synchronous.
+ */
+CSGV_API int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint32_t S_min, const uint32_t freq[32],
+                       const uint64_t *pal_off_host, const uint32_t *pal_host, const uint64_t *int_off_host,
+                       const uint16_t *int_words_host, const uint64_t *leaf_off_host, const uint16_t *leaf_words_host,
+                       const uint32_t *n_int_sym_host, const uint32_t *n_leaf_sym_host, csgv_volume **out);
+
+/* Free a volume and its device arrays (synchronises the device). */
+CSGV_API void csgv_volume_destroy(csgv_volume *vol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSGV_H */

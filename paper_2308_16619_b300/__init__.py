@@ -1,0 +1,191 @@
+"""Python binding of libcsgv (include/csgv.h): argument marshalling only.
+
+Every step of encoding and decoding runs in the CUDA kernels of libcsgv.so;
+this module passes tensor pointers, sizes and the current CUDA stream.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the
+library is missing, every call raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcsgv.so")
+
+CSGV_OK, CSGV_PENDING, CSGV_ERR_INVALID_ARG, CSGV_ERR_OOM = 0, 1, 2, 3
+CSGV_ERR_CORRUPT, CSGV_ERR_TIMEOUT, CSGV_ERR_CUDA, CSGV_ERR_RANGE = 4, 5, 6, 7
+
+SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "csgv_decode_bricks",
+           "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
+           "csgv_volume_destroy")
+
+
+class CsgvError(RuntimeError):
+    pass
+
+
+class FreqTable(C.Structure):
+    _fields_ = [("freq", C.c_uint32 * 32), ("counts", C.c_uint64 * 32)]
+
+    def freq_array(self):
+        return np.array(self.freq[:], np.uint32)
+
+
+class Config(C.Structure):
+    _fields_ = [("K_max", C.c_uint32), ("S_min", C.c_uint32)]
+
+
+class VolumeInfo(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("dims", C.c_uint64 * 3), ("grid", C.c_uint64 * 3), ("n_bricks", C.c_uint64),
+                ("K_max", C.c_uint32), ("S_min", C.c_uint32), ("max_palette", C.c_uint32),
+                ("palette_labels", C.c_uint64), ("int_words", C.c_uint64), ("leaf_words", C.c_uint64),
+                ("compressed_bytes", C.c_uint64), ("freq", C.c_uint32 * 32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcsgv.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise CsgvError(f"{LIB_PATH} is missing: build it with `python -m paper_2308_16619_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+        L.csgv_last_error.restype = C.c_char_p
+        L.csgv_build_freq_table.argtypes = [vp, vp, u32, u32, C.POINTER(FreqTable), vp]
+        L.csgv_encode_bricks.argtypes = [vp, vp, u32, C.POINTER(FreqTable), C.POINTER(Config), C.POINTER(vp), vp]
+        for f in (L.csgv_decode_bricks, L.csgv_decode_bricks_plain):
+            f.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp]
+        L.csgv_volume_info_get.argtypes = [vp, C.POINTER(VolumeInfo)]
+        L.csgv_volume_export.argtypes = [vp] * 9
+        L.csgv_volume_import.argtypes = [u32, vp, u32, u32, vp] + [vp] * 8 + [C.POINTER(vp)]
+        L.csgv_volume_destroy.argtypes = [vp]
+        L.csgv_volume_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != CSGV_OK:
+        raise CsgvError(f"csgv error {rc}: {lib().csgv_last_error().decode()}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dims3(vol):
+    Z, Y, X = vol.shape
+    return (C.c_uint64 * 3)(X, Y, Z)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Volume:
+    """A compressed volume held on the device by libcsgv (owns its arrays)."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = VolumeInfo()
+        _check(lib().csgv_volume_info_get(self._h, C.byref(inf)))
+        return inf
+
+    def export(self):
+        """Host copies of the packed arrays (layout as csgv_volume_export)."""
+        inf = self.info()
+        n = inf.n_bricks
+        arrs = dict(pal_off=np.zeros(n + 1, np.uint64), pal=np.zeros(max(inf.palette_labels, 1), np.uint32),
+                    int_off=np.zeros(n + 1, np.uint64), int_words=np.zeros(max(inf.int_words, 1), np.uint16),
+                    leaf_off=np.zeros(n + 1, np.uint64), leaf_words=np.zeros(max(inf.leaf_words, 1), np.uint16),
+                    n_int_sym=np.zeros(n, np.uint32), n_leaf_sym=np.zeros(n, np.uint32))
+        order = ("pal_off", "pal", "int_off", "int_words", "leaf_off", "leaf_words", "n_int_sym", "n_leaf_sym")
+        _check(lib().csgv_volume_export(self._h, *[arrs[k].ctypes.data_as(C.c_void_p) for k in order]))
+        arrs["pal"] = arrs["pal"][:inf.palette_labels]
+        arrs["int_words"] = arrs["int_words"][:inf.int_words]
+        arrs["leaf_words"] = arrs["leaf_words"][:inf.leaf_words]
+        arrs["freq"] = np.array(inf.freq[:], np.uint32)
+        return arrs
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().csgv_volume_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def csgv_build_freq_table(vol, b, sample_stride=1, stream=None):
+    """vol: CUDA tensor [Z, Y, X] of uint32 labels (any 32-bit dtype).  Returns FreqTable."""
+    assert vol.is_cuda and vol.element_size() == 4 and vol.is_contiguous()
+    t = FreqTable()
+    _check(lib().csgv_build_freq_table(_ptr(vol), _dims3(vol), b, sample_stride, C.byref(t), _stream(stream)))
+    return t
+
+
+def csgv_encode_bricks(vol, b, table, K_max=32, S_min=256, stream=None):
+    assert vol.is_cuda and vol.element_size() == 4 and vol.is_contiguous()
+    cfg = Config(K_max, S_min)
+    h = C.c_void_p()
+    _check(lib().csgv_encode_bricks(_ptr(vol), _dims3(vol), b, C.byref(table), C.byref(cfg), C.byref(h),
+                                    _stream(stream)))
+    return Volume(h.value)
+
+
+def csgv_decode_bricks(volume, brick_ids, lods, out, out_offsets, status, stream=None, plain=False):
+    """Device tensors: brick_ids (n, 32-bit), lods (n, uint8), out (32-bit), out_offsets (n, int64), status (n, int32)."""
+    n = brick_ids.numel()
+    for t in (brick_ids, lods, out, out_offsets, status):
+        assert t.is_cuda and t.is_contiguous()
+    assert brick_ids.element_size() == 4 and lods.element_size() == 1 and out.element_size() == 4
+    assert out_offsets.element_size() == 8 and status.element_size() == 4
+    f = lib().csgv_decode_bricks_plain if plain else lib().csgv_decode_bricks
+    _check(f(volume.handle, _ptr(brick_ids), _ptr(lods), n, _ptr(out), _ptr(out_offsets), _ptr(status),
+             _stream(stream)))
+
+
+def csgv_decode_bricks_plain(volume, brick_ids, lods, out, out_offsets, status, stream=None):
+    csgv_decode_bricks(volume, brick_ids, lods, out, out_offsets, status, stream, plain=True)
+
+
+def csgv_volume_import(N, dims_xyz, K_max, S_min, freq, pal_off, pal, int_off, int_words, leaf_off, leaf_words,
+                       n_int_sym, n_leaf_sym):
+    """Build a device volume from host numpy arrays (layout of Volume.export)."""
+    def p(a, dt):
+        a = np.ascontiguousarray(a, dt)
+        return a, a.ctypes.data_as(C.c_void_p)
+    keep = [p(freq, np.uint32), p(pal_off, np.uint64), p(pal if len(pal) else np.zeros(1), np.uint32),
+            p(int_off, np.uint64), p(int_words if len(int_words) else np.zeros(1), np.uint16),
+            p(leaf_off, np.uint64), p(leaf_words if len(leaf_words) else np.zeros(1), np.uint16),
+            p(n_int_sym, np.uint32), p(n_leaf_sym, np.uint32)]
+    h = C.c_void_p()
+    dims = (C.c_uint64 * 3)(*[int(d) for d in dims_xyz])
+    _check(lib().csgv_volume_import(N, dims, K_max, S_min, *[k[1] for k in keep], C.byref(h)))
+    return Volume(h.value)
+
+
+def request_layout(b, lods):
+    """Output offsets (int64) for requests decoded back to back: sizes (b >> lod)^3 (host helper for callers)."""
+    lods = np.asarray(lods, np.int64)
+    sizes = (b >> lods) ** 3
+    off = np.zeros(len(lods), np.int64)
+    if len(lods):
+        off[1:] = np.cumsum(sizes)[:-1]
+    return off, int(sizes.sum())

@@ -1,0 +1,453 @@
+// api.cu -- C ABI of libcsgv (declared in include/csgv.h): argument checks,
+// device allocations owned by volume handles, and kernel launches.
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <atomic>
+
+#include "csgv_internal.cuh"
+#include "../../include/csgv.h"
+
+// kernels' launchers (decode.cu, encode.cu)
+namespace csgv {
+uint32_t decode_smem_bytes(bool wide, uint32_t warps);
+cudaError_t launch_decode_persistent(const VolDev &V, bool wide, const uint32_t *ids, const uint8_t *lods, uint32_t n,
+                                     uint32_t *out, const uint64_t *out_off, int32_t *status, uint32_t *work,
+                                     uint32_t warps, uint32_t blocks, cudaStream_t st);
+cudaError_t launch_decode_single(const VolDev &V, bool wide, const uint32_t *ids, const uint8_t *lods, uint32_t r,
+                                 uint32_t *out, const uint64_t *out_off, int32_t *status, cudaStream_t st);
+}  // namespace csgv
+
+#include "encode_api.cuh"
+
+struct csgv_volume {
+    uint32_t N;
+    uint64_t dims[3], grid[3], n_bricks;
+    uint32_t K_max, S_min, max_palette;
+    uint32_t freq[32];
+    uint64_t n_pal, n_iw, n_lw;
+    uint64_t *pal_off, *int_off, *leaf_off;
+    uint32_t *pal;
+    uint16_t *int_words, *leaf_words;
+    uint32_t *n_int_sym, *n_leaf_sym;
+    uint32_t *lut;
+    uint32_t *work;  // kWorkSlots work counters for persistent decodes
+    std::atomic<uint32_t> next_slot;
+};
+
+namespace {
+
+constexpr uint32_t kWorkSlots = 256;
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(CSGV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+bool pow2_brick(uint32_t b, uint32_t &N) {
+    for (N = 1; N <= (uint32_t)csgv::kMaxN; N++)
+        if ((1u << N) == b) return true;
+    return false;
+}
+
+void build_lut(const uint32_t freq[32], std::vector<uint32_t> &lut) {
+    lut.assign(2 * csgv::kM, 0);
+    for (int t = 0; t < 2; t++) {
+        uint32_t cum = 0;
+        for (uint32_t s = 0; s < 16; s++) {
+            const uint32_t f = freq[16 * t + s];
+            for (uint32_t k = 0; k < f; k++) lut[t * csgv::kM + cum + k] = csgv::lut_pack(s, f, k);
+            cum += f;
+        }
+    }
+}
+
+bool valid_table(const uint32_t *f) {
+    for (int t = 0; t < 2; t++) {
+        uint32_t sum = 0;
+        for (int s = 0; s < 16; s++) {
+            if (f[16 * t + s] == 0 || f[16 * t + s] > csgv::kM) return false;
+            sum += f[16 * t + s];
+        }
+        if (sum != csgv::kM) return false;
+    }
+    return true;
+}
+
+void vol_free_arrays(csgv_volume *v) {
+    cudaFree(v->pal_off); cudaFree(v->int_off); cudaFree(v->leaf_off);
+    cudaFree(v->pal); cudaFree(v->int_words); cudaFree(v->leaf_words);
+    cudaFree(v->n_int_sym); cudaFree(v->n_leaf_sym);
+    cudaFree(v->lut); cudaFree(v->work);
+}
+
+int vol_finish(csgv_volume *v) {
+    std::vector<uint32_t> lut;
+    build_lut(v->freq, lut);
+    CK(cudaMalloc(&v->lut, lut.size() * 4));
+    CK(cudaMemcpy(v->lut, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&v->work, kWorkSlots * 4));
+    CK(cudaMemset(v->work, 0, kWorkSlots * 4));
+    v->next_slot = 0;
+    return CSGV_OK;
+}
+
+csgv::VolDev dev_view(const csgv_volume *v) {
+    csgv::VolDev V;
+    V.pal_off = v->pal_off; V.int_off = v->int_off; V.leaf_off = v->leaf_off;
+    V.pal = v->pal; V.int_words = v->int_words; V.leaf_words = v->leaf_words;
+    V.n_int_sym = v->n_int_sym; V.n_leaf_sym = v->n_leaf_sym;
+    V.lut = v->lut;
+    V.n_bricks = v->n_bricks;
+    V.N = v->N; V.K_max = v->K_max; V.S_min = v->S_min;
+    return V;
+}
+
+int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
+    if (!dims) return fail(CSGV_ERR_INVALID_ARG, "dims is NULL");
+    if (!pow2_brick(b, N)) return fail(CSGV_ERR_INVALID_ARG, "brick size %u is not a power of two in [2, 32]", b);
+    for (int a = 0; a < 3; a++)
+        if (dims[a] == 0 || dims[a] > (1ull << 31)) return fail(CSGV_ERR_INVALID_ARG, "bad dimension %d", a);
+    return CSGV_OK;
+}
+
+int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cudaStream_t st) {
+    if (need <= cap) return CSGV_OK;
+    uint64_t nc = cap ? cap : 1024;
+    while (nc < need) nc = nc + nc / 2 + 1024;
+    void *q = nullptr;
+    CK(cudaMalloc(&q, nc * elem));
+    if (*p && used) CK(cudaMemcpyAsync(q, *p, used * elem, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(*p);
+    *p = q;
+    cap = nc;
+    return CSGV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *csgv_last_error(void) { return g_err.c_str(); }
+
+int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, uint32_t sample_stride,
+                          csgv_freq_table *out, void *stream) {
+    uint32_t N;
+    int rc = check_dims(dims, b, N);
+    if (rc) return rc;
+    if (!vol_dev || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL volume or output");
+    if (sample_stride == 0) return fail(CSGV_ERR_INVALID_ARG, "sample_stride must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    csgv::EncVol EV;
+    EV.vol = vol_dev;
+    uint64_t n = 1;
+    for (int a = 0; a < 3; a++) {
+        EV.dims[a] = dims[a];
+        EV.nb[a] = (dims[a] + b - 1) / b;
+        n *= EV.nb[a];
+    }
+    const uint64_t n_sampled = (n + sample_stride - 1) / sample_stride;
+    csgv::EncGeom G = csgv::make_geom(N, 32, 256);
+    unsigned long long *cnt = nullptr;
+    uint32_t *freq = nullptr;
+    CK(cudaMalloc(&cnt, 32 * 8));
+    CK(cudaMalloc(&freq, 32 * 4));
+    CK(cudaMemsetAsync(cnt, 0, 32 * 8, st));
+    csgv::EncScratch SC{};
+    for (uint64_t first = 0; first < n_sampled; first += 65535) {
+        const uint32_t m = (uint32_t)std::min<uint64_t>(65535, n_sampled - first);
+        cudaError_t e = csgv::launch_encode(EV, G, first * sample_stride, sample_stride, m, nullptr, SC, cnt, st);
+        if (e != cudaSuccess) {
+            cudaFree(cnt); cudaFree(freq);
+            return cuda_fail(e, "encode (count mode)");
+        }
+    }
+    cudaError_t e = csgv::launch_normalize(cnt, freq, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->freq, freq, 32 * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->counts, cnt, 32 * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(cnt);
+    cudaFree(freq);
+    if (e != cudaSuccess) return cuda_fail(e, "frequency prepass");
+    return CSGV_OK;
+}
+
+int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
+                       const csgv_config *cfg, csgv_volume **out, void *stream) {
+    uint32_t N;
+    int rc = check_dims(dims, b, N);
+    if (rc) return rc;
+    if (!vol_dev || !table || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    if (!valid_table(table->freq)) return fail(CSGV_ERR_INVALID_ARG, "frequency tables must sum to 4096 with f >= 1");
+    const uint32_t K_max = cfg ? cfg->K_max : 32, S_min = cfg ? cfg->S_min : 256;
+    if (K_max < 1 || K_max > 32 || S_min < 1) return fail(CSGV_ERR_INVALID_ARG, "K_max must be 1..32, S_min >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    *out = nullptr;
+
+    csgv_volume *v = new csgv_volume();
+    v->N = N;
+    v->K_max = K_max;
+    v->S_min = S_min;
+    memcpy(v->freq, table->freq, sizeof v->freq);
+    csgv::EncVol EV;
+    EV.vol = vol_dev;
+    v->n_bricks = 1;
+    for (int a = 0; a < 3; a++) {
+        v->dims[a] = dims[a];
+        v->grid[a] = EV.nb[a] = (dims[a] + b - 1) / b;
+        EV.dims[a] = dims[a];
+        v->n_bricks *= v->grid[a];
+    }
+    const uint64_t n = v->n_bricks;
+    csgv::EncGeom G = csgv::make_geom(N, K_max, S_min);
+    const size_t per = csgv::scratch_bytes_per_brick(G);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t budget = std::min<size_t>(free_b / 4, (size_t)6 << 30);
+    uint64_t C = std::max<uint64_t>(1, std::min<uint64_t>(n, budget / per));
+    C = std::min<uint64_t>(C, 65535);
+
+    auto cleanup = [&](int code) {
+        vol_free_arrays(v);
+        delete v;
+        return code;
+    };
+    csgv::EncScratch SC{};
+    uint32_t *freq_d = nullptr, *maxpal_d = nullptr;
+    uint64_t *tot_d = nullptr;
+    auto free_tmp = [&]() {
+        cudaFree(SC.pal); cudaFree(SC.nib_int); cudaFree(SC.nib_leaf); cudaFree(SC.w_int); cudaFree(SC.w_leaf);
+        cudaFree(SC.sizes); cudaFree(freq_d); cudaFree(tot_d); cudaFree(maxpal_d);
+    };
+#define CKE(call)                                                  \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) {                                   \
+            free_tmp();                                            \
+            return cleanup(cuda_fail(e_, #call));                  \
+        }                                                          \
+    } while (0)
+    CKE(cudaMalloc(&SC.pal, C * G.pal_cap * 4));
+    CKE(cudaMalloc(&SC.nib_int, C * G.int_cap));
+    CKE(cudaMalloc(&SC.nib_leaf, C * G.leaf_cap));
+    CKE(cudaMalloc(&SC.w_int, C * (G.int_cap + 64) * 2));
+    CKE(cudaMalloc(&SC.w_leaf, C * (G.leaf_cap + 64) * 2));
+    CKE(cudaMalloc(&SC.sizes, C * 8 * 4));
+    CKE(cudaMalloc(&freq_d, 32 * 4));
+    CKE(cudaMalloc(&tot_d, 3 * 8));
+    CKE(cudaMalloc(&maxpal_d, 4));
+    CKE(cudaMalloc(&v->pal_off, (n + 1) * 8));
+    CKE(cudaMalloc(&v->int_off, (n + 1) * 8));
+    CKE(cudaMalloc(&v->leaf_off, (n + 1) * 8));
+    CKE(cudaMalloc(&v->n_int_sym, n * 4));
+    CKE(cudaMalloc(&v->n_leaf_sym, n * 4));
+    CKE(cudaMemcpyAsync(freq_d, table->freq, 32 * 4, cudaMemcpyHostToDevice, st));
+    CKE(cudaMemsetAsync(tot_d, 0, 3 * 8, st));
+    CKE(cudaMemsetAsync(maxpal_d, 0, 4, st));
+    uint64_t cap_p = 0, cap_i = 0, cap_l = 0;
+    uint64_t tot[3] = {0, 0, 0};
+    for (uint64_t first = 0; first < n; first += C) {
+        const uint32_t m = (uint32_t)std::min<uint64_t>(C, n - first);
+        CKE(csgv::launch_encode(EV, G, first, 1, m, freq_d, SC, nullptr, st));
+        CKE(csgv::launch_scan(SC.sizes, m, first, v->pal_off, v->int_off, v->leaf_off, tot_d, st));
+        const uint64_t prev[3] = {tot[0], tot[1], tot[2]};
+        CKE(cudaMemcpyAsync(tot, tot_d, 3 * 8, cudaMemcpyDeviceToHost, st));
+        CKE(cudaStreamSynchronize(st));
+        int g;
+        if ((g = grow((void **)&v->pal, cap_p, std::max<uint64_t>(tot[0], 1), 4, prev[0], st)) ||
+            (g = grow((void **)&v->int_words, cap_i, std::max<uint64_t>(tot[1], 1), 2, prev[1], st)) ||
+            (g = grow((void **)&v->leaf_words, cap_l, std::max<uint64_t>(tot[2], 1), 2, prev[2], st))) {
+            free_tmp();
+            return cleanup(g);
+        }
+        CKE(csgv::launch_compact(G, SC, first, m, v->pal_off, v->int_off, v->leaf_off, v->pal, v->int_words,
+                                 v->leaf_words, v->n_int_sym, v->n_leaf_sym, maxpal_d, st));
+    }
+    CKE(cudaMemcpyAsync(&v->max_palette, maxpal_d, 4, cudaMemcpyDeviceToHost, st));
+    CKE(cudaStreamSynchronize(st));
+    free_tmp();
+#undef CKE
+    v->n_pal = tot[0];
+    v->n_iw = tot[1];
+    v->n_lw = tot[2];
+    rc = vol_finish(v);
+    if (rc) return cleanup(rc);
+    *out = v;
+    return CSGV_OK;
+}
+
+static int decode_args(const csgv_volume *vol, const uint32_t *ids, const uint8_t *lods, uint32_t n, uint32_t *out,
+                       const uint64_t *off, int32_t *status) {
+    if (!vol) return fail(CSGV_ERR_INVALID_ARG, "NULL volume");
+    if (n == 0) return CSGV_OK;
+    if (!ids || !lods || !out || !off || !status) return fail(CSGV_ERR_INVALID_ARG, "NULL request array");
+    return CSGV_OK;
+}
+
+int csgv_decode_bricks(const csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
+                       uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream) {
+    int rc = decode_args(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev);
+    if (rc || n == 0) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    csgv_volume *v = const_cast<csgv_volume *>(vol);
+    const bool wide = v->max_palette > 253;
+    const uint32_t warps = wide ? 8 : 16;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t slot = v->next_slot.fetch_add(1) % kWorkSlots;
+    uint32_t *work = v->work + slot;
+    CK(cudaMemsetAsync(work, 0, 4, st));
+    uint32_t blocks = (uint32_t)sms;
+    const uint32_t need = (n + warps - 1) / warps;
+    if (need < blocks) blocks = need;
+    CK(csgv::launch_decode_persistent(dev_view(v), wide, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev,
+                                      status_dev, work, warps, blocks, st));
+    return CSGV_OK;
+}
+
+int csgv_decode_bricks_plain(const csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev,
+                             uint32_t n, uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev,
+                             void *stream) {
+    int rc = decode_args(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev);
+    if (rc || n == 0) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool wide = vol->max_palette > 253;
+    const csgv::VolDev V = dev_view(vol);
+    for (uint32_t r = 0; r < n; r++)
+        CK(csgv::launch_decode_single(V, wide, brick_ids_dev, lods_dev, r, out_dev, out_offsets_dev, status_dev, st));
+    return CSGV_OK;
+}
+
+int csgv_volume_info_get(const csgv_volume *v, csgv_volume_info *info) {
+    if (!v || !info) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof *info);
+    info->N = v->N;
+    for (int a = 0; a < 3; a++) {
+        info->dims[a] = v->dims[a];
+        info->grid[a] = v->grid[a];
+    }
+    info->n_bricks = v->n_bricks;
+    info->K_max = v->K_max;
+    info->S_min = v->S_min;
+    info->max_palette = v->max_palette;
+    info->palette_labels = v->n_pal;
+    info->int_words = v->n_iw;
+    info->leaf_words = v->n_lw;
+    info->compressed_bytes = v->n_pal * 4 + (v->n_iw + v->n_lw) * 2 + v->n_bricks * (3 * 8 + 2 * 4);
+    memcpy(info->freq, v->freq, sizeof info->freq);
+    return CSGV_OK;
+}
+
+int csgv_volume_export(const csgv_volume *v, uint64_t *pal_off_host, uint32_t *pal_host, uint64_t *int_off_host,
+                       uint16_t *int_words_host, uint64_t *leaf_off_host, uint16_t *leaf_words_host,
+                       uint32_t *n_int_sym_host, uint32_t *n_leaf_sym_host) {
+    if (!v) return fail(CSGV_ERR_INVALID_ARG, "NULL volume");
+    const uint64_t n = v->n_bricks;
+    CK(cudaDeviceSynchronize());
+    if (pal_off_host) CK(cudaMemcpy(pal_off_host, v->pal_off, (n + 1) * 8, cudaMemcpyDeviceToHost));
+    if (int_off_host) CK(cudaMemcpy(int_off_host, v->int_off, (n + 1) * 8, cudaMemcpyDeviceToHost));
+    if (leaf_off_host) CK(cudaMemcpy(leaf_off_host, v->leaf_off, (n + 1) * 8, cudaMemcpyDeviceToHost));
+    if (pal_host && v->n_pal) CK(cudaMemcpy(pal_host, v->pal, v->n_pal * 4, cudaMemcpyDeviceToHost));
+    if (int_words_host && v->n_iw) CK(cudaMemcpy(int_words_host, v->int_words, v->n_iw * 2, cudaMemcpyDeviceToHost));
+    if (leaf_words_host && v->n_lw)
+        CK(cudaMemcpy(leaf_words_host, v->leaf_words, v->n_lw * 2, cudaMemcpyDeviceToHost));
+    if (n_int_sym_host) CK(cudaMemcpy(n_int_sym_host, v->n_int_sym, n * 4, cudaMemcpyDeviceToHost));
+    if (n_leaf_sym_host) CK(cudaMemcpy(n_leaf_sym_host, v->n_leaf_sym, n * 4, cudaMemcpyDeviceToHost));
+    return CSGV_OK;
+}
+
+int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint32_t S_min, const uint32_t freq[32],
+                       const uint64_t *pal_off_host, const uint32_t *pal_host, const uint64_t *int_off_host,
+                       const uint16_t *int_words_host, const uint64_t *leaf_off_host, const uint16_t *leaf_words_host,
+                       const uint32_t *n_int_sym_host, const uint32_t *n_leaf_sym_host, csgv_volume **out) {
+    uint32_t NN;
+    int rc = check_dims(dims, N >= 1 && N <= 5 ? (1u << N) : 0u, NN);
+    if (rc) return rc;
+    if (!out || !freq || !pal_off_host || !int_off_host || !leaf_off_host || !n_int_sym_host || !n_leaf_sym_host)
+        return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    if (!valid_table(freq)) return fail(CSGV_ERR_INVALID_ARG, "frequency tables must sum to 4096 with f >= 1");
+    if (K_max < 1 || K_max > 32 || S_min < 1) return fail(CSGV_ERR_INVALID_ARG, "K_max must be 1..32, S_min >= 1");
+    csgv_volume *v = new csgv_volume();
+    v->N = N;
+    v->K_max = K_max;
+    v->S_min = S_min;
+    memcpy(v->freq, freq, sizeof v->freq);
+    const uint32_t b = 1u << N;
+    v->n_bricks = 1;
+    for (int a = 0; a < 3; a++) {
+        v->dims[a] = dims[a];
+        v->grid[a] = (dims[a] + b - 1) / b;
+        v->n_bricks *= v->grid[a];
+    }
+    const uint64_t n = v->n_bricks;
+    v->n_pal = pal_off_host[n];
+    v->n_iw = int_off_host[n];
+    v->n_lw = leaf_off_host[n];
+    uint32_t maxp = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (pal_off_host[i + 1] < pal_off_host[i] || int_off_host[i + 1] < int_off_host[i] ||
+            leaf_off_host[i + 1] < leaf_off_host[i]) {
+            delete v;
+            return fail(CSGV_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        }
+        maxp = std::max<uint32_t>(maxp, (uint32_t)(pal_off_host[i + 1] - pal_off_host[i]));
+    }
+    v->max_palette = maxp;
+    auto up = [&](void **d, const void *h, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(d, bytes ? bytes : 4);
+        if (e == cudaSuccess && bytes && h) e = cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice);
+        return e;
+    };
+    cudaError_t e = up((void **)&v->pal_off, pal_off_host, (n + 1) * 8);
+    if (e == cudaSuccess) e = up((void **)&v->int_off, int_off_host, (n + 1) * 8);
+    if (e == cudaSuccess) e = up((void **)&v->leaf_off, leaf_off_host, (n + 1) * 8);
+    if (e == cudaSuccess) e = up((void **)&v->pal, pal_host, v->n_pal * 4);
+    if (e == cudaSuccess) e = up((void **)&v->int_words, int_words_host, v->n_iw * 2);
+    if (e == cudaSuccess) e = up((void **)&v->leaf_words, leaf_words_host, v->n_lw * 2);
+    if (e == cudaSuccess) e = up((void **)&v->n_int_sym, n_int_sym_host, n * 4);
+    if (e == cudaSuccess) e = up((void **)&v->n_leaf_sym, n_leaf_sym_host, n * 4);
+    if (e != cudaSuccess) {
+        vol_free_arrays(v);
+        delete v;
+        return cuda_fail(e, "volume import");
+    }
+    rc = vol_finish(v);
+    if (rc) {
+        vol_free_arrays(v);
+        delete v;
+        return rc;
+    }
+    *out = v;
+    return CSGV_OK;
+}
+
+void csgv_volume_destroy(csgv_volume *vol) {
+    if (!vol) return;
+    cudaDeviceSynchronize();
+    vol_free_arrays(vol);
+    delete vol;
+}
+
+}  // extern "C"

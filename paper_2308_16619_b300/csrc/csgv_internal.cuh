@@ -1,0 +1,53 @@
+// csgv_internal.cuh -- constants and device-side structs of libcsgv (CUDA
+// side only).  The stream format is the one documented in include/csgv.h.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace csgv {
+
+// rANS parameters (Sec. 3.3; reading R9): 32-bit state, 12-bit scale,
+// lower bound 2^16, 16-bit renormalisation words.
+constexpr uint32_t kScaleBits = 12;
+constexpr uint32_t kM = 1u << kScaleBits;
+constexpr uint32_t kL = 1u << 16;
+
+// operation codes (reading R6)
+enum : uint32_t { OP_RP = 0, OP_RX = 1, OP_RY = 2, OP_RZ = 3, OP_P0 = 4, OP_PD = 5, OP_PA = 6 };
+
+constexpr int kMaxN = 5;         // b <= 32
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// per-request status codes written by the decoder (same values as the ABI)
+constexpr int32_t kStOk = 0, kStCorrupt = 4, kStRange = 7;
+
+// Morton masks of the x / y / z bits (x = bit 0, R5), up to 5 bits per axis
+constexpr uint32_t kMX = 0x1249u, kMY = 0x2492u, kMZ = 0x4924u;
+
+// Device view of a compressed volume (passed to kernels by value).
+struct VolDev {
+    const uint64_t *pal_off, *int_off, *leaf_off;  // n_bricks + 1 each
+    const uint32_t *pal;
+    const uint16_t *int_words, *leaf_words;
+    const uint32_t *n_int_sym, *n_leaf_sym;
+    const uint32_t *lut;                           // 2 x 4096 packed decode entries
+    uint64_t n_bricks;
+    uint32_t N, K_max, S_min;
+};
+
+// Packed decode table entry for slot s of a table: symbol (4 bits) |
+// frequency (13 bits) << 4 | (s - cum[symbol]) (12 bits) << 17.
+__host__ __device__ inline uint32_t lut_pack(uint32_t sym, uint32_t f, uint32_t bias) {
+    return sym | (f << 4) | (bias << 17);
+}
+
+// number of interleaved states for a stream of n symbols (R10)
+__host__ __device__ inline uint32_t lanes_for(uint32_t n, uint32_t K_max, uint32_t S_min) {
+    if (n == 0) return 0;
+    uint32_t k = n / S_min;
+    if (k < 1) k = 1;
+    if (k > K_max) k = K_max;
+    return k;
+}
+
+}  // namespace csgv

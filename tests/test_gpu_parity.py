@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer codec, so the bar is bit-exact: decoded labels equal the oracle's
+decode (and the original volume at LOD 0), GPU-encoded streams and tables are
+byte-identical to the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _csgv():
+    import paper_2308_16619_b300 as csgv
+    return csgv
+
+
+def to_dev(a):
+    torch = _torch()
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).cuda()
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    return torch.from_numpy(a).cuda()
+
+
+def import_oracle_volume(V):
+    csgv = _csgv()
+    return csgv.csgv_volume_import(V.N, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words,
+                                   V.leaf_off, V.leaf_words, V.n_int_sym, V.n_leaf_sym)
+
+
+def gpu_decode(volume, N, ids, lods, plain=False, offsets=None, total=None):
+    torch = _torch()
+    csgv = _csgv()
+    ids = np.asarray(ids, np.uint32)
+    lods = np.asarray(lods, np.uint8)
+    if offsets is None:
+        offsets, total = csgv.request_layout(1 << N, lods)
+    out = torch.full((max(total, 1),), -1, dtype=torch.int32, device="cuda")
+    status = torch.full((len(ids),), -99, dtype=torch.int32, device="cuda")
+    csgv.csgv_decode_bricks(volume, to_dev(ids), to_dev(lods), out, to_dev(np.asarray(offsets, np.int64)), status,
+                            plain=plain)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32), np.asarray(offsets, np.int64), status.cpu().numpy()
+
+
+def assert_same_arrays(gpu, V):
+    assert np.array_equal(gpu["freq"], V.freq)
+    for k in ("pal_off", "int_off", "leaf_off"):
+        assert np.array_equal(gpu[k], getattr(V, k)), k
+    for k in ("pal", "int_words", "leaf_words", "n_int_sym", "n_leaf_sym"):
+        assert np.array_equal(gpu[k], getattr(V, k)), k
+
+
+def structured_volume(seed, shape, n_sites, n_labels=None, warp=0, bg=0):
+    if n_labels is None:
+        return synth.voronoi(shape, n_sites, seed=seed, warp_amp=warp, bg_permille=bg)
+    v = synth.voronoi(shape, n_sites, seed=seed, warp_amp=warp, bg_permille=bg)
+    # fold labels into a small alphabet to force palette back references and duplicates
+    u, inv = np.unique(v, return_inverse=True)
+    return (inv.reshape(v.shape) % n_labels).astype(np.uint32) * 977 + 5
+
+
+CASES = [
+    # (name, shape zyx, b, sites, n_labels, K_max, S_min)
+    ("b2", (6, 7, 9), 2, 12, 4, 32, 256),
+    ("b4", (12, 16, 20), 4, 30, None, 4, 8),
+    ("b8", (24, 40, 33), 8, 60, 9, 32, 16),
+    ("b16", (48, 32, 64), 16, 80, None, 32, 64),
+    ("b16_small_alphabet", (32, 48, 32), 16, 200, 5, 8, 32),
+    ("b32", (64, 64, 96), 32, 120, None, 32, 256),
+    ("b32_single_state", (64, 32, 64), 32, 200, 7, 1, 256),
+    ("b32_many_states", (32, 64, 64), 32, 300, None, 32, 16),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_decode_oracle_streams_all_lods(case):
+    name, shape, b, sites, nl, K_max, S_min = case
+    N = b.bit_length() - 1
+    vol = structured_volume(7, shape, sites, nl)
+    V = O.encode_volume(vol, N, stride=1, K_max=K_max, S_min=S_min)
+    gv = import_oracle_volume(V)
+    n = V.n_bricks
+    ids = np.repeat(np.arange(n, dtype=np.uint32), N + 1)
+    lods = np.tile(np.arange(N + 1, dtype=np.uint8), n)
+    out, off, st = gpu_decode(gv, N, ids, lods)
+    ref, roff, rst = O.decode_bricks(V, ids, lods)
+    assert (rst == 0).all()
+    assert (st == 0).all(), np.unique(st, return_counts=True)
+    assert np.array_equal(off, roff.astype(np.int64))
+    assert np.array_equal(out[:len(ref)], ref)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_gpu_encode_byte_identical(case):
+    torch = _torch()
+    csgv = _csgv()
+    name, shape, b, sites, nl, K_max, S_min = case
+    N = b.bit_length() - 1
+    vol = structured_volume(11, shape, sites, nl)
+    stride = 3
+    V = O.encode_volume(vol, N, stride=stride, K_max=K_max, S_min=S_min)
+    d = to_dev(vol)
+    table = csgv.csgv_build_freq_table(d, b, stride)
+    assert np.array_equal(table.freq_array(), V.freq)
+    gv = csgv.csgv_encode_bricks(d, b, table, K_max=K_max, S_min=S_min)
+    torch.cuda.synchronize()
+    assert_same_arrays(gv.export(), V)
+
+
+def test_prepass_counts_match_oracle():
+    csgv = _csgv()
+    vol = structured_volume(3, (64, 64, 64), 90)
+    for N, stride in ((4, 1), (4, 5), (5, 2)):
+        ci, cl = O.count_nibbles(vol, N, stride)
+        t = csgv.csgv_build_freq_table(to_dev(vol), 1 << N, stride)
+        assert np.array_equal(np.array(t.counts[:16], np.uint64), ci)
+        assert np.array_equal(np.array(t.counts[16:], np.uint64), cl)
+
+
+def test_voronoi128_roundtrip_and_streams():
+    """128^3, 150 Voronoi cells, b = 32 (64 bricks), table from the whole volume."""
+    torch = _torch()
+    csgv = _csgv()
+    vol = synth.make("voronoi128")
+    V = O.encode_volume(vol, 5, stride=1)
+    d = to_dev(vol)
+    table = csgv.csgv_build_freq_table(d, 32, 1)
+    gv = csgv.csgv_encode_bricks(d, 32, table)
+    assert_same_arrays(gv.export(), V)
+    n = V.n_bricks
+    for t in range(6):
+        ids = np.arange(n, dtype=np.uint32)
+        out, off, st = gpu_decode(gv, 5, ids, np.full(n, t, np.uint8))
+        ref, _, _ = O.decode_bricks(V, ids, np.full(n, t, np.uint8))
+        assert (st == 0).all() and np.array_equal(out, ref), t
+    # LOD 0 equals the original volume brick by brick
+    out, off, st = gpu_decode(gv, 5, np.arange(n, dtype=np.uint32), np.zeros(n, np.uint8))
+    bricks = out.reshape(4, 4, 4, 32, 32, 32)  # [bz, by, bx, z, y, x]
+    rebuilt = bricks.transpose(0, 3, 1, 4, 2, 5).reshape(128, 128, 128)
+    assert np.array_equal(rebuilt, vol)
+    del torch
+
+
+@pytest.mark.parametrize("b", [32, 16])
+def test_voronoi512_full_roundtrip(b):
+    """512^3 warped Voronoi, 30 % background: full GPU encode then decode, bit-exact against the volume;
+    streams byte-identical to the oracle's on every brick."""
+    torch = _torch()
+    csgv = _csgv()
+    N = b.bit_length() - 1
+    vol = synth.make("voronoi512")
+    d = to_dev(vol)
+    table = csgv.csgv_build_freq_table(d, b, 512)
+    gv = csgv.csgv_encode_bricks(d, b, table)
+    V = O.encode_volume(vol, N, stride=512)
+    assert_same_arrays(gv.export(), V)
+    n = V.n_bricks
+    ids = torch.arange(n, dtype=torch.int32, device="cuda")
+    lods = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    offs = torch.arange(n, dtype=torch.int64, device="cuda") * b ** 3
+    out = torch.empty(n * b ** 3, dtype=torch.int32, device="cuda")
+    status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    csgv.csgv_decode_bricks(gv, ids, lods, out, offs, status)
+    g = 512 // b
+    rebuilt = out.view(g, g, g, b, b, b).permute(0, 3, 1, 4, 2, 5).reshape(512, 512, 512)
+    assert bool((status == 0).all())
+    assert bool((rebuilt == d).all())
+
+
+def test_plain_equals_batched_and_mixed_batch_equals_alone():
+    vol = structured_volume(5, (64, 96, 64), 150, warp=0)
+    V = O.encode_volume(vol, 5, stride=1)
+    gv = import_oracle_volume(V)
+    rng = np.random.default_rng(1)
+    ids = rng.integers(0, V.n_bricks, size=300).astype(np.uint32)  # duplicates included
+    lods = rng.integers(0, 6, size=300).astype(np.uint8)
+    out, off, st = gpu_decode(gv, 5, ids, lods)
+    outp, offp, stp = gpu_decode(gv, 5, ids, lods, plain=True)
+    assert (st == 0).all() and (stp == 0).all()
+    assert np.array_equal(out, outp)
+    # each request decoded alone gives the same bytes as inside the mix; order does not matter
+    perm = rng.permutation(300)
+    outq, offq, stq = gpu_decode(gv, 5, ids[perm], lods[perm])
+    for k, r in enumerate(perm[:60]):
+        B3 = (32 >> int(lods[r])) ** 3
+        alone, _, sa = gpu_decode(gv, 5, ids[r:r + 1], lods[r:r + 1])
+        assert sa[0] == 0
+        assert np.array_equal(alone[:B3], out[off[r]:off[r] + B3])
+        assert np.array_equal(outq[offq[k]:offq[k] + B3], out[off[r]:off[r] + B3])
+
+
+def test_unaligned_output_offsets_use_scalar_stores():
+    vol = structured_volume(9, (32, 32, 64), 40)
+    V = O.encode_volume(vol, 4, stride=1)
+    gv = import_oracle_volume(V)
+    n = V.n_bricks
+    ids = np.arange(n, dtype=np.uint32)
+    lods = np.zeros(n, np.uint8)
+    offsets = 3 + np.arange(n, dtype=np.int64) * (4096 + 1)  # not multiples of 4 elements
+    out, _, st = gpu_decode(gv, 4, ids, lods, offsets=offsets, total=int(offsets[-1]) + 4096 + 1)
+    ref, roff, _ = O.decode_bricks(V, ids, lods)
+    assert (st == 0).all()
+    for i in range(n):
+        assert np.array_equal(out[offsets[i]:offsets[i] + 4096], ref[roff[i]:roff[i] + 4096])
+
+
+def test_wide_palette_path():
+    """Bricks with more than 253 palette entries use 16-bit indices in shared memory."""
+    rng = np.random.default_rng(2)
+    vol = rng.integers(0, 5000, size=(32, 32, 64)).astype(np.uint32)
+    vol[:, :, 32:] = 17  # one noise brick, one homogeneous brick
+    V = O.encode_volume(vol, 5, stride=1)
+    assert int(np.diff(V.pal_off.astype(np.int64)).max()) > 253
+    gv = import_oracle_volume(V)
+    assert gv.info().max_palette > 253
+    ids = np.array([0, 1, 0, 1, 0], np.uint32)
+    lods = np.array([0, 0, 1, 3, 5], np.uint8)
+    out, off, st = gpu_decode(gv, 5, ids, lods)
+    ref, _, _ = O.decode_bricks(V, ids, lods)
+    assert (st == 0).all() and np.array_equal(out, ref)
+    csgv = _csgv()
+    d = to_dev(vol)
+    t = csgv.csgv_build_freq_table(d, 32, 1)
+    g2 = csgv.csgv_encode_bricks(d, 32, t)
+    assert_same_arrays(g2.export(), V)
+
+
+def test_range_and_corrupt_status():
+    vol = structured_volume(4, (32, 32, 64), 50)
+    V = O.encode_volume(vol, 5, stride=1)
+    gv = import_oracle_volume(V)
+    # out-of-range brick id and LOD
+    out, off, st = gpu_decode(gv, 5, [0, 2, 1, 0, 1], [0, 0, 0, 6, 5])
+    assert st.tolist() == [0, 7, 0, 7, 0]
+    csgv = _csgv()
+    ids = np.array([0, 1], np.uint32)
+    lods = np.zeros(2, np.uint8)
+    # truncated leaf stream of brick 0: fewer words than its symbols need
+    lo = V.leaf_off.copy()
+    lw = np.delete(V.leaf_words, np.arange(int(lo[1]) - 5, int(lo[1])))
+    lo[1:] -= 5
+    bad = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words, lo,
+                                  lw, V.n_int_sym, V.n_leaf_sym)
+    out, off, st = gpu_decode(bad, 5, ids, lods)
+    ref, _, _ = O.decode_bricks(V, ids, lods)
+    assert st[0] == 4 and st[1] == 0
+    assert np.array_equal(out[off[1]:], ref[off[1]:])
+    # palette of brick 0 cut to one entry: P_a runs past the palette
+    po = V.pal_off.copy()
+    cut = int(po[1]) - 1
+    pal = np.delete(V.pal, np.arange(1, 1 + cut))
+    po[1:] -= cut
+    bad = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, po, pal, V.int_off, V.int_words, V.leaf_off,
+                                  V.leaf_words, V.n_int_sym, V.n_leaf_sym)
+    out, off, st = gpu_decode(bad, 5, ids, lods)
+    assert st[0] == 4 and st[1] == 0
+    # random word flips: never a fault; untouched bricks stay exact
+    rng = np.random.default_rng(8)
+    for trial in range(5):
+        iw = V.int_words.copy()
+        lw = V.leaf_words.copy()
+        k = rng.integers(int(V.int_off[0]), int(V.int_off[1]), size=3)
+        iw[k] ^= rng.integers(1, 65535, size=3).astype(np.uint16)
+        k = rng.integers(int(V.leaf_off[0]), int(V.leaf_off[1]), size=3)
+        lw[k] ^= rng.integers(1, 65535, size=3).astype(np.uint16)
+        bad = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, iw,
+                                      V.leaf_off, lw, V.n_int_sym, V.n_leaf_sym)
+        out, off, st = gpu_decode(bad, 5, ids, lods)
+        assert st[0] in (0, 4) and st[1] == 0
+        assert np.array_equal(out[off[1]:], ref[off[1]:])
