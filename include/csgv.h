@@ -148,6 +148,38 @@ CSGV_API int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_m
                        const uint16_t *int_words_host, const uint64_t *leaf_off_host, const uint16_t *leaf_words_host,
                        const uint32_t *n_int_sym_host, const uint32_t *n_leaf_sym_host, csgv_volume **out);
 
+/*
+ * Allocation-free brick encoder, for callers that cannot call cudaMalloc:
+ * programs whose device memory belongs to their own pool allocator, and
+ * loops that cannot afford cudaFree's device-wide synchronisation.  The
+ * paper has no counterpart; it is the encoder of csgv_encode_bricks
+ * (same kernels, byte-identical output) working in a fixed 32 MiB scratch
+ * array that the library keeps on every GPU that loads it, and writing into
+ * device arrays the caller provides, in the layout of csgv_volume_export:
+ * offsets with n_bricks + 1 entries (u64), palettes (u32), interior and leaf
+ * words (u16), symbol counts (u32, n_bricks).  *_capacity give the sizes of
+ * pal_dev, int_words_dev and leaf_words_dev in elements.
+ * Limits: at most 89 bricks of 32^3 (712 of 16^3, 5466 of 8^3, 32960 of 4^3,
+ * 88764 of 2^3) per call; larger volumes are rejected with
+ * CSGV_ERR_INVALID_ARG and a message.  totals[3] (host) receives the number of
+ * palette labels, interior words and leaf words; if an output array is too
+ * small the call returns CSGV_ERR_INVALID_ARG with totals filled and writes
+ * nothing past the offset arrays.  Synchronises `stream` once (to read the
+ * totals), then packs asynchronously on it.
+ * Every call shares the scratch array, which keeps the previous call's
+ * contents (the call clears what must start at zero); calls that overlap on
+ * the GPU race on it and must not be issued.  The first call on a device,
+ * made with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.
+ */
+CSGV_API int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b,
+                                        const csgv_freq_table *table, const csgv_config *cfg, uint64_t *pal_off_dev,
+                                        uint32_t *pal_dev, uint64_t pal_capacity, uint64_t *int_off_dev,
+                                        uint16_t *int_words_dev, uint64_t int_capacity, uint64_t *leaf_off_dev,
+                                        uint16_t *leaf_words_dev, uint64_t leaf_capacity, uint32_t *n_int_sym_dev,
+                                        uint32_t *n_leaf_sym_dev, uint64_t totals[3], void *stream);
+
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
 

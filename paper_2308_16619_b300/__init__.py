@@ -18,7 +18,7 @@ CSGV_ERR_CORRUPT, CSGV_ERR_TIMEOUT, CSGV_ERR_CUDA, CSGV_ERR_RANGE = 4, 5, 6, 7
 
 SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "csgv_decode_bricks",
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
-           "csgv_volume_destroy")
+           "csgv_volume_destroy", "csgv_encode_bricks_noalloc")
 
 
 class CsgvError(RuntimeError):
@@ -64,6 +64,8 @@ def lib():
         L.csgv_volume_import.argtypes = [u32, vp, u32, u32, vp] + [vp] * 8 + [C.POINTER(vp)]
         L.csgv_volume_destroy.argtypes = [vp]
         L.csgv_volume_destroy.restype = None
+        L.csgv_encode_bricks_noalloc.argtypes = [vp, vp, u32, C.POINTER(FreqTable), C.POINTER(Config),
+                                                 vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -163,6 +165,24 @@ def csgv_decode_bricks(volume, brick_ids, lods, out, out_offsets, status, stream
 
 def csgv_decode_bricks_plain(volume, brick_ids, lods, out, out_offsets, status, stream=None):
     csgv_decode_bricks(volume, brick_ids, lods, out, out_offsets, status, stream, plain=True)
+
+
+def csgv_encode_bricks_noalloc(vol, b, table, pal_off, pal, int_off, int_words, leaf_off, leaf_words, n_int_sym,
+                               n_leaf_sym, K_max=32, S_min=256, stream=None):
+    """Allocation-free encoder, for callers that cannot allocate device memory.
+
+    Writes into the given device tensors (layout of Volume.export) using a fixed scratch array inside
+    the library.  Returns (rc, totals): rc is the C status code (0 = OK), totals the numbers of palette
+    labels, interior words and leaf words.
+    """
+    assert vol.is_cuda and vol.element_size() == 4 and vol.is_contiguous()
+    cfg = Config(K_max, S_min)
+    totals = (C.c_uint64 * 3)()
+    rc = lib().csgv_encode_bricks_noalloc(_ptr(vol), _dims3(vol), b, C.byref(table), C.byref(cfg), _ptr(pal_off),
+                                          _ptr(pal), pal.numel(), _ptr(int_off), _ptr(int_words), int_words.numel(),
+                                          _ptr(leaf_off), _ptr(leaf_words), leaf_words.numel(), _ptr(n_int_sym),
+                                          _ptr(n_leaf_sym), totals, _stream(stream))
+    return rc, [int(t) for t in totals]
 
 
 def csgv_volume_import(N, dims_xyz, K_max, S_min, freq, pal_off, pal, int_off, int_words, leaf_off, leaf_words,

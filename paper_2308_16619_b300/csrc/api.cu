@@ -147,6 +147,11 @@ int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cud
 
 }  // namespace
 
+namespace csgv {
+// lets other translation units of the library report a message through csgv_last_error()
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace csgv
+
 extern "C" {
 
 const char *csgv_last_error(void) { return g_err.c_str(); }
