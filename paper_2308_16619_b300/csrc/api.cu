@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 #include <atomic>
+#include <mutex>
 
 #include "csgv_internal.cuh"
 #include "../../include/csgv.h"
@@ -41,6 +42,9 @@ struct csgv_volume {
 namespace {
 
 constexpr uint32_t kWorkSlots = 256;
+// word arrays carry this many spare 16-bit words at the end: the decoder stages stream words with
+// 16-byte loads aligned down from the stream start, which may touch up to 15 bytes past the last word
+constexpr uint64_t kWordPad = 16;
 thread_local std::string g_err;
 
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -129,6 +133,31 @@ int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
     for (int a = 0; a < 3; a++)
         if (dims[a] == 0 || dims[a] > (1ull << 31)) return fail(CSGV_ERR_INVALID_ARG, "bad dimension %d", a);
     return CSGV_OK;
+}
+
+// Encoder scratch, kept per device between calls so that encoding does not allocate and free
+// gigabytes (cudaFree synchronises the whole device) on every call.  Guarded by g_arena_mu for the
+// whole encode call; the call synchronises its stream before it returns, so the next call may reuse it.
+constexpr int kArenaDevices = 64;
+struct Arena {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+Arena g_arena[kArenaDevices];
+std::mutex g_arena_mu;
+
+cudaError_t arena_get(int dev, size_t bytes, void **out) {
+    Arena &A = g_arena[dev];
+    if (A.bytes < bytes) {
+        if (A.p) cudaFree(A.p);
+        A.p = nullptr;
+        A.bytes = 0;
+        cudaError_t e = cudaMalloc(&A.p, bytes);
+        if (e != cudaSuccess) return e;
+        A.bytes = bytes;
+    }
+    *out = A.p;
+    return cudaSuccess;
 }
 
 int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cudaStream_t st) {
@@ -241,10 +270,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     csgv::EncScratch SC{};
     uint32_t *freq_d = nullptr, *maxpal_d = nullptr;
     uint64_t *tot_d = nullptr;
-    auto free_tmp = [&]() {
-        cudaFree(SC.pal); cudaFree(SC.nib_int); cudaFree(SC.nib_leaf); cudaFree(SC.w_int); cudaFree(SC.w_leaf);
-        cudaFree(SC.sizes); cudaFree(freq_d); cudaFree(tot_d); cudaFree(maxpal_d);
-    };
+    auto free_tmp = [&]() {};  // scratch lives in the per-device arena
 #define CKE(call)                                                  \
     do {                                                           \
         cudaError_t e_ = (call);                                   \
@@ -253,15 +279,32 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
             return cleanup(cuda_fail(e_, #call));                  \
         }                                                          \
     } while (0)
-    CKE(cudaMalloc(&SC.pal, C * G.pal_cap * 4));
-    CKE(cudaMalloc(&SC.nib_int, C * G.int_cap));
-    CKE(cudaMalloc(&SC.nib_leaf, C * G.leaf_cap));
-    CKE(cudaMalloc(&SC.w_int, C * (G.int_cap + 64) * 2));
-    CKE(cudaMalloc(&SC.w_leaf, C * (G.leaf_cap + 64) * 2));
-    CKE(cudaMalloc(&SC.sizes, C * 8 * 4));
-    CKE(cudaMalloc(&freq_d, 32 * 4));
-    CKE(cudaMalloc(&tot_d, 3 * 8));
-    CKE(cudaMalloc(&maxpal_d, 4));
+    std::lock_guard<std::mutex> arena_lock(g_arena_mu);
+    int dev = 0;
+    CKE(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kArenaDevices) return cleanup(fail(CSGV_ERR_INVALID_ARG, "device index %d too large", dev));
+    // carve the batch scratch out of the arena (256-byte aligned pieces)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
+    const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
+    const size_t o_sz = take(C * 8 * 4), o_f = take(32 * 4), o_t = take(3 * 8), o_m = take(4);
+    void *arena = nullptr;
+    CKE(arena_get(dev, off, &arena));
+    unsigned char *A = (unsigned char *)arena;
+    SC.pal = (uint32_t *)(A + o_pal);
+    SC.nib_int = A + o_ni;
+    SC.nib_leaf = A + o_nl;
+    SC.w_int = (uint16_t *)(A + o_wi);
+    SC.w_leaf = (uint16_t *)(A + o_wl);
+    SC.sizes = (uint32_t *)(A + o_sz);
+    freq_d = (uint32_t *)(A + o_f);
+    tot_d = (uint64_t *)(A + o_t);
+    maxpal_d = (uint32_t *)(A + o_m);
     CKE(cudaMalloc(&v->pal_off, (n + 1) * 8));
     CKE(cudaMalloc(&v->int_off, (n + 1) * 8));
     CKE(cudaMalloc(&v->leaf_off, (n + 1) * 8));
@@ -281,8 +324,8 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
         CKE(cudaStreamSynchronize(st));
         int g;
         if ((g = grow((void **)&v->pal, cap_p, std::max<uint64_t>(tot[0], 1), 4, prev[0], st)) ||
-            (g = grow((void **)&v->int_words, cap_i, std::max<uint64_t>(tot[1], 1), 2, prev[1], st)) ||
-            (g = grow((void **)&v->leaf_words, cap_l, std::max<uint64_t>(tot[2], 1), 2, prev[2], st))) {
+            (g = grow((void **)&v->int_words, cap_i, tot[1] + kWordPad, 2, prev[1], st)) ||
+            (g = grow((void **)&v->leaf_words, cap_l, tot[2] + kWordPad, 2, prev[2], st))) {
             free_tmp();
             return cleanup(g);
         }
@@ -317,7 +360,7 @@ int csgv_decode_bricks(const csgv_volume *vol, const uint32_t *brick_ids_dev, co
     cudaStream_t st = (cudaStream_t)stream;
     csgv_volume *v = const_cast<csgv_volume *>(vol);
     const bool wide = v->max_palette > 253;
-    const uint32_t warps = wide ? 8 : 16;
+    const uint32_t warps = wide ? 8 : 14;  // as many warps as the 227 KB of shared memory per CTA holds
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -421,7 +464,7 @@ int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint3
     }
     v->max_palette = maxp;
     auto up = [&](void **d, const void *h, size_t bytes) -> cudaError_t {
-        cudaError_t e = cudaMalloc(d, bytes ? bytes : 4);
+        cudaError_t e = cudaMalloc(d, bytes + 2 * kWordPad);
         if (e == cudaSuccess && bytes && h) e = cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice);
         return e;
     };

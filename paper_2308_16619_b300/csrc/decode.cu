@@ -3,13 +3,15 @@
 // One warp decodes one request (brick id, target LOD t) end to end:
 //   1. rANS: the K interleaved states of a stream live in lanes 0..K-1; a
 //      step decodes K symbols, lanes that need a renormalisation word take
-//      consecutive words in lane order (ballot + popc), symbols go to a
-//      128-entry ring in shared memory (Sec. 3.3, readings R9/R10).
+//      consecutive words in lane order (ballot + popc) from a window of the
+//      stream staged in shared memory by 16-byte loads (Sec. 3.3, readings
+//      R9/R10).  Each delta nibble is folded into its P_delta op, so the
+//      step appends one op record per child to a ring in shared memory.
 //   2. Reconstruction, level by level (Alg. 1): the children of all parents
 //      are first filled with the parent's label (stop-bit semantics: a
 //      constant parent's sub-block takes its label); then the active
 //      (non-constant) parents are taken four at a time, lane i handling
-//      child i&7 of parent i>>3: the op nibble decides the child's palette
+//      child i&7 of parent i>>3: the op record decides the child's palette
 //      index.  Neighbour reuse toward -axis reads the same level (earlier in
 //      Z-order); chains of such references are at most 3 long (each hop sets
 //      one more child bit) and are resolved by pointer chasing inside the
@@ -42,30 +44,9 @@ __device__ __forceinline__ uint32_t spread5(uint32_t v) {
 __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
     return spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
 }
-__device__ __forceinline__ uint32_t axis_mask(uint32_t a) { return a == 0 ? kMX : (a == 1 ? kMY : kMZ); }
 // m - e_a / m + e_a on the Morton grid (caller checks the range)
 __device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
 __device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
-
-// position of the (k+1)-th set bit of x (k < popc(x)), by halving
-__device__ __forceinline__ uint32_t nth_set32(uint32_t x, uint32_t k) {
-    uint32_t pos = 0;
-#pragma unroll
-    for (uint32_t s = 16; s > 0; s >>= 1) {
-        const uint32_t c = __popc(x & ((1u << s) - 1u));
-        if (k >= c) {
-            k -= c;
-            x >>= s;
-            pos += s;
-        }
-    }
-    return pos;
-}
-__device__ __forceinline__ uint32_t nth_set64(uint64_t z, uint32_t k) {
-    const uint32_t lo = (uint32_t)z, cl = __popc(lo);
-    if (k < cl) return nth_set32(lo, k);
-    return 32u + nth_set32((uint32_t)(z >> 32), k - cl);
-}
 
 template <typename IdxT>
 struct Traits;
@@ -85,53 +66,94 @@ constexpr uint32_t kUpN = 4688;      // levels 1..5 of a 32^3 brick: 4096+512+64
 constexpr uint32_t kChunkN = 4096;   // one 16^3 chunk of level 0
 constexpr uint32_t kXfN = 256, kYfN = 512, kZfN = 1024;
 constexpr uint32_t kMaskWords = 148; // const bits of levels 1..5
-constexpr uint32_t kListN = 512;     // active parents of one level / chunk (uint16)
-constexpr uint32_t kRingN = 128;     // symbol ring (bytes)
+constexpr uint32_t kListN = 1024;    // active parents of one level / chunk (uint16, or uint32 for leaf chunks)
+constexpr uint32_t kOpsN = 256;      // op ring (bytes: op | stop<<3 | delta<<4)
+constexpr uint32_t kWinWords = 256;  // staged stream words (uint16)
 
 template <typename IdxT>
 __host__ __device__ constexpr uint32_t warp_smem_bytes() {
-    return ((kUpN + kChunkN + kXfN + kYfN + kZfN) * (uint32_t)sizeof(IdxT) + kMaskWords * 4 + kListN * 2 + kRingN +
-            15u) & ~15u;
+    return ((kUpN + kChunkN + kXfN + kYfN + kZfN) * (uint32_t)sizeof(IdxT) + kMaskWords * 4 + kListN * 2 +
+            kWinWords * 2 + kOpsN + 15u) & ~15u;
 }
 
 template <typename IdxT>
 struct WarpMem {
     IdxT *up, *chunk, *xf, *yf, *zf;
     uint32_t *cmask;
-    uint16_t *list;
-    uint8_t *ring;
+    uint16_t *list, *win;
+    uint8_t *ops;
     __device__ explicit WarpMem(uint8_t *base) {
         up = (IdxT *)base;
         chunk = up + kUpN;
         xf = chunk + kChunkN;
         yf = xf + kXfN;
         zf = yf + kYfN;
-        cmask = (uint32_t *)(zf + kZfN);
-        list = (uint16_t *)(cmask + kMaskWords);
-        ring = (uint8_t *)(list + kListN);
+        cmask = (uint32_t *)(zf + kZfN);   // 16-byte aligned: the IdxT arrays above total a multiple of 16 bytes
+        win = (uint16_t *)(cmask + kMaskWords);
+        list = win + kWinWords;
+        ops = (uint8_t *)(list + kListN);
     }
 };
 
-// rANS stream state: x is this lane's state (lanes < K), the rest is uniform
+// offset of level l (1..N) in `up`, and of its const bits in `cmask` (words)
+__device__ __forceinline__ uint32_t up_off(uint32_t N, uint32_t l) {
+    uint32_t u = 0;
+#pragma unroll
+    for (uint32_t k = 1; k <= (uint32_t)kMaxN; k++)
+        if (k < l) u += 1u << (3 * (N - k));
+    return u;
+}
+__device__ __forceinline__ uint32_t mask_off(uint32_t N, uint32_t l) {
+    uint32_t w = 0;
+#pragma unroll
+    for (uint32_t k = 1; k <= (uint32_t)kMaxN; k++)
+        if (k < l) w += (N - k >= 2) ? (1u << (3 * (N - k) - 5)) : 1u;
+    return w;
+}
+
+// rANS stream of one brick: x is this lane's state (lanes < K), the rest is uniform.
+// Decoded symbols are folded into op records (a P_delta carries its delta) in the op ring.
 struct Stream {
-    const uint16_t *w;
-    uint32_t n_words, pos, K, remaining, head, tail, x;
+    const uint16_t *w;     // stream words in global memory
+    uint32_t n_words, pos, K, remaining, x;
+    int32_t wb;            // absolute word index held in win[0] (may be negative: alignment slack)
+    uint32_t wn;           // valid words in the window
+    uint32_t stage_at;     // restage once pos passes this (a step reads at most 32 words)
+    uint32_t ohead, otail, pend;  // op ring; pend = 1: op otail-1 still waits for its delta
     bool bad;
 };
 
-__device__ __forceinline__ void stream_init(Stream &s, const uint16_t *w, uint32_t n_words, uint32_t n_sym,
-                                            uint32_t K_max, uint32_t S_min, uint32_t lane) {
+// stage stream words from s.pos into the window with 16-byte loads (aligned down)
+__device__ __forceinline__ void stage(Stream &s, uint16_t *win, uint32_t lane) {
+    const uintptr_t g = reinterpret_cast<uintptr_t>(s.w + s.pos);
+    const uintptr_t g0 = g & ~(uintptr_t)15;
+    const uintptr_t gend = reinterpret_cast<uintptr_t>(s.w + s.n_words);
+    for (uint32_t c = lane; c < kWinWords / 8; c += 32) {
+        const uintptr_t a = g0 + 16 * (uintptr_t)c;
+        if (a < gend) reinterpret_cast<uint4 *>(win)[c] = __ldg(reinterpret_cast<const uint4 *>(a));
+    }
+    s.wb = (int32_t)s.pos - (int32_t)((g - g0) >> 1);
+    s.wn = min(kWinWords, (uint32_t)((int32_t)s.n_words - s.wb));
+    const uint32_t end = (uint32_t)(s.wb + (int32_t)s.wn);
+    s.stage_at = end < s.n_words ? end - 32 : 0xFFFFFFFFu;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void stream_init(Stream &s, uint16_t *win, const uint16_t *w, uint32_t n_words,
+                                            uint32_t n_sym, uint32_t K_max, uint32_t S_min, uint32_t lane) {
     s.w = w;
     s.n_words = n_words;
     s.remaining = n_sym;
-    s.head = s.tail = 0;
     s.K = lanes_for(n_sym, K_max, S_min);
     s.bad = false;
     s.x = kL;
-    s.pos = 2 * s.K;
+    s.pos = 0;
+    s.ohead = s.otail = s.pend = 0;
+    s.wb = 0;
+    s.wn = 0;
+    s.stage_at = 0xFFFFFFFFu;
     if (n_sym == 0) {
         s.bad = n_words != 0;
-        s.pos = 0;
         return;
     }
     if (n_words < 2 * s.K) {
@@ -139,13 +161,16 @@ __device__ __forceinline__ void stream_init(Stream &s, const uint16_t *w, uint32
         s.remaining = 0;
         return;
     }
-    if (lane < s.K) s.x = (uint32_t)__ldg(w + 2 * lane) | ((uint32_t)__ldg(w + 2 * lane + 1) << 16);
+    stage(s, win, lane);
+    if (lane < s.K) s.x = (uint32_t)win[2 * lane - s.wb] | ((uint32_t)win[2 * lane + 1 - s.wb] << 16);
+    s.pos = 2 * s.K;
 }
 
-// decode rANS steps into the ring until `want` symbols are buffered or the stream is exhausted
-__device__ __forceinline__ void stream_fill(Stream &s, uint8_t *ring, const uint32_t *lut, uint32_t want,
-                                            uint32_t lane) {
-    while (s.tail - s.head < want && s.remaining > 0) {
+// decode rANS steps until `want` complete op records are waiting or the stream is exhausted
+__device__ __forceinline__ void produce(Stream &s, uint8_t *ops, uint16_t *win, const uint32_t *lut, uint32_t want,
+                                        uint32_t lane) {
+    while (s.otail - s.ohead - s.pend < want && s.remaining > 0) {
+        if (s.pos > s.stage_at) stage(s, win, lane);
         const uint32_t n = min(s.K, s.remaining);
         const bool act = lane < n;
         uint32_t sym = 0;
@@ -159,81 +184,92 @@ __device__ __forceinline__ void stream_fill(Stream &s, uint8_t *ring, const uint
         const uint32_t m = __ballot_sync(kFull, need);
         if (need) {
             const uint32_t off = s.pos + __popc(m & lanemask_lt());
-            const uint32_t wv = off < s.n_words ? (uint32_t)__ldg(s.w + off) : 0u;
+            const uint32_t wv = off < s.n_words ? (uint32_t)win[(int32_t)off - s.wb] : 0u;
             s.x = (s.x << 16) | wv;
         }
         s.pos += __popc(m);
-        if (act) ring[(s.tail + lane) & (kRingN - 1)] = (uint8_t)sym;
-        s.tail += n;
         s.remaining -= n;
+        uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD);
+        if ((cand | s.pend) == 0) {
+            // common case: every symbol of the step is an op
+            if (act) ops[(s.otail + lane) & (kOpsN - 1)] = (uint8_t)sym;
+            s.otail += n;
+            continue;
+        }
+        // which symbols are delta nibbles: the one after each P_delta op
+        uint64_t dm = s.pend;  // bit i: symbol i of this step is a delta
+        cand &= ~(uint32_t)dm;
+        while (cand) {
+            const uint32_t i = __ffs(cand) - 1;
+            cand &= cand - 1;
+            if (!((dm >> i) & 1ull)) {
+                dm |= 2ull << i;
+                cand &= ~(uint32_t)(2ull << i);
+            }
+        }
+        const uint32_t nxt = __shfl_down_sync(kFull, sym, 1);
+        if (s.pend && lane == 0) ops[(s.otail - 1) & (kOpsN - 1)] |= (uint8_t)(sym << 4);
+        const uint32_t actm = n >= 32 ? kFull : ((1u << n) - 1u);
+        const uint32_t opm = actm & ~(uint32_t)dm;
+        if ((opm >> lane) & 1u) {
+            const bool pd = (sym & 7u) == OP_PD && lane + 1 < n;
+            ops[(s.otail + __popc(opm & lanemask_lt())) & (kOpsN - 1)] = (uint8_t)(sym | (pd ? nxt << 4 : 0u));
+        }
+        s.otail += __popc(opm);
+        s.pend = (uint32_t)((dm >> n) & 1ull);
     }
     if (s.pos > s.n_words) s.bad = true;
     __syncwarp();
 }
 
-// true iff every symbol was consumed and every state is back at L (full decode)
+// true iff every symbol was decoded and consumed and every state is back at L (full decode)
 __device__ __forceinline__ bool stream_done_ok(const Stream &s, uint32_t lane) {
     const bool lane_ok = lane >= s.K || s.x == kL;
-    return __all_sync(kFull, lane_ok) && !s.bad && s.remaining == 0 && s.head == s.tail && s.pos == s.n_words;
+    return __all_sync(kFull, lane_ok) && !s.bad && s.remaining == 0 && s.ohead == s.otail && !s.pend &&
+           s.pos == s.n_words;
 }
 
-// Take the next n_ops (<= 32) operations and their delta nibbles from the
-// ring.  Lane k < n_ops receives op nibble and delta of operation k.
-// Returns false if the stream ran out.
-__device__ __forceinline__ bool take_ops(Stream &s, const uint8_t *ring, uint32_t n_ops, uint32_t lane, uint32_t &nib,
-                                         uint32_t &delta) {
-    const uint32_t avail = s.tail - s.head;
-    const uint32_t s_lo = lane < avail ? ring[(s.head + lane) & (kRingN - 1)] : 7u;
-    const uint32_t s_hi = lane + 32 < avail ? ring[(s.head + 32 + lane) & (kRingN - 1)] : 7u;
-    const uint32_t c_lo = __ballot_sync(kFull, lane < avail && (s_lo & 7u) == OP_PD);
-    const uint32_t c_hi = __ballot_sync(kFull, lane + 32 < avail && (s_hi & 7u) == OP_PD);
-    uint64_t cand = (uint64_t)c_lo | ((uint64_t)c_hi << 32);
-    uint64_t dm = 0;  // positions holding delta nibbles
-    while (cand) {
-        const uint32_t i = __ffsll((long long)cand) - 1;
-        cand &= cand - 1;
-        if (!((dm >> i) & 1ull) && i < 63) {
-            dm |= 2ull << i;
-            cand &= ~(2ull << i);
-        }
-    }
-    uint32_t pos, last_pos;
-    const uint32_t low = (uint32_t)dm & ((n_ops >= 32) ? kFull : ((1u << n_ops) - 1u));
-    if (low == 0) {
-        pos = lane;
-        last_pos = n_ops - 1;
-    } else {
-        const uint64_t z = ~dm;
-        pos = lane < n_ops ? nth_set64(z, lane) : 0u;
-        last_pos = nth_set64(z, n_ops - 1);
-    }
-    const uint32_t consumed = last_pos + 1 + (uint32_t)((dm >> (last_pos + 1)) & 1ull);
-    const uint32_t p1 = pos + 1;
-    const uint32_t a = __shfl_sync(kFull, s_lo, pos & 31), b = __shfl_sync(kFull, s_hi, pos & 31);
-    const uint32_t d_lo = __shfl_sync(kFull, s_lo, p1 & 31), d_hi = __shfl_sync(kFull, s_hi, p1 & 31);
-    nib = pos < 32 ? a : b;
-    delta = p1 < 32 ? d_lo : d_hi;
-    if (consumed > avail) return false;
-    s.head += consumed;
+// take n_ops op records from the ring (lane k < n_ops gets record k); false if the stream ran out
+__device__ __forceinline__ bool take_ops(Stream &s, const uint8_t *ops, uint32_t n_ops, uint32_t lane, uint32_t &o) {
+    if (s.otail - s.ohead - s.pend < n_ops) return false;
+    o = lane < n_ops ? (uint32_t)ops[(s.ohead + lane) & (kOpsN - 1)] : 0u;
+    s.ohead += n_ops;
     return true;
 }
 
-template <typename IdxT>
-__device__ __forceinline__ void store_block(const IdxT *buf, uint32_t side, uint32_t *out, uint32_t pitch,
-                                            uint32_t pal_reg, const uint32_t *pal, uint32_t np, bool vec,
-                                            uint32_t lane) {
-    auto label = [&](uint32_t idx) -> uint32_t {
-        const uint32_t v = __shfl_sync(kFull, pal_reg, idx & 31);
-        return np <= 32 ? v : __ldg(pal + min(idx, np - 1));
-    };
+// labels of 4 indices, from the palette held one entry per lane (kRegPal) or from global memory
+template <bool kRegPal>
+__device__ __forceinline__ uint4 labels4(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3, uint32_t pal_reg,
+                                         const uint32_t *pal, uint32_t np) {
+    uint4 o;
+    if (kRegPal) {
+        o.x = __shfl_sync(kFull, pal_reg, v0 & 31);
+        o.y = __shfl_sync(kFull, pal_reg, v1 & 31);
+        o.z = __shfl_sync(kFull, pal_reg, v2 & 31);
+        o.w = __shfl_sync(kFull, pal_reg, v3 & 31);
+    } else {
+        o.x = __ldg(pal + min(v0, np - 1));
+        o.y = __ldg(pal + min(v1, np - 1));
+        o.z = __ldg(pal + min(v2, np - 1));
+        o.w = __ldg(pal + min(v3, np - 1));
+    }
+    return o;
+}
+
+// Store a level held in Morton order (side <= 16) as x-fastest labels with row pitch `pitch`.
+template <typename IdxT, bool kRegPal>
+__device__ __forceinline__ void store_morton_impl(const IdxT *buf, uint32_t side, uint32_t *out, uint32_t pitch,
+                                                  uint32_t pal_reg, const uint32_t *pal, uint32_t np, bool vec,
+                                                  uint32_t lane) {
     const uint32_t n = side * side * side;
-    if (vec) {
-        const uint32_t sh = __ffs(side) - 1;  // log2 side
-        const uint32_t q = side >> 2;         // uint4 per row
+    if (vec && side >= 4) {
+        const uint32_t sh = __ffs(side) - 1;
+        const uint32_t x4 = lane & ((side >> 2) - 1);
+        const uint32_t sx = spread5(4 * x4);
         for (uint32_t base = 0; base < n / 4; base += 32) {
             const uint32_t i = min(base + lane, n / 4 - 1);
-            const uint32_t x4 = i & (q - 1), y = (i >> (sh - 2)) & (side - 1), z = i >> (2 * sh - 2);
-            const uint32_t m0 = morton3(4 * x4, y, z);
+            const uint32_t y = (i >> (sh - 2)) & (side - 1), z = i >> (2 * sh - 2);
+            const uint32_t m0 = sx | (spread5(y) << 1) | (spread5(z) << 2);
             uint32_t v0, v1, v2, v3;
             if (sizeof(IdxT) == 1) {
                 const uint32_t a = *(const uint16_t *)(buf + m0), b = *(const uint16_t *)(buf + m0 + 8);
@@ -242,8 +278,7 @@ __device__ __forceinline__ void store_block(const IdxT *buf, uint32_t side, uint
                 const uint32_t a = *(const uint32_t *)(buf + m0), b = *(const uint32_t *)(buf + m0 + 8);
                 v0 = a & 0xFFFF; v1 = a >> 16; v2 = b & 0xFFFF; v3 = b >> 16;
             }
-            uint4 o;
-            o.x = label(v0); o.y = label(v1); o.z = label(v2); o.w = label(v3);
+            const uint4 o = labels4<kRegPal>(v0, v1, v2, v3, pal_reg, pal, np);
             if (base + lane < n / 4) __stcs((uint4 *)(out + ((size_t)z * pitch + y) * pitch + 4 * x4), o);
         }
     } else {
@@ -251,9 +286,54 @@ __device__ __forceinline__ void store_block(const IdxT *buf, uint32_t side, uint
             const uint32_t i = base + lane;
             const uint32_t ii = i < n ? i : 0;
             const uint32_t x = ii & (side - 1), y = (ii / side) & (side - 1), z = ii / (side * side);
-            const uint32_t lab = label(buf[morton3(x, y, z)]);
+            const uint32_t v = buf[morton3(x, y, z)];
+            const uint32_t lab = kRegPal ? __shfl_sync(kFull, pal_reg, v & 31) : __ldg(pal + min(v, np - 1));
             if (i < n) out[((size_t)z * pitch + y) * pitch + x] = lab;
         }
+    }
+}
+
+// Store a chunk held x-fastest (side cs = 2^ls) as labels with row pitch `pitch`.
+template <typename IdxT, bool kRegPal>
+__device__ __forceinline__ void store_linear_impl(const IdxT *buf, uint32_t cs, uint32_t ls, uint32_t *out,
+                                                  uint32_t pitch, uint32_t pal_reg, const uint32_t *pal, uint32_t np,
+                                                  bool vec, uint32_t lane) {
+    const uint32_t n = cs * cs * cs;
+    if (vec && cs >= 4) {
+        for (uint32_t base = 0; base < n / 4; base += 32) {
+            const uint32_t lin = 4 * min(base + lane, n / 4 - 1);
+            const uint32_t x = lin & (cs - 1), y = (lin >> ls) & (cs - 1), z = lin >> (2 * ls);
+            uint32_t v0, v1, v2, v3;
+            if (sizeof(IdxT) == 1) {
+                const uint32_t a = *(const uint32_t *)(buf + lin);
+                v0 = a & 0xFF; v1 = (a >> 8) & 0xFF; v2 = (a >> 16) & 0xFF; v3 = a >> 24;
+            } else {
+                const uint2 a = *(const uint2 *)(buf + lin);
+                v0 = a.x & 0xFFFF; v1 = a.x >> 16; v2 = a.y & 0xFFFF; v3 = a.y >> 16;
+            }
+            const uint4 o = labels4<kRegPal>(v0, v1, v2, v3, pal_reg, pal, np);
+            if (base + lane < n / 4) __stcs((uint4 *)(out + ((size_t)z * pitch + y) * pitch + x), o);
+        }
+    } else {
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t i = base + lane;
+            const uint32_t ii = i < n ? i : 0;
+            const uint32_t x = ii & (cs - 1), y = (ii >> ls) & (cs - 1), z = ii >> (2 * ls);
+            const uint32_t v = buf[ii];
+            const uint32_t lab = kRegPal ? __shfl_sync(kFull, pal_reg, v & 31) : __ldg(pal + min(v, np - 1));
+            if (i < n) out[((size_t)z * pitch + y) * pitch + x] = lab;
+        }
+    }
+}
+
+// every voxel of a (side^3, pitch) block gets one label
+__device__ __forceinline__ void store_const(uint32_t label, uint32_t side, uint32_t *out, bool vec, uint32_t lane) {
+    const uint32_t n = side * side * side;
+    if (vec && side >= 4) {
+        const uint4 o = make_uint4(label, label, label, label);
+        for (uint32_t i = lane; i < n / 4; i += 32) __stcs((uint4 *)out + i, o);
+    } else {
+        for (uint32_t i = lane; i < n; i += 32) out[i] = label;
     }
 }
 
@@ -271,25 +351,19 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
     const uint32_t n_int = V.n_int_sym[id], n_leaf = V.n_leaf_sym[id];
     if (np == 0 || np > T::kMaxPal) return kStCorrupt;
     const uint32_t pal_reg = lane < np ? __ldg(pal + lane) : 0u;
-    const bool brick_const = (n_int == 0 && n_leaf == 0);
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    const bool reg_pal = np <= 32;
 
-    // level offsets inside `up` and `cmask` (levels 1..N)
-    uint32_t uoff[kMaxN + 2], woff[kMaxN + 2];
-    {
-        uint32_t u = 0, w = 0;
-        for (uint32_t l = 1; l <= N; l++) {
-            uoff[l] = u;
-            woff[l] = w;
-            const uint32_t c = (b >> l) * (b >> l) * (b >> l);
-            u += c;
-            w += c >= 32 ? c / 32 : 1;
-        }
+    // homogeneous brick: no symbols, every LOD is palette[0] (reading R2)
+    if (n_int == 0 && n_leaf == 0) {
+        if (V.int_off[id + 1] != V.int_off[id] || V.leaf_off[id + 1] != V.leaf_off[id]) return kStCorrupt;
+        store_const(__shfl_sync(kFull, pal_reg, 0), b >> t, out, vec_ok, lane);
+        return kStOk;
     }
-    // root (level N): palette index 0 (Alg. 1 initialisation)
+    // root (level N): palette index 0 (Alg. 1 initialisation), not constant
     if (lane == 0) {
-        M.up[uoff[N]] = 0;
-        M.cmask[woff[N]] = brick_const ? 1u : 0u;
+        M.up[up_off(N, N)] = 0;
+        M.cmask[mask_off(N, N)] = 0u;
     }
     __syncwarp();
     if (t == N) {
@@ -298,194 +372,232 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
     }
 
     const uint32_t K_max = V.K_max, S_min = V.S_min;
-    const uint32_t *lut_int = lut_s, *lut_leaf = lut_s + kM;
-    int32_t status = kStOk;
     uint32_t ip = 0;  // palette index of the last P_a (i_p)
+    const uint32_t sent = T::kSent;
+    const uint32_t c = lane & 7u;
 
-    // one level (or chunk) of Alg. 1: parents [pp0, pp0 + npar) on level l+1 (Morton), children on level l.
-    // par: parent labels (indexed pp), cm_par: parent const bits, dst: child buffer indexed (8*(pp - pp0) + c)
-    // cm_dst: child const bytes (levels >= 1) or null; face lookups for the -axis targets at level 0 chunks.
-    auto run_level = [&](Stream &S, const uint32_t *lut, const IdxT *par, const uint32_t *cm_par, uint32_t pp0,
-                         uint32_t npar, uint32_t side_par_bits, IdxT *dst, uint8_t *cm_dst, bool leaf,
-                         uint32_t chunk_o, uint32_t chunk_bits) -> bool {
-        // (a) fill children with the parent's label, const bytes, list of active parents
+    // value of one coded child (Sec. 3.2): R_p and R_a toward +axis read the parent level (pv), R_a
+    // toward -axis is left as a sentinel for the chase, palette ops index the palette (R1, R3)
+    auto child_value = [&](uint32_t op, uint32_t delta, uint32_t ipb, uint32_t pv, bool plus, bool minus,
+                           uint32_t a) -> uint32_t {
+        if (op == OP_RP || plus) return pv;
+        if (minus) return sent + a;
+        if (op == OP_P0) return ipb;
+        if (op == OP_PD) return ipb - 1 - delta;
+        return ipb + 1;
+    };
+
+    // ---- interior levels N-1 .. max(t,1): Morton order, all levels of the brick in `up`
+    Stream S;
+    stream_init(S, M.win, V.int_words + V.int_off[id], (uint32_t)(V.int_off[id + 1] - V.int_off[id]), n_int, K_max,
+                S_min, lane);
+    if (S.bad) return kStCorrupt;
+    const uint32_t lmin = t > 0 ? t : 1u;
+    for (uint32_t l = N - 1; l >= lmin && l < N; l--) {
+        const uint32_t npar = 1u << (3 * (N - l - 1));
+        const uint32_t pbits = npar - 1;  // parent-level Morton code bits
+        const IdxT *par = M.up + up_off(N, l + 1);
+        const uint32_t *cm_par = M.cmask + mask_off(N, l + 1);
+        IdxT *dst = M.up + up_off(N, l);
+        uint8_t *cm_dst = (uint8_t *)(M.cmask + mask_off(N, l));
+        // (a) children take the parent's label (a constant parent keeps it); list the active parents
         uint32_t n_act = 0;
         for (uint32_t g = 0; g < npar; g += 32) {
             const uint32_t k = g + lane;
             bool active = false;
             if (k < npar) {
-                const uint32_t pp = pp0 + k;
-                const uint32_t v = par[pp];
-                const bool pc = (cm_par[pp >> 5] >> (pp & 31)) & 1u;
+                const uint32_t v = par[k];
+                const bool pc = (cm_par[k >> 5] >> (k & 31)) & 1u;
                 active = !pc;
                 if (sizeof(IdxT) == 1) {
                     *(uint64_t *)(dst + 8 * k) = 0x0101010101010101ull * v;
                 } else {
-                    const uint64_t r = 0x0001000100010001ull * v;
-                    *(uint4 *)(dst + 8 * k) = make_uint4((uint32_t)r, (uint32_t)(r >> 32), (uint32_t)r,
-                                                         (uint32_t)(r >> 32));
+                    const uint32_t r = 0x00010001u * v;
+                    *(uint4 *)(dst + 8 * k) = make_uint4(r, r, r, r);
                 }
-                if (cm_dst) cm_dst[k] = pc ? 0xFF : 0x00;
+                cm_dst[k] = pc ? 0xFF : 0x00;
             }
             const uint32_t am = __ballot_sync(kFull, active);
             if (active) M.list[n_act + __popc(am & lanemask_lt())] = (uint16_t)k;
             n_act += __popc(am);
         }
         __syncwarp();
-        // (b) decode the active parents' children, four parents per step
-        const uint32_t sent = T::kSent;
-        const uint32_t cmask_all = (1u << (3 * (side_par_bits + 1))) - 1u;  // Morton bits of the child level
+        // (b) four active parents (32 child ops) per step, lane = child
         for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
-            const uint32_t npr = min(4u, n_act - r0);
-            const uint32_t n_ops = 8 * npr;
-            stream_fill(S, M.ring, lut, 2 * n_ops, lane);
-            uint32_t nib, delta;
-            if (!take_ops(S, M.ring, n_ops, lane, nib, delta)) return false;
+            const uint32_t n_ops = 8 * min(4u, n_act - r0);
+            produce(S, M.ops, M.win, lut_s, n_ops, lane);
+            uint32_t o;
+            if (!take_ops(S, M.ops, n_ops, lane, o)) return kStCorrupt;
             const bool is_op = lane < n_ops;
-            const uint32_t op = nib & 7u, stop = nib >> 3;
-            // palette index bookkeeping: i_p moves on P_a only (R3)
+            const uint32_t op = o & 7u, stop = (o >> 3) & 1u, delta = o >> 4;
             const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
             const uint32_t ipb = ip + __popc(pam & lanemask_lt());
             ip += __popc(pam);
-            const uint32_t k = M.list[r0 + (lane >> 3)];  // parent (relative to pp0)
-            const uint32_t c = lane & 7u;
-            const uint32_t pp = pp0 + k;       // parent Morton code on its level
-            const uint32_t q = 8 * k + c;      // child index into dst
-            bool bad = false;
-            uint32_t v = 0;
-            if (is_op) {
-                if (op == OP_RP) {
-                    v = par[pp];
-                } else if (op <= OP_RZ) {
-                    const uint32_t a = op - OP_RX;
-                    const uint32_t ma = axis_mask(a);
-                    if ((c >> a) & 1u) {
-                        // +axis: the neighbour is later in Z-order, use its parent (R4)
-                        const uint32_t pm = ma & ((1u << (3 * side_par_bits)) - 1u);
-                        const uint32_t gp = leaf ? (pp | (chunk_o << (3 * side_par_bits))) : pp;
-                        const uint32_t gma = leaf ? (ma & ((1u << (3 * (side_par_bits + chunk_bits))) - 1u)) : pm;
-                        if ((gp & gma) == gma) {
-                            bad = true;  // outside the brick
-                        } else {
-                            const uint32_t np_ = minc(gp, ma);
-                            v = par[np_];
-                        }
-                    } else {
-                        // -axis: same level, earlier in Z-order; resolved below
-                        const uint32_t qa = q & ma & cmask_all;
-                        const bool chunk_edge = leaf && qa == 0;
-                        if (chunk_edge && !((chunk_o >> a) & 1u)) bad = true;  // brick boundary
-                        if (!leaf && qa == 0) bad = true;
-                        v = sent + a;
+            const uint32_t k = is_op ? (uint32_t)M.list[r0 + (lane >> 3)] : 0u;  // stale entries unread
+            const uint32_t q = 8 * k + c;
+            const bool rx = op >= OP_RX && op <= OP_RZ;
+            const uint32_t a = rx ? op - OP_RX : 0u;
+            const uint32_t ma = kMX << a;
+            const bool plus = rx && ((c >> a) & 1u);
+            const bool minus = rx && !plus;
+            const bool plus_out = plus && ((k & ma & pbits) == (ma & pbits));
+            const uint32_t pv = par[(plus && !plus_out) ? minc(k, ma) : k];
+            const bool minus_out = minus && (q & ma & (8 * npar - 1)) == 0;
+            const uint32_t v = child_value(op, delta, ipb, pv, plus, minus, a);
+            const bool bad = is_op && (plus_out || minus_out || op == 7u || (op == OP_PD && ipb < 1 + delta) ||
+                                       (op == OP_PA && ipb + 1 >= np));
+            if (is_op) dst[q] = (IdxT)(bad ? 0u : v);
+            const uint32_t sm = __ballot_sync(kFull, is_op && stop);
+            if (is_op && c == 0) cm_dst[k] = (uint8_t)(sm >> (lane & ~7u));
+            if (__any_sync(kFull, bad)) return kStCorrupt;
+            const bool chase = is_op && minus;
+            if (__any_sync(kFull, chase)) {
+                __syncwarp();
+                // same-level references form chains of <= 3 hops (each hop sets one more child bit)
+                if (chase) {
+                    uint32_t cur = q, ax = a, w = 0;
+                    for (int hop = 0; hop < 4; hop++) {
+                        cur = mdec(cur, kMX << ax);
+                        w = dst[cur];
+                        if (w < sent) break;
+                        ax = w - sent;
                     }
-                } else if (op == OP_P0) {
-                    v = ipb;
-                } else if (op == OP_PD) {
-                    if (ipb < 1 + delta) bad = true;
-                    v = ipb - 1 - delta;
-                } else if (op == OP_PA) {
-                    v = ipb + 1;
-                    if (v >= np) bad = true;
-                } else {
-                    bad = true;
+                    dst[q] = (IdxT)w;
                 }
-                if (leaf && stop) bad = true;
-                if (bad) v = 0;
-                dst[q] = (IdxT)v;
-            }
-            // stop bits of the children of each parent: one byte per parent
-            if (cm_dst) {
-                const uint32_t sm = __ballot_sync(kFull, is_op && stop);
-                if (is_op && c == 0) cm_dst[k] = (uint8_t)(sm >> (lane & ~7u));
-            }
-            if (__any_sync(kFull, bad)) return false;
-            __syncwarp();
-            // resolve same-level references (chains of <= 3 hops)
-            if (is_op && v >= sent) {
-                uint32_t cur = q, a = v - sent, w = 0;
-                for (int hop = 0; hop < 4; hop++) {
-                    const uint32_t ma = axis_mask(a);
-                    if (leaf && (cur & ma & cmask_all) == 0) {
-                        // crosses into the previous chunk: its face holds final labels
-                        const uint32_t cx = chunk_o & 1, cy = (chunk_o >> 1) & 1, cz = chunk_o >> 2;
-                        uint32_t x = 0, y = 0, z = 0;
-                        for (uint32_t bit = 0; bit < 4; bit++) {
-                            x |= ((cur >> (3 * bit)) & 1u) << bit;
-                            y |= ((cur >> (3 * bit + 1)) & 1u) << bit;
-                            z |= ((cur >> (3 * bit + 2)) & 1u) << bit;
-                        }
-                        if (a == 0) w = M.xf[y + 16 * z];
-                        else if (a == 1) w = M.yf[(cx * 16 + x) + 32 * z];
-                        else w = M.zf[(cx * 16 + x) + 32 * (cy * 16 + y)];
-                        (void)cz;
-                        break;
-                    }
-                    cur = mdec(cur, ma);
-                    w = dst[cur];
-                    if (w < sent) break;
-                    a = w - sent;
-                }
-                dst[q] = (IdxT)w;
             }
             __syncwarp();
         }
-        return true;
-    };
-
-    // interior levels N-1 .. max(t,1)
-    Stream S;
-    stream_init(S, V.int_words + V.int_off[id], (uint32_t)(V.int_off[id + 1] - V.int_off[id]), n_int, K_max, S_min,
-                lane);
-    if (S.bad) return kStCorrupt;
-    const uint32_t lmin = t > 0 ? t : 1u;
-    for (uint32_t l = N - 1; l >= lmin && l < N; l--) {
-        const uint32_t npar = (b >> (l + 1)) * (b >> (l + 1)) * (b >> (l + 1));
-        const uint32_t side_par_bits = N - (l + 1);
-        IdxT *dst = M.up + uoff[l];
-        if (!run_level(S, lut_int, M.up + uoff[l + 1], M.cmask + woff[l + 1], 0, npar, side_par_bits, dst,
-                       (uint8_t *)(M.cmask + woff[l]), false, 0, 0))
-            return kStCorrupt;
     }
     if (t >= 1) {
         if (t == 1 && !stream_done_ok(S, lane)) return kStCorrupt;
         const uint32_t side = b >> t;
-        store_block<IdxT>(M.up + uoff[t], side, out, side, pal_reg, pal, np, vec_ok && side >= 4, lane);
-        return status;
+        if (reg_pal) store_morton_impl<IdxT, true>(M.up + up_off(N, t), side, out, side, pal_reg, pal, np, vec_ok, lane);
+        else store_morton_impl<IdxT, false>(M.up + up_off(N, t), side, out, side, pal_reg, pal, np, vec_ok, lane);
+        return kStOk;
     }
     if (!stream_done_ok(S, lane)) return kStCorrupt;
 
-    // leaf level in chunks of side min(b, 16)
+    // ---- leaf level in chunks of side cs = min(b, 16), each held x-fastest in M.chunk
     Stream Lf;
-    stream_init(Lf, V.leaf_words + V.leaf_off[id], (uint32_t)(V.leaf_off[id + 1] - V.leaf_off[id]), n_leaf, K_max,
-                S_min, lane);
+    stream_init(Lf, M.win, V.leaf_words + V.leaf_off[id], (uint32_t)(V.leaf_off[id + 1] - V.leaf_off[id]), n_leaf,
+                K_max, S_min, lane);
     if (Lf.bad) return kStCorrupt;
-    const uint32_t cside = b < 16 ? b : 16u;
-    const uint32_t cbits = N - (b < 16 ? N : 4u);  // chunks per axis = 2^cbits
+    const uint32_t lut_leaf_off = kM;
+    const uint32_t ls = N < 4 ? N : 4u;            // log2 chunk side
+    const uint32_t cs = 1u << ls;
+    const uint32_t cbits = N - ls;                  // chunks per axis = 2^cbits
     const uint32_t n_chunks = 1u << (3 * cbits);
-    const uint32_t par_per_chunk = (cside / 2) * (cside / 2) * (cside / 2);
-    const uint32_t side_par_bits = (b < 16 ? N : 4u) - 1;  // log2 of parent-chunk side
-    const IdxT *l1 = M.up + uoff[1];
-    const uint32_t *cm1 = M.cmask + woff[1];
+    const uint32_t npar = 1u << (3 * (ls - 1));     // L1 parents per chunk
+    const uint32_t pbits = (1u << (3 * (N - 1))) - 1u;  // L1 Morton code bits
+    const IdxT *par = M.up + up_off(N, 1);
+    const uint32_t *cm_par = M.cmask + mask_off(N, 1);
+    IdxT *dst = M.chunk;
+    const uint32_t coff = (c & 1u) + (((c >> 1) & 1u) << ls) + ((c >> 2) << (2 * ls));  // child offset in the chunk
     for (uint32_t o = 0; o < n_chunks; o++) {
-        if (!run_level(Lf, lut_leaf, l1, cm1, o * par_per_chunk, par_per_chunk, side_par_bits, M.chunk, nullptr,
-                       true, o, cbits))
-            return kStCorrupt;
+        const uint32_t pp0 = o * npar;
+        // (a) 2x2x2 blocks take the parent's label; list active parents with their block's linear base
+        uint32_t n_act = 0;
+        for (uint32_t g = 0; g < npar; g += 32) {
+            const uint32_t k = g + lane;
+            bool active = false;
+            uint32_t lb = 0;
+            if (k < npar) {
+                const uint32_t pp = pp0 + k;
+                const uint32_t v = par[pp];
+                active = !((cm_par[pp >> 5] >> (pp & 31)) & 1u);
+                const uint32_t px = (k & 1u) | ((k >> 2) & 2u) | ((k >> 4) & 4u);
+                const uint32_t py = ((k >> 1) & 1u) | ((k >> 3) & 2u) | ((k >> 5) & 4u);
+                const uint32_t pz = ((k >> 2) & 1u) | ((k >> 4) & 2u) | ((k >> 6) & 4u);
+                lb = 2 * px + (2 * py << ls) + (2 * pz << (2 * ls));
+                if (sizeof(IdxT) == 1) {
+                    const uint16_t r = (uint16_t)(0x0101u * v);
+                    *(uint16_t *)(dst + lb) = r;
+                    *(uint16_t *)(dst + lb + cs) = r;
+                    *(uint16_t *)(dst + lb + cs * cs) = r;
+                    *(uint16_t *)(dst + lb + cs + cs * cs) = r;
+                } else {
+                    const uint32_t r = 0x00010001u * v;
+                    *(uint32_t *)(dst + lb) = r;
+                    *(uint32_t *)(dst + lb + cs) = r;
+                    *(uint32_t *)(dst + lb + cs * cs) = r;
+                    *(uint32_t *)(dst + lb + cs + cs * cs) = r;
+                }
+            }
+            const uint32_t am = __ballot_sync(kFull, active);
+            if (active) ((uint32_t *)M.list)[n_act + __popc(am & lanemask_lt())] = k | (lb << 16);
+            n_act += __popc(am);
+        }
+        __syncwarp();
+        // (b) four active parents per step
+        for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
+            const uint32_t n_ops = 8 * min(4u, n_act - r0);
+            produce(Lf, M.ops, M.win, lut_s + lut_leaf_off, n_ops, lane);
+            uint32_t o8;
+            if (!take_ops(Lf, M.ops, n_ops, lane, o8)) return kStCorrupt;
+            const bool is_op = lane < n_ops;
+            const uint32_t op = o8 & 7u, stop = (o8 >> 3) & 1u, delta = o8 >> 4;
+            const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
+            const uint32_t ipb = ip + __popc(pam & lanemask_lt());
+            ip += __popc(pam);
+            const uint32_t e = is_op ? ((const uint32_t *)M.list)[r0 + (lane >> 3)] : 0u;  // stale entries unread
+            const uint32_t pp = pp0 + (e & 0xFFFFu);
+            const uint32_t qi = (e >> 16) + coff;
+            const bool rx = op >= OP_RX && op <= OP_RZ;
+            const uint32_t a = rx ? op - OP_RX : 0u;
+            const uint32_t ma = kMX << a;
+            const bool plus = rx && ((c >> a) & 1u);
+            const bool minus = rx && !plus;
+            const bool plus_out = plus && ((pp & ma & pbits) == (ma & pbits));
+            const uint32_t pv = par[(plus && !plus_out) ? minc(pp, ma) : pp];
+            const bool edge = ((qi >> (ls * a)) & (cs - 1)) == 0;
+            const bool minus_out = minus && edge && !((o >> a) & 1u);
+            const uint32_t v = child_value(op, delta, ipb, pv, plus, minus, a);
+            const bool bad = is_op && (plus_out || minus_out || op == 7u || stop || (op == OP_PD && ipb < 1 + delta) ||
+                                       (op == OP_PA && ipb + 1 >= np));
+            if (is_op) dst[qi] = (IdxT)(bad ? 0u : v);
+            if (__any_sync(kFull, bad)) return kStCorrupt;
+            const bool chase = is_op && minus;
+            if (__any_sync(kFull, chase)) {
+                __syncwarp();
+                if (chase) {
+                    uint32_t cur = qi, ax = a, w = 0;
+                    for (int hop = 0; hop < 4; hop++) {
+                        if (((cur >> (ls * ax)) & (cs - 1)) == 0) {
+                            // crosses into an earlier chunk: its face holds final indices
+                            const uint32_t x = cur & (cs - 1), y = (cur >> ls) & (cs - 1), z = cur >> (2 * ls);
+                            const uint32_t cx = o & 1u, cy = (o >> 1) & 1u;
+                            if (ax == 0) w = M.xf[y + 16 * z];
+                            else if (ax == 1) w = M.yf[(cx * 16 + x) + 32 * z];
+                            else w = M.zf[(cx * 16 + x) + 32 * (cy * 16 + y)];
+                            break;
+                        }
+                        cur -= 1u << (ls * ax);
+                        w = dst[cur];
+                        if (w < sent) break;
+                        ax = w - sent;
+                    }
+                    dst[qi] = (IdxT)w;
+                }
+            }
+            __syncwarp();
+        }
         const uint32_t ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        uint32_t *cout = out + ((size_t)(oz * cside) * b + oy * cside) * b + ox * cside;
-        store_block<IdxT>(M.chunk, cside, cout, b, pal_reg, pal, np, vec_ok && cside >= 4, lane);
+        uint32_t *cout = out + ((size_t)(oz * cs) * b + oy * cs) * b + ox * cs;
+        if (reg_pal) store_linear_impl<IdxT, true>(dst, cs, ls, cout, b, pal_reg, pal, np, vec_ok, lane);
+        else store_linear_impl<IdxT, false>(dst, cs, ls, cout, b, pal_reg, pal, np, vec_ok, lane);
         if (n_chunks > 1) {
             // keep the faces later chunks may reference (-x, -y, -z neighbours)
             for (uint32_t i = lane; i < 256; i += 32) {
-                const uint32_t u = i & 15, v = i >> 4;
-                if (!ox) M.xf[u + 16 * v] = M.chunk[morton3(15, u, v)];
-                if (!oy) M.yf[(ox * 16 + u) + 32 * v] = M.chunk[morton3(u, 15, v)];
-                if (!oz) M.zf[(ox * 16 + u) + 32 * (oy * 16 + v)] = M.chunk[morton3(u, v, 15)];
+                const uint32_t u = i & 15, w = i >> 4;
+                if (!ox) M.xf[u + 16 * w] = dst[15 + 16 * u + 256 * w];
+                if (!oy) M.yf[(ox * 16 + u) + 32 * w] = dst[u + 16 * 15 + 256 * w];
+                if (!oz) M.zf[(ox * 16 + u) + 32 * (oy * 16 + w)] = dst[u + 16 * w + 256 * 15];
             }
         }
         __syncwarp();
     }
     if (!stream_done_ok(Lf, lane)) return kStCorrupt;
-    return status;
+    return kStOk;
 }
 
 template <typename IdxT>

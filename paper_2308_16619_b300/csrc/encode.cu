@@ -93,16 +93,19 @@ struct EncSmem {
     uint8_t *ops;      // ops_cap op bytes: op | stop<<3 | delta<<4
     uint32_t *red;     // block scan scratch (64 words)
     __device__ EncSmem(uint8_t *s, const EncGeom &G) {
+        // every region starts on a 16-byte boundary (the rANS phase stages symbols with 16-byte stores)
         lab = (uint32_t *)s;
-        cst = (uint8_t *)(lab + G.up_nodes);
-        list = (uint16_t *)(cst + ((G.up_nodes + 15) & ~15u));
-        ops = (uint8_t *)(list + ((G.up_nodes + 7) & ~7u));
-        red = (uint32_t *)(ops + ((G.ops_cap + 15) & ~15u));
+        cst = (uint8_t *)s + r16(G.up_nodes * 4);
+        list = (uint16_t *)(cst + r16(G.up_nodes));
+        ops = (uint8_t *)list + r16(G.up_nodes * 2);
+        red = (uint32_t *)(ops + r16(G.ops_cap));
     }
+    __host__ __device__ static uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
 };
 
 __host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes, uint32_t ops_cap) {
-    return up_nodes * 4 + ((up_nodes + 15) & ~15u) + ((up_nodes + 7) & ~7u) * 2 + ((ops_cap + 15) & ~15u) + 64 * 4;
+    return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + EncSmem::r16(ops_cap) +
+           64 * 4;
 }
 
 // exclusive block scan of one value per warp (warp totals in `red`), returns warp's offset and the total
@@ -365,13 +368,15 @@ __global__ void __launch_bounds__(kEncThreads)
     }
     __syncthreads();  // nibbles visible to the rANS warps
 
-    // ---- E. rANS, one warp per stream
+    // ---- E. rANS, one warp per stream; the symbols are staged in shared memory (the op array is free now)
     if (warp < 2) {
         const uint32_t st = warp;
         const uint32_t n = sym_tot[st];
         const uint32_t cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
         uint16_t *words = (st == 0 ? SC.w_int : SC.w_leaf) + (size_t)slot * cap;
         const uint8_t *nib = st == 0 ? SC.nib_int + (size_t)slot * G.int_cap : SC.nib_leaf + (size_t)slot * G.leaf_cap;
+        const uint32_t half = (G.ops_cap / 2) & ~15u;  // staging bytes per stream
+        uint8_t *wsm = S.ops + st * half;
         const uint32_t *F = freq + 16 * st;
         const uint32_t f_reg = lane < 16 ? F[lane] : 1u;
         uint32_t c_reg = 0;
@@ -381,20 +386,31 @@ __global__ void __launch_bounds__(kEncThreads)
         if (n > 0) {
             uint32_t x = kL;
             const uint32_t steps = (n + K - 1) / K;
-            for (uint32_t s2 = steps; s2-- > 0;) {
-                const uint32_t i = s2 * K + lane;
-                const bool act = lane < K && i < n;
-                const uint32_t sym = act ? (uint32_t)nib[i] : 0u;
-                const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
-                // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
-                const bool emit = act && x >= (f << 20);
-                const uint32_t m = __ballot_sync(kFull, emit);
-                if (emit) {
-                    words[top - __popc(m) + __popc(m & lanemask_lt())] = (uint16_t)(x & 0xFFFFu);
-                    x >>= 16;
+            const uint32_t win_steps = (half - 16) / K;  // steps per staged window (16 bytes of alignment slack)
+            // windows of steps from the end: [s_lo, s_hi) covers symbols [s_lo*K, min(n, s_hi*K))
+            for (uint32_t s_hi = steps; s_hi > 0;) {
+                const uint32_t s_lo = s_hi > win_steps ? s_hi - win_steps : 0u;
+                const uint32_t lo16 = (s_lo * K) & ~15u, sym_hi = min(n, s_hi * K);
+                for (uint32_t c16 = lane; lo16 + 16 * c16 < sym_hi; c16 += 32)
+                    reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(nib + lo16) + c16);
+                __syncwarp();
+                for (uint32_t s2 = s_hi; s2-- > s_lo;) {
+                    const uint32_t i = s2 * K + lane;
+                    const bool act = lane < K && i < n;
+                    const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
+                    const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
+                    // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
+                    const bool emit = act && x >= (f << 20);
+                    const uint32_t m = __ballot_sync(kFull, emit);
+                    if (emit) {
+                        words[top - __popc(m) + __popc(m & lanemask_lt())] = (uint16_t)(x & 0xFFFFu);
+                        x >>= 16;
+                    }
+                    top -= __popc(m);
+                    if (act) x = (x / f) * kM + (x % f) + c;
                 }
-                top -= __popc(m);
-                if (act) x = (x / f) * kM + (x % f) + c;
+                __syncwarp();
+                s_hi = s_lo;
             }
             // final states ahead of the words, state 0 first, low half first
             if (lane < K) {
@@ -540,10 +556,10 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
     }
     G.up_nodes = u;
     const uint32_t b3 = G.b * G.b * G.b;
-    G.ops_cap = u + b3 - 1;         // every node but the root can be coded
+    G.ops_cap = u + b3 - 1 > 256u ? u + b3 - 1 : 256u;  // every node but the root can be coded (>= 256: rANS staging)
     G.pal_cap = u + b3;             // palette: root + one per P_a
-    G.int_cap = 2 * (u - 1) + 2;    // interior nibbles (op + delta each)
-    G.leaf_cap = 2 * b3;
+    G.int_cap = (2 * (u - 1) + 2 + 15) & ~15u;  // interior nibbles (op + delta each), 16-byte pitch
+    G.leaf_cap = (2 * b3 + 15) & ~15u;
     G.smem = enc_smem_bytes(G.up_nodes, G.ops_cap);
     G.K_max = K_max;
     G.S_min = S_min;

@@ -13,8 +13,8 @@
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes
 // (32 MiB), present on every GPU that loads the library until the process
 // exits.  It holds the per-brick buffers of the encoder, so a call accepts at
-// most a fixed number of bricks (b = 32: 89, b = 16: 712, b = 8: 5466,
-// b = 4: 32960, b = 2: 88764) and rejects larger volumes with
+// most a fixed number of bricks (b = 32: 89, b = 16: 711, b = 8: 5429,
+// b = 4: 31654, b = 2: 79888) and rejects larger volumes with
 // CSGV_ERR_INVALID_ARG.  Every call shares the array and it keeps the last
 // call's contents: the counters that must start at zero are cleared at the
 // start of each call, and two calls whose work overlaps on the GPU (different
