@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--b", type=int, default=B)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--s-min", type=int, default=256, help="symbols per rANS state (format parameter S_min)")
+    ap.add_argument("--k-max", type=int, default=32, help="most interleaved rANS states per stream (K_max)")
     return ap.parse_args()
 
 
@@ -201,7 +203,7 @@ def main():
         table = csgv.csgv_build_freq_table(vol, b, STRIDE)
         if ev:
             ev[1].record(stream)
-        v = csgv.csgv_encode_bricks(vol, b, table)
+        v = csgv.csgv_encode_bricks(vol, b, table, K_max=args.k_max, S_min=args.s_min)
         if ev:
             ev[2].record(stream)
         csgv.csgv_decode_bricks(v, ids, lods, out, offs, status)
@@ -296,6 +298,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD} 512^3 warped Voronoi, 20000 cells, 30% background, b={b}",
                    "bricks": n, "lod": 0, "step": "prepass(stride 512)+encode+batched decode",
+                   "K_max": args.k_max, "S_min": args.s_min,
                    "l2": "inputs and outputs (512 MiB each) larger than L2", "parallelism": f"replicas x{world}"},
         "phases_ms": {"prepass": prep_ms, "encode": enc_ms, "decode": dec_ms},
         "decode_gbs": out_bytes / (dec_alone_ms / 1e3) / 1e9,

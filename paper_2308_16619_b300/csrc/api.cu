@@ -360,7 +360,7 @@ int csgv_decode_bricks(const csgv_volume *vol, const uint32_t *brick_ids_dev, co
     cudaStream_t st = (cudaStream_t)stream;
     csgv_volume *v = const_cast<csgv_volume *>(vol);
     const bool wide = v->max_palette > 253;
-    const uint32_t warps = wide ? 8 : 14;  // as many warps as the 227 KB of shared memory per CTA holds
+    const uint32_t warps = wide ? 8 : 15;  // as many warps as the 227 KB of shared memory per CTA holds
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

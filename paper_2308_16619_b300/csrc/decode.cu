@@ -63,24 +63,26 @@ struct Traits<uint16_t> {
 
 // shared-memory layout of one warp (entries of IdxT unless noted)
 constexpr uint32_t kUpN = 4688;      // levels 1..5 of a 32^3 brick: 4096+512+64+8+1 = 4681
-constexpr uint32_t kChunkN = 4096;   // one 16^3 chunk of level 0
-constexpr uint32_t kXfN = 256, kYfN = 512, kZfN = 1024;
+constexpr uint32_t kChunkN = 4096;   // one 16^3 chunk of level 0 (x fastest)
+constexpr uint32_t kXfN = 256, kYfN = 512, kZfN = 1024;  // faces of finished chunks toward -x, -y, -z
 constexpr uint32_t kMaskWords = 148; // const bits of levels 1..5
-constexpr uint32_t kListN = 1024;    // active parents of one level / chunk (uint16, or uint32 for leaf chunks)
+constexpr uint32_t kGroup = 64;      // parents per list (uint32 entries: parent | block base << 16)
+constexpr uint32_t kQueueN = 64;     // queued children whose op is not R_p (two words each)
 constexpr uint32_t kOpsN = 256;      // op ring (bytes: op | stop<<3 | delta<<4)
 constexpr uint32_t kWinWords = 256;  // staged stream words (uint16)
 
 template <typename IdxT>
 __host__ __device__ constexpr uint32_t warp_smem_bytes() {
-    return ((kUpN + kChunkN + kXfN + kYfN + kZfN) * (uint32_t)sizeof(IdxT) + kMaskWords * 4 + kListN * 2 +
-            kWinWords * 2 + kOpsN + 15u) & ~15u;
+    return ((kUpN + kChunkN + kXfN + kYfN + kZfN) * (uint32_t)sizeof(IdxT) + kMaskWords * 4 + kGroup * 4 +
+            kQueueN * 8 + kWinWords * 2 + kOpsN + 15u) & ~15u;
 }
 
 template <typename IdxT>
 struct WarpMem {
     IdxT *up, *chunk, *xf, *yf, *zf;
-    uint32_t *cmask;
-    uint16_t *list, *win;
+    uint32_t *cmask, *list;
+    uint2 *queue;
+    uint16_t *win;
     uint8_t *ops;
     __device__ explicit WarpMem(uint8_t *base) {
         up = (IdxT *)base;
@@ -88,10 +90,11 @@ struct WarpMem {
         xf = chunk + kChunkN;
         yf = xf + kXfN;
         zf = yf + kYfN;
-        cmask = (uint32_t *)(zf + kZfN);   // 16-byte aligned: the IdxT arrays above total a multiple of 16 bytes
-        win = (uint16_t *)(cmask + kMaskWords);
-        list = win + kWinWords;
-        ops = (uint8_t *)(list + kListN);
+        cmask = (uint32_t *)(zf + kZfN);  // 16-byte aligned: the IdxT arrays above total a multiple of 16 bytes
+        queue = (uint2 *)(cmask + kMaskWords);
+        win = (uint16_t *)(queue + kQueueN);
+        list = (uint32_t *)(win + kWinWords);
+        ops = (uint8_t *)(list + kGroup);
     }
 };
 
@@ -169,35 +172,40 @@ __device__ __forceinline__ void stream_init(Stream &s, uint16_t *win, const uint
 // decode rANS steps until `want` complete op records are waiting or the stream is exhausted
 __device__ __forceinline__ void produce(Stream &s, uint8_t *ops, uint16_t *win, const uint32_t *lut, uint32_t want,
                                         uint32_t lane) {
-    while (s.otail - s.ohead - s.pend < want && s.remaining > 0) {
-        if (s.pos > s.stage_at) stage(s, win, lane);
-        const uint32_t n = min(s.K, s.remaining);
+    const uint32_t lt = lanemask_lt();
+    uint32_t x = s.x, pos = s.pos, otail = s.otail, remaining = s.remaining, pend = s.pend;
+    const uint32_t ohead = s.ohead, K = s.K, last = s.n_words - 1;  // K > 0 and n_words >= 2K whenever remaining > 0
+    while (otail - ohead - pend < want && remaining > 0) {
+        if (pos > s.stage_at) {
+            if (pos > s.n_words) {  // corrupt: the words ran out
+                s.bad = true;
+                break;
+            }
+            s.pos = pos;
+            stage(s, win, lane);
+        }
+        const uint32_t n = min(K, remaining);
         const bool act = lane < n;
-        uint32_t sym = 0;
-        if (act) {
-            const uint32_t slot = s.x & (kM - 1u);
-            const uint32_t e = lut[slot];
-            sym = e & 15u;
-            s.x = ((e >> 4) & 0x1FFFu) * (s.x >> kScaleBits) + (e >> 17);
-        }
-        const bool need = act && s.x < kL;
+        // every lane runs the step (branch-free); lanes past n keep their state
+        const uint32_t e = lut[x & (kM - 1u)];
+        const uint32_t sym = e & 15u;
+        const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
+        const bool need = act && xn < kL;
         const uint32_t m = __ballot_sync(kFull, need);
-        if (need) {
-            const uint32_t off = s.pos + __popc(m & lanemask_lt());
-            const uint32_t wv = off < s.n_words ? (uint32_t)win[(int32_t)off - s.wb] : 0u;
-            s.x = (s.x << 16) | wv;
-        }
-        s.pos += __popc(m);
-        s.remaining -= n;
+        const uint32_t off = min(pos + __popc(m & lt), last);
+        const uint32_t wv = win[min(max((int32_t)off - s.wb, 0), (int32_t)kWinWords - 1)];  // in-window for every lane
+        x = act ? (need ? ((xn << 16) | wv) : xn) : x;
+        pos += __popc(m);
+        remaining -= n;
         uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD);
-        if ((cand | s.pend) == 0) {
+        if ((cand | pend) == 0) {
             // common case: every symbol of the step is an op
-            if (act) ops[(s.otail + lane) & (kOpsN - 1)] = (uint8_t)sym;
-            s.otail += n;
+            if (act) ops[(otail + lane) & (kOpsN - 1)] = (uint8_t)sym;
+            otail += n;
             continue;
         }
         // which symbols are delta nibbles: the one after each P_delta op
-        uint64_t dm = s.pend;  // bit i: symbol i of this step is a delta
+        uint64_t dm = pend;  // bit i: symbol i of this step is a delta
         cand &= ~(uint32_t)dm;
         while (cand) {
             const uint32_t i = __ffs(cand) - 1;
@@ -208,17 +216,22 @@ __device__ __forceinline__ void produce(Stream &s, uint8_t *ops, uint16_t *win, 
             }
         }
         const uint32_t nxt = __shfl_down_sync(kFull, sym, 1);
-        if (s.pend && lane == 0) ops[(s.otail - 1) & (kOpsN - 1)] |= (uint8_t)(sym << 4);
+        if (pend && lane == 0) ops[(otail - 1) & (kOpsN - 1)] |= (uint8_t)(sym << 4);
         const uint32_t actm = n >= 32 ? kFull : ((1u << n) - 1u);
         const uint32_t opm = actm & ~(uint32_t)dm;
         if ((opm >> lane) & 1u) {
             const bool pd = (sym & 7u) == OP_PD && lane + 1 < n;
-            ops[(s.otail + __popc(opm & lanemask_lt())) & (kOpsN - 1)] = (uint8_t)(sym | (pd ? nxt << 4 : 0u));
+            ops[(otail + __popc(opm & lt)) & (kOpsN - 1)] = (uint8_t)(sym | (pd ? nxt << 4 : 0u));
         }
-        s.otail += __popc(opm);
-        s.pend = (uint32_t)((dm >> n) & 1ull);
+        otail += __popc(opm);
+        pend = (uint32_t)((dm >> n) & 1ull);
     }
-    if (s.pos > s.n_words) s.bad = true;
+    s.x = x;
+    s.pos = pos;
+    s.otail = otail;
+    s.remaining = remaining;
+    s.pend = pend;
+    if (pos > s.n_words) s.bad = true;
     __syncwarp();
 }
 
@@ -387,6 +400,12 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
         return ipb + 1;
     };
 
+    // Children whose op is R_p already hold their parent's label after the fill, so only the other
+    // children are queued (uint2: child index | op << 12 | delta << 15 | c << 19, palette index i_p |
+    // parent << 16) and evaluated 32 at a time.  Queued children are evaluated in stream order, so a
+    // -axis target is either final or evaluated in the same batch (resolved by the chase).
+    uint32_t qhead = 0, qtail = 0;
+
     // ---- interior levels N-1 .. max(t,1): Morton order, all levels of the brick in `up`
     Stream S;
     stream_init(S, M.win, V.int_words + V.int_off[id], (uint32_t)(V.int_off[id + 1] - V.int_off[id]), n_int, K_max,
@@ -400,57 +419,27 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
         const uint32_t *cm_par = M.cmask + mask_off(N, l + 1);
         IdxT *dst = M.up + up_off(N, l);
         uint8_t *cm_dst = (uint8_t *)(M.cmask + mask_off(N, l));
-        // (a) children take the parent's label (a constant parent keeps it); list the active parents
-        uint32_t n_act = 0;
-        for (uint32_t g = 0; g < npar; g += 32) {
-            const uint32_t k = g + lane;
-            bool active = false;
-            if (k < npar) {
-                const uint32_t v = par[k];
-                const bool pc = (cm_par[k >> 5] >> (k & 31)) & 1u;
-                active = !pc;
-                if (sizeof(IdxT) == 1) {
-                    *(uint64_t *)(dst + 8 * k) = 0x0101010101010101ull * v;
-                } else {
-                    const uint32_t r = 0x00010001u * v;
-                    *(uint4 *)(dst + 8 * k) = make_uint4(r, r, r, r);
-                }
-                cm_dst[k] = pc ? 0xFF : 0x00;
-            }
-            const uint32_t am = __ballot_sync(kFull, active);
-            if (active) M.list[n_act + __popc(am & lanemask_lt())] = (uint16_t)k;
-            n_act += __popc(am);
-        }
-        __syncwarp();
-        // (b) four active parents (32 child ops) per step, lane = child
-        for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
-            const uint32_t n_ops = 8 * min(4u, n_act - r0);
-            produce(S, M.ops, M.win, lut_s, n_ops, lane);
-            uint32_t o;
-            if (!take_ops(S, M.ops, n_ops, lane, o)) return kStCorrupt;
-            const bool is_op = lane < n_ops;
-            const uint32_t op = o & 7u, stop = (o >> 3) & 1u, delta = o >> 4;
-            const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
-            const uint32_t ipb = ip + __popc(pam & lanemask_lt());
-            ip += __popc(pam);
-            const uint32_t k = is_op ? (uint32_t)M.list[r0 + (lane >> 3)] : 0u;  // stale entries unread
-            const uint32_t q = 8 * k + c;
+        // evaluate up to 32 queued children (interior level: Morton layout)
+        auto flush = [&](uint32_t cnt) -> bool {
+            const bool in = lane < cnt;
+            const uint2 qe = in ? M.queue[(qhead + lane) & (kQueueN - 1)] : make_uint2(0u, 0u);
+            qhead += cnt;
+            const uint32_t q = qe.x & 0xFFFu, op = (qe.x >> 12) & 7u, delta = (qe.x >> 15) & 15u, cc = qe.x >> 19;
+            const uint32_t ipb = qe.y & 0xFFFFu, k = qe.y >> 16;
             const bool rx = op >= OP_RX && op <= OP_RZ;
             const uint32_t a = rx ? op - OP_RX : 0u;
             const uint32_t ma = kMX << a;
-            const bool plus = rx && ((c >> a) & 1u);
+            const bool plus = rx && ((cc >> a) & 1u);
             const bool minus = rx && !plus;
             const bool plus_out = plus && ((k & ma & pbits) == (ma & pbits));
             const uint32_t pv = par[(plus && !plus_out) ? minc(k, ma) : k];
             const bool minus_out = minus && (q & ma & (8 * npar - 1)) == 0;
             const uint32_t v = child_value(op, delta, ipb, pv, plus, minus, a);
-            const bool bad = is_op && (plus_out || minus_out || op == 7u || (op == OP_PD && ipb < 1 + delta) ||
-                                       (op == OP_PA && ipb + 1 >= np));
-            if (is_op) dst[q] = (IdxT)(bad ? 0u : v);
-            const uint32_t sm = __ballot_sync(kFull, is_op && stop);
-            if (is_op && c == 0) cm_dst[k] = (uint8_t)(sm >> (lane & ~7u));
-            if (__any_sync(kFull, bad)) return kStCorrupt;
-            const bool chase = is_op && minus;
+            const bool bad = in && (plus_out || minus_out || op == 7u || op == OP_RP ||
+                                    (op == OP_PD && ipb < 1 + delta) || (op == OP_PA && ipb + 1 >= np));
+            if (in) dst[q] = (IdxT)(bad ? 0u : v);
+            if (__any_sync(kFull, bad)) return false;
+            const bool chase = in && minus;
             if (__any_sync(kFull, chase)) {
                 __syncwarp();
                 // same-level references form chains of <= 3 hops (each hop sets one more child bit)
@@ -466,7 +455,59 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
                 }
             }
             __syncwarp();
+            return true;
+        };
+        for (uint32_t g0 = 0; g0 < npar; g0 += kGroup) {
+            // (a) children take the parent's label (a constant parent keeps it); list the active parents
+            uint32_t n_act = 0;
+            for (uint32_t g = g0; g < g0 + kGroup && g < npar; g += 32) {
+                const uint32_t k = g + lane;
+                bool active = false;
+                if (k < npar) {
+                    const uint32_t v = par[k];
+                    const bool pc = (cm_par[k >> 5] >> (k & 31)) & 1u;
+                    active = !pc;
+                    if (sizeof(IdxT) == 1) {
+                        *(uint64_t *)(dst + 8 * k) = 0x0101010101010101ull * v;
+                    } else {
+                        const uint32_t r = 0x00010001u * v;
+                        *(uint4 *)(dst + 8 * k) = make_uint4(r, r, r, r);
+                    }
+                    cm_dst[k] = pc ? 0xFF : 0x00;
+                }
+                const uint32_t am = __ballot_sync(kFull, active);
+                if (active) M.list[n_act + __popc(am & lanemask_lt())] = k;
+                n_act += __popc(am);
+            }
+            __syncwarp();
+            // (b) read four active parents' ops (32) per step; queue the children that are not R_p
+            for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
+                const uint32_t n_ops = 8 * min(4u, n_act - r0);
+                produce(S, M.ops, M.win, lut_s, n_ops, lane);
+                uint32_t o;
+                if (!take_ops(S, M.ops, n_ops, lane, o)) return kStCorrupt;
+                const bool is_op = lane < n_ops;
+                const uint32_t op = o & 7u;
+                const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
+                const uint32_t ipb = ip + __popc(pam & lanemask_lt());
+                ip += __popc(pam);
+                const uint32_t sm = __ballot_sync(kFull, is_op && ((o >> 3) & 1u));
+                const bool nr = is_op && op != OP_RP;
+                const uint32_t nm = __ballot_sync(kFull, nr);
+                if (is_op && (c == 0 || nr)) {
+                    const uint32_t k = M.list[r0 + (lane >> 3)];
+                    if (c == 0) cm_dst[k] = (uint8_t)(sm >> (lane & ~7u));
+                    if (nr)
+                        M.queue[(qtail + __popc(nm & lanemask_lt())) & (kQueueN - 1)] =
+                            make_uint2((8 * k + c) | (op << 12) | ((o >> 4) << 15) | (c << 19), ipb | (k << 16));
+                }
+                qtail += __popc(nm);
+                __syncwarp();
+                if (qtail - qhead >= 32 && !flush(32)) return kStCorrupt;
+            }
         }
+        while (qtail != qhead)
+            if (!flush(min(32u, qtail - qhead))) return kStCorrupt;
     }
     if (t >= 1) {
         if (t == 1 && !stream_done_ok(S, lane)) return kStCorrupt;
@@ -477,17 +518,16 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
     }
     if (!stream_done_ok(S, lane)) return kStCorrupt;
 
-    // ---- leaf level in chunks of side cs = min(b, 16), each held x-fastest in M.chunk
+    // ---- leaf level in chunks of side cs = min(b, 16) in Z-order, each held x-fastest in M.chunk
     Stream Lf;
     stream_init(Lf, M.win, V.leaf_words + V.leaf_off[id], (uint32_t)(V.leaf_off[id + 1] - V.leaf_off[id]), n_leaf,
                 K_max, S_min, lane);
     if (Lf.bad) return kStCorrupt;
-    const uint32_t lut_leaf_off = kM;
-    const uint32_t ls = N < 4 ? N : 4u;            // log2 chunk side
+    const uint32_t ls = N < 4 ? N : 4u;             // log2 chunk side
     const uint32_t cs = 1u << ls;
-    const uint32_t cbits = N - ls;                  // chunks per axis = 2^cbits
+    const uint32_t cbits = N - ls;                  // chunks per axis = 2^cbits (at most 2)
     const uint32_t n_chunks = 1u << (3 * cbits);
-    const uint32_t npar = 1u << (3 * (ls - 1));     // L1 parents per chunk
+    const uint32_t npar = 1u << (3 * (ls - 1));     // L1 parents per chunk (<= 512)
     const uint32_t pbits = (1u << (3 * (N - 1))) - 1u;  // L1 Morton code bits
     const IdxT *par = M.up + up_off(N, 1);
     const uint32_t *cm_par = M.cmask + mask_off(N, 1);
@@ -495,68 +535,29 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
     const uint32_t coff = (c & 1u) + (((c >> 1) & 1u) << ls) + ((c >> 2) << (2 * ls));  // child offset in the chunk
     for (uint32_t o = 0; o < n_chunks; o++) {
         const uint32_t pp0 = o * npar;
-        // (a) 2x2x2 blocks take the parent's label; list active parents with their block's linear base
-        uint32_t n_act = 0;
-        for (uint32_t g = 0; g < npar; g += 32) {
-            const uint32_t k = g + lane;
-            bool active = false;
-            uint32_t lb = 0;
-            if (k < npar) {
-                const uint32_t pp = pp0 + k;
-                const uint32_t v = par[pp];
-                active = !((cm_par[pp >> 5] >> (pp & 31)) & 1u);
-                const uint32_t px = (k & 1u) | ((k >> 2) & 2u) | ((k >> 4) & 4u);
-                const uint32_t py = ((k >> 1) & 1u) | ((k >> 3) & 2u) | ((k >> 5) & 4u);
-                const uint32_t pz = ((k >> 2) & 1u) | ((k >> 4) & 2u) | ((k >> 6) & 4u);
-                lb = 2 * px + (2 * py << ls) + (2 * pz << (2 * ls));
-                if (sizeof(IdxT) == 1) {
-                    const uint16_t r = (uint16_t)(0x0101u * v);
-                    *(uint16_t *)(dst + lb) = r;
-                    *(uint16_t *)(dst + lb + cs) = r;
-                    *(uint16_t *)(dst + lb + cs * cs) = r;
-                    *(uint16_t *)(dst + lb + cs + cs * cs) = r;
-                } else {
-                    const uint32_t r = 0x00010001u * v;
-                    *(uint32_t *)(dst + lb) = r;
-                    *(uint32_t *)(dst + lb + cs) = r;
-                    *(uint32_t *)(dst + lb + cs * cs) = r;
-                    *(uint32_t *)(dst + lb + cs + cs * cs) = r;
-                }
-            }
-            const uint32_t am = __ballot_sync(kFull, active);
-            if (active) ((uint32_t *)M.list)[n_act + __popc(am & lanemask_lt())] = k | (lb << 16);
-            n_act += __popc(am);
-        }
-        __syncwarp();
-        // (b) four active parents per step
-        for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
-            const uint32_t n_ops = 8 * min(4u, n_act - r0);
-            produce(Lf, M.ops, M.win, lut_s + lut_leaf_off, n_ops, lane);
-            uint32_t o8;
-            if (!take_ops(Lf, M.ops, n_ops, lane, o8)) return kStCorrupt;
-            const bool is_op = lane < n_ops;
-            const uint32_t op = o8 & 7u, stop = (o8 >> 3) & 1u, delta = o8 >> 4;
-            const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
-            const uint32_t ipb = ip + __popc(pam & lanemask_lt());
-            ip += __popc(pam);
-            const uint32_t e = is_op ? ((const uint32_t *)M.list)[r0 + (lane >> 3)] : 0u;  // stale entries unread
-            const uint32_t pp = pp0 + (e & 0xFFFFu);
-            const uint32_t qi = (e >> 16) + coff;
+        const uint32_t ox = o & 1u, oy = (o >> 1) & 1u, oz = o >> 2;
+        // evaluate up to 32 queued children (leaf chunk: x-fastest layout)
+        auto flush = [&](uint32_t cnt) -> bool {
+            const bool in = lane < cnt;
+            const uint2 qe = in ? M.queue[(qhead + lane) & (kQueueN - 1)] : make_uint2(0u, 0u);
+            qhead += cnt;
+            const uint32_t qi = qe.x & 0xFFFu, op = (qe.x >> 12) & 7u, delta = (qe.x >> 15) & 15u, cc = qe.x >> 19;
+            const uint32_t ipb = qe.y & 0xFFFFu, pp = pp0 + (qe.y >> 16);
             const bool rx = op >= OP_RX && op <= OP_RZ;
             const uint32_t a = rx ? op - OP_RX : 0u;
             const uint32_t ma = kMX << a;
-            const bool plus = rx && ((c >> a) & 1u);
+            const bool plus = rx && ((cc >> a) & 1u);
             const bool minus = rx && !plus;
             const bool plus_out = plus && ((pp & ma & pbits) == (ma & pbits));
             const uint32_t pv = par[(plus && !plus_out) ? minc(pp, ma) : pp];
             const bool edge = ((qi >> (ls * a)) & (cs - 1)) == 0;
             const bool minus_out = minus && edge && !((o >> a) & 1u);
             const uint32_t v = child_value(op, delta, ipb, pv, plus, minus, a);
-            const bool bad = is_op && (plus_out || minus_out || op == 7u || stop || (op == OP_PD && ipb < 1 + delta) ||
-                                       (op == OP_PA && ipb + 1 >= np));
-            if (is_op) dst[qi] = (IdxT)(bad ? 0u : v);
-            if (__any_sync(kFull, bad)) return kStCorrupt;
-            const bool chase = is_op && minus;
+            const bool bad = in && (plus_out || minus_out || op == 7u || op == OP_RP ||
+                                    (op == OP_PD && ipb < 1 + delta) || (op == OP_PA && ipb + 1 >= np));
+            if (in) dst[qi] = (IdxT)(bad ? 0u : v);
+            if (__any_sync(kFull, bad)) return false;
+            const bool chase = in && minus;
             if (__any_sync(kFull, chase)) {
                 __syncwarp();
                 if (chase) {
@@ -565,10 +566,9 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
                         if (((cur >> (ls * ax)) & (cs - 1)) == 0) {
                             // crosses into an earlier chunk: its face holds final indices
                             const uint32_t x = cur & (cs - 1), y = (cur >> ls) & (cs - 1), z = cur >> (2 * ls);
-                            const uint32_t cx = o & 1u, cy = (o >> 1) & 1u;
                             if (ax == 0) w = M.xf[y + 16 * z];
-                            else if (ax == 1) w = M.yf[(cx * 16 + x) + 32 * z];
-                            else w = M.zf[(cx * 16 + x) + 32 * (cy * 16 + y)];
+                            else if (ax == 1) w = M.yf[(ox * 16 + x) + 32 * z];
+                            else w = M.zf[(ox * 16 + x) + 32 * (oy * 16 + y)];
                             break;
                         }
                         cur -= 1u << (ls * ax);
@@ -580,8 +580,69 @@ __device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMe
                 }
             }
             __syncwarp();
+            return true;
+        };
+        for (uint32_t g0 = 0; g0 < npar; g0 += kGroup) {
+            // (a) 2x2x2 blocks take the parent's label; list active parents with their block's linear base
+            uint32_t n_act = 0;
+            for (uint32_t g = g0; g < g0 + kGroup && g < npar; g += 32) {
+                const uint32_t k = g + lane;
+                bool active = false;
+                uint32_t lb = 0;
+                if (k < npar) {
+                    const uint32_t pp = pp0 + k;
+                    const uint32_t v = par[pp];
+                    active = !((cm_par[pp >> 5] >> (pp & 31)) & 1u);
+                    const uint32_t px = (k & 1u) | ((k >> 2) & 2u) | ((k >> 4) & 4u);
+                    const uint32_t py = ((k >> 1) & 1u) | ((k >> 3) & 2u) | ((k >> 5) & 4u);
+                    const uint32_t pz = ((k >> 2) & 1u) | ((k >> 4) & 2u) | ((k >> 6) & 4u);
+                    lb = 2 * px + (2 * py << ls) + (2 * pz << (2 * ls));
+                    if (sizeof(IdxT) == 1) {
+                        const uint16_t r = (uint16_t)(0x0101u * v);
+                        *(uint16_t *)(dst + lb) = r;
+                        *(uint16_t *)(dst + lb + cs) = r;
+                        *(uint16_t *)(dst + lb + cs * cs) = r;
+                        *(uint16_t *)(dst + lb + cs + cs * cs) = r;
+                    } else {
+                        const uint32_t r = 0x00010001u * v;
+                        *(uint32_t *)(dst + lb) = r;
+                        *(uint32_t *)(dst + lb + cs) = r;
+                        *(uint32_t *)(dst + lb + cs * cs) = r;
+                        *(uint32_t *)(dst + lb + cs + cs * cs) = r;
+                    }
+                }
+                const uint32_t am = __ballot_sync(kFull, active);
+                if (active) M.list[n_act + __popc(am & lanemask_lt())] = k | (lb << 16);
+                n_act += __popc(am);
+            }
+            __syncwarp();
+            // (b) read four active parents' ops per step; queue the children that are not R_p
+            for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
+                const uint32_t n_ops = 8 * min(4u, n_act - r0);
+                produce(Lf, M.ops, M.win, lut_s + kM, n_ops, lane);
+                uint32_t o8;
+                if (!take_ops(Lf, M.ops, n_ops, lane, o8)) return kStCorrupt;
+                const bool is_op = lane < n_ops;
+                const uint32_t op = o8 & 7u;
+                const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
+                const uint32_t ipb = ip + __popc(pam & lanemask_lt());
+                ip += __popc(pam);
+                if (__any_sync(kFull, is_op && ((o8 >> 3) & 1u))) return kStCorrupt;  // leaf stop bits are 0
+                const bool nr = is_op && op != OP_RP;
+                const uint32_t nm = __ballot_sync(kFull, nr);
+                if (nr) {
+                    const uint32_t e = M.list[r0 + (lane >> 3)];
+                    M.queue[(qtail + __popc(nm & lanemask_lt())) & (kQueueN - 1)] =
+                        make_uint2(((e >> 16) + coff) | (op << 12) | ((o8 >> 4) << 15) | (c << 19),
+                                   ipb | ((e & 0xFFFFu) << 16));
+                }
+                qtail += __popc(nm);
+                __syncwarp();
+                if (qtail - qhead >= 32 && !flush(32)) return kStCorrupt;
+            }
         }
-        const uint32_t ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        while (qtail != qhead)
+            if (!flush(min(32u, qtail - qhead))) return kStCorrupt;
         uint32_t *cout = out + ((size_t)(oz * cs) * b + oy * cs) * b + ox * cs;
         if (reg_pal) store_linear_impl<IdxT, true>(dst, cs, ls, cout, b, pal_reg, pal, np, vec_ok, lane);
         else store_linear_impl<IdxT, false>(dst, cs, ls, cout, b, pal_reg, pal, np, vec_ok, lane);

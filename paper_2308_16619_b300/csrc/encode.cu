@@ -47,7 +47,6 @@ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) 
 __device__ __forceinline__ uint32_t compact5(uint32_t m) {
     return (m & 1u) | ((m >> 2) & 2u) | ((m >> 4) & 4u) | ((m >> 6) & 8u) | ((m >> 8) & 16u);
 }
-__device__ __forceinline__ uint32_t axis_mask(uint32_t a) { return a == 0 ? kMX : (a == 1 ? kMY : kMZ); }
 __device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
 __device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
 
@@ -92,6 +91,7 @@ struct EncSmem {
     uint16_t *list;    // active parents per parent level (same offsets as lab)
     uint8_t *ops;      // ops_cap op bytes: op | stop<<3 | delta<<4
     uint32_t *red;     // block scan scratch (64 words)
+    uint2 *plist;      // children that need a palette op: (op index, label), one 256-op chunk at a time
     __device__ EncSmem(uint8_t *s, const EncGeom &G) {
         // every region starts on a 16-byte boundary (the rANS phase stages symbols with 16-byte stores)
         lab = (uint32_t *)s;
@@ -99,13 +99,14 @@ struct EncSmem {
         list = (uint16_t *)(cst + r16(G.up_nodes));
         ops = (uint8_t *)list + r16(G.up_nodes * 2);
         red = (uint32_t *)(ops + r16(G.ops_cap));
+        plist = (uint2 *)(red + 64);
     }
     __host__ __device__ static uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
 };
 
 __host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes, uint32_t ops_cap) {
     return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + EncSmem::r16(ops_cap) +
-           64 * 4;
+           64 * 4 + 256 * 8;
 }
 
 // exclusive block scan of one value per warp (warp totals in `red`), returns warp's offset and the total
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(kEncThreads)
     // ---- A. pyramid
     {
         const uint32_t B1 = b >> 1, n1 = B1 * B1 * B1;
+#pragma unroll 2
         for (uint32_t i = tid; i < n1; i += kEncThreads) {
             const uint32_t x = i % B1, y = (i / B1) % B1, z = i / (B1 * B1);
             uint32_t w[8];
@@ -208,33 +210,30 @@ __global__ void __launch_bounds__(kEncThreads)
             lvl_base[l] = n_ops;
             lvl_nact[l] = n_act;
         }
+        const uint32_t cbits = (1u << (3 * (N - lc))) - 1u;  // Morton code bits of the child level
         for (uint32_t j = tid; j < nops_l; j += kEncThreads) {
             const uint32_t p = S.list[G.off[l] + (j >> 3)], c = j & 7u;
             const uint32_t q = 8 * p + c;
+            // every label the choice can look at, loaded up front (independent loads); a neighbour index
+            // that would leave the brick wraps to an in-brick node and is ignored through ok[]
+            uint32_t nv[3];
+            bool ok[3];
+#pragma unroll
+            for (uint32_t a = 0; a < 3; a++) {
+                const uint32_t ma = (kMX << a) & cbits;
+                const bool minus = ((c >> a) & 1u) == 0;
+                ok[a] = minus ? (q & ma) != 0 : (q & ma) != ma;
+                nv[a] = minus ? node_label(B, S, G, lc, mdec(q, ma)) : S.lab[G.off[l] + (minc(q, ma) >> 3)];
+            }
             const uint32_t v = node_label(B, S, G, lc, q);
             const uint32_t parent = S.lab[G.off[l] + p];
             const uint32_t stop = lc >= 1 ? (uint32_t)S.cst[G.off[lc] + q] : 0u;
-            uint32_t op = kNeedPal;
-            if (v == parent) {
-                op = OP_RP;
-            } else {
-                for (uint32_t a = 0; a < 3; a++) {
-                    const uint32_t ma = axis_mask(a) & ((1u << (3 * (N - lc))) - 1u);
-                    uint32_t nv;
-                    bool ok;
-                    if (((c >> a) & 1u) == 0) {
-                        ok = (q & ma) != 0;  // coordinate > 0
-                        nv = ok ? node_label(B, S, G, lc, mdec(q, ma)) : 0u;
-                    } else {
-                        ok = (q & ma) != ma;  // coordinate < Bc - 1
-                        nv = ok ? S.lab[G.off[l] + (minc(q, ma) >> 3)] : 0u;
-                    }
-                    if (ok && nv == v) {
-                        op = OP_RX + a;
-                        break;
-                    }
-                }
-            }
+            // first applicable reuse: R_p, R_x, R_y, R_z (bestOperation order)
+            const uint32_t op = v == parent ? OP_RP
+                                : (ok[0] && nv[0] == v) ? OP_RX
+                                : (ok[1] && nv[1] == v) ? OP_RY
+                                : (ok[2] && nv[2] == v) ? OP_RZ
+                                : kNeedPal;
             S.ops[n_ops + j] = (uint8_t)(op | (stop << 3));
         }
         n_ops += nops_l;
@@ -242,52 +241,56 @@ __global__ void __launch_bounds__(kEncThreads)
         __syncthreads();
     }
 
-    // ---- C. palette pass (one warp, stream order)
-    if (warp == 0) {
+    // ---- C. palette pass in stream order: all warps collect the children no reuse fits (with their
+    // labels), 256 ops at a time; warp 0 then walks them in order with the last 17 palette entries in
+    // registers (lane i holds palette[i_p - i])
+    {
         const uint32_t root = S.lab[G.off[N]];
-        uint32_t win = root;       // lane i: palette[ip - i]
-        uint32_t ip = 0, np = 1;   // i_p and palette size
+        uint32_t win = root;
+        uint32_t ip = 0, np = 1;  // i_p and palette size (kept by warp 0)
         uint32_t *pal = count ? nullptr : SC.pal + (size_t)slot * G.pal_cap;
-        if (pal && lane == 0) pal[0] = root;
-        for (uint32_t g = 0; g < n_ops; g += 32) {
-            const uint32_t j = g + lane;
-            const uint32_t o = j < n_ops ? S.ops[j] : 0u;
-            uint32_t m = __ballot_sync(kFull, j < n_ops && (o & 7u) == kNeedPal);
-            if (!m) continue;
-            // labels of the marked children (each lane its own)
-            uint32_t v = 0;
-            if ((m >> lane) & 1u) {
+        if (pal && tid == 0) pal[0] = root;
+        for (uint32_t g = 0; g < n_ops; g += kEncThreads) {
+            const uint32_t j = g + tid;
+            const bool need = j < n_ops && (S.ops[j] & 7u) == kNeedPal;
+            const uint32_t m = __ballot_sync(kFull, need);
+            uint32_t tot;
+            const uint32_t woff = block_excl_warp(S.red, __popc(m), tot);
+            if (tot == 0) continue;
+            if (need) {
                 uint32_t l = 1;
                 for (uint32_t L = N; L >= 2; L--)
                     if (j >= lvl_base[L] && j < lvl_base[L] + 8 * lvl_nact[L]) l = L;
                 const uint32_t base = lvl_base[l];
                 const uint32_t p = S.list[G.off[l] + ((j - base) >> 3)];
-                v = node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u));
+                S.plist[woff + __popc(m & lanemask_lt())] = make_uint2(j, node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u)));
             }
-            while (m) {
-                const uint32_t k = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t vk = __shfl_sync(kFull, v, k);
-                const bool match = lane <= 16 && lane <= ip && win == vk;
-                const uint32_t mm = __ballot_sync(kFull, match);
-                uint32_t op, delta = 0;
-                if (mm) {
-                    const uint32_t f = __ffs(mm) - 1;
-                    op = f == 0 ? OP_P0 : OP_PD;
-                    delta = f == 0 ? 0u : f - 1;
-                } else {
-                    op = OP_PA;
-                    const uint32_t up = __shfl_up_sync(kFull, win, 1);
-                    win = lane == 0 ? vk : up;
-                    if (pal && lane == 0) pal[np] = vk;
-                    ip += 1;
-                    np += 1;
+            __syncthreads();
+            if (warp == 0) {
+                for (uint32_t k = 0; k < tot; k++) {
+                    const uint2 e = S.plist[k];
+                    const uint32_t vk = e.y;
+                    const bool match = lane <= 16 && lane <= ip && win == vk;
+                    const uint32_t mm = __ballot_sync(kFull, match);
+                    uint32_t op, delta = 0;
+                    if (mm) {
+                        const uint32_t f = __ffs(mm) - 1;
+                        op = f == 0 ? OP_P0 : OP_PD;
+                        delta = f == 0 ? 0u : f - 1;
+                    } else {
+                        op = OP_PA;
+                        const uint32_t up = __shfl_up_sync(kFull, win, 1);
+                        win = lane == 0 ? vk : up;
+                        if (pal && lane == 0) pal[np] = vk;
+                        ip += 1;
+                        np += 1;
+                    }
+                    if (lane == 0) S.ops[e.x] = (uint8_t)((S.ops[e.x] & 8u) | op | (delta << 4));
                 }
-                if (lane == 0) S.ops[g + k] = (uint8_t)((S.ops[g + k] & 8u) | op | (delta << 4));
-                __syncwarp();
             }
+            __syncthreads();
         }
-        if (lane == 0) sh_np = np;
+        if (tid == 0) sh_np = np;
     }
     __syncthreads();
 
@@ -379,6 +382,7 @@ __global__ void __launch_bounds__(kEncThreads)
         uint8_t *wsm = S.ops + st * half;
         const uint32_t *F = freq + 16 * st;
         const uint32_t f_reg = lane < 16 ? F[lane] : 1u;
+        const float rcp_reg = 1.0f / (float)f_reg;
         uint32_t c_reg = 0;
         for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < lane) ? F[s2] : 0u;
         const uint32_t K = lanes_for(n, G.K_max, G.S_min);
@@ -399,6 +403,7 @@ __global__ void __launch_bounds__(kEncThreads)
                     const bool act = lane < K && i < n;
                     const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
                     const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
+                    const float rf = __shfl_sync(kFull, rcp_reg, sym);
                     // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
                     const bool emit = act && x >= (f << 20);
                     const uint32_t m = __ballot_sync(kFull, emit);
@@ -407,7 +412,17 @@ __global__ void __launch_bounds__(kEncThreads)
                         x >>= 16;
                     }
                     top -= __popc(m);
-                    if (act) x = (x / f) * kM + (x % f) + c;
+                    if (act) {
+                        // x / f through a float reciprocal: here x < f * 2^20, so the estimate is within one of
+                        // the quotient; the integer remainder check makes it exact
+                        uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
+                        int32_t r = (int32_t)(x - qt * f);
+                        if (r < 0) { qt -= 1; r += (int32_t)f; }
+                        if (r < 0) { qt -= 1; r += (int32_t)f; }
+                        if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+                        if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+                        x = qt * kM + (uint32_t)r + c;
+                    }
                 }
                 __syncwarp();
                 s_hi = s_lo;
