@@ -180,6 +180,64 @@ CSGV_API int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t 
                                         uint16_t *leaf_words_dev, uint64_t leaf_capacity, uint32_t *n_int_sym_dev,
                                         uint32_t *n_leaf_sym_dev, uint64_t totals[3], void *stream);
 
+/* ---------------------------------------------------------------- serving (Sec. 4.1) */
+
+typedef struct csgv_server csgv_server;
+
+typedef struct {
+    uint64_t cache_bytes; /* decoded-brick cache in device memory (0: 8 GiB) */
+    uint32_t max_batch;   /* most requests per decode launch (0: 16384) */
+    uint32_t n_streams;   /* CUDA streams for overlapping batches (0: 3, at most 16) */
+} csgv_serve_config;
+
+typedef struct {
+    const uint32_t *labels_dev; /* (b >> lod)^3 labels, x fastest, inside the cache; NULL on error */
+    int32_t status;             /* CSGV_OK, CSGV_ERR_CORRUPT or CSGV_ERR_RANGE */
+    uint32_t brick;
+    uint8_t lod;
+    uint8_t pad[3];
+} csgv_result;
+
+typedef struct {
+    uint64_t submitted, hits, shared, misses, evictions, rebuilds, batches, decoded_labels;
+    uint64_t cache_labels_used, cache_entries;
+} csgv_serve_stats;
+
+/*
+ * Start a decode server for `vol` (which must outlive it): a cache of decoded
+ * bricks in device memory and a worker thread.  Requests are deduplicated
+ * against the cache (hits are served from it; a brick being decoded for
+ * another ticket is shared), misses are admitted while cache space can be
+ * found (free slot of the LOD's size, fresh space, least recently used
+ * unpinned entry of the same LOD, or a rebuild when nothing is pinned) and
+ * decoded in batches, one persistent launch each, round-robin over several
+ * streams, so work submitted while other batches run overlaps on the device.
+ * All requests of one ticket must fit in the cache together.
+ */
+CSGV_API int csgv_serve_create(const csgv_volume *vol, const csgv_serve_config *cfg, csgv_server **out);
+
+/* Queue n requests (host arrays: brick ids, LODs); *ticket identifies them.  Never blocks on the GPU. */
+CSGV_API int csgv_serve_submit(csgv_server *s, const uint32_t *bricks_host, const uint8_t *lods_host, uint32_t n,
+                               uint64_t *ticket);
+
+/*
+ * Wait up to timeout_us for a ticket: CSGV_OK when every request is decoded
+ * (results[n] filled, in submit order), CSGV_PENDING when timeout_us == 0 and
+ * it is not finished, CSGV_ERR_TIMEOUT when the wait ran out.  Results point
+ * into the cache and stay valid until csgv_serve_release.
+ */
+CSGV_API int csgv_serve_poll(csgv_server *s, uint64_t ticket, uint32_t timeout_us, csgv_result *results);
+
+/* Unpin a finished ticket's cache entries (they become evictable) and forget the ticket. */
+CSGV_API int csgv_serve_release(csgv_server *s, uint64_t ticket);
+
+/* Counters, and the submit-to-completion latency (ms) of finished tickets in completion order. */
+CSGV_API int csgv_serve_stats_get(csgv_server *s, csgv_serve_stats *out, double *latency_ms_host,
+                                  uint32_t max_latencies, uint32_t *n_latencies);
+
+/* Stop the worker, wait for batches in flight, free the cache. */
+CSGV_API void csgv_serve_destroy(csgv_server *s);
+
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
 

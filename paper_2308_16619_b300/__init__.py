@@ -18,7 +18,8 @@ CSGV_ERR_CORRUPT, CSGV_ERR_TIMEOUT, CSGV_ERR_CUDA, CSGV_ERR_RANGE = 4, 5, 6, 7
 
 SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "csgv_decode_bricks",
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
-           "csgv_volume_destroy", "csgv_encode_bricks_noalloc")
+           "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
+           "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy")
 
 
 class CsgvError(RuntimeError):
@@ -41,6 +42,20 @@ class VolumeInfo(C.Structure):
                 ("K_max", C.c_uint32), ("S_min", C.c_uint32), ("max_palette", C.c_uint32),
                 ("palette_labels", C.c_uint64), ("int_words", C.c_uint64), ("leaf_words", C.c_uint64),
                 ("compressed_bytes", C.c_uint64), ("freq", C.c_uint32 * 32)]
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("cache_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("n_streams", C.c_uint32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("labels_dev", C.c_void_p), ("status", C.c_int32), ("brick", C.c_uint32), ("lod", C.c_uint8),
+                ("pad", C.c_uint8 * 3)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("submitted", "hits", "shared", "misses", "evictions", "rebuilds", "batches",
+                                          "decoded_labels", "cache_labels_used", "cache_entries")]
 
 
 _lib = None
@@ -66,6 +81,13 @@ def lib():
         L.csgv_volume_destroy.restype = None
         L.csgv_encode_bricks_noalloc.argtypes = [vp, vp, u32, C.POINTER(FreqTable), C.POINTER(Config),
                                                  vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]
+        L.csgv_serve_create.argtypes = [vp, C.POINTER(ServeConfig), C.POINTER(vp)]
+        L.csgv_serve_submit.argtypes = [vp, vp, vp, u32, C.POINTER(C.c_uint64)]
+        L.csgv_serve_poll.argtypes = [vp, u64, u32, C.POINTER(Result)]
+        L.csgv_serve_release.argtypes = [vp, u64]
+        L.csgv_serve_stats_get.argtypes = [vp, C.POINTER(ServeStats), vp, u32, C.POINTER(C.c_uint32)]
+        L.csgv_serve_destroy.argtypes = [vp]
+        L.csgv_serve_destroy.restype = None
         _lib = L
     return _lib
 
@@ -209,3 +231,70 @@ def request_layout(b, lods):
     if len(lods):
         off[1:] = np.cumsum(sizes)[:-1]
     return off, int(sizes.sum())
+
+
+class DeviceView:
+    """Zero-copy view of n uint32 labels at a device address (for torch.as_tensor)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<u4", "data": (int(ptr), False),
+                                         "version": 3}
+
+
+class Server:
+    """csgv_serve_*: decode server with a device cache of decoded bricks (see include/csgv.h)."""
+
+    def __init__(self, volume, cache_bytes=0, max_batch=0, n_streams=0):
+        self.volume = volume  # keep the volume alive
+        h = C.c_void_p()
+        cfg = ServeConfig(cache_bytes, max_batch, n_streams)
+        _check(lib().csgv_serve_create(volume.handle, C.byref(cfg), C.byref(h)))
+        self._h = h
+        self.N = volume.info().N
+
+    def submit(self, bricks, lods):
+        bricks = np.ascontiguousarray(bricks, np.uint32)
+        lods = np.ascontiguousarray(lods, np.uint8)
+        t = C.c_uint64()
+        _check(lib().csgv_serve_submit(self._h, bricks.ctypes.data_as(C.c_void_p), lods.ctypes.data_as(C.c_void_p),
+                                       len(bricks), C.byref(t)))
+        return t.value, len(bricks)
+
+    def poll(self, ticket, timeout_us=1_000_000):
+        """Returns (rc, results): rc CSGV_OK / CSGV_PENDING / CSGV_ERR_TIMEOUT."""
+        tid, n = ticket
+        res = (Result * max(n, 1))()
+        rc = lib().csgv_serve_poll(self._h, tid, timeout_us, res)
+        return rc, (list(res[:n]) if rc == CSGV_OK else None)
+
+    def release(self, ticket):
+        _check(lib().csgv_serve_release(self._h, ticket[0]))
+
+    def stats(self, with_latencies=False):
+        st = ServeStats()
+        cnt = C.c_uint32()
+        _check(lib().csgv_serve_stats_get(self._h, C.byref(st), None, 0, C.byref(cnt)))
+        lat = None
+        if with_latencies:
+            lat = np.zeros(max(cnt.value, 1), np.float64)
+            _check(lib().csgv_serve_stats_get(self._h, C.byref(st), lat.ctypes.data_as(C.c_void_p), len(lat),
+                                              C.byref(cnt)))
+            lat = lat[:cnt.value]
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}, lat
+
+    def labels(self, result, b):
+        """torch view of a result's labels (valid until the ticket is released)."""
+        import torch
+        n = (b >> result.lod) ** 3
+        return torch.as_tensor(DeviceView(result.labels_dev, n), device="cuda")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().csgv_serve_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

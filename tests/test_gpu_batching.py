@@ -1,0 +1,80 @@
+"""Batched decoding at scale: the 1024^3 packed-ellipsoid volume, 60 000 requests over all 32 768
+bricks of 32^3 at random LOD 0..5 (uneven stream lengths, duplicates), decoded in one persistent launch.
+
+Checked against the oracle on a seeded sample of requests (the oracle's pyramid of the same brick),
+plus the invariant that every request decodes alone to the same bytes as inside the batch.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def cells_volume():
+    if "vol" not in _cache:
+        _cache["vol"] = synth.make("cells1024")
+    return _cache["vol"]
+
+
+def batch_requests(n_bricks, n=60000, seed=3):
+    rng = np.random.default_rng(seed)
+    ids = rng.integers(0, n_bricks, size=n).astype(np.uint32)
+    lods = rng.integers(0, 6, size=n).astype(np.uint8)
+    return ids, lods
+
+
+def brick_of(vol, b, bid):
+    Z, Y, X = vol.shape
+    nbx, nby = X // b, Y // b
+    bx, by, bz = bid % nbx, (bid // nbx) % nby, bid // (nbx * nby)
+    return np.ascontiguousarray(vol[bz * b:(bz + 1) * b, by * b:(by + 1) * b, bx * b:(bx + 1) * b])
+
+
+def test_cells1024_mixed_lod_batch():
+    import torch
+    import paper_2308_16619_b300 as csgv
+    vol = cells_volume()
+    b = 32
+    d = torch.from_numpy(vol.view(np.int32)).cuda()
+    table = csgv.csgv_build_freq_table(d, b, 512)
+    v = csgv.csgv_encode_bricks(d, b, table)
+    del d
+    n_bricks = v.info().n_bricks
+    assert n_bricks == 32768
+    ids, lods = batch_requests(n_bricks)
+    offs, total = csgv.request_layout(b, lods)
+    assert abs(total * 4 / 1e9 - 1.5) < 0.05  # about 1.5 GB of labels, mean 6241.5 voxels per request
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    status = torch.full((len(ids),), -1, dtype=torch.int32, device="cuda")
+    ids_d = torch.from_numpy(ids.view(np.int32)).cuda()
+    lods_d = torch.from_numpy(lods).cuda()
+    offs_d = torch.from_numpy(offs).cuda()
+    csgv.csgv_decode_bricks(v, ids_d, lods_d, out, offs_d, status)
+    torch.cuda.synchronize()
+    assert bool((status == 0).all())
+    rng = np.random.default_rng(11)
+    sample = rng.choice(len(ids), size=400, replace=False)
+    out_h = out.cpu().numpy().view(np.uint32)
+    for r in sample:
+        t = int(lods[r])
+        B = b >> t
+        got = out_h[offs[r]:offs[r] + B ** 3].reshape(B, B, B)
+        want = O.pyramid(brick_of(vol, b, int(ids[r])))[t][0]
+        assert np.array_equal(got, want), (r, int(ids[r]), t)
+    # each request alone gives the same bytes as inside the batch
+    for r in sample[:40]:
+        t = int(lods[r])
+        B3 = (b >> t) ** 3
+        o1 = torch.empty(B3, dtype=torch.int32, device="cuda")
+        s1 = torch.empty(1, dtype=torch.int32, device="cuda")
+        z = torch.zeros(1, dtype=torch.int64, device="cuda")
+        csgv.csgv_decode_bricks(v, ids_d[r:r + 1], lods_d[r:r + 1], o1, z, s1)
+        torch.cuda.synchronize()
+        assert int(s1.item()) == 0
+        assert np.array_equal(o1.cpu().numpy().view(np.uint32), out_h[offs[r]:offs[r] + B3])
+    v.close()
