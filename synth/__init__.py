@@ -14,8 +14,30 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "gen.c")
 LIB = os.path.join(HERE, "libsynth.so")
+GPU_SRC = os.path.join(HERE, "gen_gpu.cu")
+GPU_LIB = os.path.join(HERE, "libsynth_gpu.so")
 
 _lib = None
+_gpu_lib = None
+
+
+def build_gpu(force=False):
+    if not force and os.path.exists(GPU_LIB) and os.path.getmtime(GPU_LIB) >= os.path.getmtime(GPU_SRC):
+        return GPU_LIB
+    tmp = GPU_LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                           "-shared", "-Xcompiler", "-fPIC", GPU_SRC, "-o", tmp])
+    os.replace(tmp, GPU_LIB)
+    return GPU_LIB
+
+
+def gpu_lib():
+    global _gpu_lib
+    if _gpu_lib is None:
+        _gpu_lib = C.CDLL(build_gpu())
+        _gpu_lib.synth_worley_dev.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
+                                              C.c_uint64, C.c_void_p]
+    return _gpu_lib
 
 
 def build(force=False):
@@ -38,6 +60,8 @@ def lib():
         _lib.synth_ellipsoids.restype = C.c_uint64
         _lib.synth_ellipsoids.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
                                           C.c_double, C.c_double, C.c_double, C.c_uint64]
+        _lib.synth_worley.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint64,
+                                      C.c_int]
         _lib.synth_label.restype = C.c_uint32
         _lib.synth_label.argtypes = [C.c_uint64, C.c_uint64]
     return _lib
@@ -64,6 +88,93 @@ def ellipsoids(shape_zyx, n_target, seed, len_lo=12.0, len_hi=40.0, short_lo=4.0
     return vol, int(placed)
 
 
+def worley(shape_zyx, cell, seed, n_threads=None):
+    """Worley F1 cells on a jittered grid (host): label = hash of the nearest of the 27 neighbouring features."""
+    Z, Y, X = shape_zyx
+    vol = np.empty((Z, Y, X), np.uint32)
+    assert lib().synth_worley(vol.ctypes.data_as(C.c_void_p), X, Y, Z, cell, seed, _threads(n_threads)) == 0
+    return vol
+
+
+def worley_device(shape_zyx, cell, seed):
+    """Same volume made on the current CUDA device; returns an int32-typed torch tensor of the uint32 labels."""
+    import torch
+    Z, Y, X = shape_zyx
+    vol = torch.empty((Z, Y, X), dtype=torch.int32, device="cuda")
+    rc = gpu_lib().synth_worley_dev(C.c_void_p(vol.data_ptr()), X, Y, Z, cell, seed,
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    return vol
+
+
+def camera_trace(dims_xyz, b, n_frames, seed, width=1920, height=1080, fov_deg=45.0, device=None,
+                 r_lo=1.05, r_hi=1.9):
+    """Brick requests of a fly-around camera, one (bricks, lods) pair of numpy arrays per frame.
+
+    The camera follows a closed Catmull-Rom spline through 8 seeded points on a shell around the
+    volume (radius r_lo..r_hi times the half diagonal) and looks at the centre.  Each of the
+    width x height rays stops at the first brick it enters (labels are dense, so the ray-march's first
+    hit is where the ray enters the volume); that brick is requested at LOD
+    clamp(floor(log2(d / f_px)), 0, log2 b), d the distance to the brick centre and f_px the focal
+    length in pixels, so that one voxel covers about one pixel.
+    """
+    import torch
+    dev = torch.device(device or ("cuda" if torch.cuda.is_available() else "cpu"))
+    X, Y, Z = dims_xyz
+    N = b.bit_length() - 1
+    grid = torch.tensor([X // b, Y // b, Z // b], device=dev)
+    size = torch.tensor([X, Y, Z], dtype=torch.float32, device=dev)
+    centre = size / 2
+    half_diag = float(torch.linalg.norm(size / 2))
+    rng = np.random.default_rng(seed)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    radii = rng.uniform(r_lo, r_hi, size=8) * half_diag
+    ctrl = torch.tensor(dirs * radii[:, None], dtype=torch.float32, device=dev) + centre
+    f_px = (height / 2) / np.tan(np.radians(fov_deg) / 2)
+    ys, xs = torch.meshgrid(torch.arange(height, device=dev, dtype=torch.float32) + 0.5,
+                            torch.arange(width, device=dev, dtype=torch.float32) + 0.5, indexing="ij")
+    px = ((xs - width / 2) / f_px).reshape(-1)
+    py = ((ys - height / 2) / f_px).reshape(-1)
+    frames = []
+    for f in range(n_frames):
+        u = 8.0 * f / n_frames
+        k = int(u)
+        t = u - k
+        p0, p1, p2, p3 = (ctrl[(k + d) % 8] for d in (-1, 0, 1, 2))
+        # Catmull-Rom (uniform) point
+        cam = 0.5 * ((2 * p1) + (-p0 + p2) * t + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t * t +
+                     (-p0 + 3 * p1 - 3 * p2 + p3) * t * t * t)
+        fwd = centre - cam
+        fwd = fwd / torch.linalg.norm(fwd)
+        up = torch.tensor([0.0, 0.0, 1.0], device=dev)
+        right = torch.linalg.cross(fwd, up)
+        right = right / torch.linalg.norm(right)
+        up = torch.linalg.cross(right, fwd)
+        d = fwd[None, :] + px[:, None] * right[None, :] - py[:, None] * up[None, :]
+        d = d / torch.linalg.norm(d, dim=1, keepdim=True)
+        # slab test against the volume box
+        inv = 1.0 / torch.where(d.abs() < 1e-12, torch.full_like(d, 1e-12), d)
+        t0 = (0 - cam) * inv
+        t1 = (size - cam) * inv
+        tn = torch.minimum(t0, t1).amax(dim=1)
+        tf = torch.maximum(t0, t1).amin(dim=1)
+        hit = (tf >= torch.clamp(tn, min=0)) & (tf > 0)
+        tin = torch.clamp(tn, min=0)[hit] + 1e-3
+        pin = cam + d[hit] * tin[:, None]
+        bidx = torch.minimum(torch.clamp((pin / b).floor().long(), min=0), grid - 1)
+        bid = bidx[:, 0] + grid[0] * (bidx[:, 1] + grid[1] * bidx[:, 2])
+        bid = torch.unique(bid)
+        bz = bid // (grid[0] * grid[1])
+        by = (bid // grid[0]) % grid[1]
+        bx = bid % grid[0]
+        bc = (torch.stack([bx, by, bz], dim=1).float() + 0.5) * b
+        dist = torch.linalg.norm(bc - cam, dim=1)
+        lod = torch.clamp(torch.floor(torch.log2(torch.clamp(dist / f_px, min=1e-6))), 0, N).to(torch.uint8)
+        frames.append((bid.to(torch.int64).cpu().numpy().astype(np.uint32), lod.cpu().numpy()))
+    return frames
+
+
 # Workload recipes.  "small" is the 128^3 plain-method case; "voronoi512" the
 # 512^3 warped Voronoi with 30 % background; "cells1024" the 1024^3 packed
 # ellipsoid cells used for mixed-LOD batching.
@@ -72,6 +183,8 @@ WORKLOADS = {
     "voronoi512": dict(shape=(512, 512, 512),
                        make=lambda: voronoi((512, 512, 512), 20000, seed=2, warp_amp=4, bg_permille=300)),
     "cells1024": dict(shape=(1024, 1024, 1024), make=lambda: ellipsoids((1024, 1024, 1024), 200000, seed=3)[0]),
+    # 2048 x 2048 x 1024 Worley cells on a 24-voxel jittered grid (made on the device: 16 GB)
+    "worley2048": dict(shape=(1024, 2048, 2048), make=lambda: worley_device((1024, 2048, 2048), 24, seed=4)),
 }
 
 

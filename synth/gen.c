@@ -322,3 +322,57 @@ uint64_t synth_ellipsoids(uint32_t *vol, uint64_t X, uint64_t Y, uint64_t Z, uin
     free(occ);
     return placed;
 }
+
+/* ------------------------------------------------------------------ */
+/* Worley F1 cells on a jittered grid                                  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Feature point of grid cell (i,j,k), cell side C voxels: the cell origin
+ * plus a hashed jitter in [0, C) per axis, in 1/256 voxel.  Shared formula
+ * with gen_gpu.cu (same integers on both sides).
+ */
+static void worley_feature(uint64_t seed, int64_t i, int64_t j, int64_t k, int64_t C, int64_t f[3]) {
+    uint64_t key = ((uint64_t)(i + 1) << 42) ^ ((uint64_t)(j + 1) << 21) ^ (uint64_t)(k + 1);
+    uint64_t h = hash2(seed ^ 0x3A0E1Eull, key);
+    f[0] = i * C * FP + (int64_t)((h & 0xFFFFFull) % (uint64_t)(C * FP));
+    f[1] = j * C * FP + (int64_t)(((h >> 20) & 0xFFFFFull) % (uint64_t)(C * FP));
+    f[2] = k * C * FP + (int64_t)(((h >> 40) & 0xFFFFFull) % (uint64_t)(C * FP));
+}
+
+typedef struct {
+    uint32_t *vol;
+    uint64_t X, Y, Z, seed;
+    int64_t C;
+} worley_ctx;
+
+static void worley_slab(void *ctx, uint64_t z0, uint64_t z1) {
+    const worley_ctx *W = (const worley_ctx *)ctx;
+    for (uint64_t z = z0; z < z1; z++)
+        for (uint64_t y = 0; y < W->Y; y++)
+            for (uint64_t x = 0; x < W->X; x++) {
+                int64_t p[3] = {(int64_t)x * FP + FP / 2, (int64_t)y * FP + FP / 2, (int64_t)z * FP + FP / 2};
+                int64_t ci = (int64_t)x / W->C, cj = (int64_t)y / W->C, ck = (int64_t)z / W->C;
+                int64_t best = INT64_MAX, bi = 0, bj = 0, bk = 0;
+                /* the 27 neighbouring cells; ties go to the lexicographically smallest (i, j, k) */
+                for (int64_t i = ci - 1; i <= ci + 1; i++)
+                    for (int64_t j = cj - 1; j <= cj + 1; j++)
+                        for (int64_t k = ck - 1; k <= ck + 1; k++) {
+                            int64_t f[3];
+                            worley_feature(W->seed, i, j, k, W->C, f);
+                            int64_t d0 = f[0] - p[0], d1 = f[1] - p[1], d2 = f[2] - p[2];
+                            int64_t d = d0 * d0 + d1 * d1 + d2 * d2;
+                            if (d < best) { best = d; bi = i; bj = j; bk = k; }
+                        }
+                uint64_t cell = ((uint64_t)(bi + 1) << 42) ^ ((uint64_t)(bj + 1) << 21) ^ (uint64_t)(bk + 1);
+                W->vol[x + W->X * (y + W->Y * z)] = synth_label(W->seed, cell);
+            }
+}
+
+/* Worley F1 labels: nearest feature point among the 27 cells around the voxel's cell. */
+int synth_worley(uint32_t *vol, uint64_t X, uint64_t Y, uint64_t Z, uint32_t cell, uint64_t seed, int n_threads) {
+    if (!cell || !X || !Y || !Z) return 1;
+    worley_ctx W = {vol, X, Y, Z, seed, (int64_t)cell};
+    run_slabs(worley_slab, &W, Z, n_threads);
+    return 0;
+}
