@@ -95,6 +95,14 @@ CSGV_API int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[
                           csgv_freq_table *out, void *stream);
 
 /*
+ * Tables from nibble counts (Sec. 3.3; normalisation as in csgv_build_freq_table): counts[0..15]
+ * interior, counts[16..31] leaf.  For sharded volumes: every rank counts its bricks with
+ * csgv_build_freq_table, the counts are summed across ranks, and this turns the sums into the shared
+ * tables.  Host only; fills out->freq and copies the counts to out->counts.
+ */
+CSGV_API int csgv_freq_table_from_counts(const uint64_t counts[32], csgv_freq_table *out);
+
+/*
  * Brick encoder (Alg. 2, Sec. 3.2-3.4) for every brick of the volume, then
  * entropy coding and packing.  The library allocates the compressed arrays;
  * the returned volume owns them until csgv_volume_destroy.  cfg may be NULL

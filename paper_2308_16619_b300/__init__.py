@@ -19,7 +19,8 @@ CSGV_ERR_CORRUPT, CSGV_ERR_TIMEOUT, CSGV_ERR_CUDA, CSGV_ERR_RANGE = 4, 5, 6, 7
 SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "csgv_decode_bricks",
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
-           "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy")
+           "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
+           "csgv_freq_table_from_counts")
 
 
 class CsgvError(RuntimeError):
@@ -88,6 +89,7 @@ def lib():
         L.csgv_serve_stats_get.argtypes = [vp, C.POINTER(ServeStats), vp, u32, C.POINTER(C.c_uint32)]
         L.csgv_serve_destroy.argtypes = [vp]
         L.csgv_serve_destroy.restype = None
+        L.csgv_freq_table_from_counts.argtypes = [vp, C.POINTER(FreqTable)]
         _lib = L
     return _lib
 
@@ -161,6 +163,15 @@ def csgv_build_freq_table(vol, b, sample_stride=1, stream=None):
     assert vol.is_cuda and vol.element_size() == 4 and vol.is_contiguous()
     t = FreqTable()
     _check(lib().csgv_build_freq_table(_ptr(vol), _dims3(vol), b, sample_stride, C.byref(t), _stream(stream)))
+    return t
+
+
+def csgv_freq_table_from_counts(counts):
+    """Tables from 32 nibble counts (interior then leaf), e.g. counts summed over the ranks of a sharded volume."""
+    counts = np.ascontiguousarray(counts, np.uint64)
+    assert counts.shape == (32,)
+    t = FreqTable()
+    _check(lib().csgv_freq_table_from_counts(counts.ctypes.data_as(C.c_void_p), C.byref(t)))
     return t
 
 

@@ -185,6 +185,39 @@ extern "C" {
 
 const char *csgv_last_error(void) { return g_err.c_str(); }
 
+int csgv_freq_table_from_counts(const uint64_t counts[32], csgv_freq_table *out) {
+    if (!counts || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    uint64_t c[32];
+    memcpy(c, counts, sizeof c);  // counts may alias out->counts
+    for (int t = 0; t < 2; t++) {
+        const uint64_t *ct = c + 16 * t;
+        uint32_t *f = out->freq + 16 * t;
+        uint64_t total = 0;
+        for (int s = 0; s < 16; s++) total += ct[s];
+        if (total == 0) {
+            for (int s = 0; s < 16; s++) f[s] = csgv::kM / 16;
+            continue;
+        }
+        // f = 1 + floor(c * (M - 16) / total); the r < 16 leftover units go +1 to the largest counts
+        uint32_t sum = 0;
+        for (int s = 0; s < 16; s++) {
+            const unsigned __int128 q = (unsigned __int128)ct[s] * (csgv::kM - 16) / total;
+            f[s] = 1u + (uint32_t)q;
+            sum += f[s];
+        }
+        bool used[16] = {false};
+        for (uint32_t k = 0; k < csgv::kM - sum; k++) {
+            int best = -1;
+            for (int s = 0; s < 16; s++)
+                if (!used[s] && (best < 0 || ct[s] > ct[best])) best = s;
+            used[best] = true;
+            f[best] += 1;
+        }
+    }
+    memcpy(out->counts, c, sizeof c);
+    return CSGV_OK;
+}
+
 int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, uint32_t sample_stride,
                           csgv_freq_table *out, void *stream) {
     uint32_t N;
@@ -204,27 +237,22 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
     const uint64_t n_sampled = (n + sample_stride - 1) / sample_stride;
     csgv::EncGeom G = csgv::make_geom(N, 32, 256);
     unsigned long long *cnt = nullptr;
-    uint32_t *freq = nullptr;
     CK(cudaMalloc(&cnt, 32 * 8));
-    CK(cudaMalloc(&freq, 32 * 4));
     CK(cudaMemsetAsync(cnt, 0, 32 * 8, st));
     csgv::EncScratch SC{};
     for (uint64_t first = 0; first < n_sampled; first += 65535) {
         const uint32_t m = (uint32_t)std::min<uint64_t>(65535, n_sampled - first);
         cudaError_t e = csgv::launch_encode(EV, G, first * sample_stride, sample_stride, m, nullptr, SC, cnt, st);
         if (e != cudaSuccess) {
-            cudaFree(cnt); cudaFree(freq);
+            cudaFree(cnt);
             return cuda_fail(e, "encode (count mode)");
         }
     }
-    cudaError_t e = csgv::launch_normalize(cnt, freq, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out->freq, freq, 32 * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out->counts, cnt, 32 * 8, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(out->counts, cnt, 32 * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(cnt);
-    cudaFree(freq);
     if (e != cudaSuccess) return cuda_fail(e, "frequency prepass");
-    return CSGV_OK;
+    return csgv_freq_table_from_counts(out->counts, out);
 }
 
 int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,

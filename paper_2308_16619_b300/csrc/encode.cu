@@ -524,38 +524,6 @@ __global__ void __launch_bounds__(256) compact_kernel(EncGeom G, EncScratch SC, 
     }
 }
 
-// Normalise 2 x 16 nibble counts to 4096 each (reading R11): f = 1 + floor(c * 4080 / total), the
-// remaining units +1 to the largest counts (ties: lower symbol); all-zero counts give 256 each.
-__global__ void normalize_kernel(const unsigned long long *count, uint32_t *freq) {
-    const uint32_t t = threadIdx.x;
-    if (t >= 2) return;
-    const unsigned long long *c = count + 16 * t;
-    uint32_t *f = freq + 16 * t;
-    unsigned long long total = 0;
-    for (int s = 0; s < 16; s++) total += c[s];
-    if (total == 0) {
-        for (int s = 0; s < 16; s++) f[s] = kM / 16;
-        return;
-    }
-    uint32_t sum = 0;
-    for (int s = 0; s < 16; s++) {
-        f[s] = 1u + (uint32_t)((c[s] * (unsigned long long)(kM - 16)) / total);
-        sum += f[s];
-    }
-    uint32_t r = kM - sum;
-    bool used[16];
-    for (int s = 0; s < 16; s++) used[s] = false;
-    for (uint32_t k = 0; k < r; k++) {
-        int best = -1;
-        for (int s = 0; s < 16; s++) {
-            if (used[s]) continue;
-            if (best < 0 || c[s] > c[best]) best = s;
-        }
-        used[best] = true;
-        f[best] += 1;
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- host helpers
@@ -611,9 +579,5 @@ cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t firs
     return cudaGetLastError();
 }
 
-cudaError_t launch_normalize(const unsigned long long *count, uint32_t *freq, cudaStream_t st) {
-    normalize_kernel<<<1, 32, 0, st>>>(count, freq);
-    return cudaGetLastError();
-}
 
 }  // namespace csgv

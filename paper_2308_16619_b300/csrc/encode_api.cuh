@@ -41,6 +41,5 @@ cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t firs
                            const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal, uint16_t *int_words,
                            uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, uint32_t *max_pal,
                            cudaStream_t st);
-cudaError_t launch_normalize(const unsigned long long *count, uint32_t *freq, cudaStream_t st);
 
 }  // namespace csgv

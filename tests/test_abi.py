@@ -42,3 +42,21 @@ def test_binding_loads_and_reports_argument_errors_without_gpu():
 def test_sm103a_cubin_only():
     # the library carries sm_103a machine code (checked through the build flags, not by reading the binary)
     assert "arch=compute_103a,code=sm_103a" in " ".join(csgv_build.FLAGS)
+
+
+def test_table_from_counts_matches_oracle_normalisation():
+    # host-only entry point; the oracle's normalisation is an independent implementation of the same rule
+    import numpy as np
+    import oracle as O
+    rng = np.random.default_rng(21)
+    for trial in range(300):
+        counts = rng.integers(0, 10 ** int(rng.integers(1, 15)), size=32).astype(np.uint64)
+        counts[rng.random(32) < 0.3] = 0
+        if trial == 0:
+            counts[:] = 0
+        if trial == 1:
+            counts[:] = np.uint64(2 ** 58)  # totals stay below 2^64
+        t = csgv.csgv_freq_table_from_counts(counts)
+        want = np.concatenate([O.normalize(counts[:16]), O.normalize(counts[16:])])
+        assert list(t.freq) == want.tolist()
+        assert list(t.counts) == counts.tolist()
