@@ -14,12 +14,17 @@
 
 // kernels' launchers (decode.cu, encode.cu)
 namespace csgv {
-uint32_t decode_smem_bytes(bool wide, uint32_t warps);
-cudaError_t launch_decode_persistent(const VolDev &V, bool wide, const uint32_t *ids, const uint8_t *lods, uint32_t n,
-                                     uint32_t *out, const uint64_t *out_off, int32_t *status, uint32_t *work,
-                                     uint32_t warps, uint32_t blocks, cudaStream_t st);
-cudaError_t launch_decode_single(const VolDev &V, bool wide, const uint32_t *ids, const uint8_t *lods, uint32_t r,
-                                 uint32_t *out, const uint64_t *out_off, int32_t *status, cudaStream_t st);
+struct RecJob {
+    const uint32_t *ids;
+    const uint8_t *lods;
+    uint32_t n;
+    uint8_t *recs;
+    uint64_t stride, leaf_at, t8_at, t8_leaf_at;
+    uint32_t *info;
+    uint32_t *counter;
+};
+cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uint32_t *out, const uint64_t *out_off,
+                                int32_t *status, uint32_t rec_blocks, cudaStream_t st);
 }  // namespace csgv
 
 #include "encode_api.cuh"
@@ -35,13 +40,11 @@ struct csgv_volume {
     uint16_t *int_words, *leaf_words;
     uint32_t *n_int_sym, *n_leaf_sym;
     uint32_t *lut;
-    uint32_t *work;  // kWorkSlots work counters for persistent decodes
-    std::atomic<uint32_t> next_slot;
+    uint32_t max_int_sym, max_leaf_sym;  // largest per-brick symbol counts: size the decode workspace
 };
 
 namespace {
 
-constexpr uint32_t kWorkSlots = 256;
 // word arrays carry this many spare 16-bit words at the end: the decoder stages stream words with
 // 16-byte loads aligned down from the stream start, which may touch up to 15 bytes past the last word
 constexpr uint64_t kWordPad = 16;
@@ -102,7 +105,7 @@ void vol_free_arrays(csgv_volume *v) {
     cudaFree(v->pal_off); cudaFree(v->int_off); cudaFree(v->leaf_off);
     cudaFree(v->pal); cudaFree(v->int_words); cudaFree(v->leaf_words);
     cudaFree(v->n_int_sym); cudaFree(v->n_leaf_sym);
-    cudaFree(v->lut); cudaFree(v->work);
+    cudaFree(v->lut);
 }
 
 int vol_finish(csgv_volume *v) {
@@ -110,9 +113,6 @@ int vol_finish(csgv_volume *v) {
     build_lut(v->freq, lut);
     CK(cudaMalloc(&v->lut, lut.size() * 4));
     CK(cudaMemcpy(v->lut, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&v->work, kWorkSlots * 4));
-    CK(cudaMemset(v->work, 0, kWorkSlots * 4));
-    v->next_slot = 0;
     return CSGV_OK;
 }
 
@@ -125,6 +125,33 @@ csgv::VolDev dev_view(const csgv_volume *v) {
     V.n_bricks = v->n_bricks;
     V.N = v->N; V.K_max = v->K_max; V.S_min = v->S_min;
     return V;
+}
+
+// Decode workspace: op records of a slice of requests, taken from a per-device stream-ordered pool that
+// keeps up to kDecodePoolKeep bytes between calls (concurrent calls on different streams get their own).
+constexpr uint64_t kDecodeWorkspace = 64ull << 20;
+constexpr uint64_t kDecodePoolKeep = 256ull << 20;
+constexpr int kPoolDevices = 64;
+cudaMemPool_t g_pools[kPoolDevices];
+std::mutex g_pool_mu;
+
+int decode_pool(int dev, cudaMemPool_t *pool) {
+    if (dev < 0 || dev >= kPoolDevices) return fail(CSGV_ERR_INVALID_ARG, "device index %d too large", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps p;
+        memset(&p, 0, sizeof p);
+        p.allocType = cudaMemAllocationTypePinned;
+        p.location.type = cudaMemLocationTypeDevice;
+        p.location.id = dev;
+        cudaMemPool_t mp;
+        CK(cudaMemPoolCreate(&mp, &p));
+        uint64_t keep = kDecodePoolKeep;
+        CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = mp;
+    }
+    *pool = g_pools[dev];
+    return CSGV_OK;
 }
 
 int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
@@ -320,7 +347,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     };
     const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
     const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
-    const size_t o_sz = take(C * 8 * 4), o_f = take(32 * 4), o_t = take(3 * 8), o_m = take(4);
+    const size_t o_sz = take(C * 8 * 4), o_f = take(32 * 4), o_t = take(3 * 8), o_m = take(3 * 4);
     void *arena = nullptr;
     CKE(arena_get(dev, off, &arena));
     unsigned char *A = (unsigned char *)arena;
@@ -340,7 +367,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     CKE(cudaMalloc(&v->n_leaf_sym, n * 4));
     CKE(cudaMemcpyAsync(freq_d, table->freq, 32 * 4, cudaMemcpyHostToDevice, st));
     CKE(cudaMemsetAsync(tot_d, 0, 3 * 8, st));
-    CKE(cudaMemsetAsync(maxpal_d, 0, 4, st));
+    CKE(cudaMemsetAsync(maxpal_d, 0, 3 * 4, st));
     uint64_t cap_p = 0, cap_i = 0, cap_l = 0;
     uint64_t tot[3] = {0, 0, 0};
     for (uint64_t first = 0; first < n; first += C) {
@@ -360,8 +387,12 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
         CKE(csgv::launch_compact(G, SC, first, m, v->pal_off, v->int_off, v->leaf_off, v->pal, v->int_words,
                                  v->leaf_words, v->n_int_sym, v->n_leaf_sym, maxpal_d, st));
     }
-    CKE(cudaMemcpyAsync(&v->max_palette, maxpal_d, 4, cudaMemcpyDeviceToHost, st));
+    uint32_t maxes[3] = {0, 0, 0};
+    CKE(cudaMemcpyAsync(maxes, maxpal_d, 3 * 4, cudaMemcpyDeviceToHost, st));
     CKE(cudaStreamSynchronize(st));
+    v->max_palette = maxes[0];
+    v->max_int_sym = maxes[1];
+    v->max_leaf_sym = maxes[2];
     free_tmp();
 #undef CKE
     v->n_pal = tot[0];
@@ -381,26 +412,55 @@ static int decode_args(const csgv_volume *vol, const uint32_t *ids, const uint8_
     return CSGV_OK;
 }
 
+// Decode requests [r0, r0 + n) in slices whose op records fit the workspace (stream-ordered allocation).
+static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t *lods, uint32_t n, uint32_t *out,
+                        const uint64_t *off, int32_t *status, bool one_per_launch, cudaStream_t st) {
+    int dev = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaMemPool_t pool;
+    int rc = decode_pool(dev, &pool);
+    if (rc) return rc;
+    const bool wide = v->max_palette > 253;
+    // a request's workspace: interior records at 0, leaf records at leaf_at (one byte per op record, at
+    // most one per symbol), then the P_a counts before every 8th record of each stream (uint16)
+    auto a16 = [](uint64_t x) { return (x + 15) & ~15ull; };
+    const uint64_t leaf_at = ((uint64_t)v->max_int_sym + 7) & ~7ull;
+    const uint64_t t8_at = a16(leaf_at + (((uint64_t)v->max_leaf_sym + 7) & ~7ull));
+    const uint64_t t8_leaf_at = t8_at + a16((leaf_at / 8 + 1) * 2);
+    const uint64_t stride = t8_leaf_at + a16(((t8_at - leaf_at) / 8 + 1) * 2);
+    uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, kDecodeWorkspace / stride));
+    const size_t info_bytes = ((size_t)S * 8 + 255) & ~(size_t)255;
+    const size_t bytes = 256 + info_bytes + (size_t)S * stride;
+    void *ws = nullptr;
+    CK(cudaMallocFromPoolAsync(&ws, bytes, pool, st));
+    csgv::RecJob J;
+    J.counter = (uint32_t *)ws;
+    J.info = (uint32_t *)((uint8_t *)ws + 256);
+    J.recs = (uint8_t *)ws + 256 + info_bytes;
+    J.stride = stride;
+    J.leaf_at = leaf_at;
+    J.t8_at = t8_at;
+    J.t8_leaf_at = t8_leaf_at;
+    cudaError_t e = cudaSuccess;
+    for (uint64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += S) {
+        J.n = (uint32_t)std::min<uint64_t>(S, n - r0);
+        J.ids = ids + r0;
+        J.lods = lods + r0;
+        e = csgv::launch_decode_slice(dev_view(v), wide, J, out, off + r0, status + r0, 3 * (uint32_t)sms, st);
+    }
+    cudaError_t ef = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+    return CSGV_OK;
+}
+
 int csgv_decode_bricks(const csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
                        uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream) {
     int rc = decode_args(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev);
     if (rc || n == 0) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    csgv_volume *v = const_cast<csgv_volume *>(vol);
-    const bool wide = v->max_palette > 253;
-    const uint32_t warps = wide ? 8 : 15;  // as many warps as the 227 KB of shared memory per CTA holds
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint32_t slot = v->next_slot.fetch_add(1) % kWorkSlots;
-    uint32_t *work = v->work + slot;
-    CK(cudaMemsetAsync(work, 0, 4, st));
-    uint32_t blocks = (uint32_t)sms;
-    const uint32_t need = (n + warps - 1) / warps;
-    if (need < blocks) blocks = need;
-    CK(csgv::launch_decode_persistent(dev_view(v), wide, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev,
-                                      status_dev, work, warps, blocks, st));
-    return CSGV_OK;
+    return decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, false,
+                        (cudaStream_t)stream);
 }
 
 int csgv_decode_bricks_plain(const csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev,
@@ -408,12 +468,8 @@ int csgv_decode_bricks_plain(const csgv_volume *vol, const uint32_t *brick_ids_d
                              void *stream) {
     int rc = decode_args(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev);
     if (rc || n == 0) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool wide = vol->max_palette > 253;
-    const csgv::VolDev V = dev_view(vol);
-    for (uint32_t r = 0; r < n; r++)
-        CK(csgv::launch_decode_single(V, wide, brick_ids_dev, lods_dev, r, out_dev, out_offsets_dev, status_dev, st));
-    return CSGV_OK;
+    return decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, true,
+                        (cudaStream_t)stream);
 }
 
 int csgv_volume_info_get(const csgv_volume *v, csgv_volume_info *info) {
@@ -489,6 +545,8 @@ int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint3
             return fail(CSGV_ERR_INVALID_ARG, "offsets must be non-decreasing");
         }
         maxp = std::max<uint32_t>(maxp, (uint32_t)(pal_off_host[i + 1] - pal_off_host[i]));
+        v->max_int_sym = std::max(v->max_int_sym, n_int_sym_host[i]);
+        v->max_leaf_sym = std::max(v->max_leaf_sym, n_leaf_sym_host[i]);
     }
     v->max_palette = maxp;
     auto up = [&](void **d, const void *h, size_t bytes) -> cudaError_t {

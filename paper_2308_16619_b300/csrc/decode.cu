@@ -1,35 +1,56 @@
 // decode.cu -- batched brick decoding (Alg. 1 of the paper) for sm_103a.
 //
-// One warp decodes one request (brick id, target LOD t) end to end:
-//   1. rANS: the K interleaved states of a stream live in lanes 0..K-1; a
-//      step decodes K symbols, lanes that need a renormalisation word take
-//      consecutive words in lane order (ballot + popc) from a window of the
-//      stream staged in shared memory by 16-byte loads (Sec. 3.3, readings
-//      R9/R10).  Each delta nibble is folded into its P_delta op, so the
-//      step appends one op record per child to a ring in shared memory.
-//   2. Reconstruction, level by level (Alg. 1): the children of all parents
-//      are first filled with the parent's label (stop-bit semantics: a
-//      constant parent's sub-block takes its label); then the active
-//      (non-constant) parents are taken four at a time, lane i handling
-//      child i&7 of parent i>>3: the op record decides the child's palette
-//      index.  Neighbour reuse toward -axis reads the same level (earlier in
-//      Z-order); chains of such references are at most 3 long (each hop sets
-//      one more child bit) and are resolved by pointer chasing inside the
-//      step.  Toward +axis the neighbour's parent is read (reading R4).
-//   3. Labels are stored as palette[index] in x-fastest order with 16-byte
-//      vector stores.
-// Palette indices, not labels, are kept in shared memory (uint8 when every
-// palette has <= 253 entries, else uint16).  For b = 32 the leaf level is
-// processed in eight 16^3 chunks in Z-order; the -x/-y/-z faces of finished
-// chunks are kept for later chunks' neighbour references.
+// A batch of requests (brick id, target LOD t) is decoded in slices of requests; a slice takes two
+// launches:
 //
-// The persistent kernel takes requests from a global work counter (atomic
-// add per warp); the plain kernel decodes one request per launch.
+//   rans_records (one warp per rANS stream; persistent CTAs hold both decode tables in shared memory).
+//     The K interleaved states of a stream live in lanes 0..K-1; a step decodes K symbols and the lanes
+//     that renormalise take consecutive words, in lane order (ballot + popc), from a window of the
+//     stream staged in shared memory by 16-byte loads (Sec. 3.3, readings R9/R10).  Each delta nibble
+//     is folded into the P_delta op before it, so the warp writes exactly one op record per coded
+//     child, in stream order (byte: op | stop << 3 | delta << 4), plus the number of P_a records before
+//     every 8th record (the palette position i_p there, reading R3), and checks the stream's end (every
+//     state back at L, every word read).
+//
+//   rebuild (one CTA of 256 threads per request).  Alg. 1 level by level, in parallel over the nodes of
+//     a level.  With one record per child, the 8 records of the j-th non-constant parent of a level
+//     sit at 8j, and i_p at them is known, so a level takes two barrier-separated passes:
+//       1. every child takes its parent's palette index (the stop-bit semantics: a constant parent's
+//          block keeps its label), and each warp lists the non-constant parents of its range of the
+//          level in Morton (= stream) order;
+//       2. one thread per listed parent decodes its records whose op is not R_p: R_a toward +axis
+//          reads the neighbour's parent (reading R4), palette ops index the palette (R1, R3), and R_a
+//          toward -axis is written as a sentinel naming the axis (and noted per listed parent);
+//       3. the sentinels are resolved by following them: a chain has at most 3 hops, since each hop
+//          lands on a child index with one more bit set.
+//     Levels with at most 64 parents are rebuilt by one warp without CTA barriers.  All levels
+//     of the brick, L0 included, are held as palette indices in shared memory (uint8 when every palette
+//     has <= 253 entries, else uint16); level t is then written as x-fastest labels with 16-byte
+//     streaming stores.
 #include "csgv_internal.cuh"
 
 namespace csgv {
 
+// Workspace of one slice.  Request i owns recs + i * stride: interior records at 0, leaf records at
+// leaf_at, and the P_a counts before every 8th record (uint16) of the two streams at t8_at and
+// t8_leaf_at; info[2i + s] = record count of stream s | kRecBad if the stream is malformed.
+struct RecJob {
+    const uint32_t *ids;
+    const uint8_t *lods;
+    uint32_t n;
+    uint8_t *recs;
+    uint64_t stride, leaf_at, t8_at, t8_leaf_at;
+    uint32_t *info;
+    uint32_t *counter;
+};
+
 namespace {
+
+constexpr uint32_t kRecBad = 0x80000000u;
+constexpr uint32_t kWinWords = 256;   // staged stream words per warp (uint16)
+constexpr uint32_t kRecWarps = 16;    // rans_records: warps per CTA
+constexpr uint32_t kRbThreads = 256;  // rebuild: threads per CTA
+constexpr uint32_t kRbWarps = kRbThreads / 32;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -37,175 +58,74 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Morton code helpers for up to 5 bits per axis (x at bit 0, reading R5)
-__device__ __forceinline__ uint32_t spread5(uint32_t v) {
-    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8);
-}
-__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
-    return spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
-}
-// m - e_a / m + e_a on the Morton grid (caller checks the range)
-__device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
-__device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
+// ------------------------------------------------------------------ rans_records
 
-template <typename IdxT>
-struct Traits;
-template <>
-struct Traits<uint8_t> {
-    static constexpr uint32_t kSent = 0xFDu;  // 0xFD,0xFE,0xFF: unresolved R_x-, R_y-, R_z-
-    static constexpr uint32_t kMaxPal = 0xFDu;
-};
-template <>
-struct Traits<uint16_t> {
-    static constexpr uint32_t kSent = 0xFFFDu;
-    static constexpr uint32_t kMaxPal = 0xFFFDu;
-};
-
-// shared-memory layout of one warp (entries of IdxT unless noted)
-constexpr uint32_t kUpN = 4688;      // levels 1..5 of a 32^3 brick: 4096+512+64+8+1 = 4681
-constexpr uint32_t kChunkN = 4096;   // one 16^3 chunk of level 0 (x fastest)
-constexpr uint32_t kXfN = 256, kYfN = 512, kZfN = 1024;  // faces of finished chunks toward -x, -y, -z
-constexpr uint32_t kMaskWords = 148; // const bits of levels 1..5
-constexpr uint32_t kGroup = 64;      // parents per list (uint32 entries: parent | block base << 16)
-constexpr uint32_t kQueueN = 64;     // queued children whose op is not R_p (two words each)
-constexpr uint32_t kOpsN = 256;      // op ring (bytes: op | stop<<3 | delta<<4)
-constexpr uint32_t kWinWords = 256;  // staged stream words (uint16)
-
-template <typename IdxT>
-__host__ __device__ constexpr uint32_t warp_smem_bytes() {
-    return ((kUpN + kChunkN + kXfN + kYfN + kZfN) * (uint32_t)sizeof(IdxT) + kMaskWords * 4 + kGroup * 4 +
-            kQueueN * 8 + kWinWords * 2 + kOpsN + 15u) & ~15u;
-}
-
-template <typename IdxT>
-struct WarpMem {
-    IdxT *up, *chunk, *xf, *yf, *zf;
-    uint32_t *cmask, *list;
-    uint2 *queue;
-    uint16_t *win;
-    uint8_t *ops;
-    __device__ explicit WarpMem(uint8_t *base) {
-        up = (IdxT *)base;
-        chunk = up + kUpN;
-        xf = chunk + kChunkN;
-        yf = xf + kXfN;
-        zf = yf + kYfN;
-        cmask = (uint32_t *)(zf + kZfN);  // 16-byte aligned: the IdxT arrays above total a multiple of 16 bytes
-        queue = (uint2 *)(cmask + kMaskWords);
-        win = (uint16_t *)(queue + kQueueN);
-        list = (uint32_t *)(win + kWinWords);
-        ops = (uint8_t *)(list + kGroup);
-    }
-};
-
-// offset of level l (1..N) in `up`, and of its const bits in `cmask` (words)
-__device__ __forceinline__ uint32_t up_off(uint32_t N, uint32_t l) {
-    uint32_t u = 0;
-#pragma unroll
-    for (uint32_t k = 1; k <= (uint32_t)kMaxN; k++)
-        if (k < l) u += 1u << (3 * (N - k));
-    return u;
-}
-__device__ __forceinline__ uint32_t mask_off(uint32_t N, uint32_t l) {
-    uint32_t w = 0;
-#pragma unroll
-    for (uint32_t k = 1; k <= (uint32_t)kMaxN; k++)
-        if (k < l) w += (N - k >= 2) ? (1u << (3 * (N - k) - 5)) : 1u;
-    return w;
-}
-
-// rANS stream of one brick: x is this lane's state (lanes < K), the rest is uniform.
-// Decoded symbols are folded into op records (a P_delta carries its delta) in the op ring.
-struct Stream {
-    const uint16_t *w;     // stream words in global memory
-    uint32_t n_words, pos, K, remaining, x;
-    int32_t wb;            // absolute word index held in win[0] (may be negative: alignment slack)
-    uint32_t wn;           // valid words in the window
-    uint32_t stage_at;     // restage once pos passes this (a step reads at most 32 words)
-    uint32_t ohead, otail, pend;  // op ring; pend = 1: op otail-1 still waits for its delta
-    bool bad;
-};
-
-// stage stream words from s.pos into the window with 16-byte loads (aligned down)
-__device__ __forceinline__ void stage(Stream &s, uint16_t *win, uint32_t lane) {
-    const uintptr_t g = reinterpret_cast<uintptr_t>(s.w + s.pos);
-    const uintptr_t g0 = g & ~(uintptr_t)15;
-    const uintptr_t gend = reinterpret_cast<uintptr_t>(s.w + s.n_words);
-    for (uint32_t c = lane; c < kWinWords / 8; c += 32) {
-        const uintptr_t a = g0 + 16 * (uintptr_t)c;
-        if (a < gend) reinterpret_cast<uint4 *>(win)[c] = __ldg(reinterpret_cast<const uint4 *>(a));
-    }
-    s.wb = (int32_t)s.pos - (int32_t)((g - g0) >> 1);
-    s.wn = min(kWinWords, (uint32_t)((int32_t)s.n_words - s.wb));
-    const uint32_t end = (uint32_t)(s.wb + (int32_t)s.wn);
-    s.stage_at = end < s.n_words ? end - 32 : 0xFFFFFFFFu;
-    __syncwarp();
-}
-
-__device__ __forceinline__ void stream_init(Stream &s, uint16_t *win, const uint16_t *w, uint32_t n_words,
-                                            uint32_t n_sym, uint32_t K_max, uint32_t S_min, uint32_t lane) {
-    s.w = w;
-    s.n_words = n_words;
-    s.remaining = n_sym;
-    s.K = lanes_for(n_sym, K_max, S_min);
-    s.bad = false;
-    s.x = kL;
-    s.pos = 0;
-    s.ohead = s.otail = s.pend = 0;
-    s.wb = 0;
-    s.wn = 0;
-    s.stage_at = 0xFFFFFFFFu;
+// Decode one stream (whole warp) into records and P_a counts; returns the record count, | kRecBad if
+// malformed.
+__device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t n_sym, uint32_t K_max,
+                                  uint32_t S_min, const uint32_t *lut, uint16_t *win, uint8_t *rec, uint16_t *t8,
+                                  uint64_t cap, uint32_t lane) {
     if (n_sym == 0) {
-        s.bad = n_words != 0;
-        return;
+        if (lane == 0) t8[0] = 0;
+        return n_words == 0 ? 0u : kRecBad;
     }
-    if (n_words < 2 * s.K) {
-        s.bad = true;
-        s.remaining = 0;
-        return;
-    }
-    stage(s, win, lane);
-    if (lane < s.K) s.x = (uint32_t)win[2 * lane - s.wb] | ((uint32_t)win[2 * lane + 1 - s.wb] << 16);
-    s.pos = 2 * s.K;
-}
-
-// decode rANS steps until `want` complete op records are waiting or the stream is exhausted
-__device__ __forceinline__ void produce(Stream &s, uint8_t *ops, uint16_t *win, const uint32_t *lut, uint32_t want,
-                                        uint32_t lane) {
-    const uint32_t lt = lanemask_lt();
-    uint32_t x = s.x, pos = s.pos, otail = s.otail, remaining = s.remaining, pend = s.pend;
-    const uint32_t ohead = s.ohead, K = s.K, last = s.n_words - 1;  // K > 0 and n_words >= 2K whenever remaining > 0
-    while (otail - ohead - pend < want && remaining > 0) {
-        if (pos > s.stage_at) {
-            if (pos > s.n_words) {  // corrupt: the words ran out
-                s.bad = true;
+    const uint32_t K = lanes_for(n_sym, K_max, S_min);
+    if (n_sym > cap || n_words < 2 * K) return kRecBad;
+    const uint32_t lt = lanemask_lt(), last = n_words - 1;
+    int32_t wb = 0;             // absolute word index held in win[0] (negative: alignment slack)
+    uint32_t stage_at = 0;      // restage once pos passes this (a step reads at most 32 words)
+    auto stage = [&](uint32_t pos) {
+        const uintptr_t g = reinterpret_cast<uintptr_t>(w + pos);
+        const uintptr_t g0 = g & ~(uintptr_t)15;
+        const uintptr_t gend = reinterpret_cast<uintptr_t>(w + n_words);
+        __syncwarp();
+        for (uint32_t c = lane; c < kWinWords / 8; c += 32) {
+            const uintptr_t a = g0 + 16 * (uintptr_t)c;
+            if (a < gend) reinterpret_cast<uint4 *>(win)[c] = __ldg(reinterpret_cast<const uint4 *>(a));
+        }
+        wb = (int32_t)pos - (int32_t)((g - g0) >> 1);
+        const uint32_t end = (uint32_t)(wb + (int32_t)kWinWords);
+        stage_at = end < n_words ? end - 32 : 0xFFFFFFFFu;
+        __syncwarp();
+    };
+    stage(0);
+    uint32_t x = kL;
+    if (lane < K) x = (uint32_t)win[2 * lane - wb] | ((uint32_t)win[2 * lane + 1 - wb] << 16);
+    uint32_t pos = 2 * K, remaining = n_sym, otail = 0, pend = 0, held = 0, pa_run = 0;
+    bool bad = false;
+    while (remaining > 0) {
+        if (pos > stage_at) {
+            if (pos > n_words) {  // the words ran out
+                bad = true;
                 break;
             }
-            s.pos = pos;
-            stage(s, win, lane);
+            stage(pos);
         }
         const uint32_t n = min(K, remaining);
         const bool act = lane < n;
-        // every lane runs the step (branch-free); lanes past n keep their state
         const uint32_t e = lut[x & (kM - 1u)];
         const uint32_t sym = e & 15u;
         const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
         const bool need = act && xn < kL;
         const uint32_t m = __ballot_sync(kFull, need);
         const uint32_t off = min(pos + __popc(m & lt), last);
-        const uint32_t wv = win[min(max((int32_t)off - s.wb, 0), (int32_t)kWinWords - 1)];  // in-window for every lane
+        const uint32_t wv = win[min((uint32_t)((int32_t)off - wb), kWinWords - 1)];  // in the window
         x = act ? (need ? ((xn << 16) | wv) : xn) : x;
         pos += __popc(m);
         remaining -= n;
-        uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD);
-        if ((cand | pend) == 0) {
-            // common case: every symbol of the step is an op
-            if (act) ops[(otail + lane) & (kOpsN - 1)] = (uint8_t)sym;
+        const uint32_t rare = __ballot_sync(kFull, act && (sym & 7u) >= OP_PD);  // P_delta, P_a (or 7)
+        if ((rare | pend) == 0) {  // common case: every symbol is an op, none of them P_a
+            if (act) {
+                const uint32_t r = otail + lane;
+                rec[r] = (uint8_t)sym;
+                if ((r & 7u) == 0) t8[r >> 3] = (uint16_t)pa_run;
+            }
             otail += n;
             continue;
         }
-        // which symbols are delta nibbles: the one after each P_delta op
-        uint64_t dm = pend;  // bit i: symbol i of this step is a delta
+        // which symbols are delta nibbles: the one after each P_delta op (bit n: in the next step)
+        uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD);
+        uint64_t dm = pend;
         cand &= ~(uint32_t)dm;
         while (cand) {
             const uint32_t i = __ffs(cand) - 1;
@@ -216,537 +136,539 @@ __device__ __forceinline__ void produce(Stream &s, uint8_t *ops, uint16_t *win, 
             }
         }
         const uint32_t nxt = __shfl_down_sync(kFull, sym, 1);
-        if (pend && lane == 0) ops[(otail - 1) & (kOpsN - 1)] |= (uint8_t)(sym << 4);
-        const uint32_t actm = n >= 32 ? kFull : ((1u << n) - 1u);
-        const uint32_t opm = actm & ~(uint32_t)dm;
-        if ((opm >> lane) & 1u) {
-            const bool pd = (sym & 7u) == OP_PD && lane + 1 < n;
-            ops[(otail + __popc(opm & lt)) & (kOpsN - 1)] = (uint8_t)(sym | (pd ? nxt << 4 : 0u));
+        const uint32_t sym0 = __shfl_sync(kFull, sym, 0);
+        const uint32_t symlast = __shfl_sync(kFull, sym, (n - 1) & 31u);
+        uint32_t base = otail;
+        if (pend) {  // the P_delta held back from the previous step takes symbol 0 as its delta
+            if (lane == 0) {
+                rec[otail] = (uint8_t)(held | (sym0 << 4));
+                if ((otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
+            }
+            base++;
         }
-        otail += __popc(opm);
-        pend = (uint32_t)((dm >> n) & 1ull);
+        const uint32_t actm = n >= 32 ? kFull : ((1u << n) - 1u);
+        const bool hold = (dm >> n) & 1ull;  // the last symbol is a P_delta whose delta comes next step
+        const uint32_t emit = actm & ~(uint32_t)dm & ~(hold ? (1u << (n - 1)) : 0u);
+        const bool em = (emit >> lane) & 1u;
+        const uint32_t pam = __ballot_sync(kFull, em && (sym & 7u) == OP_PA);
+        if (em) {
+            const bool pd = (sym & 7u) == OP_PD;
+            const uint32_t r = base + __popc(emit & lt);
+            rec[r] = (uint8_t)(sym | (pd ? nxt << 4 : 0u));
+            if ((r & 7u) == 0) t8[r >> 3] = (uint16_t)min(pa_run + __popc(pam & lt), 0xFFFFu);
+        }
+        pa_run = min(pa_run + __popc(pam), 0xFFFFu);  // saturated: a count past any palette is caught later
+        otail = base + __popc(emit);
+        pend = hold;
+        held = symlast;
     }
-    s.x = x;
-    s.pos = pos;
-    s.otail = otail;
-    s.remaining = remaining;
-    s.pend = pend;
-    if (pos > s.n_words) s.bad = true;
+    if (lane == 0 && (otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
+    const bool lane_ok = lane >= K || x == kL;
+    const bool ok = __all_sync(kFull, lane_ok) && !bad && remaining == 0 && !pend && pos == n_words;
     __syncwarp();
+    return ok ? otail : (otail | kRecBad);
 }
 
-// true iff every symbol was decoded and consumed and every state is back at L (full decode)
-__device__ __forceinline__ bool stream_done_ok(const Stream &s, uint32_t lane) {
-    const bool lane_ok = lane >= s.K || s.x == kL;
-    return __all_sync(kFull, lane_ok) && !s.bad && s.remaining == 0 && s.ohead == s.otail && !s.pend &&
-           s.pos == s.n_words;
-}
-
-// take n_ops op records from the ring (lane k < n_ops gets record k); false if the stream ran out
-__device__ __forceinline__ bool take_ops(Stream &s, const uint8_t *ops, uint32_t n_ops, uint32_t lane, uint32_t &o) {
-    if (s.otail - s.ohead - s.pend < n_ops) return false;
-    o = lane < n_ops ? (uint32_t)ops[(s.ohead + lane) & (kOpsN - 1)] : 0u;
-    s.ohead += n_ops;
-    return true;
-}
-
-// labels of 4 indices, from the palette held one entry per lane (kRegPal) or from global memory
-template <bool kRegPal>
-__device__ __forceinline__ uint4 labels4(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3, uint32_t pal_reg,
-                                         const uint32_t *pal, uint32_t np) {
-    uint4 o;
-    if (kRegPal) {
-        o.x = __shfl_sync(kFull, pal_reg, v0 & 31);
-        o.y = __shfl_sync(kFull, pal_reg, v1 & 31);
-        o.z = __shfl_sync(kFull, pal_reg, v2 & 31);
-        o.w = __shfl_sync(kFull, pal_reg, v3 & 31);
-    } else {
-        o.x = __ldg(pal + min(v0, np - 1));
-        o.y = __ldg(pal + min(v1, np - 1));
-        o.z = __ldg(pal + min(v2, np - 1));
-        o.w = __ldg(pal + min(v3, np - 1));
+__global__ void __launch_bounds__(kRecWarps * 32, 3) rans_records(VolDev V, RecJob J) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *lut_s = (uint32_t *)smem;
+    for (uint32_t i = threadIdx.x; i < 2 * kM / 4; i += blockDim.x)
+        ((uint4 *)lut_s)[i] = __ldg((const uint4 *)V.lut + i);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint16_t *win = (uint16_t *)(smem + 2 * kM * 4) + warp * kWinWords;
+    for (;;) {
+        uint32_t q = 0;
+        if (lane == 0) q = atomicAdd(J.counter, 1u);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= 2 * J.n) break;
+        const uint32_t i = q >> 1, s = q & 1u;
+        const uint32_t id = J.ids[i], t = J.lods[i];
+        // interior stream: needed below the root (t < N); leaf stream: needed for t == 0
+        if (id >= V.n_bricks || t > V.N || (s == 0 ? t >= V.N : t != 0)) continue;
+        const uint64_t *offs = s ? V.leaf_off : V.int_off;
+        const uint64_t w0 = offs[id];
+        const uint32_t n_words = (uint32_t)(offs[id + 1] - w0);
+        const uint32_t n_sym = s ? V.n_leaf_sym[id] : V.n_int_sym[id];
+        uint8_t *base = J.recs + (uint64_t)i * J.stride;
+        uint8_t *rec = base + (s ? J.leaf_at : 0);
+        uint16_t *t8 = (uint16_t *)(base + (s ? J.t8_leaf_at : J.t8_at));
+        const uint64_t cap = s ? J.t8_at - J.leaf_at : J.leaf_at;  // the records' room: 8 * (t8 entries - 1)
+        const uint32_t r = decode_stream((s ? V.leaf_words : V.int_words) + w0, n_words, n_sym, V.K_max, V.S_min,
+                                         lut_s + s * kM, win, rec, t8, cap, lane);
+        if (lane == 0) J.info[2 * i + s] = r;
     }
+}
+
+// ------------------------------------------------------------------ rebuild
+
+template <typename IdxT>
+struct RbTraits;
+template <>
+struct RbTraits<uint8_t> {
+    static constexpr uint32_t kSent = 0xFDu;  // 0xFD, 0xFE, 0xFF: unresolved R_x-, R_y-, R_z-
+    static constexpr uint32_t kRep = 0x01010101u;
+};
+template <>
+struct RbTraits<uint16_t> {
+    static constexpr uint32_t kSent = 0xFFFDu;
+    static constexpr uint32_t kRep = 0x00010001u;
+};
+
+constexpr uint32_t kWarpLevelPar = 64;  // levels with at most this many parents are rebuilt by warp 0 alone
+
+// m - e_a / m + e_a on the Morton grid (caller checks the range)
+__device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
+__device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
+
+__host__ __device__ __forceinline__ uint32_t spread5(uint32_t v) {
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8);
+}
+
+// bit 7 of each byte of v gathered into bits 0..3
+__device__ __forceinline__ uint32_t gather4(uint32_t v) { return (((v >> 7) & 0x01010101u) * 0x00204081u) >> 21 & 15u; }
+
+// Per-byte masks of 8 op records: ops other than R_p, P_a ops, stop bits (bit c = record c)
+__device__ __forceinline__ void rec_masks(uint64_t r8, uint32_t &nr, uint32_t &pa, uint32_t &st) {
+    const uint32_t lo = (uint32_t)r8, hi = (uint32_t)(r8 >> 32);
+    const uint32_t ol = lo & 0x07070707u, oh = hi & 0x07070707u;
+    nr = gather4(ol + 0x7F7F7F7Fu) | gather4(oh + 0x7F7F7F7Fu) << 4;
+    pa = gather4(~((ol ^ 0x06060606u) + 0x7F7F7F7Fu)) | gather4(~((oh ^ 0x06060606u) + 0x7F7F7F7Fu)) << 4;
+    st = gather4(lo << 4) | gather4(hi << 4) << 4;
+}
+
+// Final index of node q of a level whose value w is a -axis sentinel: follow the chain (at most 3 hops).
+template <typename IdxT>
+__device__ __forceinline__ uint32_t chase(const volatile IdxT *L, uint32_t q, uint32_t w, uint32_t lbits) {
+    const uint32_t sent = RbTraits<IdxT>::kSent;
+    for (int hop = 0; hop < 4 && w >= sent; hop++) {
+        q = mdec(q, kMX << (w - sent)) & lbits;
+        w = L[q];
+    }
+    return w < sent ? w : 0u;
+}
+
+// shared-memory layout of a rebuild CTA for a brick of side 2^N (byte offsets)
+struct RbLayout {
+    uint32_t lev, cm, act, mls, misc, pal, total;
+};
+// const bytes of level l (1..N-1): one byte per parent (bit c = child c constant), 16-byte aligned levels
+__host__ __device__ __forceinline__ uint32_t cm_off(uint32_t N, uint32_t l) {
+    uint32_t o = 0;
+    for (uint32_t L = N - 1; L > l; L--) o += ((1u << (3 * (N - L - 1))) + 15u) & ~15u;
     return o;
 }
-
-// Store a level held in Morton order (side <= 16) as x-fastest labels with row pitch `pitch`.
-template <typename IdxT, bool kRegPal>
-__device__ __forceinline__ void store_morton_impl(const IdxT *buf, uint32_t side, uint32_t *out, uint32_t pitch,
-                                                  uint32_t pal_reg, const uint32_t *pal, uint32_t np, bool vec,
-                                                  uint32_t lane) {
-    const uint32_t n = side * side * side;
-    if (vec && side >= 4) {
-        const uint32_t sh = __ffs(side) - 1;
-        const uint32_t x4 = lane & ((side >> 2) - 1);
-        const uint32_t sx = spread5(4 * x4);
-        for (uint32_t base = 0; base < n / 4; base += 32) {
-            const uint32_t i = min(base + lane, n / 4 - 1);
-            const uint32_t y = (i >> (sh - 2)) & (side - 1), z = i >> (2 * sh - 2);
-            const uint32_t m0 = sx | (spread5(y) << 1) | (spread5(z) << 2);
-            uint32_t v0, v1, v2, v3;
-            if (sizeof(IdxT) == 1) {
-                const uint32_t a = *(const uint16_t *)(buf + m0), b = *(const uint16_t *)(buf + m0 + 8);
-                v0 = a & 0xFF; v1 = a >> 8; v2 = b & 0xFF; v3 = b >> 8;
-            } else {
-                const uint32_t a = *(const uint32_t *)(buf + m0), b = *(const uint32_t *)(buf + m0 + 8);
-                v0 = a & 0xFFFF; v1 = a >> 16; v2 = b & 0xFFFF; v3 = b >> 16;
-            }
-            const uint4 o = labels4<kRegPal>(v0, v1, v2, v3, pal_reg, pal, np);
-            if (base + lane < n / 4) __stcs((uint4 *)(out + ((size_t)z * pitch + y) * pitch + 4 * x4), o);
-        }
-    } else {
-        for (uint32_t base = 0; base < n; base += 32) {
-            const uint32_t i = base + lane;
-            const uint32_t ii = i < n ? i : 0;
-            const uint32_t x = ii & (side - 1), y = (ii / side) & (side - 1), z = ii / (side * side);
-            const uint32_t v = buf[morton3(x, y, z)];
-            const uint32_t lab = kRegPal ? __shfl_sync(kFull, pal_reg, v & 31) : __ldg(pal + min(v, np - 1));
-            if (i < n) out[((size_t)z * pitch + y) * pitch + x] = lab;
-        }
-    }
+struct RbMisc {
+    uint32_t wcnt[kRbWarps];  // listed parents per warp (pass 1)
+    uint32_t used, ip0, bad, pad;
+};
+template <typename IdxT>
+__host__ __device__ constexpr RbLayout rb_layout(uint32_t N) {
+    uint32_t nodes = 0;
+    for (uint32_t l = 0; l <= N; l++) nodes += 1u << (3 * (N - l));
+    const uint32_t maxpar = 1u << (3 * (N - 1));  // parents of the leaf level
+    RbLayout L{};
+    L.lev = 0;
+    L.cm = (nodes * (uint32_t)sizeof(IdxT) + 15u) & ~15u;
+    L.act = L.cm + cm_off(N, 0);
+    L.mls = L.act + ((maxpar * 2u + 15u) & ~15u);
+    L.misc = L.mls + ((maxpar + 15u) & ~15u);
+    L.pal = L.misc + (((uint32_t)sizeof(RbMisc) + 15u) & ~15u);
+    L.total = L.pal + (sizeof(IdxT) == 1 ? 256u * 4u : 0u);
+    return L;
 }
 
-// Store a chunk held x-fastest (side cs = 2^ls) as labels with row pitch `pitch`.
-template <typename IdxT, bool kRegPal>
-__device__ __forceinline__ void store_linear_impl(const IdxT *buf, uint32_t cs, uint32_t ls, uint32_t *out,
-                                                  uint32_t pitch, uint32_t pal_reg, const uint32_t *pal, uint32_t np,
-                                                  bool vec, uint32_t lane) {
-    const uint32_t n = cs * cs * cs;
-    if (vec && cs >= 4) {
-        for (uint32_t base = 0; base < n / 4; base += 32) {
-            const uint32_t lin = 4 * min(base + lane, n / 4 - 1);
-            const uint32_t x = lin & (cs - 1), y = (lin >> ls) & (cs - 1), z = lin >> (2 * ls);
-            uint32_t v0, v1, v2, v3;
-            if (sizeof(IdxT) == 1) {
-                const uint32_t a = *(const uint32_t *)(buf + lin);
-                v0 = a & 0xFF; v1 = (a >> 8) & 0xFF; v2 = (a >> 16) & 0xFF; v3 = a >> 24;
-            } else {
-                const uint2 a = *(const uint2 *)(buf + lin);
-                v0 = a.x & 0xFFFF; v1 = a.x >> 16; v2 = a.y & 0xFFFF; v3 = a.y >> 16;
-            }
-            const uint4 o = labels4<kRegPal>(v0, v1, v2, v3, pal_reg, pal, np);
-            if (base + lane < n / 4) __stcs((uint4 *)(out + ((size_t)z * pitch + y) * pitch + x), o);
-        }
-    } else {
-        for (uint32_t base = 0; base < n; base += 32) {
-            const uint32_t i = base + lane;
-            const uint32_t ii = i < n ? i : 0;
-            const uint32_t x = ii & (cs - 1), y = (ii >> ls) & (cs - 1), z = ii >> (2 * ls);
-            const uint32_t v = buf[ii];
-            const uint32_t lab = kRegPal ? __shfl_sync(kFull, pal_reg, v & 31) : __ldg(pal + min(v, np - 1));
-            if (i < n) out[((size_t)z * pitch + y) * pitch + x] = lab;
-        }
-    }
+// offset (entries) of level l in the level array: L0 first, then L1 .. LN
+__device__ __forceinline__ uint32_t lev_off(uint32_t N, uint32_t l) {
+    uint32_t u = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < (uint32_t)kMaxN; k++)
+        if (k < l) u += 1u << (3 * (N - k));
+    return u;
 }
 
-// every voxel of a (side^3, pitch) block gets one label
-__device__ __forceinline__ void store_const(uint32_t label, uint32_t side, uint32_t *out, bool vec, uint32_t lane) {
+// every voxel of a side^3 block gets one label
+__device__ __forceinline__ void store_const(uint32_t label, uint32_t side, uint32_t *out, bool vec) {
     const uint32_t n = side * side * side;
     if (vec && side >= 4) {
         const uint4 o = make_uint4(label, label, label, label);
-        for (uint32_t i = lane; i < n / 4; i += 32) __stcs((uint4 *)out + i, o);
+        for (uint32_t i = threadIdx.x; i < n / 4; i += kRbThreads) __stcs((uint4 *)out + i, o);
     } else {
-        for (uint32_t i = lane; i < n; i += 32) out[i] = label;
+        for (uint32_t i = threadIdx.x; i < n; i += kRbThreads) out[i] = label;
     }
 }
 
-// Decode one request into out (already offset).  Returns a status code.
+template <typename IdxT, int kPal>  // kPal: 0 palette in lanes (<= 32 entries), 1 in shared memory, 2 global
+__device__ __forceinline__ uint32_t lab(uint32_t v, uint32_t pal_reg, const uint32_t *pal_s, const uint32_t *pal,
+                                        uint32_t np) {
+    if (kPal == 0) return __shfl_sync(kFull, pal_reg, v);  // the source lane is v mod 32
+    if (kPal == 1) return pal_s[v & 0xFFu];
+    return __ldg(pal + min(v & 0xFFFFu, np - 1));
+}
+
+// Write level t (Morton order, side = 2^s) as x-fastest labels.
+template <typename IdxT, int kPal>
+__device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t *out, bool vec, uint32_t pal_reg,
+                                            const uint32_t *pal_s, const uint32_t *pal, uint32_t np) {
+    const uint32_t side = 1u << s;
+    if (vec && side >= 4) {
+        // a unit is 4 voxels along x in 2 rows (y, y+1): Morton m0..m0+3 and m0+8..m0+11.  With at most
+        // 2^7 (x4, y2) pairs per slice (side <= 32), a thread keeps its (x4, y2) and steps z.
+        const uint32_t xs = s - 2, ys = s - 1, xy = xs + ys;
+        const uint32_t units = 1u << (xy + s);
+        const uint32_t u = threadIdx.x;
+        const uint32_t x4 = u & ((1u << xs) - 1), y2 = (u >> xs) & ((1u << ys) - 1);
+        const uint32_t dz = kRbThreads >> xy;  // z step per iteration
+        const uint32_t mxy = spread5(4 * x4) | (spread5(2 * y2) << 1);
+        const uint32_t mdz = spread5(dz & 31u) << 2;
+        uint32_t mz = spread5((u >> xy) & 31u) << 2;
+        uint32_t *o = out + (((size_t)(u >> xy) << s) + 2 * y2) * side + 4 * x4;
+        const size_t ostep = (size_t)dz << (2 * s);
+        for (uint32_t u0 = 0; u0 < units; u0 += kRbThreads) {
+            const bool in = u0 + u < units;
+            const uint32_t m0 = in ? (mxy | mz) : 0u;
+            uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+            if constexpr (sizeof(IdxT) == 1) {
+                const uint32_t A = *(const uint32_t *)(C + m0), B = *(const uint32_t *)(C + m0 + 8);
+                a0 = A; a1 = A >> 8; a2 = A >> 16; a3 = A >> 24;
+                b0 = B; b1 = B >> 8; b2 = B >> 16; b3 = B >> 24;
+            } else {
+                const uint2 A = *(const uint2 *)(C + m0), B = *(const uint2 *)(C + m0 + 8);
+                a0 = A.x; a1 = A.x >> 16; a2 = A.y; a3 = A.y >> 16;
+                b0 = B.x; b1 = B.x >> 16; b2 = B.y; b3 = B.y >> 16;
+            }
+            const uint4 r0 = make_uint4(lab<IdxT, kPal>(a0, pal_reg, pal_s, pal, np),
+                                        lab<IdxT, kPal>(a1, pal_reg, pal_s, pal, np),
+                                        lab<IdxT, kPal>(b0, pal_reg, pal_s, pal, np),
+                                        lab<IdxT, kPal>(b1, pal_reg, pal_s, pal, np));
+            const uint4 r1 = make_uint4(lab<IdxT, kPal>(a2, pal_reg, pal_s, pal, np),
+                                        lab<IdxT, kPal>(a3, pal_reg, pal_s, pal, np),
+                                        lab<IdxT, kPal>(b2, pal_reg, pal_s, pal, np),
+                                        lab<IdxT, kPal>(b3, pal_reg, pal_s, pal, np));
+            if (in) {
+                __stcs((uint4 *)o, r0);
+                __stcs((uint4 *)(o + side), r1);
+            }
+            mz = ((mz | ~kMZ) + mdz) & kMZ;  // z += dz on the Morton z bits
+            o += ostep;
+        }
+    } else {
+        const uint32_t n = side * side * side;
+        for (uint32_t i0 = 0; i0 < n; i0 += kRbThreads) {
+            const uint32_t i = i0 + threadIdx.x;
+            const uint32_t ii = i < n ? i : 0u;
+            const uint32_t x = ii & (side - 1), y = (ii >> s) & (side - 1), z = ii >> (2 * s);
+            const uint32_t v = C[spread5(x) | (spread5(y) << 1) | (spread5(z) << 2)];
+            const uint32_t l = lab<IdxT, kPal>(v, pal_reg, pal_s, pal, np);
+            if (i < n) out[i] = l;
+        }
+    }
+}
+
+// Rebuild children level l from its parents (see the file comment); returns false if the records are
+// malformed.  kWarp: warp 0 alone (levels with <= kWarpLevelPar parents), else the whole CTA.  R: this
+// level's records (in shared memory if kSmemRec); T8: P_a counts before every 8th record of the stream
+// from R's first record on;
+// ip0: i_p at the stream's start.  Sets n_act (listed parents: 8 * n_act records were used).
+template <typename IdxT, bool kWarp, bool kSmemRec>
+__device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
+                                              const uint8_t *R, const uint16_t *T8, uint32_t n_left, uint32_t ip0,
+                                              uint32_t np, uint32_t &n_act) {
+    typedef RbTraits<IdxT> T;
+    constexpr uint32_t nw = kWarp ? 1u : kRbWarps;
+    const uint32_t lane = threadIdx.x & 31, warp = kWarp ? 0u : threadIdx.x >> 5;
+    IdxT *lev = (IdxT *)(smem + Ly.lev);
+    uint8_t *cm = smem + Ly.cm;
+    uint16_t *act = (uint16_t *)(smem + Ly.act);
+    RbMisc *ms = (RbMisc *)(smem + Ly.misc);
+    const uint32_t npar = 1u << (3 * (N - l - 1));
+    IdxT *P = lev + lev_off(N, l + 1);
+    IdxT *C = lev + lev_off(N, l);
+    const uint8_t *cmP = (l + 1 < N) ? cm + cm_off(N, l + 1) : nullptr;  // the root is never constant here
+    uint8_t *cmC = l >= 1 ? cm + cm_off(N, l) : nullptr;
+    const uint32_t pbits = npar - 1, cbits = 8 * npar - 1;  // Morton code bits of the parent / child level
+    const uint32_t sent = T::kSent;
+
+    // pass 1: children take the parent's index; each warp lists the non-constant parents of its
+    // contiguous range of 32-parent blocks
+    const uint32_t nb = (npar + 31) / 32, bpw = (nb + nw - 1) / nw;
+    const uint32_t b0 = min(warp * bpw, nb), b1 = min(b0 + bpw, nb);
+    uint16_t *mylist = act + 32 * b0;
+    uint32_t cnt = 0;
+    for (uint32_t b = b0; b < b1; b++) {
+        const uint32_t k = 32 * b + lane;
+        const bool in = k < npar;
+        const uint32_t cw = !cmP ? 0u : npar >= 32 ? *(const uint32_t *)(cmP + 4 * b) : (uint32_t)cmP[0];
+        const bool pc = (cw >> lane) & 1u;
+        if (in) {
+            const uint32_t r = T::kRep * (uint32_t)P[k];
+            if (sizeof(IdxT) == 1) *(uint2 *)(C + 8 * k) = make_uint2(r, r);
+            else *(uint4 *)(C + 8 * k) = make_uint4(r, r, r, r);
+            if (cmC && pc) cmC[k] = 0xFF;
+        }
+        const uint32_t am = __ballot_sync(kFull, in && !pc);
+        if ((am >> lane) & 1u) mylist[cnt + __popc(am & lanemask_lt())] = (uint16_t)k;
+        cnt += __popc(am);
+    }
+    if (kWarp) {
+        __syncwarp();
+    } else {
+        if (lane == 0) ms->wcnt[warp] = cnt;
+        __syncthreads();
+    }
+
+    // pass 2: one thread per listed parent decodes its records whose op is not R_p
+    uint32_t wbase[nw];  // first listed index of each warp's list
+    n_act = 0;
+#pragma unroll
+    for (uint32_t v = 0; v < nw; v++) {
+        wbase[v] = n_act;
+        n_act += kWarp ? cnt : ms->wcnt[v];
+    }
+    if (8 * n_act > n_left) return false;  // uniform: every thread sees the same counts
+    const uint32_t nlb = (n_act + 31) / 32;
+    uint8_t *mm = smem + Ly.mls;  // children toward -axis of listed parent j (bit c = child c)
+    bool bad = false;
+    for (uint32_t b = warp; b < nlb; b += nw) {
+        const uint32_t j = 32 * b + lane;
+        const bool in = j < n_act;
+        uint32_t w = 0;
+#pragma unroll
+        for (uint32_t v = 1; v < nw; v++) w += j >= wbase[v] ? 1u : 0u;
+        uint32_t wb = 0;
+#pragma unroll
+        for (uint32_t v = 0; v < nw; v++) wb = v == w ? wbase[v] : wb;
+        const uint32_t k = in ? act[32 * bpw * w + (j - wb)] : 0u;
+        uint64_t r8 = 0;
+        uint32_t ipl = 0;
+        if (in) {
+            r8 = kSmemRec ? *(const uint64_t *)(R + 8 * j) : __ldg((const unsigned long long *)(R + 8 * j));
+            ipl = ip0 + (kSmemRec ? T8[j] : __ldg(T8 + j));
+        }
+        uint32_t nr, pm, st;
+        rec_masks(r8, nr, pm, st);
+        if (in) {
+            if (cmC) cmC[k] = (uint8_t)st;
+            else bad |= st != 0;  // leaf stop bits are 0
+        }
+        uint32_t minus_m = 0;
+        while (nr) {
+            const uint32_t c = __ffs(nr) - 1;
+            nr &= nr - 1;
+            const uint32_t o = (uint32_t)(r8 >> (8 * c)) & 0xFFu;
+            const uint32_t op = o & 7u, delta = o >> 4;
+            const uint32_t ipc = ipl + __popc(pm & ((1u << c) - 1u));
+            const bool rx = op <= OP_RZ;  // R_x, R_y, R_z (op != R_p here)
+            const uint32_t a = (op - OP_RX) & 3u, ma = kMX << a;
+            const bool plus = rx && ((c >> a) & 1u);
+            const bool minus = rx && !plus;
+            const uint32_t pv = P[minc(k, ma) & pbits];  // +axis: the neighbour's parent (R4)
+            uint32_t v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);  // R1, R3
+            v = plus ? pv : v;
+            v = minus ? sent + a : v;
+            bad |= (plus && (k & ma & pbits) == (ma & pbits)) || (minus && ((8 * k + c) & ma & cbits) == 0) ||
+                   op == 7u || (op == OP_PD && ipc < 1 + delta) || (op == OP_PA && ipc + 1 >= np);
+            C[8 * k + c] = (IdxT)v;
+            minus_m |= (minus ? 1u : 0u) << c;
+        }
+        if (in) mm[j] = (uint8_t)minus_m;
+    }
+    if (kWarp) {
+        __syncwarp();
+    } else {
+        if (threadIdx.x == 0) ms->bad = 0;
+        __syncthreads();
+        if (bad) ms->bad = 1;
+    }
+
+    // pass 3: resolve the -axis children of this warp's listed parents (chains of at most 3 hops;
+    // a target is final or a sentinel itself)
+    volatile IdxT *Cv = C;
+    for (uint32_t b = warp; b < nlb; b += nw) {
+        const uint32_t j = 32 * b + lane;
+        uint32_t m = j < n_act ? mm[j] : 0u;
+        if (!m) continue;
+        uint32_t w = 0;
+#pragma unroll
+        for (uint32_t v = 1; v < nw; v++) w += j >= wbase[v] ? 1u : 0u;
+        uint32_t wb = 0;
+#pragma unroll
+        for (uint32_t v = 0; v < nw; v++) wb = v == w ? wbase[v] : wb;
+        const uint32_t k = act[32 * bpw * w + (j - wb)];
+        while (m) {
+            const uint32_t c = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t q = 8 * k + c;
+            Cv[q] = (IdxT)chase<IdxT>(Cv, q, Cv[q], cbits);
+        }
+    }
+    if (kWarp) {
+        __syncwarp();
+        return !__any_sync(kFull, bad);
+    }
+    __syncthreads();
+    return ms->bad == 0;
+}
+
 template <typename IdxT>
-__device__ int32_t decode_request(const VolDev &V, const uint32_t *lut_s, WarpMem<IdxT> &M, uint32_t id, uint32_t t,
-                                  uint32_t *out, uint32_t lane) {
-    typedef Traits<IdxT> T;
+__device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *smem, uint32_t i, uint32_t *out) {
     const uint32_t N = V.N;
+    const uint32_t id = J.ids[i], t = J.lods[i];
     if (id >= V.n_bricks || t > N) return kStRange;
-    const uint32_t b = 1u << N;
+    const RbLayout Ly = rb_layout<IdxT>(N);
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t p0 = V.pal_off[id];
     const uint32_t np = (uint32_t)(V.pal_off[id + 1] - p0);
     const uint32_t *pal = V.pal + p0;
     const uint32_t n_int = V.n_int_sym[id], n_leaf = V.n_leaf_sym[id];
-    if (np == 0 || np > T::kMaxPal) return kStCorrupt;
-    const uint32_t pal_reg = lane < np ? __ldg(pal + lane) : 0u;
-    const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-    const bool reg_pal = np <= 32;
+    if (np == 0 || np > RbTraits<IdxT>::kSent) return kStCorrupt;
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    const uint32_t side = 1u << (N - t);
 
     // homogeneous brick: no symbols, every LOD is palette[0] (reading R2)
     if (n_int == 0 && n_leaf == 0) {
         if (V.int_off[id + 1] != V.int_off[id] || V.leaf_off[id + 1] != V.leaf_off[id]) return kStCorrupt;
-        store_const(__shfl_sync(kFull, pal_reg, 0), b >> t, out, vec_ok, lane);
+        store_const(__ldg(pal), side, out, vec);
         return kStOk;
     }
-    // root (level N): palette index 0 (Alg. 1 initialisation), not constant
-    if (lane == 0) {
-        M.up[up_off(N, N)] = 0;
-        M.cmask[mask_off(N, N)] = 0u;
-    }
-    __syncwarp();
-    if (t == N) {
-        if (lane == 0) out[0] = pal_reg;
+    if (t == N) {  // the root: palette index 0 (Alg. 1 initialisation)
+        if (threadIdx.x == 0) out[0] = __ldg(pal);
         return kStOk;
     }
+    const uint32_t info_int = J.info[2 * i], info_leaf = t == 0 ? J.info[2 * i + 1] : 0u;
+    if ((info_int | info_leaf) & kRecBad) return kStCorrupt;
+    const uint8_t *base = J.recs + (uint64_t)i * J.stride;
+    const uint16_t *t8i = (const uint16_t *)(base + J.t8_at), *t8l = (const uint16_t *)(base + J.t8_leaf_at);
 
-    const uint32_t K_max = V.K_max, S_min = V.S_min;
-    uint32_t ip = 0;  // palette index of the last P_a (i_p)
-    const uint32_t sent = T::kSent;
-    const uint32_t c = lane & 7u;
-
-    // value of one coded child (Sec. 3.2): R_p and R_a toward +axis read the parent level (pv), R_a
-    // toward -axis is left as a sentinel for the chase, palette ops index the palette (R1, R3)
-    auto child_value = [&](uint32_t op, uint32_t delta, uint32_t ipb, uint32_t pv, bool plus, bool minus,
-                           uint32_t a) -> uint32_t {
-        if (op == OP_RP || plus) return pv;
-        if (minus) return sent + a;
-        if (op == OP_P0) return ipb;
-        if (op == OP_PD) return ipb - 1 - delta;
-        return ipb + 1;
-    };
-
-    // Children whose op is R_p already hold their parent's label after the fill, so only the other
-    // children are queued (uint2: child index | op << 12 | delta << 15 | c << 19, palette index i_p |
-    // parent << 16) and evaluated 32 at a time.  Queued children are evaluated in stream order, so a
-    // -axis target is either final or evaluated in the same batch (resolved by the chase).
-    uint32_t qhead = 0, qtail = 0;
-
-    // ---- interior levels N-1 .. max(t,1): Morton order, all levels of the brick in `up`
-    Stream S;
-    stream_init(S, M.win, V.int_words + V.int_off[id], (uint32_t)(V.int_off[id + 1] - V.int_off[id]), n_int, K_max,
-                S_min, lane);
-    if (S.bad) return kStCorrupt;
-    const uint32_t lmin = t > 0 ? t : 1u;
-    for (uint32_t l = N - 1; l >= lmin && l < N; l--) {
-        const uint32_t npar = 1u << (3 * (N - l - 1));
-        const uint32_t pbits = npar - 1;  // parent-level Morton code bits
-        const IdxT *par = M.up + up_off(N, l + 1);
-        const uint32_t *cm_par = M.cmask + mask_off(N, l + 1);
-        IdxT *dst = M.up + up_off(N, l);
-        uint8_t *cm_dst = (uint8_t *)(M.cmask + mask_off(N, l));
-        // evaluate up to 32 queued children (interior level: Morton layout)
-        auto flush = [&](uint32_t cnt) -> bool {
-            const bool in = lane < cnt;
-            const uint2 qe = in ? M.queue[(qhead + lane) & (kQueueN - 1)] : make_uint2(0u, 0u);
-            qhead += cnt;
-            const uint32_t q = qe.x & 0xFFFu, op = (qe.x >> 12) & 7u, delta = (qe.x >> 15) & 15u, cc = qe.x >> 19;
-            const uint32_t ipb = qe.y & 0xFFFFu, k = qe.y >> 16;
-            const bool rx = op >= OP_RX && op <= OP_RZ;
-            const uint32_t a = rx ? op - OP_RX : 0u;
-            const uint32_t ma = kMX << a;
-            const bool plus = rx && ((cc >> a) & 1u);
-            const bool minus = rx && !plus;
-            const bool plus_out = plus && ((k & ma & pbits) == (ma & pbits));
-            const uint32_t pv = par[(plus && !plus_out) ? minc(k, ma) : k];
-            const bool minus_out = minus && (q & ma & (8 * npar - 1)) == 0;
-            const uint32_t v = child_value(op, delta, ipb, pv, plus, minus, a);
-            const bool bad = in && (plus_out || minus_out || op == 7u || op == OP_RP ||
-                                    (op == OP_PD && ipb < 1 + delta) || (op == OP_PA && ipb + 1 >= np));
-            if (in) dst[q] = (IdxT)(bad ? 0u : v);
-            if (__any_sync(kFull, bad)) return false;
-            const bool chase = in && minus;
-            if (__any_sync(kFull, chase)) {
-                __syncwarp();
-                // same-level references form chains of <= 3 hops (each hop sets one more child bit)
-                if (chase) {
-                    uint32_t cur = q, ax = a, w = 0;
-                    for (int hop = 0; hop < 4; hop++) {
-                        cur = mdec(cur, kMX << ax);
-                        w = dst[cur];
-                        if (w < sent) break;
-                        ax = w - sent;
-                    }
-                    dst[q] = (IdxT)w;
-                }
-            }
-            __syncwarp();
-            return true;
-        };
-        for (uint32_t g0 = 0; g0 < npar; g0 += kGroup) {
-            // (a) children take the parent's label (a constant parent keeps it); list the active parents
-            uint32_t n_act = 0;
-            for (uint32_t g = g0; g < g0 + kGroup && g < npar; g += 32) {
-                const uint32_t k = g + lane;
-                bool active = false;
-                if (k < npar) {
-                    const uint32_t v = par[k];
-                    const bool pc = (cm_par[k >> 5] >> (k & 31)) & 1u;
-                    active = !pc;
-                    if (sizeof(IdxT) == 1) {
-                        *(uint64_t *)(dst + 8 * k) = 0x0101010101010101ull * v;
-                    } else {
-                        const uint32_t r = 0x00010001u * v;
-                        *(uint4 *)(dst + 8 * k) = make_uint4(r, r, r, r);
-                    }
-                    cm_dst[k] = pc ? 0xFF : 0x00;
-                }
-                const uint32_t am = __ballot_sync(kFull, active);
-                if (active) M.list[n_act + __popc(am & lanemask_lt())] = k;
-                n_act += __popc(am);
-            }
-            __syncwarp();
-            // (b) read four active parents' ops (32) per step; queue the children that are not R_p
-            for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
-                const uint32_t n_ops = 8 * min(4u, n_act - r0);
-                produce(S, M.ops, M.win, lut_s, n_ops, lane);
-                uint32_t o;
-                if (!take_ops(S, M.ops, n_ops, lane, o)) return kStCorrupt;
-                const bool is_op = lane < n_ops;
-                const uint32_t op = o & 7u;
-                const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
-                const uint32_t ipb = ip + __popc(pam & lanemask_lt());
-                ip += __popc(pam);
-                const uint32_t sm = __ballot_sync(kFull, is_op && ((o >> 3) & 1u));
-                const bool nr = is_op && op != OP_RP;
-                const uint32_t nm = __ballot_sync(kFull, nr);
-                if (is_op && (c == 0 || nr)) {
-                    const uint32_t k = M.list[r0 + (lane >> 3)];
-                    if (c == 0) cm_dst[k] = (uint8_t)(sm >> (lane & ~7u));
-                    if (nr)
-                        M.queue[(qtail + __popc(nm & lanemask_lt())) & (kQueueN - 1)] =
-                            make_uint2((8 * k + c) | (op << 12) | ((o >> 4) << 15) | (c << 19), ipb | (k << 16));
-                }
-                qtail += __popc(nm);
-                __syncwarp();
-                if (qtail - qhead >= 32 && !flush(32)) return kStCorrupt;
-            }
-        }
-        while (qtail != qhead)
-            if (!flush(min(32u, qtail - qhead))) return kStCorrupt;
+    IdxT *lev = (IdxT *)(smem + Ly.lev);
+    RbMisc *ms = (RbMisc *)(smem + Ly.misc);
+    uint32_t *pal_s = (uint32_t *)(smem + Ly.pal);
+    // The interior stream (at most 8 records per parent of an interior level) and its P_a counts are
+    // staged in the L0 area, which is free until the leaf level.
+    if (info_int > 8 * (((1u << (3 * (N - 1))) - 1u) / 7u)) return kStCorrupt;
+    uint8_t *srec = smem + Ly.lev;
+    const uint32_t ri16 = (info_int + 15u) & ~15u;
+    const uint16_t *st8 = (const uint16_t *)(srec + ri16);
+    if (info_int > 0) {
+        const uint32_t t8b = ((info_int / 8 + 1) * 2 + 15u) & ~15u;
+        for (uint32_t q = threadIdx.x; q < ri16 / 16; q += kRbThreads) ((uint4 *)srec)[q] = __ldg((const uint4 *)base + q);
+        for (uint32_t q = threadIdx.x; q < t8b / 16; q += kRbThreads)
+            ((uint4 *)(srec + ri16))[q] = __ldg((const uint4 *)(base + J.t8_at) + q);
     }
-    if (t >= 1) {
-        if (t == 1 && !stream_done_ok(S, lane)) return kStCorrupt;
-        const uint32_t side = b >> t;
-        if (reg_pal) store_morton_impl<IdxT, true>(M.up + up_off(N, t), side, out, side, pal_reg, pal, np, vec_ok, lane);
-        else store_morton_impl<IdxT, false>(M.up + up_off(N, t), side, out, side, pal_reg, pal, np, vec_ok, lane);
-        return kStOk;
-    }
-    if (!stream_done_ok(S, lane)) return kStCorrupt;
+    if (sizeof(IdxT) == 1)
+        for (uint32_t k = threadIdx.x; k < np; k += kRbThreads) pal_s[k] = __ldg(pal + k);
+    const uint32_t pal_reg = lane < np ? __ldg(pal + lane) : 0u;
+    if (threadIdx.x == 0) lev[lev_off(N, N)] = 0;
+    __syncthreads();
 
-    // ---- leaf level in chunks of side cs = min(b, 16) in Z-order, each held x-fastest in M.chunk
-    Stream Lf;
-    stream_init(Lf, M.win, V.leaf_words + V.leaf_off[id], (uint32_t)(V.leaf_off[id + 1] - V.leaf_off[id]), n_leaf,
-                K_max, S_min, lane);
-    if (Lf.bad) return kStCorrupt;
-    const uint32_t ls = N < 4 ? N : 4u;             // log2 chunk side
-    const uint32_t cs = 1u << ls;
-    const uint32_t cbits = N - ls;                  // chunks per axis = 2^cbits (at most 2)
-    const uint32_t n_chunks = 1u << (3 * cbits);
-    const uint32_t npar = 1u << (3 * (ls - 1));     // L1 parents per chunk (<= 512)
-    const uint32_t pbits = (1u << (3 * (N - 1))) - 1u;  // L1 Morton code bits
-    const IdxT *par = M.up + up_off(N, 1);
-    const uint32_t *cm_par = M.cmask + mask_off(N, 1);
-    IdxT *dst = M.chunk;
-    const uint32_t coff = (c & 1u) + (((c >> 1) & 1u) << ls) + ((c >> 2) << (2 * ls));  // child offset in the chunk
-    for (uint32_t o = 0; o < n_chunks; o++) {
-        const uint32_t pp0 = o * npar;
-        const uint32_t ox = o & 1u, oy = (o >> 1) & 1u, oz = o >> 2;
-        // evaluate up to 32 queued children (leaf chunk: x-fastest layout)
-        auto flush = [&](uint32_t cnt) -> bool {
-            const bool in = lane < cnt;
-            const uint2 qe = in ? M.queue[(qhead + lane) & (kQueueN - 1)] : make_uint2(0u, 0u);
-            qhead += cnt;
-            const uint32_t qi = qe.x & 0xFFFu, op = (qe.x >> 12) & 7u, delta = (qe.x >> 15) & 15u, cc = qe.x >> 19;
-            const uint32_t ipb = qe.y & 0xFFFFu, pp = pp0 + (qe.y >> 16);
-            const bool rx = op >= OP_RX && op <= OP_RZ;
-            const uint32_t a = rx ? op - OP_RX : 0u;
-            const uint32_t ma = kMX << a;
-            const bool plus = rx && ((cc >> a) & 1u);
-            const bool minus = rx && !plus;
-            const bool plus_out = plus && ((pp & ma & pbits) == (ma & pbits));
-            const uint32_t pv = par[(plus && !plus_out) ? minc(pp, ma) : pp];
-            const bool edge = ((qi >> (ls * a)) & (cs - 1)) == 0;
-            const bool minus_out = minus && edge && !((o >> a) & 1u);
-            const uint32_t v = child_value(op, delta, ipb, pv, plus, minus, a);
-            const bool bad = in && (plus_out || minus_out || op == 7u || op == OP_RP ||
-                                    (op == OP_PD && ipb < 1 + delta) || (op == OP_PA && ipb + 1 >= np));
-            if (in) dst[qi] = (IdxT)(bad ? 0u : v);
-            if (__any_sync(kFull, bad)) return false;
-            const bool chase = in && minus;
-            if (__any_sync(kFull, chase)) {
-                __syncwarp();
-                if (chase) {
-                    uint32_t cur = qi, ax = a, w = 0;
-                    for (int hop = 0; hop < 4; hop++) {
-                        if (((cur >> (ls * ax)) & (cs - 1)) == 0) {
-                            // crosses into an earlier chunk: its face holds final indices
-                            const uint32_t x = cur & (cs - 1), y = (cur >> ls) & (cs - 1), z = cur >> (2 * ls);
-                            if (ax == 0) w = M.xf[y + 16 * z];
-                            else if (ax == 1) w = M.yf[(ox * 16 + x) + 32 * z];
-                            else w = M.zf[(ox * 16 + x) + 32 * (oy * 16 + y)];
-                            break;
-                        }
-                        cur -= 1u << (ls * ax);
-                        w = dst[cur];
-                        if (w < sent) break;
-                        ax = w - sent;
-                    }
-                    dst[qi] = (IdxT)w;
-                }
+    // levels with few parents: warp 0 alone; (used, i_p at the stream start) handed over in shared memory
+    int l = (int)N - 1;
+    if (threadIdx.x < 32) {
+        uint32_t used = 0, ok = 1;
+        int ll = l;
+        for (; ll >= (int)t && (1u << (3 * (N - ll - 1))) <= kWarpLevelPar; ll--) {
+            const bool leaf = ll == 0;
+            if (leaf && used != info_int) {  // the leaf stream follows the complete interior stream
+                ok = 0;
+                break;
             }
-            __syncwarp();
-            return true;
-        };
-        for (uint32_t g0 = 0; g0 < npar; g0 += kGroup) {
-            // (a) 2x2x2 blocks take the parent's label; list active parents with their block's linear base
-            uint32_t n_act = 0;
-            for (uint32_t g = g0; g < g0 + kGroup && g < npar; g += 32) {
-                const uint32_t k = g + lane;
-                bool active = false;
-                uint32_t lb = 0;
-                if (k < npar) {
-                    const uint32_t pp = pp0 + k;
-                    const uint32_t v = par[pp];
-                    active = !((cm_par[pp >> 5] >> (pp & 31)) & 1u);
-                    const uint32_t px = (k & 1u) | ((k >> 2) & 2u) | ((k >> 4) & 4u);
-                    const uint32_t py = ((k >> 1) & 1u) | ((k >> 3) & 2u) | ((k >> 5) & 4u);
-                    const uint32_t pz = ((k >> 2) & 1u) | ((k >> 4) & 2u) | ((k >> 6) & 4u);
-                    lb = 2 * px + (2 * py << ls) + (2 * pz << (2 * ls));
-                    if (sizeof(IdxT) == 1) {
-                        const uint16_t r = (uint16_t)(0x0101u * v);
-                        *(uint16_t *)(dst + lb) = r;
-                        *(uint16_t *)(dst + lb + cs) = r;
-                        *(uint16_t *)(dst + lb + cs * cs) = r;
-                        *(uint16_t *)(dst + lb + cs + cs * cs) = r;
-                    } else {
-                        const uint32_t r = 0x00010001u * v;
-                        *(uint32_t *)(dst + lb) = r;
-                        *(uint32_t *)(dst + lb + cs) = r;
-                        *(uint32_t *)(dst + lb + cs * cs) = r;
-                        *(uint32_t *)(dst + lb + cs + cs * cs) = r;
-                    }
-                }
-                const uint32_t am = __ballot_sync(kFull, active);
-                if (active) M.list[n_act + __popc(am & lanemask_lt())] = k | (lb << 16);
-                n_act += __popc(am);
+            uint32_t n_act;
+            const bool good = leaf ? rebuild_level<IdxT, true, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf,
+                                                                      __ldg(t8i + info_int / 8), np, n_act)
+                                   : rebuild_level<IdxT, true, true>(smem, Ly, N, (uint32_t)ll, srec + used,
+                                                                     st8 + used / 8, info_int - used, 0u, np, n_act);
+            if (!good) {
+                ok = 0;
+                break;
             }
-            __syncwarp();
-            // (b) read four active parents' ops per step; queue the children that are not R_p
-            for (uint32_t r0 = 0; r0 < n_act; r0 += 4) {
-                const uint32_t n_ops = 8 * min(4u, n_act - r0);
-                produce(Lf, M.ops, M.win, lut_s + kM, n_ops, lane);
-                uint32_t o8;
-                if (!take_ops(Lf, M.ops, n_ops, lane, o8)) return kStCorrupt;
-                const bool is_op = lane < n_ops;
-                const uint32_t op = o8 & 7u;
-                const uint32_t pam = __ballot_sync(kFull, is_op && op == OP_PA);
-                const uint32_t ipb = ip + __popc(pam & lanemask_lt());
-                ip += __popc(pam);
-                if (__any_sync(kFull, is_op && ((o8 >> 3) & 1u))) return kStCorrupt;  // leaf stop bits are 0
-                const bool nr = is_op && op != OP_RP;
-                const uint32_t nm = __ballot_sync(kFull, nr);
-                if (nr) {
-                    const uint32_t e = M.list[r0 + (lane >> 3)];
-                    M.queue[(qtail + __popc(nm & lanemask_lt())) & (kQueueN - 1)] =
-                        make_uint2(((e >> 16) + coff) | (op << 12) | ((o8 >> 4) << 15) | (c << 19),
-                                   ipb | ((e & 0xFFFFu) << 16));
-                }
-                qtail += __popc(nm);
-                __syncwarp();
-                if (qtail - qhead >= 32 && !flush(32)) return kStCorrupt;
-            }
+            const uint32_t u0 = leaf ? 0u : used;
+            used = u0 + 8 * n_act;
         }
-        while (qtail != qhead)
-            if (!flush(min(32u, qtail - qhead))) return kStCorrupt;
-        uint32_t *cout = out + ((size_t)(oz * cs) * b + oy * cs) * b + ox * cs;
-        if (reg_pal) store_linear_impl<IdxT, true>(dst, cs, ls, cout, b, pal_reg, pal, np, vec_ok, lane);
-        else store_linear_impl<IdxT, false>(dst, cs, ls, cout, b, pal_reg, pal, np, vec_ok, lane);
-        if (n_chunks > 1) {
-            // keep the faces later chunks may reference (-x, -y, -z neighbours)
-            for (uint32_t i = lane; i < 256; i += 32) {
-                const uint32_t u = i & 15, w = i >> 4;
-                if (!ox) M.xf[u + 16 * w] = dst[15 + 16 * u + 256 * w];
-                if (!oy) M.yf[(ox * 16 + u) + 32 * w] = dst[u + 16 * 15 + 256 * w];
-                if (!oz) M.zf[(ox * 16 + u) + 32 * (oy * 16 + w)] = dst[u + 16 * w + 256 * 15];
-            }
+        if (lane == 0) {
+            ms->used = used;
+            ms->bad = !ok;
         }
-        __syncwarp();
     }
-    if (!stream_done_ok(Lf, lane)) return kStCorrupt;
+    __syncthreads();
+    if (ms->bad) return kStCorrupt;
+    uint32_t used = ms->used;
+    while (l >= (int)t && (1u << (3 * (N - l - 1))) <= kWarpLevelPar) l--;
+    if (t == 0 && l >= 0) {  // warm L1 with the leaf stream's records and P_a counts
+        const uint8_t *lr = base + J.leaf_at;
+        for (uint32_t q = 128 * threadIdx.x; q < info_leaf; q += 128 * kRbThreads)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(lr + q));
+        const uint8_t *lt = (const uint8_t *)t8l;
+        for (uint32_t q = 128 * threadIdx.x; q < 2 * (info_leaf / 8 + 1); q += 128 * kRbThreads)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(lt + q));
+    }
+    __syncthreads();  // everyone has read ms before a level may write it
+    for (; l >= (int)t; l--) {
+        uint32_t n_act;
+        if (l == 0) {
+            if (used != info_int) return kStCorrupt;
+            if (!rebuild_level<IdxT, false, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf,
+                                                   __ldg(t8i + info_int / 8), np, n_act))
+                return kStCorrupt;
+            used = 8 * n_act;
+        } else {
+            if (!rebuild_level<IdxT, false, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
+                                                  info_int - used, 0u, np, n_act))
+                return kStCorrupt;
+            used += 8 * n_act;
+        }
+    }
+    if ((t == 1 && used != info_int) || (t == 0 && used != info_leaf)) return kStCorrupt;
+
+    const IdxT *C = lev + lev_off(N, t);
+    const uint32_t s = N - t;
+    if (np <= 32) store_level<IdxT, 0>(C, s, out, vec, pal_reg, pal_s, pal, np);
+    else if (sizeof(IdxT) == 1) store_level<IdxT, 1>(C, s, out, vec, pal_reg, pal_s, pal, np);
+    else store_level<IdxT, 2>(C, s, out, vec, pal_reg, pal_s, pal, np);
     return kStOk;
 }
 
 template <typename IdxT>
-__device__ __forceinline__ void load_lut(uint32_t *lut_s, const uint32_t *lut) {
-    for (uint32_t i = threadIdx.x; i < 2 * kM / 4; i += blockDim.x)
-        ((uint4 *)lut_s)[i] = __ldg((const uint4 *)lut + i);
-    __syncthreads();
-}
-
-template <typename IdxT>
-__global__ void __launch_bounds__(1024, 1)
-    decode_persistent(VolDev V, const uint32_t *__restrict__ ids, const uint8_t *__restrict__ lods, uint32_t n,
-                      uint32_t *__restrict__ out, const uint64_t *__restrict__ out_off, int32_t *__restrict__ status,
-                      uint32_t *__restrict__ work) {
+__global__ void __launch_bounds__(kRbThreads) rebuild(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                      const uint64_t *__restrict__ out_off,
+                                                      int32_t *__restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *lut_s = (uint32_t *)smem;
-    load_lut<IdxT>(lut_s, V.lut);
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpMem<IdxT> M(smem + 2 * kM * 4 + warp * warp_smem_bytes<IdxT>());
-    for (;;) {
-        uint32_t r = 0;
-        if (lane == 0) r = atomicAdd(work, 1u);
-        r = __shfl_sync(kFull, r, 0);
-        if (r >= n) break;
-        const int32_t st = decode_request<IdxT>(V, lut_s, M, ids[r], lods[r], out + out_off[r], lane);
-        if (lane == 0) status[r] = st;
-        __syncwarp();
-    }
-}
-
-template <typename IdxT>
-__global__ void __launch_bounds__(32, 1)
-    decode_single(VolDev V, const uint32_t *__restrict__ ids, const uint8_t *__restrict__ lods, uint32_t r,
-                  uint32_t *__restrict__ out, const uint64_t *__restrict__ out_off, int32_t *__restrict__ status) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *lut_s = (uint32_t *)smem;
-    load_lut<IdxT>(lut_s, V.lut);
-    WarpMem<IdxT> M(smem + 2 * kM * 4);
-    const int32_t st = decode_request<IdxT>(V, lut_s, M, ids[r], lods[r], out + out_off[r], threadIdx.x);
-    if (threadIdx.x == 0) status[r] = st;
+    const uint32_t i = blockIdx.x;
+    const int32_t st = rebuild_request<IdxT>(V, J, smem, i, out + out_off[i]);
+    if (threadIdx.x == 0) status[i] = st;
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- launchers (host)
 
-uint32_t decode_smem_bytes(bool wide, uint32_t warps) {
-    return 2 * kM * 4 + warps * (wide ? warp_smem_bytes<uint16_t>() : warp_smem_bytes<uint8_t>());
+uint32_t rans_records_smem_bytes() { return 2 * kM * 4 + kRecWarps * kWinWords * 2; }
+
+uint32_t rebuild_smem_bytes(uint32_t N, bool wide) {
+    return wide ? rb_layout<uint16_t>(N).total : rb_layout<uint8_t>(N).total;
 }
 
-cudaError_t launch_decode_persistent(const VolDev &V, bool wide, const uint32_t *ids, const uint8_t *lods, uint32_t n,
-                                     uint32_t *out, const uint64_t *out_off, int32_t *status, uint32_t *work,
-                                     uint32_t warps, uint32_t blocks, cudaStream_t st) {
-    const uint32_t smem = decode_smem_bytes(wide, warps);
-    cudaError_t e;
+// Decode requests [0, J.n) of a slice: records, then the rebuild (statuses and outputs already offset).
+cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uint32_t *out, const uint64_t *out_off,
+                                int32_t *status, uint32_t rec_blocks, cudaStream_t st) {
+    if (J.n == 0) return cudaSuccess;
+    const uint32_t smem_a = rans_records_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(rans_records, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_a);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(J.counter, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
+    rans_records<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint32_t smem_b = rebuild_smem_bytes(V.N, wide);
     if (wide) {
-        e = cudaFuncSetAttribute(decode_persistent<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
         if (e != cudaSuccess) return e;
-        decode_persistent<uint16_t><<<blocks, warps * 32, smem, st>>>(V, ids, lods, n, out, out_off, status, work);
+        rebuild<uint16_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     } else {
-        e = cudaFuncSetAttribute(decode_persistent<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
         if (e != cudaSuccess) return e;
-        decode_persistent<uint8_t><<<blocks, warps * 32, smem, st>>>(V, ids, lods, n, out, out_off, status, work);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_decode_single(const VolDev &V, bool wide, const uint32_t *ids, const uint8_t *lods, uint32_t r,
-                                 uint32_t *out, const uint64_t *out_off, int32_t *status, cudaStream_t st) {
-    const uint32_t smem = decode_smem_bytes(wide, 1);
-    if (wide) {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(decode_single<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        decode_single<uint16_t><<<1, 32, smem, st>>>(V, ids, lods, r, out, out_off, status);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(decode_single<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        decode_single<uint8_t><<<1, 32, smem, st>>>(V, ids, lods, r, out, out_off, status);
+        rebuild<uint8_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     }
     return cudaGetLastError();
 }

@@ -520,7 +520,9 @@ __global__ void __launch_bounds__(256) compact_kernel(EncGeom G, EncScratch SC, 
     if (threadIdx.x == 0) {
         n_int_sym[id] = sz[1];
         n_leaf_sym[id] = sz[2];
-        atomicMax(max_pal, np);
+        atomicMax(max_pal, np);  // max_pal[0..2]: largest palette, interior and leaf symbol counts
+        atomicMax(max_pal + 1, sz[1]);
+        atomicMax(max_pal + 2, sz[2]);
     }
 }
 

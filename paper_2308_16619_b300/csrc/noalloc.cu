@@ -57,7 +57,7 @@ size_t carve(const csgv::EncGeom &G, size_t C, unsigned char *base, csgv::EncScr
         o = align_up(o + bytes);
         return p;
     };
-    unsigned char *f = take(32 * 4), *t = take(3 * 8), *m = take(4);
+    unsigned char *f = take(32 * 4), *t = take(3 * 8), *m = take(3 * 4);
     unsigned char *sz = take(C * 8 * 4), *pal = take(C * G.pal_cap * 4);
     unsigned char *ni = take(C * G.int_cap), *nl = take(C * G.leaf_cap);
     unsigned char *wi = take(C * (G.int_cap + 64) * 2), *wl = take(C * (G.leaf_cap + 64) * 2);
@@ -159,7 +159,7 @@ int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], 
     carve(G, n, (unsigned char *)base, &SC, &freq_d, &tot_d, &maxpal_d);
     cudaError_t e = cudaMemcpyAsync(freq_d, table->freq, 32 * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tot_d, 0, 3 * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(maxpal_d, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(maxpal_d, 0, 3 * 4, st);
     if (e == cudaSuccess) e = csgv::launch_encode(EV, G, 0, 1, (uint32_t)n, freq_d, SC, nullptr, st);
     if (e == cudaSuccess)
         e = csgv::launch_scan(SC.sizes, (uint32_t)n, 0, pal_off_dev, int_off_dev, leaf_off_dev, tot_d, st);
