@@ -23,7 +23,7 @@
 //          toward -axis is written as a sentinel naming the axis (and noted per listed parent);
 //       3. the sentinels are resolved by following them: a chain has at most 3 hops, since each hop
 //          lands on a child index with one more bit set.
-//     Levels with at most 64 parents are rebuilt by one warp without CTA barriers.  All levels
+//     Levels with at most 64 parents are rebuilt one thread per child instead.  All levels
 //     of the brick, L0 included, are held as palette indices in shared memory (uint8 when every palette
 //     has <= 253 entries, else uint16); level t is then written as x-fastest labels with 16-byte
 //     streaming stores.
@@ -57,6 +57,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+__device__ __forceinline__ uint32_t lt_of(uint32_t lane) { return (1u << lane) - 1u; }
 
 // ------------------------------------------------------------------ rans_records
 
@@ -215,7 +216,7 @@ struct RbTraits<uint16_t> {
     static constexpr uint32_t kRep = 0x00010001u;
 };
 
-constexpr uint32_t kWarpLevelPar = 64;  // levels with at most this many parents are rebuilt by warp 0 alone
+constexpr uint32_t kSmallPar = 64;  // levels with at most this many parents are rebuilt one thread per child
 
 // m - e_a / m + e_a on the Morton grid (caller checks the range)
 __device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
@@ -260,7 +261,8 @@ __host__ __device__ __forceinline__ uint32_t cm_off(uint32_t N, uint32_t l) {
 }
 struct RbMisc {
     uint32_t wcnt[kRbWarps];  // listed parents per warp (pass 1)
-    uint32_t used, ip0, bad, pad;
+    uint32_t msk[16];         // small levels: children toward -axis per 32-child step
+    uint32_t bad, pad[3];
 };
 template <typename IdxT>
 __host__ __device__ constexpr RbLayout rb_layout(uint32_t N) {
@@ -365,57 +367,118 @@ __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t 
     }
 }
 
-// Rebuild children level l from its parents (see the file comment); returns false if the records are
-// malformed.  kWarp: warp 0 alone (levels with <= kWarpLevelPar parents), else the whole CTA.  R: this
-// level's records (in shared memory if kSmemRec); T8: P_a counts before every 8th record of the stream
-// from R's first record on;
-// ip0: i_p at the stream's start.  Sets n_act (listed parents: 8 * n_act records were used).
-template <typename IdxT, bool kWarp, bool kSmemRec>
-__device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
-                                              const uint8_t *R, const uint16_t *T8, uint32_t n_left, uint32_t ip0,
-                                              uint32_t np, uint32_t &n_act) {
+// Levels with at most kSmallPar parents (the top of the tree): one thread per child in Morton order,
+// the whole CTA.  The j-th non-constant parent's records sit at 8j; j, i_p and the stop bits come from
+// the active-parent mask and warp ballots over a parent's 8 lanes.  Arguments as for rebuild_level.
+template <typename IdxT, bool kSmemRec>
+__device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
+                                                    const uint8_t *R, const uint16_t *T8, uint32_t n_left,
+                                                    uint32_t ip0, uint32_t np, uint32_t &n_act) {
     typedef RbTraits<IdxT> T;
-    constexpr uint32_t nw = kWarp ? 1u : kRbWarps;
-    const uint32_t lane = threadIdx.x & 31, warp = kWarp ? 0u : threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     IdxT *lev = (IdxT *)(smem + Ly.lev);
     uint8_t *cm = smem + Ly.cm;
-    uint16_t *act = (uint16_t *)(smem + Ly.act);
     RbMisc *ms = (RbMisc *)(smem + Ly.misc);
-    const uint32_t npar = 1u << (3 * (N - l - 1));
+    const uint32_t npar = 1u << (3 * (N - l - 1));  // 1, 8 or 64
     IdxT *P = lev + lev_off(N, l + 1);
     IdxT *C = lev + lev_off(N, l);
     const uint8_t *cmP = (l + 1 < N) ? cm + cm_off(N, l + 1) : nullptr;  // the root is never constant here
     uint8_t *cmC = l >= 1 ? cm + cm_off(N, l) : nullptr;
-    const uint32_t pbits = npar - 1, cbits = 8 * npar - 1;  // Morton code bits of the parent / child level
+    const uint32_t pbits = npar - 1, cbits = 8 * npar - 1;
+    const uint32_t sent = T::kSent;
+    const uint64_t amask = !cmP ? 1ull : npar == 8 ? (~(uint64_t)cmP[0] & 0xFFull) : ~*(const uint64_t *)cmP;
+    n_act = __popcll(amask);
+    if (8 * n_act > n_left) return false;  // uniform
+    const uint32_t nch = 8 * npar, steps = (nch + 31) / 32;
+    const uint32_t grp = 0xFFu << (lane & 24u), lt = lanemask_lt();
+    bool bad = false;
+    for (uint32_t s = warp; s < steps; s += kRbWarps) {
+        const uint32_t q = 32 * s + lane;
+        const bool in = q < nch;
+        const uint32_t k = (q >> 3) & pbits, c = q & 7u;
+        const bool act = in && ((amask >> k) & 1ull);
+        uint32_t o = 0, ipl = 0;
+        if (act) {
+            const uint32_t j = __popcll(amask & ((1ull << k) - 1ull));
+            o = kSmemRec ? R[8 * j + c] : __ldg(R + 8 * j + c);
+            ipl = ip0 + (kSmemRec ? T8[j] : __ldg(T8 + j));
+        }
+        const uint32_t op = o & 7u, delta = o >> 4;
+        const uint32_t pam = __ballot_sync(kFull, act && op == OP_PA);
+        const uint32_t stm = __ballot_sync(kFull, act && (o & 8u));
+        const uint32_t ipc = ipl + __popc(pam & grp & lt);
+        const bool rx = act && op >= OP_RX && op <= OP_RZ;
+        const uint32_t a = (op - OP_RX) & 3u, ma = kMX << a;
+        const bool plus = rx && ((c >> a) & 1u);
+        const bool minus = rx && !plus;
+        uint32_t v = P[k];  // constant parent, or R_p
+        if (act && op >= OP_P0) v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);
+        if (plus) v = P[minc(k, ma) & pbits];
+        if (minus) v = sent + a;
+        bad |= act && ((plus && (k & ma & pbits) == (ma & pbits)) || (minus && (q & ma & cbits) == 0) || op == 7u ||
+                       (op == OP_PD && ipc < 1 + delta) || (op == OP_PA && ipc + 1 >= np) || (!cmC && (o & 8u)));
+        if (in) C[q] = (IdxT)v;
+        if (cmC && in && c == 0) cmC[k] = act ? (uint8_t)(stm >> (lane & 24u)) : (uint8_t)0xFF;
+        const uint32_t mm = __ballot_sync(kFull, minus);
+        if (lane == 0) ms->msk[s] = mm;
+    }
+    if (threadIdx.x == 0) ms->bad = 0;
+    __syncthreads();
+    if (bad) ms->bad = 1;
+    volatile IdxT *Cv = C;
+    for (uint32_t s = warp; s < steps; s += kRbWarps) {
+        if ((ms->msk[s] >> lane) & 1u) {
+            const uint32_t q = 32 * s + lane;
+            Cv[q] = (IdxT)chase<IdxT>(Cv, q, Cv[q], cbits);
+        }
+    }
+    __syncthreads();
+    return ms->bad == 0;
+}
+
+// Rebuild children level l from its parents, one thread per listed (non-constant) parent, the whole CTA
+// (see the file comment); returns false if the records are malformed.  R: this level's records (in
+// shared memory if kSmemRec); T8: P_a counts before every 8th record of the stream from R's first
+// record on; n_left: records of the stream from R on; ip0: i_p at the stream's start.  Sets n_act
+// (listed parents: 8 * n_act records were used).
+template <typename IdxT, bool kSmemRec>
+__device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
+                                              const uint8_t *R, const uint16_t *T8, uint32_t n_left, uint32_t ip0,
+                                              uint32_t np, uint32_t &n_act) {
+    typedef RbTraits<IdxT> T;
+    constexpr uint32_t nw = kRbWarps;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    IdxT *lev = (IdxT *)(smem + Ly.lev);
+    uint8_t *cm = smem + Ly.cm;
+    uint16_t *act = (uint16_t *)(smem + Ly.act);
+    RbMisc *ms = (RbMisc *)(smem + Ly.misc);
+    const uint32_t npar = 1u << (3 * (N - l - 1));  // >= 512
+    IdxT *P = lev + lev_off(N, l + 1);
+    IdxT *C = lev + lev_off(N, l);
+    const uint8_t *cmP = cm + cm_off(N, l + 1);  // l + 1 < N here
+    uint8_t *cmC = l >= 1 ? cm + cm_off(N, l) : nullptr;
+    const uint32_t pbits = npar - 1;  // Morton code bits of the parent level
     const uint32_t sent = T::kSent;
 
     // pass 1: children take the parent's index; each warp lists the non-constant parents of its
     // contiguous range of 32-parent blocks
-    const uint32_t nb = (npar + 31) / 32, bpw = (nb + nw - 1) / nw;
-    const uint32_t b0 = min(warp * bpw, nb), b1 = min(b0 + bpw, nb);
+    const uint32_t nb = npar / 32, bpw = nb / nw;
+    const uint32_t b0 = warp * bpw, b1 = b0 + bpw;
     uint16_t *mylist = act + 32 * b0;
     uint32_t cnt = 0;
     for (uint32_t b = b0; b < b1; b++) {
         const uint32_t k = 32 * b + lane;
-        const bool in = k < npar;
-        const uint32_t cw = !cmP ? 0u : npar >= 32 ? *(const uint32_t *)(cmP + 4 * b) : (uint32_t)cmP[0];
+        const uint32_t cw = *(const uint32_t *)(cmP + 4 * b);  // const bits of parents 32b .. 32b+31
         const bool pc = (cw >> lane) & 1u;
-        if (in) {
-            const uint32_t r = T::kRep * (uint32_t)P[k];
-            if (sizeof(IdxT) == 1) *(uint2 *)(C + 8 * k) = make_uint2(r, r);
-            else *(uint4 *)(C + 8 * k) = make_uint4(r, r, r, r);
-            if (cmC && pc) cmC[k] = 0xFF;
-        }
-        const uint32_t am = __ballot_sync(kFull, in && !pc);
-        if ((am >> lane) & 1u) mylist[cnt + __popc(am & lanemask_lt())] = (uint16_t)k;
-        cnt += __popc(am);
+        const uint32_t r = T::kRep * (uint32_t)P[k];
+        if (sizeof(IdxT) == 1) *(uint2 *)(C + 8 * k) = make_uint2(r, r);
+        else *(uint4 *)(C + 8 * k) = make_uint4(r, r, r, r);
+        if (cmC && pc) cmC[k] = 0xFF;
+        if (!pc) mylist[cnt + __popc(~cw & lt_of(lane))] = (uint16_t)k;
+        cnt += __popc(~cw);
     }
-    if (kWarp) {
-        __syncwarp();
-    } else {
-        if (lane == 0) ms->wcnt[warp] = cnt;
-        __syncthreads();
-    }
+    if (lane == 0) ms->wcnt[warp] = cnt;
+    __syncthreads();
 
     // pass 2: one thread per listed parent decodes its records whose op is not R_p
     uint32_t wbase[nw];  // first listed index of each warp's list
@@ -423,88 +486,80 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
 #pragma unroll
     for (uint32_t v = 0; v < nw; v++) {
         wbase[v] = n_act;
-        n_act += kWarp ? cnt : ms->wcnt[v];
+        n_act += ms->wcnt[v];
     }
     if (8 * n_act > n_left) return false;  // uniform: every thread sees the same counts
     const uint32_t nlb = (n_act + 31) / 32;
     uint8_t *mm = smem + Ly.mls;  // children toward -axis of listed parent j (bit c = child c)
     bool bad = false;
-    for (uint32_t b = warp; b < nlb; b += nw) {
-        const uint32_t j = 32 * b + lane;
-        const bool in = j < n_act;
+    auto parent_of = [&](uint32_t j) -> uint32_t {
         uint32_t w = 0;
 #pragma unroll
         for (uint32_t v = 1; v < nw; v++) w += j >= wbase[v] ? 1u : 0u;
         uint32_t wb = 0;
 #pragma unroll
         for (uint32_t v = 0; v < nw; v++) wb = v == w ? wbase[v] : wb;
-        const uint32_t k = in ? act[32 * bpw * w + (j - wb)] : 0u;
-        uint64_t r8 = 0;
-        uint32_t ipl = 0;
-        if (in) {
-            r8 = kSmemRec ? *(const uint64_t *)(R + 8 * j) : __ldg((const unsigned long long *)(R + 8 * j));
-            ipl = ip0 + (kSmemRec ? T8[j] : __ldg(T8 + j));
-        }
+        return act[32 * bpw * w + (j - wb)];
+    };
+    for (uint32_t b = warp; b < nlb; b += nw) {
+        const uint32_t j = 32 * b + lane;
+        if (j >= n_act) break;
+        const uint32_t k = parent_of(j);
+        const uint64_t r8 = kSmemRec ? *(const uint64_t *)(R + 8 * j) : __ldg((const unsigned long long *)(R + 8 * j));
+        const uint32_t ipl = ip0 + (kSmemRec ? T8[j] : __ldg(T8 + j));
         uint32_t nr, pm, st;
         rec_masks(r8, nr, pm, st);
-        if (in) {
-            if (cmC) cmC[k] = (uint8_t)st;
-            else bad |= st != 0;  // leaf stop bits are 0
-        }
+        if (cmC) cmC[k] = (uint8_t)st;
+        // checks that hold for the whole parent: no op 7, leaf stop bits 0, the last P_a inside the palette
+        const uint32_t lo = (uint32_t)r8, hi = (uint32_t)(r8 >> 32);
+        bad |= (((lo & 0x07070707u) + 0x01010101u) & 0x08080808u) != 0 ||
+               (((hi & 0x07070707u) + 0x01010101u) & 0x08080808u) != 0 || (!cmC && st != 0) ||
+               (pm != 0 && ipl + __popc(pm) >= np);
+        // per axis: parent on the brick's low face (-axis leaves the brick), on its high face (+axis)
+        const uint32_t lo3 = ((k & kMX & pbits) == 0 ? 1u : 0u) | ((k & kMY & pbits) == 0 ? 2u : 0u) |
+                             ((k & kMZ & pbits) == 0 ? 4u : 0u);
+        const uint32_t hi3 = ((k & kMX & pbits) == (kMX & pbits) ? 1u : 0u) |
+                             ((k & kMY & pbits) == (kMY & pbits) ? 2u : 0u) |
+                             ((k & kMZ & pbits) == (kMZ & pbits) ? 4u : 0u);
         uint32_t minus_m = 0;
         while (nr) {
             const uint32_t c = __ffs(nr) - 1;
             nr &= nr - 1;
-            const uint32_t o = (uint32_t)(r8 >> (8 * c)) & 0xFFu;
+            const uint32_t o = ((c & 4u ? hi : lo) >> (8 * (c & 3u))) & 0xFFu;
             const uint32_t op = o & 7u, delta = o >> 4;
             const uint32_t ipc = ipl + __popc(pm & ((1u << c) - 1u));
             const bool rx = op <= OP_RZ;  // R_x, R_y, R_z (op != R_p here)
-            const uint32_t a = (op - OP_RX) & 3u, ma = kMX << a;
+            const uint32_t a = (op - OP_RX) & 3u;
             const bool plus = rx && ((c >> a) & 1u);
             const bool minus = rx && !plus;
-            const uint32_t pv = P[minc(k, ma) & pbits];  // +axis: the neighbour's parent (R4)
+            const uint32_t pv = P[minc(k, kMX << a) & pbits];  // +axis: the neighbour's parent (R4)
             uint32_t v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);  // R1, R3
-            v = plus ? pv : v;
-            v = minus ? sent + a : v;
-            bad |= (plus && (k & ma & pbits) == (ma & pbits)) || (minus && ((8 * k + c) & ma & cbits) == 0) ||
-                   op == 7u || (op == OP_PD && ipc < 1 + delta) || (op == OP_PA && ipc + 1 >= np);
+            v = plus ? pv : minus ? sent + a : v;
+            bad |= (plus && ((hi3 >> a) & 1u)) || (minus && ((lo3 >> a) & 1u)) || (op == OP_PD && ipc < 1 + delta);
             C[8 * k + c] = (IdxT)v;
             minus_m |= (minus ? 1u : 0u) << c;
         }
-        if (in) mm[j] = (uint8_t)minus_m;
+        mm[j] = (uint8_t)minus_m;
     }
-    if (kWarp) {
-        __syncwarp();
-    } else {
-        if (threadIdx.x == 0) ms->bad = 0;
-        __syncthreads();
-        if (bad) ms->bad = 1;
-    }
+    if (threadIdx.x == 0) ms->bad = 0;
+    __syncthreads();
+    if (bad) ms->bad = 1;
 
     // pass 3: resolve the -axis children of this warp's listed parents (chains of at most 3 hops;
     // a target is final or a sentinel itself)
+    const uint32_t cbits = 8 * npar - 1;
     volatile IdxT *Cv = C;
     for (uint32_t b = warp; b < nlb; b += nw) {
         const uint32_t j = 32 * b + lane;
         uint32_t m = j < n_act ? mm[j] : 0u;
         if (!m) continue;
-        uint32_t w = 0;
-#pragma unroll
-        for (uint32_t v = 1; v < nw; v++) w += j >= wbase[v] ? 1u : 0u;
-        uint32_t wb = 0;
-#pragma unroll
-        for (uint32_t v = 0; v < nw; v++) wb = v == w ? wbase[v] : wb;
-        const uint32_t k = act[32 * bpw * w + (j - wb)];
+        const uint32_t k = parent_of(j);
         while (m) {
             const uint32_t c = __ffs(m) - 1;
             m &= m - 1;
             const uint32_t q = 8 * k + c;
             Cv[q] = (IdxT)chase<IdxT>(Cv, q, Cv[q], cbits);
         }
-    }
-    if (kWarp) {
-        __syncwarp();
-        return !__any_sync(kFull, bad);
     }
     __syncthreads();
     return ms->bad == 0;
@@ -541,7 +596,6 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     const uint16_t *t8i = (const uint16_t *)(base + J.t8_at), *t8l = (const uint16_t *)(base + J.t8_leaf_at);
 
     IdxT *lev = (IdxT *)(smem + Ly.lev);
-    RbMisc *ms = (RbMisc *)(smem + Ly.misc);
     uint32_t *pal_s = (uint32_t *)(smem + Ly.pal);
     // The interior stream (at most 8 records per parent of an interior level) and its P_a counts are
     // staged in the L0 area, which is free until the leaf level.
@@ -561,61 +615,35 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     if (threadIdx.x == 0) lev[lev_off(N, N)] = 0;
     __syncthreads();
 
-    // levels with few parents: warp 0 alone; (used, i_p at the stream start) handed over in shared memory
-    int l = (int)N - 1;
-    if (threadIdx.x < 32) {
-        uint32_t used = 0, ok = 1;
-        int ll = l;
-        for (; ll >= (int)t && (1u << (3 * (N - ll - 1))) <= kWarpLevelPar; ll--) {
-            const bool leaf = ll == 0;
-            if (leaf && used != info_int) {  // the leaf stream follows the complete interior stream
-                ok = 0;
-                break;
-            }
-            uint32_t n_act;
-            const bool good = leaf ? rebuild_level<IdxT, true, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf,
-                                                                      __ldg(t8i + info_int / 8), np, n_act)
-                                   : rebuild_level<IdxT, true, true>(smem, Ly, N, (uint32_t)ll, srec + used,
-                                                                     st8 + used / 8, info_int - used, 0u, np, n_act);
-            if (!good) {
-                ok = 0;
-                break;
-            }
-            const uint32_t u0 = leaf ? 0u : used;
-            used = u0 + 8 * n_act;
-        }
-        if (lane == 0) {
-            ms->used = used;
-            ms->bad = !ok;
-        }
-    }
-    __syncthreads();
-    if (ms->bad) return kStCorrupt;
-    uint32_t used = ms->used;
-    while (l >= (int)t && (1u << (3 * (N - l - 1))) <= kWarpLevelPar) l--;
-    if (t == 0 && l >= 0) {  // warm L1 with the leaf stream's records and P_a counts
-        const uint8_t *lr = base + J.leaf_at;
-        for (uint32_t q = 128 * threadIdx.x; q < info_leaf; q += 128 * kRbThreads)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(lr + q));
-        const uint8_t *lt = (const uint8_t *)t8l;
-        for (uint32_t q = 128 * threadIdx.x; q < 2 * (info_leaf / 8 + 1); q += 128 * kRbThreads)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(lt + q));
-    }
-    __syncthreads();  // everyone has read ms before a level may write it
-    for (; l >= (int)t; l--) {
+    uint32_t used = 0;  // records of the current stream consumed
+    for (int l = (int)N - 1; l >= (int)t; l--) {
+        const bool small = (1u << (3 * (N - l - 1))) <= kSmallPar;
         uint32_t n_act;
-        if (l == 0) {
+        bool good;
+        if (l == 0) {  // the leaf stream follows the complete interior stream
             if (used != info_int) return kStCorrupt;
-            if (!rebuild_level<IdxT, false, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf,
-                                                   __ldg(t8i + info_int / 8), np, n_act))
-                return kStCorrupt;
+            const uint32_t ip0 = __ldg(t8i + info_int / 8);
+            good = small ? rebuild_small_level<IdxT, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0,
+                                                            np, n_act)
+                         : rebuild_level<IdxT, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0, np,
+                                                      n_act);
             used = 8 * n_act;
         } else {
-            if (!rebuild_level<IdxT, false, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
-                                                  info_int - used, 0u, np, n_act))
-                return kStCorrupt;
+            if (l == 1 && t == 0) {  // warm L1 with the leaf stream's records and P_a counts
+                const uint8_t *lr = base + J.leaf_at;
+                for (uint32_t q = 128 * threadIdx.x; q < info_leaf; q += 128 * kRbThreads)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(lr + q));
+                const uint8_t *lt8 = (const uint8_t *)t8l;
+                for (uint32_t q = 128 * threadIdx.x; q < 2 * (info_leaf / 8 + 1); q += 128 * kRbThreads)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(lt8 + q));
+            }
+            good = small ? rebuild_small_level<IdxT, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
+                                                           info_int - used, 0u, np, n_act)
+                         : rebuild_level<IdxT, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
+                                                     info_int - used, 0u, np, n_act);
             used += 8 * n_act;
         }
+        if (!good) return kStCorrupt;
     }
     if ((t == 1 && used != info_int) || (t == 0 && used != info_leaf)) return kStCorrupt;
 

@@ -1,26 +1,28 @@
 // encode.cu -- brick encoder (Alg. 2 of the paper), frequency prepass and
 // packing for sm_103a.
 //
-// One CTA encodes one brick:
-//   A. pyramid (Sec. 3.1): L1 from the volume in global memory, L2..LN in
-//      shared memory; each node is the most frequent of its 8 children, ties
-//      to the first occurrence in the child array (Sec. 3.4), plus a
-//      constant-subtree flag.
+// encode_kernel: one CTA of 256 threads per brick:
+//   A. pyramid (Sec. 3.1): L1 from the volume (16-byte row loads for bricks
+//      inside an aligned volume), L2..LN in shared memory; each node is the
+//      most frequent of its 8 children, ties to the first occurrence in the
+//      child array (Sec. 3.4), plus a constant-subtree flag.
 //   B. per level, the list of active (non-constant) parents in Morton order
 //      and, for each of their children in parallel, the first applicable
 //      reuse operation R_p, R_x, R_y, R_z (Sec. 3.2, reading R4); children
 //      no reuse fits are marked for the palette pass.
-//   C. palette pass: one warp walks the marked children in stream order with
-//      the last 17 palette entries in registers (lane i holds palette[i_p-i]):
-//      a ballot finds P_0 (lane 0) or the smallest P_delta (lanes 1..16);
-//      otherwise P_a appends the label (Sec. 3.2, bestOperation order).
-//   D. nibble positions (one extra nibble after each P_delta, reading R18)
-//      by warp scans; interior and leaf nibbles written to scratch, or only
+//   C. palette pass: the marked children are gathered in stream order, then
+//      one warp walks them with the last 17 palette entries in registers
+//      (lane i holds palette[i_p-i]): a ballot finds P_0 (lane 0) or the
+//      smallest P_delta (lanes 1..16); otherwise P_a appends the label (Sec.
+//      3.2, bestOperation order).
+//   D. nibble positions (one extra nibble after each P_delta, reading R18):
+//      a nibble's position is its op's index in its stream plus the P_delta
+//      ops before it; interior and leaf nibbles go to scratch, or are only
 //      counted in the prepass (Sec. 3.4).
-//   E. rANS: one warp per stream, K interleaved states in lanes, symbols in
-//      reverse; renormalisation words are pushed downward from the top of
-//      the scratch area so that the decoder reads them forward in lane order
-//      (Sec. 3.3, readings R9/R10).
+// rans_encode_kernel: one warp per stream, K interleaved states in lanes,
+//   symbols in reverse; renormalisation words are pushed downward from the
+//   top of the scratch area so that the decoder reads them forward in lane
+//   order (Sec. 3.3, readings R9/R10).
 // A scan kernel turns per-brick sizes into offsets and a compaction kernel
 // packs palettes and words into the volume's arrays.
 #include "encode_api.cuh"
@@ -29,7 +31,9 @@ namespace csgv {
 
 constexpr uint32_t kEncThreads = 256;
 constexpr uint32_t kEncWarps = kEncThreads / 32;
-constexpr uint32_t kNeedPal = 7;  // op placeholder: no reuse operation applies
+constexpr uint32_t kNeedPal = 7;       // op placeholder: no reuse operation applies
+constexpr uint32_t kRansEncWarps = 16;  // rans_encode_kernel: one stream per warp
+constexpr uint32_t kRansEncWin = 2048;  // staged symbols per warp (bytes)
 
 namespace {
 
@@ -50,21 +54,31 @@ __device__ __forceinline__ uint32_t compact5(uint32_t m) {
 __device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
 __device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
 
-// most frequent of 8 labels, ties to the first occurrence (Sec. 3.4)
-__device__ __forceinline__ uint32_t mode8(const uint32_t w[8], bool &all_equal) {
-    uint32_t best = w[0];
-    int best_cnt = 0;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        int cnt = 0;
-#pragma unroll
-        for (int d = 0; d < 8; d++) cnt += (w[d] == w[c]);
-        if (cnt > best_cnt) {
-            best_cnt = cnt;
-            best = w[c];
+// Most frequent of 8 labels, ties to the first occurrence (Sec. 3.4): the distinct values are visited in
+// order of first occurrence and a later one wins only with a strictly larger count.
+__device__ __forceinline__ uint32_t mode8(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t w4, uint32_t w5,
+                                         uint32_t w6, uint32_t w7, bool &all_equal) {
+    uint32_t rem = 0xFFu, best = w0, bestc = 0;
+    while (rem) {
+        const uint32_t c = __ffs(rem) - 1;
+        uint32_t v = w0;
+        v = c == 1 ? w1 : v;
+        v = c == 2 ? w2 : v;
+        v = c == 3 ? w3 : v;
+        v = c == 4 ? w4 : v;
+        v = c == 5 ? w5 : v;
+        v = c == 6 ? w6 : v;
+        v = c == 7 ? w7 : v;
+        const uint32_t m = (w0 == v ? 1u : 0u) | (w1 == v ? 2u : 0u) | (w2 == v ? 4u : 0u) | (w3 == v ? 8u : 0u) |
+                           (w4 == v ? 16u : 0u) | (w5 == v ? 32u : 0u) | (w6 == v ? 64u : 0u) | (w7 == v ? 128u : 0u);
+        const uint32_t cnt = __popc(m);
+        if (cnt > bestc) {
+            bestc = cnt;
+            best = v;
         }
+        rem &= ~m;
     }
-    all_equal = best_cnt == 8;
+    all_equal = bestc == 8;
     return best;
 }
 
@@ -72,14 +86,15 @@ struct Brick {
     const uint32_t *vol;
     uint64_t X, Y, Z;
     uint64_t gx0, gy0, gz0;  // brick origin
+    const uint32_t *base;    // voxel (gx0, gy0, gz0)
+    uint64_t sy, sz;         // element strides of y and z
     bool interior;           // no clamping needed
     __device__ __forceinline__ uint32_t at(uint32_t x, uint32_t y, uint32_t z) const {
+        if (interior) return __ldg(base + x + sy * y + sz * z);
         uint64_t gx = gx0 + x, gy = gy0 + y, gz = gz0 + z;
-        if (!interior) {
-            gx = gx < X ? gx : X - 1;
-            gy = gy < Y ? gy : Y - 1;
-            gz = gz < Z ? gz : Z - 1;
-        }
+        gx = gx < X ? gx : X - 1;
+        gy = gy < Y ? gy : Y - 1;
+        gz = gz < Z ? gz : Z - 1;
         return __ldg(vol + gx + X * (gy + Y * gz));
     }
 };
@@ -91,9 +106,8 @@ struct EncSmem {
     uint16_t *list;    // active parents per parent level (same offsets as lab)
     uint8_t *ops;      // ops_cap op bytes: op | stop<<3 | delta<<4
     uint32_t *red;     // block scan scratch (64 words)
-    uint2 *plist;      // children that need a palette op: (op index, label), one 256-op chunk at a time
+    uint2 *plist;      // children that need a palette op: (op index, label), 256 at a time
     __device__ EncSmem(uint8_t *s, const EncGeom &G) {
-        // every region starts on a 16-byte boundary (the rANS phase stages symbols with 16-byte stores)
         lab = (uint32_t *)s;
         cst = (uint8_t *)s + r16(G.up_nodes * 4);
         list = (uint16_t *)(cst + r16(G.up_nodes));
@@ -125,17 +139,26 @@ __device__ __forceinline__ uint32_t block_excl_warp(uint32_t *red, uint32_t warp
     return off;
 }
 
+// offset of level l (1..N) in the level arrays (the same as EncGeom::off, without indexing a kernel parameter)
+__device__ __forceinline__ uint32_t loff(uint32_t N, uint32_t l) {
+    uint32_t u = 0;
+#pragma unroll
+    for (uint32_t k = 1; k <= (uint32_t)kMaxN; k++)
+        if (k < l) u += 1u << (3 * (N - k));
+    return u;
+}
+
 // label of node q (Morton) on level l of the brick
 __device__ __forceinline__ uint32_t node_label(const Brick &B, const EncSmem &S, const EncGeom &G, uint32_t l,
                                                uint32_t q) {
     if (l == 0) return B.at(compact5(q), compact5(q >> 1), compact5(q >> 2));
-    return S.lab[G.off[l] + q];
+    return S.lab[loff(G.N, l) + q];
 }
 
-// Encode (or, when count != nullptr, only count the nibbles of) one brick.
+// Encode (or, when count != nullptr, only count the nibbles of) one brick: phases A-D.
 __global__ void __launch_bounds__(kEncThreads)
     encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
-                  const uint32_t *freq, EncScratch SC, unsigned long long *count) {
+                  EncScratch SC, unsigned long long *count) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     EncSmem S(smem_raw, G);
     __shared__ uint32_t hist[32];
@@ -153,36 +176,54 @@ __global__ void __launch_bounds__(kEncThreads)
     const uint64_t bx = id % EV.nb[0], by = (id / EV.nb[0]) % EV.nb[1], bz = id / (EV.nb[0] * EV.nb[1]);
     B.gx0 = bx * b; B.gy0 = by * b; B.gz0 = bz * b;
     B.interior = B.gx0 + b <= B.X && B.gy0 + b <= B.Y && B.gz0 + b <= B.Z;
+    B.sy = B.X;
+    B.sz = B.X * B.Y;
+    B.base = B.vol + B.gx0 + B.X * (B.gy0 + B.Y * B.gz0);
     if (tid < 32) hist[tid] = 0;
 
     // ---- A. pyramid
     {
-        const uint32_t B1 = b >> 1, n1 = B1 * B1 * B1;
-#pragma unroll 2
-        for (uint32_t i = tid; i < n1; i += kEncThreads) {
-            const uint32_t x = i % B1, y = (i / B1) % B1, z = i / (B1 * B1);
-            uint32_t w[8];
-#pragma unroll
-            for (int c = 0; c < 8; c++) w[c] = B.at(2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + ((c >> 2) & 1));
-            bool eq;
-            const uint32_t m = morton3(x, y, z);
-            S.lab[G.off[1] + m] = mode8(w, eq);
-            S.cst[G.off[1] + m] = eq;
+        const uint32_t h = N - 1;  // log2 of the L1 side
+        const bool vec = B.interior && N >= 2 && (B.X & 3u) == 0 && (reinterpret_cast<uintptr_t>(B.vol) & 15u) == 0;
+        if (vec) {
+            // two x-neighbouring L1 nodes per thread: four 16-byte rows (y, z) of 4 voxels
+            const uint32_t npairs = 1u << (3 * h - 1);
+            for (uint32_t i = tid; i < npairs; i += kEncThreads) {
+                const uint32_t x2 = i & ((1u << (h - 1)) - 1u), y = (i >> (h - 1)) & ((1u << h) - 1u),
+                               z = i >> (2 * h - 1);
+                const uint32_t *r = B.base + B.sz * (2 * z) + B.sy * (2 * y) + 4 * x2;
+                const uint4 a = __ldg((const uint4 *)r), bb = __ldg((const uint4 *)(r + B.sy)),
+                            c = __ldg((const uint4 *)(r + B.sz)), d = __ldg((const uint4 *)(r + B.sz + B.sy));
+                bool e0, e1;
+                const uint32_t m = loff(G.N, 1) + morton3(2 * x2, y, z);
+                S.lab[m] = mode8(a.x, a.y, bb.x, bb.y, c.x, c.y, d.x, d.y, e0);
+                S.cst[m] = e0;
+                S.lab[m + 1] = mode8(a.z, a.w, bb.z, bb.w, c.z, c.w, d.z, d.w, e1);
+                S.cst[m + 1] = e1;
+            }
+        } else {
+            const uint32_t n1 = 1u << (3 * h);
+            for (uint32_t i = tid; i < n1; i += kEncThreads) {
+                const uint32_t x = i & ((1u << h) - 1u), y = (i >> h) & ((1u << h) - 1u), z = i >> (2 * h);
+                bool eq;
+                const uint32_t m = loff(G.N, 1) + morton3(x, y, z);
+                S.lab[m] = mode8(B.at(2 * x, 2 * y, 2 * z), B.at(2 * x + 1, 2 * y, 2 * z), B.at(2 * x, 2 * y + 1, 2 * z),
+                                 B.at(2 * x + 1, 2 * y + 1, 2 * z), B.at(2 * x, 2 * y, 2 * z + 1),
+                                 B.at(2 * x + 1, 2 * y, 2 * z + 1), B.at(2 * x, 2 * y + 1, 2 * z + 1),
+                                 B.at(2 * x + 1, 2 * y + 1, 2 * z + 1), eq);
+                S.cst[m] = eq;
+            }
         }
         __syncthreads();
         for (uint32_t l = 2; l <= N; l++) {
-            const uint32_t Bl = b >> l, nl = Bl * Bl * Bl;
+            const uint32_t nl = 1u << (3 * (N - l));
             for (uint32_t i = tid; i < nl; i += kEncThreads) {
-                uint32_t w[8];
-                bool allc = true;
-#pragma unroll
-                for (int c = 0; c < 8; c++) {
-                    w[c] = S.lab[G.off[l - 1] + 8 * i + c];
-                    allc = allc && S.cst[G.off[l - 1] + 8 * i + c];
-                }
+                const uint32_t *w = S.lab + loff(G.N, l - 1) + 8 * i;
+                const uint2 cs = *(const uint2 *)(S.cst + loff(G.N, l - 1) + 8 * i);  // 8 flags, 0 or 1 each
+                const bool allc = (cs.x & cs.y) == 0x01010101u;
                 bool eq;
-                S.lab[G.off[l] + i] = mode8(w, eq);
-                S.cst[G.off[l] + i] = eq && allc;
+                S.lab[loff(G.N, l) + i] = mode8(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], eq);
+                S.cst[loff(G.N, l) + i] = eq && allc;
             }
             __syncthreads();
         }
@@ -191,17 +232,23 @@ __global__ void __launch_bounds__(kEncThreads)
     // ---- B. active parent lists and reuse operations, level by level (Alg. 2 traversal)
     uint32_t n_ops = 0, n_int_ops = 0;
     for (uint32_t l = N; l >= 1; l--) {
-        const uint32_t Bl = b >> l, nl = Bl * Bl * Bl;
-        // compact the active parents of level l (Morton order)
-        uint32_t n_act = 0;
-        for (uint32_t g = 0; g < nl; g += kEncThreads) {
-            const uint32_t i = g + tid;
-            const bool act = i < nl && !S.cst[G.off[l] + i];
+        const uint32_t nl = 1u << (3 * (N - l));
+        // compact the active parents of level l (Morton order): each warp a contiguous range of 32-blocks
+        const uint32_t nblk = (nl + 31) / 32, bpw = (nblk + kEncWarps - 1) / kEncWarps;
+        const uint32_t b0 = min(warp * bpw, nblk), b1 = min(b0 + bpw, nblk);
+        uint32_t cnt = 0;
+        for (uint32_t bk = b0; bk < b1; bk++) {
+            const uint32_t i = 32 * bk + lane;
+            cnt += __popc(__ballot_sync(kFull, i < nl && !S.cst[loff(G.N, l) + i]));
+        }
+        uint32_t n_act;
+        uint32_t wb = block_excl_warp(S.red, cnt, n_act);
+        for (uint32_t bk = b0; bk < b1; bk++) {
+            const uint32_t i = 32 * bk + lane;
+            const bool act = i < nl && !S.cst[loff(G.N, l) + i];
             const uint32_t m = __ballot_sync(kFull, act);
-            uint32_t tot;
-            const uint32_t woff = block_excl_warp(S.red, __popc(m), tot);
-            if (act) S.list[G.off[l] + n_act + woff + __popc(m & lanemask_lt())] = (uint16_t)i;
-            n_act += tot;
+            if (act) S.list[loff(G.N, l) + wb + __popc(m & lanemask_lt())] = (uint16_t)i;
+            wb += __popc(m);
         }
         __syncthreads();
         const uint32_t lc = l - 1;
@@ -212,27 +259,45 @@ __global__ void __launch_bounds__(kEncThreads)
         }
         const uint32_t cbits = (1u << (3 * (N - lc))) - 1u;  // Morton code bits of the child level
         for (uint32_t j = tid; j < nops_l; j += kEncThreads) {
-            const uint32_t p = S.list[G.off[l] + (j >> 3)], c = j & 7u;
+            const uint32_t p = S.list[loff(G.N, l) + (j >> 3)], c = j & 7u;
             const uint32_t q = 8 * p + c;
             // every label the choice can look at, loaded up front (independent loads); a neighbour index
             // that would leave the brick wraps to an in-brick node and is ignored through ok[]
-            uint32_t nv[3];
-            bool ok[3];
-#pragma unroll
-            for (uint32_t a = 0; a < 3; a++) {
-                const uint32_t ma = (kMX << a) & cbits;
-                const bool minus = ((c >> a) & 1u) == 0;
-                ok[a] = minus ? (q & ma) != 0 : (q & ma) != ma;
-                nv[a] = minus ? node_label(B, S, G, lc, mdec(q, ma)) : S.lab[G.off[l] + (minc(q, ma) >> 3)];
+            uint32_t v, nv0, nv1, nv2;
+            bool ok0, ok1, ok2;
+            const uint32_t mx_ = kMX & cbits, my_ = kMY & cbits, mz_ = kMZ & cbits;
+            const bool mx = (c & 1u) == 0, my = (c & 2u) == 0, mz = (c & 4u) == 0;
+            // +axis: the neighbour's parent; -axis: the node before along the axis on the child level, when
+            // inside the brick (an index leaving the brick wraps to an in-brick node and is ignored)
+            const uint32_t px = S.lab[loff(G.N, l) + (minc(q, mx_) >> 3)], py = S.lab[loff(G.N, l) + (minc(q, my_) >> 3)],
+                           pz = S.lab[loff(G.N, l) + (minc(q, mz_) >> 3)];
+            if (lc == 0 && B.interior) {
+                const uint32_t x = 2 * compact5(p) + (c & 1u), y = 2 * compact5(p >> 1) + ((c >> 1) & 1u),
+                               z = 2 * compact5(p >> 2) + (c >> 2);
+                const uint32_t *r = B.base + B.sz * z + B.sy * y + x;
+                v = __ldg(r);
+                ok0 = mx ? x != 0 : (q & mx_) != mx_;
+                ok1 = my ? y != 0 : (q & my_) != my_;
+                ok2 = mz ? z != 0 : (q & mz_) != mz_;
+                nv0 = mx ? __ldg(x != 0 ? r - 1 : r) : px;
+                nv1 = my ? __ldg(y != 0 ? r - B.sy : r) : py;
+                nv2 = mz ? __ldg(z != 0 ? r - B.sz : r) : pz;
+            } else {
+                v = node_label(B, S, G, lc, q);
+                ok0 = mx ? (q & mx_) != 0 : (q & mx_) != mx_;
+                ok1 = my ? (q & my_) != 0 : (q & my_) != my_;
+                ok2 = mz ? (q & mz_) != 0 : (q & mz_) != mz_;
+                nv0 = mx ? node_label(B, S, G, lc, mdec(q, mx_)) : px;
+                nv1 = my ? node_label(B, S, G, lc, mdec(q, my_)) : py;
+                nv2 = mz ? node_label(B, S, G, lc, mdec(q, mz_)) : pz;
             }
-            const uint32_t v = node_label(B, S, G, lc, q);
-            const uint32_t parent = S.lab[G.off[l] + p];
-            const uint32_t stop = lc >= 1 ? (uint32_t)S.cst[G.off[lc] + q] : 0u;
+            const uint32_t parent = S.lab[loff(G.N, l) + p];
+            const uint32_t stop = lc >= 1 ? (uint32_t)S.cst[loff(G.N, lc) + q] : 0u;
             // first applicable reuse: R_p, R_x, R_y, R_z (bestOperation order)
             const uint32_t op = v == parent ? OP_RP
-                                : (ok[0] && nv[0] == v) ? OP_RX
-                                : (ok[1] && nv[1] == v) ? OP_RY
-                                : (ok[2] && nv[2] == v) ? OP_RZ
+                                : (ok0 && nv0 == v) ? OP_RX
+                                : (ok1 && nv1 == v) ? OP_RY
+                                : (ok2 && nv2 == v) ? OP_RZ
                                 : kNeedPal;
             S.ops[n_ops + j] = (uint8_t)(op | (stop << 3));
         }
@@ -241,33 +306,51 @@ __global__ void __launch_bounds__(kEncThreads)
         __syncthreads();
     }
 
-    // ---- C. palette pass in stream order: all warps collect the children no reuse fits (with their
-    // labels), 256 ops at a time; warp 0 then walks them in order with the last 17 palette entries in
-    // registers (lane i holds palette[i_p - i])
+    // each warp takes a contiguous range of the op array in phases C and D
+    const uint32_t per = ((n_ops + kEncWarps - 1) / kEncWarps + 31) & ~31u;
+    const uint32_t j0 = min(warp * per, n_ops), j1 = min(j0 + per, n_ops);
+
+    // ---- C. palette pass in stream order: the children no reuse fits are gathered with their labels, 256
+    // at a time; warp 0 then walks them in order with the last 17 palette entries in registers (lane i
+    // holds palette[i_p - i])
     {
-        const uint32_t root = S.lab[G.off[N]];
+        uint32_t cnt = 0;
+        for (uint32_t g = j0; g < j1; g += 32) {
+            const uint32_t j = g + lane;
+            cnt += __popc(__ballot_sync(kFull, j < j1 && (S.ops[j] & 7u) == kNeedPal));
+        }
+        uint32_t total;
+        const uint32_t wbase = block_excl_warp(S.red, cnt, total);
+        const uint32_t root = S.lab[loff(G.N, N)];
         uint32_t win = root;
         uint32_t ip = 0, np = 1;  // i_p and palette size (kept by warp 0)
         uint32_t *pal = count ? nullptr : SC.pal + (size_t)slot * G.pal_cap;
         if (pal && tid == 0) pal[0] = root;
-        for (uint32_t g = 0; g < n_ops; g += kEncThreads) {
-            const uint32_t j = g + tid;
-            const bool need = j < n_ops && (S.ops[j] & 7u) == kNeedPal;
-            const uint32_t m = __ballot_sync(kFull, need);
-            uint32_t tot;
-            const uint32_t woff = block_excl_warp(S.red, __popc(m), tot);
-            if (tot == 0) continue;
-            if (need) {
-                uint32_t l = 1;
-                for (uint32_t L = N; L >= 2; L--)
-                    if (j >= lvl_base[L] && j < lvl_base[L] + 8 * lvl_nact[L]) l = L;
-                const uint32_t base = lvl_base[l];
-                const uint32_t p = S.list[G.off[l] + ((j - base) >> 3)];
-                S.plist[woff + __popc(m & lanemask_lt())] = make_uint2(j, node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u)));
+        for (uint32_t r0 = 0; r0 < total; r0 += 256) {
+            if (wbase < r0 + 256 && wbase + cnt > r0) {
+                uint32_t rank = wbase;
+                for (uint32_t g = j0; g < j1; g += 32) {
+                    const uint32_t j = g + lane;
+                    // ranks count every child gathered in any round: children of earlier rounds already carry
+                    // their palette op (P_0, P_delta or P_a), the others still the placeholder
+                    const bool need = j < j1 && (S.ops[j] & 7u) >= OP_P0;
+                    const uint32_t m = __ballot_sync(kFull, need);
+                    const uint32_t rk = rank + __popc(m & lanemask_lt());
+                    if (need && rk >= r0 && rk < r0 + 256) {
+                        uint32_t l = 1;
+                        for (uint32_t L = N; L >= 2; L--)
+                            if (j >= lvl_base[L] && j < lvl_base[L] + 8 * lvl_nact[L]) l = L;
+                        const uint32_t base = lvl_base[l];
+                        const uint32_t p = S.list[loff(G.N, l) + ((j - base) >> 3)];
+                        S.plist[rk - r0] = make_uint2(j, node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u)));
+                    }
+                    rank += __popc(m);
+                }
             }
             __syncthreads();
             if (warp == 0) {
-                for (uint32_t k = 0; k < tot; k++) {
+                const uint32_t nk = min(256u, total - r0);
+                for (uint32_t k = 0; k < nk; k++) {
                     const uint2 e = S.plist[k];
                     const uint32_t vk = e.y;
                     const bool match = lane <= 16 && lane <= ip && win == vk;
@@ -294,74 +377,46 @@ __global__ void __launch_bounds__(kEncThreads)
     }
     __syncthreads();
 
-    // ---- D. nibble positions: per op 1 nibble, +1 after P_delta; each warp takes a contiguous range
+    // ---- D. nibble positions: an op's index in its stream plus the P_delta ops before it in that stream
     uint32_t sym_tot[2];
     {
-        const uint32_t per = ((n_ops + kEncWarps - 1) / kEncWarps + 31) & ~31u;
-        const uint32_t j0 = warp * per, j1 = min(n_ops, j0 + per);
-        // pass 1: symbols of this warp's range in each stream
-        uint32_t cnt[2] = {0, 0};
+        uint32_t pdi = 0, pdl = 0;
         for (uint32_t g = j0; g < j1; g += 32) {
             const uint32_t j = g + lane;
-            const bool in = j < j1;
-            const uint32_t o = in ? S.ops[j] : 0u;
-            const uint32_t s = in ? 1u + ((o & 7u) == OP_PD) : 0u;
-            const bool leaf = j >= n_int_ops;
-            uint32_t tot = s;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(kFull, tot, d);
-            uint32_t tl = leaf ? s : 0u;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) tl += __shfl_xor_sync(kFull, tl, d);
-            cnt[1] += tl;
-            cnt[0] += tot - tl;
+            const bool pd = j < j1 && (S.ops[j] & 7u) == OP_PD;
+            pdi += __popc(__ballot_sync(kFull, pd && j < n_int_ops));
+            pdl += __popc(__ballot_sync(kFull, pd && j >= n_int_ops));
         }
-        uint32_t base[2];
-        for (int st = 0; st < 2; st++) base[st] = block_excl_warp(S.red, cnt[st], sym_tot[st]);
-        // pass 2: write or count
-        uint32_t run[2] = {base[0], base[1]};
-        uint8_t *nib[2] = {nullptr, nullptr};
-        if (!count) {
-            nib[0] = SC.nib_int + (size_t)slot * G.int_cap;
-            nib[1] = SC.nib_leaf + (size_t)slot * G.leaf_cap;
-        }
+        uint32_t toti, totl;
+        uint32_t bi = block_excl_warp(S.red, pdi, toti);
+        uint32_t bl = block_excl_warp(S.red, pdl, totl);
+        sym_tot[0] = n_int_ops + toti;
+        sym_tot[1] = n_ops - n_int_ops + totl;
+        uint8_t *nib_i = count ? nullptr : SC.nib_int + (size_t)slot * G.int_cap;
+        uint8_t *nib_l = count ? nullptr : SC.nib_leaf + (size_t)slot * G.leaf_cap;
         for (uint32_t g = j0; g < j1; g += 32) {
             const uint32_t j = g + lane;
             const bool in = j < j1;
             const uint32_t o = in ? S.ops[j] : 0u;
             const uint32_t op = o & 7u;
             const bool pd = in && op == OP_PD;
-            const uint32_t s = in ? 1u + pd : 0u;
-            const uint32_t st = j >= n_int_ops ? 1u : 0u;
-            // inclusive scan of s among lanes of the same stream (streams split the range at most once)
-            uint32_t inc = s;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t u = __shfl_up_sync(kFull, inc, d);
-                const uint32_t ust = __shfl_up_sync(kFull, st, d);
-                if (lane >= (uint32_t)d && ust == st) inc += u;
-            }
-            const uint32_t pos = run[st] + inc - s;
+            const bool leaf = j >= n_int_ops;
+            const uint32_t mi = __ballot_sync(kFull, pd && !leaf), ml = __ballot_sync(kFull, pd && leaf);
+            const uint32_t pos = leaf ? j - n_int_ops + bl + __popc(ml & lanemask_lt()) : j + bi + __popc(mi & lanemask_lt());
             const uint32_t nibble = op | (o & 8u);
             const uint32_t delta = o >> 4;
             if (in) {
                 if (count) {
-                    atomicAdd(&hist[16 * st + nibble], 1u);
-                    if (pd) atomicAdd(&hist[16 * st + delta], 1u);
+                    atomicAdd(&hist[16 * leaf + nibble], 1u);
+                    if (pd) atomicAdd(&hist[16 * leaf + delta], 1u);
                 } else {
-                    nib[st][pos] = (uint8_t)nibble;
-                    if (pd) nib[st][pos + 1] = (uint8_t)delta;
+                    uint8_t *nb = leaf ? nib_l : nib_i;
+                    nb[pos] = (uint8_t)nibble;
+                    if (pd) nb[pos + 1] = (uint8_t)delta;
                 }
             }
-            // advance both runs by this tile's totals per stream
-            uint32_t t0 = st == 0 ? s : 0u, t1 = st == 1 ? s : 0u;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                t0 += __shfl_xor_sync(kFull, t0, d);
-                t1 += __shfl_xor_sync(kFull, t1, d);
-            }
-            run[0] += t0;
-            run[1] += t1;
+            bi += __popc(mi);
+            bl += __popc(ml);
         }
     }
     if (count) {
@@ -369,83 +424,87 @@ __global__ void __launch_bounds__(kEncThreads)
         if (tid < 32 && hist[tid]) atomicAdd(count + tid, (unsigned long long)hist[tid]);
         return;
     }
-    __syncthreads();  // nibbles visible to the rANS warps
-
-    // ---- E. rANS, one warp per stream; the symbols are staged in shared memory (the op array is free now)
-    if (warp < 2) {
-        const uint32_t st = warp;
-        const uint32_t n = sym_tot[st];
-        const uint32_t cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
-        uint16_t *words = (st == 0 ? SC.w_int : SC.w_leaf) + (size_t)slot * cap;
-        const uint8_t *nib = st == 0 ? SC.nib_int + (size_t)slot * G.int_cap : SC.nib_leaf + (size_t)slot * G.leaf_cap;
-        const uint32_t half = (G.ops_cap / 2) & ~15u;  // staging bytes per stream
-        uint8_t *wsm = S.ops + st * half;
-        const uint32_t *F = freq + 16 * st;
-        const uint32_t f_reg = lane < 16 ? F[lane] : 1u;
-        const float rcp_reg = 1.0f / (float)f_reg;
-        uint32_t c_reg = 0;
-        for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < lane) ? F[s2] : 0u;
-        const uint32_t K = lanes_for(n, G.K_max, G.S_min);
-        uint32_t top = cap;
-        if (n > 0) {
-            uint32_t x = kL;
-            const uint32_t steps = (n + K - 1) / K;
-            const uint32_t win_steps = (half - 16) / K;  // steps per staged window (16 bytes of alignment slack)
-            // windows of steps from the end: [s_lo, s_hi) covers symbols [s_lo*K, min(n, s_hi*K))
-            for (uint32_t s_hi = steps; s_hi > 0;) {
-                const uint32_t s_lo = s_hi > win_steps ? s_hi - win_steps : 0u;
-                const uint32_t lo16 = (s_lo * K) & ~15u, sym_hi = min(n, s_hi * K);
-                for (uint32_t c16 = lane; lo16 + 16 * c16 < sym_hi; c16 += 32)
-                    reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(nib + lo16) + c16);
-                __syncwarp();
-                for (uint32_t s2 = s_hi; s2-- > s_lo;) {
-                    const uint32_t i = s2 * K + lane;
-                    const bool act = lane < K && i < n;
-                    const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
-                    const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
-                    const float rf = __shfl_sync(kFull, rcp_reg, sym);
-                    // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
-                    const bool emit = act && x >= (f << 20);
-                    const uint32_t m = __ballot_sync(kFull, emit);
-                    if (emit) {
-                        words[top - __popc(m) + __popc(m & lanemask_lt())] = (uint16_t)(x & 0xFFFFu);
-                        x >>= 16;
-                    }
-                    top -= __popc(m);
-                    if (act) {
-                        // x / f through a float reciprocal: here x < f * 2^20, so the estimate is within one of
-                        // the quotient; the integer remainder check makes it exact
-                        uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
-                        int32_t r = (int32_t)(x - qt * f);
-                        if (r < 0) { qt -= 1; r += (int32_t)f; }
-                        if (r < 0) { qt -= 1; r += (int32_t)f; }
-                        if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-                        if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-                        x = qt * kM + (uint32_t)r + c;
-                    }
-                }
-                __syncwarp();
-                s_hi = s_lo;
-            }
-            // final states ahead of the words, state 0 first, low half first
-            if (lane < K) {
-                words[top - 2 * K + 2 * lane] = (uint16_t)(x & 0xFFFFu);
-                words[top - 2 * K + 2 * lane + 1] = (uint16_t)(x >> 16);
-            }
-            top -= 2 * K;
-        }
-        if (lane == 0) {
-            uint32_t *sz = SC.sizes + (size_t)slot * 8;
-            sz[3 + st] = cap - top;  // words
-            sz[5 + st] = top;        // start inside the scratch area
-        }
-    }
     if (tid == 0) {
         uint32_t *sz = SC.sizes + (size_t)slot * 8;
         sz[0] = sh_np;
         sz[1] = sym_tot[0];
         sz[2] = sym_tot[1];
         sz[7] = 0;
+    }
+}
+
+// ---- E. rANS, one warp per stream (brick slot q / 2, stream q % 2) over the nibbles in scratch; the
+// symbols are staged in shared memory window by window from the end
+__global__ void __launch_bounds__(kRansEncWarps * 32)
+    rans_encode_kernel(EncGeom G, EncScratch SC, uint32_t n_in_batch, const uint32_t *freq) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t q = blockIdx.x * kRansEncWarps + warp;
+    if (q >= 2 * n_in_batch) return;
+    const uint32_t slot = q >> 1, st = q & 1u;
+    uint32_t *sz = SC.sizes + (size_t)slot * 8;
+    const uint32_t n = sz[1 + st];
+    const uint32_t cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
+    uint16_t *words = (st == 0 ? SC.w_int : SC.w_leaf) + (size_t)slot * cap;
+    const uint8_t *nib = st == 0 ? SC.nib_int + (size_t)slot * G.int_cap : SC.nib_leaf + (size_t)slot * G.leaf_cap;
+    uint8_t *wsm = smem_raw + warp * kRansEncWin;
+    const uint32_t *F = freq + 16 * st;
+    const uint32_t f_reg = lane < 16 ? F[lane] : 1u;
+    const float rcp_reg = 1.0f / (float)f_reg;
+    uint32_t c_reg = 0;
+    for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < lane) ? F[s2] : 0u;
+    const uint32_t K = lanes_for(n, G.K_max, G.S_min);
+    uint32_t top = cap;
+    if (n > 0) {
+        uint32_t x = kL;
+        const uint32_t steps = (n + K - 1) / K;
+        const uint32_t win_steps = (kRansEncWin - 16) / K;  // steps per staged window (16 bytes of alignment slack)
+        // windows of steps from the end: [s_lo, s_hi) covers symbols [s_lo*K, min(n, s_hi*K))
+        for (uint32_t s_hi = steps; s_hi > 0;) {
+            const uint32_t s_lo = s_hi > win_steps ? s_hi - win_steps : 0u;
+            const uint32_t lo16 = (s_lo * K) & ~15u, sym_hi = min(n, s_hi * K);
+            __syncwarp();
+            for (uint32_t c16 = lane; lo16 + 16 * c16 < sym_hi; c16 += 32)
+                reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(nib + lo16) + c16);
+            __syncwarp();
+            for (uint32_t s2 = s_hi; s2-- > s_lo;) {
+                const uint32_t i = s2 * K + lane;
+                const bool act = lane < K && i < n;
+                const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
+                const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
+                const float rf = __shfl_sync(kFull, rcp_reg, sym);
+                // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
+                const bool emit = act && x >= (f << 20);
+                const uint32_t m = __ballot_sync(kFull, emit);
+                if (emit) {
+                    words[top - __popc(m) + __popc(m & lanemask_lt())] = (uint16_t)(x & 0xFFFFu);
+                    x >>= 16;
+                }
+                top -= __popc(m);
+                if (act) {
+                    // x / f through a float reciprocal: here x < f * 2^20, so the estimate is within one of
+                    // the quotient; the integer remainder check makes it exact
+                    uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
+                    int32_t r = (int32_t)(x - qt * f);
+                    if (r < 0) { qt -= 1; r += (int32_t)f; }
+                    if (r < 0) { qt -= 1; r += (int32_t)f; }
+                    if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+                    if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+                    x = qt * kM + (uint32_t)r + c;
+                }
+            }
+            s_hi = s_lo;
+        }
+        // final states ahead of the words, state 0 first, low half first
+        if (lane < K) {
+            words[top - 2 * K + 2 * lane] = (uint16_t)(x & 0xFFFFu);
+            words[top - 2 * K + 2 * lane + 1] = (uint16_t)(x >> 16);
+        }
+        top -= 2 * K;
+    }
+    if (lane == 0) {
+        sz[3 + st] = cap - top;  // words
+        sz[5 + st] = top;        // start inside the scratch area
     }
 }
 
@@ -561,7 +620,13 @@ cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, u
     cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, freq, SC, count);
+    encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || count) return e;
+    const uint32_t smem_e = kRansEncWarps * kRansEncWin;
+    e = cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
+    if (e != cudaSuccess) return e;
+    rans_encode_kernel<<<(2 * n + kRansEncWarps - 1) / kRansEncWarps, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
     return cudaGetLastError();
 }
 
