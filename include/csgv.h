@@ -249,6 +249,20 @@ CSGV_API void csgv_serve_destroy(csgv_server *s);
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
 
+/*
+ * Kernel timing (measurement aid; the paper has no counterpart).  While
+ * enabled, every kernel the library launches is bracketed by two CUDA events
+ * recorded on the launching stream.  csgv_profile_read synchronises the device,
+ * sums the elapsed time and launch count per kernel name into the caller's
+ * arrays (names: max_kernels entries of 48 bytes, NUL-terminated), sets
+ * *n_kernels, and clears the records.  Enabling costs two event records per
+ * launch; disabled (the default) it costs nothing.  Returns CSGV_ERR_INVALID_ARG
+ * for NULL outputs, CSGV_ERR_CUDA if an event fails.
+ */
+CSGV_API int csgv_profile_enable(int on);
+CSGV_API int csgv_profile_read(uint32_t max_kernels, char *names, double *total_ms, uint32_t *launches,
+                               uint32_t *n_kernels);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
-           "csgv_freq_table_from_counts")
+           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read")
 
 
 class CsgvError(RuntimeError):
@@ -70,6 +70,8 @@ def lib():
             raise CsgvError(f"{LIB_PATH} is missing: build it with `python -m paper_2308_16619_b300.build`")
         L = C.CDLL(LIB_PATH)
         vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+        L.csgv_profile_enable.argtypes = [C.c_int]
+        L.csgv_profile_read.argtypes = [u32, vp, vp, vp, vp]
         L.csgv_last_error.restype = C.c_char_p
         L.csgv_build_freq_table.argtypes = [vp, vp, u32, u32, C.POINTER(FreqTable), vp]
         L.csgv_encode_bricks.argtypes = [vp, vp, u32, C.POINTER(FreqTable), C.POINTER(Config), C.POINTER(vp), vp]
@@ -309,3 +311,22 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def profile_enable(on=True):
+    """Record CUDA events around every kernel launch of the library (csgv_profile_enable)."""
+    _check(lib().csgv_profile_enable(1 if on else 0))
+
+
+def profile_read(max_kernels=32):
+    """Per-kernel totals since the last read: {name: (total_ms, launches)} (csgv_profile_read; synchronises)."""
+    names = C.create_string_buffer(48 * max_kernels)
+    ms = (C.c_double * max_kernels)()
+    cnt = (C.c_uint32 * max_kernels)()
+    nk = C.c_uint32(0)
+    _check(lib().csgv_profile_read(max_kernels, names, ms, cnt, C.byref(nk)))
+    out = {}
+    for k in range(nk.value):
+        nm = names.raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[k], cnt[k])
+    return out

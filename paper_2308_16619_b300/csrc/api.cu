@@ -71,22 +71,38 @@ int cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
     } while (0)
 
+// Per-device stream-ordered pool for volume arrays and decode workspaces; it keeps up to kPoolKeep bytes
+// between calls.  Concurrent calls on different streams get their own allocations.
+constexpr uint64_t kPoolKeep = 1ull << 30;
+constexpr int kPoolDevices = 64;
+cudaMemPool_t g_pools[kPoolDevices];
+std::mutex g_pool_mu;
+
+int dev_pool(cudaMemPool_t *pool) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kPoolDevices) return fail(CSGV_ERR_INVALID_ARG, "device index %d too large", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps p;
+        memset(&p, 0, sizeof p);
+        p.allocType = cudaMemAllocationTypePinned;
+        p.location.type = cudaMemLocationTypeDevice;
+        p.location.id = dev;
+        cudaMemPool_t mp;
+        CK(cudaMemPoolCreate(&mp, &p));
+        uint64_t keep = kPoolKeep;
+        CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = mp;
+    }
+    *pool = g_pools[dev];
+    return CSGV_OK;
+}
+
 bool pow2_brick(uint32_t b, uint32_t &N) {
     for (N = 1; N <= (uint32_t)csgv::kMaxN; N++)
         if ((1u << N) == b) return true;
     return false;
-}
-
-void build_lut(const uint32_t freq[32], std::vector<uint32_t> &lut) {
-    lut.assign(2 * csgv::kM, 0);
-    for (int t = 0; t < 2; t++) {
-        uint32_t cum = 0;
-        for (uint32_t s = 0; s < 16; s++) {
-            const uint32_t f = freq[16 * t + s];
-            for (uint32_t k = 0; k < f; k++) lut[t * csgv::kM + cum + k] = csgv::lut_pack(s, f, k);
-            cum += f;
-        }
-    }
 }
 
 bool valid_table(const uint32_t *f) {
@@ -101,18 +117,38 @@ bool valid_table(const uint32_t *f) {
     return true;
 }
 
+// Volume arrays come from a per-device stream-ordered pool (see dev_pool), so encoding a volume costs no
+// device-wide synchronisation; they are returned when the volume is destroyed.
 void vol_free_arrays(csgv_volume *v) {
-    cudaFree(v->pal_off); cudaFree(v->int_off); cudaFree(v->leaf_off);
-    cudaFree(v->pal); cudaFree(v->int_words); cudaFree(v->leaf_words);
-    cudaFree(v->n_int_sym); cudaFree(v->n_leaf_sym);
-    cudaFree(v->lut);
+    void *arr[] = {v->pal_off, v->int_off, v->leaf_off, v->pal,       v->int_words,
+                   v->leaf_words, v->n_int_sym, v->n_leaf_sym, v->lut};
+    for (void *a : arr)
+        if (a) cudaFreeAsync(a, 0);
 }
 
-int vol_finish(csgv_volume *v) {
-    std::vector<uint32_t> lut;
-    build_lut(v->freq, lut);
-    CK(cudaMalloc(&v->lut, lut.size() * 4));
-    CK(cudaMemcpy(v->lut, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice));
+// decode table (2 x 4096 packed entries) from the frequencies, on the device
+__global__ void build_lut_kernel(csgv_freq_table t, uint32_t *lut) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * csgv::kM) return;
+    const uint32_t tb = i / csgv::kM, slot = i % csgv::kM;
+    uint32_t cum = 0, s = 0;
+    while (s < 15 && cum + t.freq[16 * tb + s] <= slot) cum += t.freq[16 * tb + s++];
+    lut[i] = csgv::lut_pack(s, t.freq[16 * tb + s], slot - cum);
+}
+
+int vol_finish(csgv_volume *v, cudaStream_t st) {
+    cudaMemPool_t pool;
+    int rc = dev_pool(&pool);
+    if (rc) return rc;
+    CK(cudaMallocFromPoolAsync((void **)&v->lut, 2 * csgv::kM * 4, pool, st));
+    csgv_freq_table t;
+    memcpy(t.freq, v->freq, sizeof t.freq);
+    {
+        csgv::ProfScope ps("build_lut", st);
+        build_lut_kernel<<<2 * csgv::kM / 256, 256, 0, st>>>(t, v->lut);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
     return CSGV_OK;
 }
 
@@ -127,32 +163,8 @@ csgv::VolDev dev_view(const csgv_volume *v) {
     return V;
 }
 
-// Decode workspace: op records of a slice of requests, taken from a per-device stream-ordered pool that
-// keeps up to kDecodePoolKeep bytes between calls (concurrent calls on different streams get their own).
-constexpr uint64_t kDecodeWorkspace = 64ull << 20;
-constexpr uint64_t kDecodePoolKeep = 256ull << 20;
-constexpr int kPoolDevices = 64;
-cudaMemPool_t g_pools[kPoolDevices];
-std::mutex g_pool_mu;
-
-int decode_pool(int dev, cudaMemPool_t *pool) {
-    if (dev < 0 || dev >= kPoolDevices) return fail(CSGV_ERR_INVALID_ARG, "device index %d too large", dev);
-    std::lock_guard<std::mutex> lk(g_pool_mu);
-    if (!g_pools[dev]) {
-        cudaMemPoolProps p;
-        memset(&p, 0, sizeof p);
-        p.allocType = cudaMemAllocationTypePinned;
-        p.location.type = cudaMemLocationTypeDevice;
-        p.location.id = dev;
-        cudaMemPool_t mp;
-        CK(cudaMemPoolCreate(&mp, &p));
-        uint64_t keep = kDecodePoolKeep;
-        CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
-        g_pools[dev] = mp;
-    }
-    *pool = g_pools[dev];
-    return CSGV_OK;
-}
+// decode workspace per slice of requests (op records and palette positions), from the device pool
+constexpr uint64_t kDecodeWorkspace = 192ull << 20;
 
 int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
     if (!dims) return fail(CSGV_ERR_INVALID_ARG, "dims is NULL");
@@ -187,15 +199,18 @@ cudaError_t arena_get(int dev, size_t bytes, void **out) {
     return cudaSuccess;
 }
 
-int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cudaStream_t st) {
+int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cudaStream_t st, bool exact) {
     if (need <= cap) return CSGV_OK;
     uint64_t nc = cap ? cap : 1024;
     while (nc < need) nc = nc + nc / 2 + 1024;
+    if (exact) nc = need;
+    cudaMemPool_t pool;
+    int rc = dev_pool(&pool);
+    if (rc) return rc;
     void *q = nullptr;
-    CK(cudaMalloc(&q, nc * elem));
+    CK(cudaMallocFromPoolAsync(&q, nc * elem, pool, st));
     if (*p && used) CK(cudaMemcpyAsync(q, *p, used * elem, cudaMemcpyDeviceToDevice, st));
-    CK(cudaStreamSynchronize(st));
-    cudaFree(*p);
+    if (*p) CK(cudaFreeAsync(*p, st));
     *p = q;
     cap = nc;
     return CSGV_OK;
@@ -206,6 +221,23 @@ int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cud
 namespace csgv {
 // lets other translation units of the library report a message through csgv_last_error()
 void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace csgv
+
+namespace csgv {
+namespace {
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+struct ProfRec {
+    const char *name;
+    cudaEvent_t e0, e1;
+};
+std::vector<ProfRec> g_prof;
+}  // namespace
+bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
+void prof_record(const char *name, cudaEvent_t e0, cudaEvent_t e1) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back({name, e0, e1});
+}
 }  // namespace csgv
 
 extern "C" {
@@ -264,20 +296,23 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
     const uint64_t n_sampled = (n + sample_stride - 1) / sample_stride;
     csgv::EncGeom G = csgv::make_geom(N, 32, 256);
     unsigned long long *cnt = nullptr;
-    CK(cudaMalloc(&cnt, 32 * 8));
+    cudaMemPool_t pool;
+    rc = dev_pool(&pool);
+    if (rc) return rc;
+    CK(cudaMallocFromPoolAsync((void **)&cnt, 32 * 8, pool, st));
     CK(cudaMemsetAsync(cnt, 0, 32 * 8, st));
     csgv::EncScratch SC{};
     for (uint64_t first = 0; first < n_sampled; first += 65535) {
         const uint32_t m = (uint32_t)std::min<uint64_t>(65535, n_sampled - first);
         cudaError_t e = csgv::launch_encode(EV, G, first * sample_stride, sample_stride, m, nullptr, SC, cnt, st);
         if (e != cudaSuccess) {
-            cudaFree(cnt);
+            cudaFreeAsync(cnt, st);
             return cuda_fail(e, "encode (count mode)");
         }
     }
     cudaError_t e = cudaMemcpyAsync(out->counts, cnt, 32 * 8, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(cnt, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(cnt);
     if (e != cudaSuccess) return cuda_fail(e, "frequency prepass");
     return csgv_freq_table_from_counts(out->counts, out);
 }
@@ -360,11 +395,13 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     freq_d = (uint32_t *)(A + o_f);
     tot_d = (uint64_t *)(A + o_t);
     maxpal_d = (uint32_t *)(A + o_m);
-    CKE(cudaMalloc(&v->pal_off, (n + 1) * 8));
-    CKE(cudaMalloc(&v->int_off, (n + 1) * 8));
-    CKE(cudaMalloc(&v->leaf_off, (n + 1) * 8));
-    CKE(cudaMalloc(&v->n_int_sym, n * 4));
-    CKE(cudaMalloc(&v->n_leaf_sym, n * 4));
+    cudaMemPool_t pool;
+    if ((rc = dev_pool(&pool))) return cleanup(rc);
+    CKE(cudaMallocFromPoolAsync((void **)&v->pal_off, (n + 1) * 8, pool, st));
+    CKE(cudaMallocFromPoolAsync((void **)&v->int_off, (n + 1) * 8, pool, st));
+    CKE(cudaMallocFromPoolAsync((void **)&v->leaf_off, (n + 1) * 8, pool, st));
+    CKE(cudaMallocFromPoolAsync((void **)&v->n_int_sym, n * 4, pool, st));
+    CKE(cudaMallocFromPoolAsync((void **)&v->n_leaf_sym, n * 4, pool, st));
     CKE(cudaMemcpyAsync(freq_d, table->freq, 32 * 4, cudaMemcpyHostToDevice, st));
     CKE(cudaMemsetAsync(tot_d, 0, 3 * 8, st));
     CKE(cudaMemsetAsync(maxpal_d, 0, 3 * 4, st));
@@ -378,9 +415,10 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
         CKE(cudaMemcpyAsync(tot, tot_d, 3 * 8, cudaMemcpyDeviceToHost, st));
         CKE(cudaStreamSynchronize(st));
         int g;
-        if ((g = grow((void **)&v->pal, cap_p, std::max<uint64_t>(tot[0], 1), 4, prev[0], st)) ||
-            (g = grow((void **)&v->int_words, cap_i, tot[1] + kWordPad, 2, prev[1], st)) ||
-            (g = grow((void **)&v->leaf_words, cap_l, tot[2] + kWordPad, 2, prev[2], st))) {
+        const bool last = first + m >= n;  // a single batch is sized exactly
+        if ((g = grow((void **)&v->pal, cap_p, std::max<uint64_t>(tot[0], 1), 4, prev[0], st, last && first == 0)) ||
+            (g = grow((void **)&v->int_words, cap_i, tot[1] + kWordPad, 2, prev[1], st, last && first == 0)) ||
+            (g = grow((void **)&v->leaf_words, cap_l, tot[2] + kWordPad, 2, prev[2], st, last && first == 0))) {
             free_tmp();
             return cleanup(g);
         }
@@ -398,7 +436,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     v->n_pal = tot[0];
     v->n_iw = tot[1];
     v->n_lw = tot[2];
-    rc = vol_finish(v);
+    rc = vol_finish(v, st);
     if (rc) return cleanup(rc);
     *out = v;
     return CSGV_OK;
@@ -419,7 +457,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     CK(cudaGetDevice(&dev));
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaMemPool_t pool;
-    int rc = decode_pool(dev, &pool);
+    int rc = dev_pool(&pool);
     if (rc) return rc;
     const bool wide = v->max_palette > 253;
     // a request's workspace: interior records at 0, leaf records at leaf_at (one byte per op record, at
@@ -549,8 +587,14 @@ int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint3
         v->max_leaf_sym = std::max(v->max_leaf_sym, n_leaf_sym_host[i]);
     }
     v->max_palette = maxp;
+    cudaMemPool_t pool;
+    rc = dev_pool(&pool);
+    if (rc) {
+        delete v;
+        return rc;
+    }
     auto up = [&](void **d, const void *h, size_t bytes) -> cudaError_t {
-        cudaError_t e = cudaMalloc(d, bytes + 2 * kWordPad);
+        cudaError_t e = cudaMallocFromPoolAsync(d, bytes + 2 * kWordPad, pool, 0);
         if (e == cudaSuccess && bytes && h) e = cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice);
         return e;
     };
@@ -567,13 +611,54 @@ int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint3
         delete v;
         return cuda_fail(e, "volume import");
     }
-    rc = vol_finish(v);
+    rc = vol_finish(v, 0);
     if (rc) {
         vol_free_arrays(v);
         delete v;
         return rc;
     }
     *out = v;
+    return CSGV_OK;
+}
+
+int csgv_profile_enable(int on) {
+    csgv::g_prof_on = on != 0;
+    return CSGV_OK;
+}
+
+int csgv_profile_read(uint32_t max_kernels, char *names, double *total_ms, uint32_t *launches, uint32_t *n_kernels) {
+    if (!names || !total_ms || !launches || !n_kernels) return fail(CSGV_ERR_INVALID_ARG, "NULL output");
+    CK(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(csgv::g_prof_mu);
+    std::vector<std::string> keys;
+    std::vector<double> ms;
+    std::vector<uint32_t> cnt;
+    cudaError_t err = cudaSuccess;
+    for (const auto &r : csgv::g_prof) {
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, r.e0, r.e1);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+        size_t k = 0;
+        while (k < keys.size() && keys[k] != r.name) k++;
+        if (k == keys.size()) {
+            keys.push_back(r.name);
+            ms.push_back(0.0);
+            cnt.push_back(0);
+        }
+        ms[k] += t;
+        cnt[k] += 1;
+    }
+    csgv::g_prof.clear();
+    if (err != cudaSuccess) return cuda_fail(err, "cudaEventElapsedTime");
+    const uint32_t nk = (uint32_t)std::min<size_t>(keys.size(), max_kernels);
+    for (uint32_t k = 0; k < nk; k++) {
+        snprintf(names + 48 * (size_t)k, 48, "%s", keys[k].c_str());
+        total_ms[k] = ms[k];
+        launches[k] = cnt[k];
+    }
+    *n_kernels = nk;
     return CSGV_OK;
 }
 

@@ -50,4 +50,26 @@ __host__ __device__ inline uint32_t lanes_for(uint32_t n, uint32_t K_max, uint32
     return k;
 }
 
+// Kernel timing (csgv_profile_*): while enabled, a ProfScope around a launch records CUDA events on the
+// launching stream before and after it (api.cu keeps the records).
+bool prof_on();
+void prof_record(const char *name, cudaEvent_t e0, cudaEvent_t e1);
+struct ProfScope {
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProfScope(const char *n, cudaStream_t s) : name(n), st(s) {
+        if (prof_on() && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, st);
+    }
+    ~ProfScope() {
+        if (!e0) return;
+        if (cudaEventCreate(&e1) == cudaSuccess) {
+            cudaEventRecord(e1, st);
+            prof_record(name, e0, e1);
+        } else {
+            cudaEventDestroy(e0);
+        }
+    }
+};
+
 }  // namespace csgv

@@ -62,10 +62,11 @@ __device__ __forceinline__ uint32_t lt_of(uint32_t lane) { return (1u << lane) -
 // ------------------------------------------------------------------ rans_records
 
 // Decode one stream (whole warp) into records and P_a counts; returns the record count, | kRecBad if
-// malformed.
+// malformed.  Decoding stops once `need` records are out (a coarse LOD uses only the stream's first
+// levels); the end of the stream is then not checked.
 __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t n_sym, uint32_t K_max,
                                   uint32_t S_min, const uint32_t *lut, uint16_t *win, uint8_t *rec, uint16_t *t8,
-                                  uint64_t cap, uint32_t lane) {
+                                  uint64_t cap, uint32_t need, uint32_t lane) {
     if (n_sym == 0) {
         if (lane == 0) t8[0] = 0;
         return n_words == 0 ? 0u : kRecBad;
@@ -94,7 +95,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     if (lane < K) x = (uint32_t)win[2 * lane - wb] | ((uint32_t)win[2 * lane + 1 - wb] << 16);
     uint32_t pos = 2 * K, remaining = n_sym, otail = 0, pend = 0, held = 0, pa_run = 0;
     bool bad = false;
-    while (remaining > 0) {
+    while (remaining > 0 && otail < need) {
         if (pos > stage_at) {
             if (pos > n_words) {  // the words ran out
                 bad = true;
@@ -164,6 +165,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
         held = symlast;
     }
     if (lane == 0 && (otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
+    if (remaining > 0 && !bad) return otail;  // stopped early: a prefix of the stream
     const bool lane_ok = lane >= K || x == kL;
     const bool ok = __all_sync(kFull, lane_ok) && !bad && remaining == 0 && !pend && pos == n_words;
     __syncwarp();
@@ -195,8 +197,10 @@ __global__ void __launch_bounds__(kRecWarps * 32, 3) rans_records(VolDev V, RecJ
         uint8_t *rec = base + (s ? J.leaf_at : 0);
         uint16_t *t8 = (uint16_t *)(base + (s ? J.t8_leaf_at : J.t8_at));
         const uint64_t cap = s ? J.t8_at - J.leaf_at : J.leaf_at;  // the records' room: 8 * (t8 entries - 1)
+        // LOD t >= 2 uses the interior levels N-1 .. t only: at most 8 records per node of levels N .. t+1
+        const uint32_t need = (s == 0 && t >= 2) ? 8u * (((1u << (3 * (V.N - t))) - 1u) / 7u) : 0xFFFFFFFFu;
         const uint32_t r = decode_stream((s ? V.leaf_words : V.int_words) + w0, n_words, n_sym, V.K_max, V.S_min,
-                                         lut_s + s * kM, win, rec, t8, cap, lane);
+                                         lut_s + s * kM, win, rec, t8, cap, need, lane);
         if (lane == 0) J.info[2 * i + s] = r;
     }
 }
@@ -685,17 +689,22 @@ cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uin
     e = cudaMemsetAsync(J.counter, 0, 4, st);
     if (e != cudaSuccess) return e;
     const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
-    rans_records<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+    {
+        ProfScope ps("rans_records", st);
+        rans_records<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t smem_b = rebuild_smem_bytes(V.N, wide);
     if (wide) {
         e = cudaFuncSetAttribute(rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
         if (e != cudaSuccess) return e;
+        ProfScope ps("rebuild", st);
         rebuild<uint16_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     } else {
         e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
         if (e != cudaSuccess) return e;
+        ProfScope ps("rebuild", st);
         rebuild<uint8_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     }
     return cudaGetLastError();

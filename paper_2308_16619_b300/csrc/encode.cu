@@ -620,19 +620,28 @@ cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, u
     cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+    {
+        ProfScope ps(count ? "encode_count" : "encode", st);
+        encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess || count) return e;
     const uint32_t smem_e = kRansEncWarps * kRansEncWin;
     e = cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
     if (e != cudaSuccess) return e;
-    rans_encode_kernel<<<(2 * n + kRansEncWarps - 1) / kRansEncWarps, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
+    {
+        ProfScope ps("rans_encode", st);
+        rans_encode_kernel<<<(2 * n + kRansEncWarps - 1) / kRansEncWarps, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const uint32_t *sizes, uint32_t n, uint64_t first, uint64_t *pal_off, uint64_t *int_off,
                         uint64_t *leaf_off, uint64_t *tot, cudaStream_t st) {
-    scan_sizes_kernel<<<1, 1024, 0, st>>>(sizes, n, first, pal_off, int_off, leaf_off, tot);
+    {
+        ProfScope ps("scan_sizes", st);
+        scan_sizes_kernel<<<1, 1024, 0, st>>>(sizes, n, first, pal_off, int_off, leaf_off, tot);
+    }
     return cudaGetLastError();
 }
 
@@ -641,8 +650,11 @@ cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t firs
                            uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, uint32_t *max_pal,
                            cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    compact_kernel<<<n, 256, 0, st>>>(G, SC, first, pal_off, int_off, leaf_off, pal, int_words, leaf_words, n_int_sym,
-                                      n_leaf_sym, max_pal);
+    {
+        ProfScope ps("compact", st);
+        compact_kernel<<<n, 256, 0, st>>>(G, SC, first, pal_off, int_off, leaf_off, pal, int_words, leaf_words, n_int_sym,
+                                          n_leaf_sym, max_pal);
+    }
     return cudaGetLastError();
 }
 
