@@ -118,6 +118,27 @@ def measured_peak_hbm():
     return 6400.0, "fallback"
 
 
+def kernel_traffic(kernel):
+    """DRAM bytes per launch of a kernel on voronoi512 b=32 from the committed ncu capture
+    (profiles/kernel_traffic_voronoi512_b32.md), or None once the kernel's source file has changed."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        lines = open(os.path.join(here, "profiles", "kernel_traffic_voronoi512_b32.md")).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        f = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(f) == 5 and f[0] == kernel:
+            src = os.path.join(here, "paper_2308_16619_b300", "csrc", f[1])
+            try:
+                sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+            except OSError:
+                return None
+            return int(f[3]) + int(f[4]) if sha == f[2] else None
+    return None
+
+
 def cpu_baseline_oracle(vol, b, max_seconds=20.0):
     """Oracle encode + decode on a bounded slab of whole bricks; returns (GB/s, cores, sample description)."""
     import oracle as O
@@ -430,7 +451,7 @@ def main():
     # decoded labels and the decode reads the compressed volume (charged to rebuild, the kernel that
     # writes the output); rans_encode / rans_records move only compressed-size data.
     alg = {"encode": out_bytes + comp_read, "rebuild": out_bytes + comp_read,
-           "rans_records": comp_read, "rans_encode": comp_read}
+           "rans_records": comp_read, "rans_encode": comp_read, "encode_count": out_bytes // STRIDE}
     kernels = {k: {"ms_per_launch": ms / n_l, "launches_per_step": n_l / args.steps,
                    "share": ms / sum(m for m, _ in prof.values())} for k, (ms, n_l) in prof.items()}
     dominant = max(prof, key=lambda k: prof[k][0])
@@ -438,8 +459,9 @@ def main():
     def roof(k):
         ms_l = prof[k][0] / prof[k][1]
         a = alg.get(k, 0) / (ms_l / 1e3) / 1e9
+        tr = kernel_traffic(k) if (WORKLOAD == "voronoi512" and b == 32) else None
         return {"bound": "hbm", "kernel": k, "achieved": a, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": a / peak, "traffic": None, "algorithmic_bytes": alg.get(k, 0), "ms_per_launch": ms_l}
+                "frac": a / peak, "traffic": tr, "algorithmic_bytes": alg.get(k, 0), "ms_per_launch": ms_l}
 
     # plain per-brick-launch decode of the same bricks
     plain_gbs = None
