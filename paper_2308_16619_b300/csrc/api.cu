@@ -302,14 +302,18 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
     CK(cudaMallocFromPoolAsync((void **)&cnt, 32 * 8, pool, st));
     CK(cudaMemsetAsync(cnt, 0, 32 * 8, st));
     csgv::EncScratch SC{};
-    for (uint64_t first = 0; first < n_sampled; first += 65535) {
-        const uint32_t m = (uint32_t)std::min<uint64_t>(65535, n_sampled - first);
+    const uint64_t per_batch = 4096;  // sampled bricks per count-mode launch (op scratch: ops_cap bytes each)
+    CK(cudaMallocFromPoolAsync((void **)&SC.ops, std::min<uint64_t>(per_batch, n_sampled) * G.ops_cap, pool, st));
+    for (uint64_t first = 0; first < n_sampled; first += per_batch) {
+        const uint32_t m = (uint32_t)std::min<uint64_t>(per_batch, n_sampled - first);
         cudaError_t e = csgv::launch_encode(EV, G, first * sample_stride, sample_stride, m, nullptr, SC, cnt, st);
         if (e != cudaSuccess) {
+            cudaFreeAsync(SC.ops, st);
             cudaFreeAsync(cnt, st);
             return cuda_fail(e, "encode (count mode)");
         }
     }
+    cudaFreeAsync(SC.ops, st);
     cudaError_t e = cudaMemcpyAsync(out->counts, cnt, 32 * 8, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(cnt, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -383,6 +387,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
     const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
     const size_t o_sz = take(C * 8 * 4), o_f = take(32 * 4), o_t = take(3 * 8), o_m = take(3 * 4);
+    const size_t o_ops = take(C * G.ops_cap);
     void *arena = nullptr;
     CKE(arena_get(dev, off, &arena));
     unsigned char *A = (unsigned char *)arena;
@@ -392,6 +397,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     SC.w_int = (uint16_t *)(A + o_wi);
     SC.w_leaf = (uint16_t *)(A + o_wl);
     SC.sizes = (uint32_t *)(A + o_sz);
+    SC.ops = A + o_ops;
     freq_d = (uint32_t *)(A + o_f);
     tot_d = (uint64_t *)(A + o_t);
     maxpal_d = (uint32_t *)(A + o_m);

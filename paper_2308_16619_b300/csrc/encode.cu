@@ -104,23 +104,20 @@ struct EncSmem {
     uint32_t *lab;     // up_nodes labels, levels 1..N
     uint8_t *cst;      // up_nodes const flags
     uint16_t *list;    // active parents per parent level (same offsets as lab)
-    uint8_t *ops;      // ops_cap op bytes: op | stop<<3 | delta<<4
     uint32_t *red;     // block scan scratch (64 words)
     uint2 *plist;      // children that need a palette op: (op index, label), 256 at a time
     __device__ EncSmem(uint8_t *s, const EncGeom &G) {
         lab = (uint32_t *)s;
         cst = (uint8_t *)s + r16(G.up_nodes * 4);
         list = (uint16_t *)(cst + r16(G.up_nodes));
-        ops = (uint8_t *)list + r16(G.up_nodes * 2);
-        red = (uint32_t *)(ops + r16(G.ops_cap));
+        red = (uint32_t *)((uint8_t *)list + r16(G.up_nodes * 2));
         plist = (uint2 *)(red + 64);
     }
     __host__ __device__ static uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
 };
 
-__host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes, uint32_t ops_cap) {
-    return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + EncSmem::r16(ops_cap) +
-           64 * 4 + 256 * 8;
+__host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes) {
+    return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + 64 * 4 + 256 * 8;
 }
 
 // exclusive block scan of one value per warp (warp totals in `red`), returns warp's offset and the total
@@ -180,6 +177,9 @@ __global__ void __launch_bounds__(kEncThreads)
     B.sz = B.X * B.Y;
     B.base = B.vol + B.gx0 + B.X * (B.gy0 + B.Y * B.gz0);
     if (tid < 32) hist[tid] = 0;
+    // op bytes (op | stop<<3 | delta<<4) of every coded child in stream order, in this brick's scratch
+    // (written and read by this CTA only, so plain loads after a barrier see them)
+    uint8_t *ops = SC.ops + (size_t)slot * G.ops_cap;
 
     // ---- A. pyramid
     {
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kEncThreads)
         if (vec) {
             // two x-neighbouring L1 nodes per thread: four 16-byte rows (y, z) of 4 voxels
             const uint32_t npairs = 1u << (3 * h - 1);
+#pragma unroll 2
             for (uint32_t i = tid; i < npairs; i += kEncThreads) {
                 const uint32_t x2 = i & ((1u << (h - 1)) - 1u), y = (i >> (h - 1)) & ((1u << h) - 1u),
                                z = i >> (2 * h - 1);
@@ -257,49 +258,74 @@ __global__ void __launch_bounds__(kEncThreads)
             lvl_base[l] = n_ops;
             lvl_nact[l] = n_act;
         }
-        const uint32_t cbits = (1u << (3 * (N - lc))) - 1u;  // Morton code bits of the child level
-        for (uint32_t j = tid; j < nops_l; j += kEncThreads) {
-            const uint32_t p = S.list[loff(G.N, l) + (j >> 3)], c = j & 7u;
-            const uint32_t q = 8 * p + c;
-            // every label the choice can look at, loaded up front (independent loads); a neighbour index
-            // that would leave the brick wraps to an in-brick node and is ignored through ok[]
-            uint32_t v, nv0, nv1, nv2;
-            bool ok0, ok1, ok2;
-            const uint32_t mx_ = kMX & cbits, my_ = kMY & cbits, mz_ = kMZ & cbits;
-            const bool mx = (c & 1u) == 0, my = (c & 2u) == 0, mz = (c & 4u) == 0;
-            // +axis: the neighbour's parent; -axis: the node before along the axis on the child level, when
-            // inside the brick (an index leaving the brick wraps to an in-brick node and is ignored)
-            const uint32_t px = S.lab[loff(G.N, l) + (minc(q, mx_) >> 3)], py = S.lab[loff(G.N, l) + (minc(q, my_) >> 3)],
-                           pz = S.lab[loff(G.N, l) + (minc(q, mz_) >> 3)];
-            if (lc == 0 && B.interior) {
-                const uint32_t x = 2 * compact5(p) + (c & 1u), y = 2 * compact5(p >> 1) + ((c >> 1) & 1u),
-                               z = 2 * compact5(p >> 2) + (c >> 2);
-                const uint32_t *r = B.base + B.sz * z + B.sy * y + x;
-                v = __ldg(r);
-                ok0 = mx ? x != 0 : (q & mx_) != mx_;
-                ok1 = my ? y != 0 : (q & my_) != my_;
-                ok2 = mz ? z != 0 : (q & mz_) != mz_;
-                nv0 = mx ? __ldg(x != 0 ? r - 1 : r) : px;
-                nv1 = my ? __ldg(y != 0 ? r - B.sy : r) : py;
-                nv2 = mz ? __ldg(z != 0 ? r - B.sz : r) : pz;
+        // one thread per active parent: its 8 children, the parents next to it toward +axis, and the nodes
+        // before its children toward -axis (children of the parent before it along that axis) are loaded
+        // once; the 8 ops are chosen in registers and stored as one 8-byte word
+        const uint32_t pbits = (1u << (3 * (N - l))) - 1u;  // Morton code bits of the parent level
+        const uint32_t pmx = kMX & pbits, pmy = kMY & pbits, pmz = kMZ & pbits;
+        const uint32_t *Lp = S.lab + loff(G.N, l);
+        for (uint32_t jj = tid; jj < n_act; jj += kEncThreads) {
+            const uint32_t p = S.list[loff(G.N, l) + jj];
+            const uint32_t pl = Lp[p];
+            // faces of the brick: no -axis neighbour on the low face, no +axis neighbour on the high face
+            const bool lox = (p & pmx) == 0, loy = (p & pmy) == 0, loz = (p & pmz) == 0;
+            const bool hix = (p & pmx) == pmx, hiy = (p & pmy) == pmy, hiz = (p & pmz) == pmz;
+            const uint32_t ppx = Lp[minc(p, pmx)], ppy = Lp[minc(p, pmy)], ppz = Lp[minc(p, pmz)];
+            uint32_t v[8], nx[8], ny[8], nz[8];  // nx[c]: the -x neighbour of child c (c with x-bit 0)
+            if (lc >= 1) {
+                const uint32_t *L = S.lab + loff(G.N, lc);
+                const uint4 a4 = *(const uint4 *)(L + 8 * p), b4 = *(const uint4 *)(L + 8 * p + 4);
+                v[0] = a4.x; v[1] = a4.y; v[2] = a4.z; v[3] = a4.w;
+                v[4] = b4.x; v[5] = b4.y; v[6] = b4.z; v[7] = b4.w;
+                const uint32_t *Lx = L + 8 * mdec(p, pmx), *Ly = L + 8 * mdec(p, pmy), *Lz = L + 8 * mdec(p, pmz);
+#pragma unroll
+                for (uint32_t c = 0; c < 8; c++) {
+                    nx[c] = Lx[c | 1u];
+                    ny[c] = Ly[c | 2u];
+                    nz[c] = Lz[c | 4u];
+                }
             } else {
-                v = node_label(B, S, G, lc, q);
-                ok0 = mx ? (q & mx_) != 0 : (q & mx_) != mx_;
-                ok1 = my ? (q & my_) != 0 : (q & my_) != my_;
-                ok2 = mz ? (q & mz_) != 0 : (q & mz_) != mz_;
-                nv0 = mx ? node_label(B, S, G, lc, mdec(q, mx_)) : px;
-                nv1 = my ? node_label(B, S, G, lc, mdec(q, my_)) : py;
-                nv2 = mz ? node_label(B, S, G, lc, mdec(q, mz_)) : pz;
+                const uint32_t x0 = 2 * compact5(p), y0 = 2 * compact5(p >> 1), z0 = 2 * compact5(p >> 2);
+                if (B.interior) {
+                    const uint32_t *r = B.base + B.sz * z0 + B.sy * y0 + x0;
+                    const int64_t sy = (int64_t)B.sy, sz = (int64_t)B.sz;
+#pragma unroll
+                    for (uint32_t c = 0; c < 8; c++) {
+                        const int64_t o = (int64_t)(c & 1u) + sy * ((c >> 1) & 1u) + sz * (c >> 2);
+                        v[c] = __ldg(r + o);
+                        nx[c] = (c & 1u) ? 0u : __ldg(r + o - (lox ? 0 : 1));
+                        ny[c] = (c & 2u) ? 0u : __ldg(r + o - (loy ? 0 : sy));
+                        nz[c] = (c & 4u) ? 0u : __ldg(r + o - (loz ? 0 : sz));
+                    }
+                } else {
+#pragma unroll
+                    for (uint32_t c = 0; c < 8; c++) {
+                        const uint32_t x = x0 + (c & 1u), y = y0 + ((c >> 1) & 1u), z = z0 + (c >> 2);
+                        v[c] = B.at(x, y, z);
+                        nx[c] = (c & 1u) ? 0u : B.at(lox ? x : x - 1, y, z);
+                        ny[c] = (c & 2u) ? 0u : B.at(x, loy ? y : y - 1, z);
+                        nz[c] = (c & 4u) ? 0u : B.at(x, y, loz ? z : z - 1);
+                    }
+                }
             }
-            const uint32_t parent = S.lab[loff(G.N, l) + p];
-            const uint32_t stop = lc >= 1 ? (uint32_t)S.cst[loff(G.N, lc) + q] : 0u;
-            // first applicable reuse: R_p, R_x, R_y, R_z (bestOperation order)
-            const uint32_t op = v == parent ? OP_RP
-                                : (ok0 && nv0 == v) ? OP_RX
-                                : (ok1 && nv1 == v) ? OP_RY
-                                : (ok2 && nv2 == v) ? OP_RZ
-                                : kNeedPal;
-            S.ops[n_ops + j] = (uint8_t)(op | (stop << 3));
+            uint2 st2 = make_uint2(0u, 0u);
+            if (lc >= 1) st2 = *(const uint2 *)(S.cst + loff(G.N, lc) + 8 * p);  // flags 0 / 1, one byte each
+            uint32_t w[2] = {0u, 0u};
+#pragma unroll
+            for (uint32_t c = 0; c < 8; c++) {
+                const bool bx = c & 1u, by = c & 2u, bz = c & 4u;
+                const bool okx = bx ? !hix : !lox, oky = by ? !hiy : !loy, okz = bz ? !hiz : !loz;
+                const uint32_t vx = bx ? ppx : nx[c], vy = by ? ppy : ny[c], vz = bz ? ppz : nz[c];
+                // first applicable reuse: R_p, R_x, R_y, R_z (bestOperation order)
+                const uint32_t op = v[c] == pl ? OP_RP
+                                    : (okx && vx == v[c]) ? OP_RX
+                                    : (oky && vy == v[c]) ? OP_RY
+                                    : (okz && vz == v[c]) ? OP_RZ
+                                    : kNeedPal;
+                const uint32_t stop = ((c < 4 ? st2.x : st2.y) >> (8 * (c & 3u))) & 1u;
+                w[c >> 2] |= (op | (stop << 3)) << (8 * (c & 3u));
+            }
+            *(uint2 *)(ops + n_ops + 8 * jj) = make_uint2(w[0], w[1]);
         }
         n_ops += nops_l;
         if (lc >= 1) n_int_ops = n_ops;
@@ -317,7 +343,7 @@ __global__ void __launch_bounds__(kEncThreads)
         uint32_t cnt = 0;
         for (uint32_t g = j0; g < j1; g += 32) {
             const uint32_t j = g + lane;
-            cnt += __popc(__ballot_sync(kFull, j < j1 && (S.ops[j] & 7u) == kNeedPal));
+            cnt += __popc(__ballot_sync(kFull, j < j1 && (ops[j] & 7u) == kNeedPal));
         }
         uint32_t total;
         const uint32_t wbase = block_excl_warp(S.red, cnt, total);
@@ -327,48 +353,59 @@ __global__ void __launch_bounds__(kEncThreads)
         uint32_t *pal = count ? nullptr : SC.pal + (size_t)slot * G.pal_cap;
         if (pal && tid == 0) pal[0] = root;
         for (uint32_t r0 = 0; r0 < total; r0 += 256) {
+            // gather this round's children (op index) in stream order ...
             if (wbase < r0 + 256 && wbase + cnt > r0) {
                 uint32_t rank = wbase;
                 for (uint32_t g = j0; g < j1; g += 32) {
                     const uint32_t j = g + lane;
                     // ranks count every child gathered in any round: children of earlier rounds already carry
                     // their palette op (P_0, P_delta or P_a), the others still the placeholder
-                    const bool need = j < j1 && (S.ops[j] & 7u) >= OP_P0;
+                    const bool need = j < j1 && (ops[j] & 7u) >= OP_P0;
                     const uint32_t m = __ballot_sync(kFull, need);
                     const uint32_t rk = rank + __popc(m & lanemask_lt());
-                    if (need && rk >= r0 && rk < r0 + 256) {
-                        uint32_t l = 1;
-                        for (uint32_t L = N; L >= 2; L--)
-                            if (j >= lvl_base[L] && j < lvl_base[L] + 8 * lvl_nact[L]) l = L;
-                        const uint32_t base = lvl_base[l];
-                        const uint32_t p = S.list[loff(G.N, l) + ((j - base) >> 3)];
-                        S.plist[rk - r0] = make_uint2(j, node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u)));
-                    }
+                    if (need && rk >= r0 && rk < r0 + 256) S.plist[rk - r0].x = j;
                     rank += __popc(m);
                 }
             }
+            __syncwarp();
+            // ... then their labels, one child per lane (the loads overlap)
+            const uint32_t e0 = max(wbase, r0), e1 = min(wbase + cnt, r0 + 256);
+            for (uint32_t e = e0 + lane; e < e1; e += 32) {
+                const uint32_t j = S.plist[e - r0].x;
+                uint32_t l = 1;
+                for (uint32_t L = N; L >= 2; L--)
+                    if (j >= lvl_base[L] && j < lvl_base[L] + 8 * lvl_nact[L]) l = L;
+                const uint32_t base = lvl_base[l];
+                const uint32_t p = S.list[loff(G.N, l) + ((j - base) >> 3)];
+                S.plist[e - r0].y = node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u));
+            }
             __syncthreads();
             if (warp == 0) {
+                // 32 children at a time in lane registers; lane k keeps child k's op for one write-back
                 const uint32_t nk = min(256u, total - r0);
-                for (uint32_t k = 0; k < nk; k++) {
-                    const uint2 e = S.plist[k];
-                    const uint32_t vk = e.y;
-                    const bool match = lane <= 16 && lane <= ip && win == vk;
-                    const uint32_t mm = __ballot_sync(kFull, match);
-                    uint32_t op, delta = 0;
-                    if (mm) {
-                        const uint32_t f = __ffs(mm) - 1;
-                        op = f == 0 ? OP_P0 : OP_PD;
-                        delta = f == 0 ? 0u : f - 1;
-                    } else {
-                        op = OP_PA;
-                        const uint32_t up = __shfl_up_sync(kFull, win, 1);
-                        win = lane == 0 ? vk : up;
-                        if (pal && lane == 0) pal[np] = vk;
-                        ip += 1;
-                        np += 1;
+                for (uint32_t k0 = 0; k0 < nk; k0 += 32) {
+                    const uint32_t kn = min(32u, nk - k0);
+                    const uint2 mine = lane < kn ? S.plist[k0 + lane] : make_uint2(0u, 0u);
+                    uint32_t res = 0;
+                    for (uint32_t k = 0; k < kn; k++) {
+                        const uint32_t vk = __shfl_sync(kFull, mine.y, k);
+                        const bool match = lane <= 16 && lane <= ip && win == vk;
+                        const uint32_t mm = __ballot_sync(kFull, match);
+                        uint32_t r;
+                        if (mm) {
+                            const uint32_t f = __ffs(mm) - 1;
+                            r = f == 0 ? OP_P0 : (OP_PD | ((f - 1) << 4));
+                        } else {
+                            r = OP_PA;
+                            const uint32_t up = __shfl_up_sync(kFull, win, 1);
+                            win = lane == 0 ? vk : up;
+                            if (pal && lane == 0) pal[np] = vk;
+                            ip += 1;
+                            np += 1;
+                        }
+                        res = lane == k ? r : res;
                     }
-                    if (lane == 0) S.ops[e.x] = (uint8_t)((S.ops[e.x] & 8u) | op | (delta << 4));
+                    if (lane < kn) ops[mine.x] = (uint8_t)((ops[mine.x] & 8u) | res);
                 }
             }
             __syncthreads();
@@ -383,13 +420,23 @@ __global__ void __launch_bounds__(kEncThreads)
         uint32_t pdi = 0, pdl = 0;
         for (uint32_t g = j0; g < j1; g += 32) {
             const uint32_t j = g + lane;
-            const bool pd = j < j1 && (S.ops[j] & 7u) == OP_PD;
+            const bool pd = j < j1 && (ops[j] & 7u) == OP_PD;
             pdi += __popc(__ballot_sync(kFull, pd && j < n_int_ops));
             pdl += __popc(__ballot_sync(kFull, pd && j >= n_int_ops));
         }
-        uint32_t toti, totl;
-        uint32_t bi = block_excl_warp(S.red, pdi, toti);
-        uint32_t bl = block_excl_warp(S.red, pdl, totl);
+        if (lane == 0) {
+            S.red[warp] = pdi;
+            S.red[kEncWarps + warp] = pdl;
+        }
+        __syncthreads();
+        uint32_t bi = 0, bl = 0, toti = 0, totl = 0;
+        for (uint32_t w2 = 0; w2 < kEncWarps; w2++) {
+            const uint32_t vi = S.red[w2], vl = S.red[kEncWarps + w2];
+            bi += w2 < warp ? vi : 0u;
+            bl += w2 < warp ? vl : 0u;
+            toti += vi;
+            totl += vl;
+        }
         sym_tot[0] = n_int_ops + toti;
         sym_tot[1] = n_ops - n_int_ops + totl;
         uint8_t *nib_i = count ? nullptr : SC.nib_int + (size_t)slot * G.int_cap;
@@ -397,7 +444,7 @@ __global__ void __launch_bounds__(kEncThreads)
         for (uint32_t g = j0; g < j1; g += 32) {
             const uint32_t j = g + lane;
             const bool in = j < j1;
-            const uint32_t o = in ? S.ops[j] : 0u;
+            const uint32_t o = in ? ops[j] : 0u;
             const uint32_t op = o & 7u;
             const bool pd = in && op == OP_PD;
             const bool leaf = j >= n_int_ops;
@@ -604,7 +651,7 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
     G.pal_cap = u + b3;             // palette: root + one per P_a
     G.int_cap = (2 * (u - 1) + 2 + 15) & ~15u;  // interior nibbles (op + delta each), 16-byte pitch
     G.leaf_cap = (2 * b3 + 15) & ~15u;
-    G.smem = enc_smem_bytes(G.up_nodes, G.ops_cap);
+    G.smem = enc_smem_bytes(G.up_nodes);
     G.K_max = K_max;
     G.S_min = S_min;
     return G;
@@ -612,7 +659,7 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
 
 size_t scratch_bytes_per_brick(const EncGeom &G) {
     return (size_t)G.pal_cap * 4 + G.int_cap + G.leaf_cap + (size_t)(G.int_cap + 64) * 2 +
-           (size_t)(G.leaf_cap + 64) * 2 + 8 * 4 + 64;
+           (size_t)(G.leaf_cap + 64) * 2 + 8 * 4 + 64 + G.ops_cap;
 }
 
 cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, uint64_t stride, uint32_t n,

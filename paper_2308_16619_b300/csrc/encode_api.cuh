@@ -23,6 +23,7 @@ struct EncScratch {
     uint16_t *w_int;    // C x (int_cap + 64)
     uint16_t *w_leaf;   // C x (leaf_cap + 64)
     uint32_t *sizes;    // C x 8: n_pal, n_int_sym, n_leaf_sym, n_int_words, n_leaf_words, int_start, leaf_start, 0
+    uint8_t *ops;       // C x ops_cap: op bytes of the brick in stream order (encode kernel only)
 };
 
 struct EncVol {

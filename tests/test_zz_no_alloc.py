@@ -64,7 +64,7 @@ def test_noalloc_encoder_rejects_volumes_beyond_its_scratch():
     import torch
     import paper_2308_16619_b300 as csgv
 
-    big = torch.zeros((128, 128, 192), dtype=torch.int32, device="cuda")  # 96 bricks of 32^3 > 89
+    big = torch.zeros((128, 128, 192), dtype=torch.int32, device="cuda")  # 96 bricks of 32^3 > 81
     table = csgv.FreqTable()
     for i in range(32):
         table.freq[i] = 256
@@ -74,7 +74,7 @@ def test_noalloc_encoder_rejects_volumes_beyond_its_scratch():
                                             small.view(torch.int32), small.view(torch.int32))
     assert rc == csgv.CSGV_ERR_INVALID_ARG
     msg = csgv.lib().csgv_last_error().decode()
-    assert "96 bricks" in msg and "at most 89" in msg
+    assert "96 bricks" in msg and "at most 81" in msg
     # output arrays that are too small are refused once the sizes are known, with the sizes reported
     vol = torch.zeros((64, 64, 64), dtype=torch.int32, device="cuda")
     vol[:, :, 17:] = 5
