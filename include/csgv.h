@@ -249,6 +249,26 @@ CSGV_API void csgv_serve_destroy(csgv_server *s);
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
 
+/* A decode configuration of a volume (csgv_decode_autotune). */
+typedef struct csgv_decode_tuning {
+    uint64_t workspace_bytes;  /* op-record workspace per slice of requests (more: fewer, larger slices) */
+    uint32_t rans_ctas_per_sm; /* CTAs per SM of the rANS record kernel (1..3) */
+    uint32_t pad;
+    double ms;                 /* measured time of the batch with this configuration */
+} csgv_decode_tuning;
+
+/*
+ * Autotuner (batching at scale): time candidate decode configurations on this
+ * batch (workspace 64 MiB .. 1 GiB per slice x rANS kernel 2 or 3 CTAs per SM;
+ * one warm-up and two timed runs each, CUDA events on the stream), keep the
+ * fastest in the volume for later csgv_decode_bricks calls, and return it in
+ * *best.  The batch's outputs are written (by every run).  Synchronises the
+ * stream.  The paper has no counterpart.
+ */
+CSGV_API int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
+                                  uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream,
+                                  csgv_decode_tuning *best);
+
 /*
  * Kernel timing (measurement aid; the paper has no counterpart).  While
  * enabled, every kernel the library launches is bracketed by two CUDA events

@@ -20,7 +20,7 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
-           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read")
+           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune")
 
 
 class CsgvError(RuntimeError):
@@ -54,6 +54,11 @@ class Result(C.Structure):
                 ("pad", C.c_uint8 * 3)]
 
 
+class DecodeTuning(C.Structure):
+    _fields_ = [("workspace_bytes", C.c_uint64), ("rans_ctas_per_sm", C.c_uint32), ("pad", C.c_uint32),
+                ("ms", C.c_double)]
+
+
 class ServeStats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("submitted", "hits", "shared", "misses", "evictions", "rebuilds", "batches",
                                           "decoded_labels", "cache_labels_used", "cache_entries")]
@@ -70,6 +75,7 @@ def lib():
             raise CsgvError(f"{LIB_PATH} is missing: build it with `python -m paper_2308_16619_b300.build`")
         L = C.CDLL(LIB_PATH)
         vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+        L.csgv_decode_autotune.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, C.POINTER(DecodeTuning)]
         L.csgv_profile_enable.argtypes = [C.c_int]
         L.csgv_profile_read.argtypes = [u32, vp, vp, vp, vp]
         L.csgv_last_error.restype = C.c_char_p
@@ -196,6 +202,17 @@ def csgv_decode_bricks(volume, brick_ids, lods, out, out_offsets, status, stream
     f = lib().csgv_decode_bricks_plain if plain else lib().csgv_decode_bricks
     _check(f(volume.handle, _ptr(brick_ids), _ptr(lods), n, _ptr(out), _ptr(out_offsets), _ptr(status),
              _stream(stream)))
+
+
+def csgv_decode_autotune(volume, brick_ids, lods, out, out_offsets, status, stream=None):
+    """Time decode configurations on this batch, keep the fastest in the volume; returns DecodeTuning."""
+    n = brick_ids.numel()
+    for t in (brick_ids, lods, out, out_offsets, status):
+        assert t.is_cuda and t.is_contiguous()
+    best = DecodeTuning()
+    _check(lib().csgv_decode_autotune(volume.handle, _ptr(brick_ids), _ptr(lods), n, _ptr(out), _ptr(out_offsets),
+                                      _ptr(status), _stream(stream), C.byref(best)))
+    return best
 
 
 def csgv_decode_bricks_plain(volume, brick_ids, lods, out, out_offsets, status, stream=None):

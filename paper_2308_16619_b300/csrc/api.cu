@@ -41,6 +41,8 @@ struct csgv_volume {
     uint32_t *n_int_sym, *n_leaf_sym;
     uint32_t *lut;
     uint32_t max_int_sym, max_leaf_sym;  // largest per-brick symbol counts: size the decode workspace
+    uint64_t dec_ws_bytes = 192ull << 20;  // decode configuration (csgv_decode_autotune)
+    uint32_t dec_rec_per_sm = 3;
 };
 
 namespace {
@@ -163,8 +165,6 @@ csgv::VolDev dev_view(const csgv_volume *v) {
     return V;
 }
 
-// decode workspace per slice of requests (op records and palette positions), from the device pool
-constexpr uint64_t kDecodeWorkspace = 192ull << 20;
 
 int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
     if (!dims) return fail(CSGV_ERR_INVALID_ARG, "dims is NULL");
@@ -473,7 +473,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     const uint64_t t8_at = a16(leaf_at + (((uint64_t)v->max_leaf_sym + 7) & ~7ull));
     const uint64_t t8_leaf_at = t8_at + a16((leaf_at / 8 + 1) * 2);
     const uint64_t stride = t8_leaf_at + a16(((t8_at - leaf_at) / 8 + 1) * 2);
-    uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, kDecodeWorkspace / stride));
+    uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, v->dec_ws_bytes / stride));
     const size_t info_bytes = ((size_t)S * 8 + 255) & ~(size_t)255;
     const size_t bytes = 256 + info_bytes + (size_t)S * stride;
     void *ws = nullptr;
@@ -491,7 +491,8 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
         J.n = (uint32_t)std::min<uint64_t>(S, n - r0);
         J.ids = ids + r0;
         J.lods = lods + r0;
-        e = csgv::launch_decode_slice(dev_view(v), wide, J, out, off + r0, status + r0, 3 * (uint32_t)sms, st);
+        e = csgv::launch_decode_slice(dev_view(v), wide, J, out, off + r0, status + r0,
+                                      v->dec_rec_per_sm * (uint32_t)sms, st);
     }
     cudaError_t ef = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
@@ -514,6 +515,56 @@ int csgv_decode_bricks_plain(const csgv_volume *vol, const uint32_t *brick_ids_d
     if (rc || n == 0) return rc;
     return decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, true,
                         (cudaStream_t)stream);
+}
+
+int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
+                         uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream,
+                         csgv_decode_tuning *best) {
+    int rc = decode_args(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev);
+    if (rc) return rc;
+    if (!best) return fail(CSGV_ERR_INVALID_ARG, "NULL output");
+    cudaStream_t st = (cudaStream_t)stream;
+    csgv_decode_tuning b{};
+    b.ms = 1e30;
+    b.workspace_bytes = vol->dec_ws_bytes;
+    b.rans_ctas_per_sm = vol->dec_rec_per_sm;
+    if (n == 0) {
+        *best = b;
+        return CSGV_OK;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const uint64_t ws[] = {64ull << 20, 192ull << 20, 512ull << 20, 1024ull << 20};
+    const uint32_t rec[] = {2, 3};
+    for (uint64_t w : ws)
+        for (uint32_t r : rec) {
+            vol->dec_ws_bytes = w;
+            vol->dec_rec_per_sm = r;
+            float t_min = 1e30f;
+            for (int k = 0; k < 3 && rc == CSGV_OK; k++) {
+                cudaEventRecord(e0, st);
+                rc = decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, false, st);
+                cudaEventRecord(e1, st);
+                float t = 0.f;
+                if (rc == CSGV_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && k > 0)
+                    t_min = std::min(t_min, t);
+            }
+            if (rc != CSGV_OK) break;
+            if (t_min < b.ms) {
+                b.ms = t_min;
+                b.workspace_bytes = w;
+                b.rans_ctas_per_sm = r;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    vol->dec_ws_bytes = b.workspace_bytes;
+    vol->dec_rec_per_sm = b.rans_ctas_per_sm;
+    if (rc) return rc;
+    *best = b;
+    return CSGV_OK;
 }
 
 int csgv_volume_info_get(const csgv_volume *v, csgv_volume_info *info) {
