@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--b", type=int, default=B)
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--workload", default="voronoi512", choices=["voronoi512", "cells1024", "worley2048"],
+    ap.add_argument("--workload", default="voronoi512", choices=["voronoi512", "cells1024", "worley2048", "variants"],
                     help="voronoi512: the headline step (prepass+encode+decode of all bricks at LOD 0); "
                          "cells1024: one batched decode of 60000 mixed-LOD requests per step; "
                          "worley2048: serve a 600-frame camera trace (a step is one frame)")
@@ -299,6 +299,63 @@ def run_cells1024(args):
     print(json.dumps(line))
 
 
+def run_variants(args):
+    """Coding variants on voronoi512 b=32 (compression ratio and decode speed): two tables with K_max = 32
+    (default), 16 and 1 (the paper's single rANS state), one table for both streams, and no rANS (raw
+    nibbles, two per byte; size from the symbol counts)."""
+    import torch
+    import synth
+    import paper_2308_16619_b300 as csgv
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    b = args.b
+    vol_np = synth.make("voronoi512")
+    vol = torch.from_numpy(vol_np.view(np.int32)).to(dev)
+    raw = vol_np.nbytes
+    n = vol_np.size // b ** 3
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    lods = torch.zeros(n, dtype=torch.uint8, device=dev)
+    offs = torch.arange(n, dtype=torch.int64, device=dev) * b ** 3
+    out = torch.empty(n * b ** 3, dtype=torch.int32, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    two = csgv.csgv_build_freq_table(vol, b, 1)
+    c = np.array(two.counts[:], np.uint64)
+    one = csgv.csgv_freq_table_from_counts(np.concatenate([c[:16] + c[16:], c[:16] + c[16:]]))
+    rows = {}
+    for name, table, km in (("two tables, K_max=32", two, 32), ("two tables, K_max=16", two, 16),
+                            ("two tables, K_max=1", two, 1), ("one table, K_max=32", one, 32)):
+        v = csgv.csgv_encode_bricks(vol, b, table, K_max=km, S_min=args.s_min)
+        ts = []
+        for r in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            csgv.csgv_decode_bricks(v, ids, lods, out, offs, status)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if r >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        assert bool((status == 0).all())
+        assert torch.equal(out.view(n, b, b, b)[0].cpu(), vol[:b, :b, :b].cpu())
+        inf = v.info()
+        rows[name] = {"cr_percent": 100.0 * inf.compressed_bytes / raw,
+                      "decode_gbs": n * b ** 3 * 4 / (float(np.median(ts)) / 1e3) / 1e9}
+        if km == 32 and table is two:
+            ex = v.export()
+            nib = ex["n_int_sym"].astype(np.int64), ex["n_leaf_sym"].astype(np.int64)
+            raw_nibbles = int(((nib[0] + 1) // 2 + (nib[1] + 1) // 2).sum())
+            rows["no rANS (raw nibbles)"] = {
+                "cr_percent": 100.0 * (len(ex["pal"]) * 4 + raw_nibbles + n * (3 * 8 + 2 * 4)) / raw,
+                "decode_gbs": None}
+        v.close()
+    line = {"metric": "compression ratio and decoded GB/s of coding variants", "value": rows["two tables, K_max=32"]["cr_percent"],
+            "unit": "% of raw", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"voronoi512 512^3 warped Voronoi, b={b}, S_min={args.s_min}"}, "variants": rows}
+    print(json.dumps(line))
+
+
 def run_worley2048(args):
     """Serving: 2048x2048x1024 Worley cells (24-voxel jittered grid) made and compressed on the device,
     an 8 GiB decoded-brick cache, and a 600-frame fly-around trace at 1920x1080 (distance-based LOD).
@@ -373,6 +430,8 @@ def main():
     if args.workload == "cells1024":
         run_cells1024(args)
         return
+    if args.workload == "variants":
+        return run_variants(args)
     if args.workload == "worley2048":
         run_worley2048(args)
         return

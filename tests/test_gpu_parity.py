@@ -280,3 +280,28 @@ def test_range_and_corrupt_status():
         out, off, st = gpu_decode(bad, 5, ids, lods)
         assert st[0] in (0, 4) and st[1] == 0
         assert np.array_equal(out[off[1]:], ref[off[1]:])
+
+
+def test_one_table_and_single_state_variants_round_trip():
+    """Coding variants (one table for both streams; K_max = 1, the paper's single rANS state) decode exactly."""
+    import torch
+    import paper_2308_16619_b300 as csgv
+    vol = synth.voronoi((64, 96, 128), 120, seed=31, warp_amp=4, bg_permille=300)
+    d = torch.from_numpy(vol.view(np.int32)).cuda()
+    two = csgv.csgv_build_freq_table(d, 16, 1)
+    c = np.array(two.counts[:], np.uint64)
+    one = csgv.csgv_freq_table_from_counts(np.concatenate([c[:16] + c[16:], c[:16] + c[16:]]))
+    assert one.freq[:16] == one.freq[16:]
+    for table, km in ((one, 32), (two, 1)):
+        v = csgv.csgv_encode_bricks(d, 16, table, K_max=km)
+        n = v.info().n_bricks
+        out = torch.empty(n * 16 ** 3, dtype=torch.int32, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        csgv.csgv_decode_bricks(v, torch.arange(n, dtype=torch.int32, device="cuda"),
+                                torch.zeros(n, dtype=torch.uint8, device="cuda"), out,
+                                torch.arange(n, dtype=torch.int64, device="cuda") * 16 ** 3, st)
+        torch.cuda.synchronize()
+        assert bool((st == 0).all())
+        got = out.cpu().numpy().view(np.uint32).reshape(4, 6, 8, 16, 16, 16).transpose(0, 3, 1, 4, 2, 5)
+        assert np.array_equal(got.reshape(vol.shape), vol)
+        v.close()
