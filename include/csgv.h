@@ -249,6 +249,17 @@ CSGV_API void csgv_serve_destroy(csgv_server *s);
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
 
+/*
+ * Detail separation (Sec. 4.2 of the paper): move the leaf streams (the data of
+ * level 0, about two thirds of the compressed words) to page-locked host
+ * memory that the GPU maps, and free their device copy.  Decoding then reads
+ * them in place over the host link when a request needs LOD 0; coarser LODs
+ * never touch them.  Returns CSGV_ERR_OOM if the host allocation fails.
+ * csgv_volume_leaves_to_device moves them back.  Both synchronise the device.
+ */
+CSGV_API int csgv_volume_leaves_to_host(csgv_volume *vol);
+CSGV_API int csgv_volume_leaves_to_device(csgv_volume *vol);
+
 /* A decode configuration of a volume (csgv_decode_autotune). */
 typedef struct csgv_decode_tuning {
     uint64_t workspace_bytes;  /* op-record workspace per slice of requests (more: fewer, larger slices) */

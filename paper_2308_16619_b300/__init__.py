@@ -20,7 +20,8 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
-           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune")
+           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune",
+           "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device")
 
 
 class CsgvError(RuntimeError):
@@ -76,6 +77,8 @@ def lib():
         L = C.CDLL(LIB_PATH)
         vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
         L.csgv_decode_autotune.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, C.POINTER(DecodeTuning)]
+        L.csgv_volume_leaves_to_host.argtypes = [vp]
+        L.csgv_volume_leaves_to_device.argtypes = [vp]
         L.csgv_profile_enable.argtypes = [C.c_int]
         L.csgv_profile_read.argtypes = [u32, vp, vp, vp, vp]
         L.csgv_last_error.restype = C.c_char_p
@@ -153,6 +156,13 @@ class Volume:
         arrs["leaf_words"] = arrs["leaf_words"][:inf.leaf_words]
         arrs["freq"] = np.array(inf.freq[:], np.uint32)
         return arrs
+
+    def leaves_to_host(self):
+        """Detail separation: leaf streams to mapped host memory, read in place by LOD-0 decodes."""
+        _check(lib().csgv_volume_leaves_to_host(self._h))
+
+    def leaves_to_device(self):
+        _check(lib().csgv_volume_leaves_to_device(self._h))
 
     def close(self):
         if self._h and self._h.value:

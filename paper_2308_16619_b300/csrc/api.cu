@@ -41,6 +41,7 @@ struct csgv_volume {
     uint32_t *n_int_sym, *n_leaf_sym;
     uint32_t *lut;
     uint32_t max_int_sym, max_leaf_sym;  // largest per-brick symbol counts: size the decode workspace
+    uint16_t *leaf_host = nullptr;        // leaf words in mapped host memory (csgv_volume_leaves_to_host)
     uint64_t dec_ws_bytes = 192ull << 20;  // decode configuration (csgv_decode_autotune)
     uint32_t dec_rec_per_sm = 3;
 };
@@ -123,9 +124,11 @@ bool valid_table(const uint32_t *f) {
 // device-wide synchronisation; they are returned when the volume is destroyed.
 void vol_free_arrays(csgv_volume *v) {
     void *arr[] = {v->pal_off, v->int_off, v->leaf_off, v->pal,       v->int_words,
-                   v->leaf_words, v->n_int_sym, v->n_leaf_sym, v->lut};
+                   v->leaf_host ? nullptr : v->leaf_words, v->n_int_sym, v->n_leaf_sym, v->lut};
     for (void *a : arr)
         if (a) cudaFreeAsync(a, 0);
+    if (v->leaf_host) cudaFreeHost(v->leaf_host);
+    v->leaf_host = nullptr;
 }
 
 // decode table (2 x 4096 packed entries) from the frequencies, on the device
@@ -515,6 +518,45 @@ int csgv_decode_bricks_plain(const csgv_volume *vol, const uint32_t *brick_ids_d
     if (rc || n == 0) return rc;
     return decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, true,
                         (cudaStream_t)stream);
+}
+
+int csgv_volume_leaves_to_host(csgv_volume *v) {
+    if (!v) return fail(CSGV_ERR_INVALID_ARG, "NULL volume");
+    if (v->leaf_host) return CSGV_OK;
+    const size_t bytes = (v->n_lw + kWordPad) * 2;
+    CK(cudaDeviceSynchronize());
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess || !h)
+        return fail(CSGV_ERR_OOM, "cannot allocate %zu bytes of mapped host memory", bytes);
+    void *dptr = nullptr;
+    cudaError_t e = cudaMemcpy(h, v->leaf_words, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dptr, h, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        return cuda_fail(e, "leaves to host");
+    }
+    cudaFreeAsync(v->leaf_words, 0);
+    CK(cudaDeviceSynchronize());
+    v->leaf_words = (uint16_t *)dptr;
+    v->leaf_host = (uint16_t *)h;
+    return CSGV_OK;
+}
+
+int csgv_volume_leaves_to_device(csgv_volume *v) {
+    if (!v) return fail(CSGV_ERR_INVALID_ARG, "NULL volume");
+    if (!v->leaf_host) return CSGV_OK;
+    const size_t bytes = (v->n_lw + kWordPad) * 2;
+    cudaMemPool_t pool;
+    int rc = dev_pool(&pool);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    void *d = nullptr;
+    CK(cudaMallocFromPoolAsync(&d, bytes, pool, 0));
+    CK(cudaMemcpy(d, v->leaf_host, bytes, cudaMemcpyHostToDevice));
+    cudaFreeHost(v->leaf_host);
+    v->leaf_host = nullptr;
+    v->leaf_words = (uint16_t *)d;
+    return CSGV_OK;
 }
 
 int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
