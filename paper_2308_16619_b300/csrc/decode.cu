@@ -312,51 +312,55 @@ __device__ __forceinline__ uint32_t lab(uint32_t v, uint32_t pal_reg, const uint
     return __ldg(pal + min(v & 0xFFFFu, np - 1));
 }
 
-// Write level t (Morton order, side = 2^s) as x-fastest labels.
+// Write level t (Morton order, side = 2^s) as x-fastest labels.  A unit is 16 consecutive Morton nodes, a
+// 4 x 2 x 2 block (Morton bits x0 y0 z0 x1): one 16-byte shared-memory load per thread (two for uint16
+// indices) and four 16-byte rows out.  Units go to threads x-fastest, so that the threads of a warp
+// complete whole 128-byte rows; their loads are at most 2-way bank conflicts.
 template <typename IdxT, int kPal>
 __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t *out, bool vec, uint32_t pal_reg,
                                             const uint32_t *pal_s, const uint32_t *pal, uint32_t np) {
     const uint32_t side = 1u << s;
     if (vec && side >= 4) {
-        // a unit is 4 voxels along x in 2 rows (y, y+1): Morton m0..m0+3 and m0+8..m0+11.  With at most
-        // 2^7 (x4, y2) pairs per slice (side <= 32), a thread keeps its (x4, y2) and steps z.
-        const uint32_t xs = s - 2, ys = s - 1, xy = xs + ys;
-        const uint32_t units = 1u << (xy + s);
-        const uint32_t u = threadIdx.x;
-        const uint32_t x4 = u & ((1u << xs) - 1), y2 = (u >> xs) & ((1u << ys) - 1);
-        const uint32_t dz = kRbThreads >> xy;  // z step per iteration
-        const uint32_t mxy = spread5(4 * x4) | (spread5(2 * y2) << 1);
-        const uint32_t mdz = spread5(dz & 31u) << 2;
-        uint32_t mz = spread5((u >> xy) & 31u) << 2;
-        uint32_t *o = out + (((size_t)(u >> xy) << s) + 2 * y2) * side + 4 * x4;
-        const size_t ostep = (size_t)dz << (2 * s);
+        const uint32_t units = 1u << (3 * s - 4);
+        const uint32_t xb = s - 2, yb = s - 1;  // bits of the unit's x and y index
         for (uint32_t u0 = 0; u0 < units; u0 += kRbThreads) {
-            const bool in = u0 + u < units;
-            const uint32_t m0 = in ? (mxy | mz) : 0u;
-            uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+            const uint32_t u = u0 + threadIdx.x;
+            const bool in = u < units;
+            const uint32_t uu = in ? u : 0u;
+            const uint32_t x0 = 4 * (uu & ((1u << xb) - 1u)), y0 = 2 * ((uu >> xb) & ((1u << yb) - 1u)),
+                           z0 = 2 * (uu >> (xb + yb));
+            const uint32_t m = spread5(x0) | (spread5(y0) << 1) | (spread5(z0) << 2);
+            // row (dy, dz) holds Morton offsets o, o+1, o+8, o+9 with o = 2 dy + 4 dz
+            uint32_t r[4][4];
             if constexpr (sizeof(IdxT) == 1) {
-                const uint32_t A = *(const uint32_t *)(C + m0), B = *(const uint32_t *)(C + m0 + 8);
-                a0 = A; a1 = A >> 8; a2 = A >> 16; a3 = A >> 24;
-                b0 = B; b1 = B >> 8; b2 = B >> 16; b3 = B >> 24;
+                const uint4 q = *(const uint4 *)(C + m);
+                const uint32_t lo[2] = {q.x, q.y}, hi[2] = {q.z, q.w};  // Morton offsets 0..7, 8..15
+#pragma unroll
+                for (uint32_t k = 0; k < 4; k++) {  // k = dy + 2 dz: word k/2, byte pair (k % 2) * 2
+                    const uint32_t a = lo[k >> 1] >> (16 * (k & 1u)), c = hi[k >> 1] >> (16 * (k & 1u));
+                    r[k][0] = lab<IdxT, kPal>(a, pal_reg, pal_s, pal, np);
+                    r[k][1] = lab<IdxT, kPal>(a >> 8, pal_reg, pal_s, pal, np);
+                    r[k][2] = lab<IdxT, kPal>(c, pal_reg, pal_s, pal, np);
+                    r[k][3] = lab<IdxT, kPal>(c >> 8, pal_reg, pal_s, pal, np);
+                }
             } else {
-                const uint2 A = *(const uint2 *)(C + m0), B = *(const uint2 *)(C + m0 + 8);
-                a0 = A.x; a1 = A.x >> 16; a2 = A.y; a3 = A.y >> 16;
-                b0 = B.x; b1 = B.x >> 16; b2 = B.y; b3 = B.y >> 16;
+                const uint4 q0 = *(const uint4 *)(C + m), q1 = *(const uint4 *)(C + m + 8);
+                const uint32_t lo[4] = {q0.x, q0.y, q0.z, q0.w}, hi[4] = {q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+                for (uint32_t k = 0; k < 4; k++) {  // k = dy + 2 dz: word k holds offsets 2k, 2k+1
+                    r[k][0] = lab<IdxT, kPal>(lo[k], pal_reg, pal_s, pal, np);
+                    r[k][1] = lab<IdxT, kPal>(lo[k] >> 16, pal_reg, pal_s, pal, np);
+                    r[k][2] = lab<IdxT, kPal>(hi[k], pal_reg, pal_s, pal, np);
+                    r[k][3] = lab<IdxT, kPal>(hi[k] >> 16, pal_reg, pal_s, pal, np);
+                }
             }
-            const uint4 r0 = make_uint4(lab<IdxT, kPal>(a0, pal_reg, pal_s, pal, np),
-                                        lab<IdxT, kPal>(a1, pal_reg, pal_s, pal, np),
-                                        lab<IdxT, kPal>(b0, pal_reg, pal_s, pal, np),
-                                        lab<IdxT, kPal>(b1, pal_reg, pal_s, pal, np));
-            const uint4 r1 = make_uint4(lab<IdxT, kPal>(a2, pal_reg, pal_s, pal, np),
-                                        lab<IdxT, kPal>(a3, pal_reg, pal_s, pal, np),
-                                        lab<IdxT, kPal>(b2, pal_reg, pal_s, pal, np),
-                                        lab<IdxT, kPal>(b3, pal_reg, pal_s, pal, np));
             if (in) {
-                __stcs((uint4 *)o, r0);
-                __stcs((uint4 *)(o + side), r1);
+                uint32_t *o = out + ((size_t)z0 * side + y0) * side + x0;
+#pragma unroll
+                for (uint32_t k = 0; k < 4; k++)
+                    __stcs((uint4 *)(o + (size_t)(k >> 1) * side * side + (k & 1u) * side),
+                           make_uint4(r[k][0], r[k][1], r[k][2], r[k][3]));
             }
-            mz = ((mz | ~kMZ) + mdz) & kMZ;  // z += dz on the Morton z bits
-            o += ostep;
         }
     } else {
         const uint32_t n = side * side * side;

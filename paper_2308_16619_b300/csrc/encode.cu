@@ -186,17 +186,18 @@ __global__ void __launch_bounds__(kEncThreads)
         const uint32_t h = N - 1;  // log2 of the L1 side
         const bool vec = B.interior && N >= 2 && (B.X & 3u) == 0 && (reinterpret_cast<uintptr_t>(B.vol) & 15u) == 0;
         if (vec) {
-            // two x-neighbouring L1 nodes per thread: four 16-byte rows (y, z) of 4 voxels
+            // two x-neighbouring L1 nodes per thread, Morton 2i and 2i+1 (consecutive threads store consecutive
+            // words): four 16-byte rows (y, z) of 4 voxels
             const uint32_t npairs = 1u << (3 * h - 1);
 #pragma unroll 2
             for (uint32_t i = tid; i < npairs; i += kEncThreads) {
-                const uint32_t x2 = i & ((1u << (h - 1)) - 1u), y = (i >> (h - 1)) & ((1u << h) - 1u),
-                               z = i >> (2 * h - 1);
-                const uint32_t *r = B.base + B.sz * (2 * z) + B.sy * (2 * y) + 4 * x2;
+                const uint32_t m2 = 2 * i;
+                const uint32_t x = compact5(m2), y = compact5(m2 >> 1), z = compact5(m2 >> 2);  // x even
+                const uint32_t *r = B.base + B.sz * (2 * z) + B.sy * (2 * y) + 2 * x;
                 const uint4 a = __ldg((const uint4 *)r), bb = __ldg((const uint4 *)(r + B.sy)),
                             c = __ldg((const uint4 *)(r + B.sz)), d = __ldg((const uint4 *)(r + B.sz + B.sy));
                 bool e0, e1;
-                const uint32_t m = loff(G.N, 1) + morton3(2 * x2, y, z);
+                const uint32_t m = loff(G.N, 1) + m2;
                 S.lab[m] = mode8(a.x, a.y, bb.x, bb.y, c.x, c.y, d.x, d.y, e0);
                 S.cst[m] = e0;
                 S.lab[m + 1] = mode8(a.z, a.w, bb.z, bb.w, c.z, c.w, d.z, d.w, e1);
@@ -219,11 +220,12 @@ __global__ void __launch_bounds__(kEncThreads)
         for (uint32_t l = 2; l <= N; l++) {
             const uint32_t nl = 1u << (3 * (N - l));
             for (uint32_t i = tid; i < nl; i += kEncThreads) {
-                const uint32_t *w = S.lab + loff(G.N, l - 1) + 8 * i;
+                const uint4 wa = *(const uint4 *)(S.lab + loff(G.N, l - 1) + 8 * i),
+                            wb = *(const uint4 *)(S.lab + loff(G.N, l - 1) + 8 * i + 4);
                 const uint2 cs = *(const uint2 *)(S.cst + loff(G.N, l - 1) + 8 * i);  // 8 flags, 0 or 1 each
                 const bool allc = (cs.x & cs.y) == 0x01010101u;
                 bool eq;
-                S.lab[loff(G.N, l) + i] = mode8(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], eq);
+                S.lab[loff(G.N, l) + i] = mode8(wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w, eq);
                 S.cst[loff(G.N, l) + i] = eq && allc;
             }
             __syncthreads();
