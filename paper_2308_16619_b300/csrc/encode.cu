@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(kEncThreads)
     EncSmem S(smem_raw, G);
     __shared__ uint32_t hist[32];
     __shared__ uint32_t sh_np;
+    __shared__ uint32_t sh_npc;                 // children that need a palette op (phase B)
+    __shared__ uint32_t sh_pd[2 * kEncWarps];   // P_delta ops per warp range of phase D, per stream (phase C)
     __shared__ uint32_t lvl_base[kMaxN + 2], lvl_nact[kMaxN + 2];  // ops of children of parent level l
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t slot = blockIdx.x;
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(kEncThreads)
     B.sz = B.X * B.Y;
     B.base = B.vol + B.gx0 + B.X * (B.gy0 + B.Y * B.gz0);
     if (tid < 32) hist[tid] = 0;
+    if (tid == 0) sh_npc = 0;
     // op bytes (op | stop<<3 | delta<<4) of every coded child in stream order, in this brick's scratch
     // (written and read by this CTA only, so plain loads after a barrier see them)
     uint8_t *ops = SC.ops + (size_t)slot * G.ops_cap;
@@ -326,6 +329,10 @@ __global__ void __launch_bounds__(kEncThreads)
                                     : kNeedPal;
                 const uint32_t stop = ((c < 4 ? st2.x : st2.y) >> (8 * (c & 3u))) & 1u;
                 w[c >> 2] |= (op | (stop << 3)) << (8 * (c & 3u));
+                if (op == kNeedPal) {  // gathered with its label for the palette pass (first 256)
+                    const uint32_t at = atomicAdd(&sh_npc, 1u);
+                    if (at < 256) S.plist[at] = make_uint2(n_ops + 8 * jj + c, v[c]);
+                }
             }
             *(uint2 *)(ops + n_ops + 8 * jj) = make_uint2(w[0], w[1]);
         }
@@ -338,10 +345,61 @@ __global__ void __launch_bounds__(kEncThreads)
     const uint32_t per = ((n_ops + kEncWarps - 1) / kEncWarps + 31) & ~31u;
     const uint32_t j0 = min(warp * per, n_ops), j1 = min(j0 + per, n_ops);
 
-    // ---- C. palette pass in stream order: the children no reuse fits are gathered with their labels, 256
-    // at a time; warp 0 then walks them in order with the last 17 palette entries in registers (lane i
-    // holds palette[i_p - i])
-    {
+    // ---- C. palette pass in stream order: warp 0 walks the children no reuse fits, with the last 17 palette
+    // entries in registers (lane i holds palette[i_p - i]).  Phase B gathered up to 256 of them with their
+    // labels; they are put in stream order by rank and the walk also counts the P_delta ops per warp range
+    // of phase D.  Bricks with more go through the gathering below, 256 at a time.
+    const uint32_t n_need = sh_npc;
+    const bool fast = n_need <= 256;
+    if (fast) {
+        uint2 mine = make_uint2(0u, 0u);
+        uint32_t rank = 0;
+        if (tid < n_need) {
+            mine = S.plist[tid];
+            for (uint32_t k = 0; k < n_need; k++) rank += S.plist[k].x < mine.x ? 1u : 0u;
+        }
+        if (tid < 2 * kEncWarps) sh_pd[tid] = 0;
+        __syncthreads();
+        if (tid < n_need) S.plist[rank] = mine;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t root = S.lab[loff(G.N, N)];
+            uint32_t win = root;
+            uint32_t ip = 0, np = 1;
+            uint32_t *pal = count ? nullptr : SC.pal + (size_t)slot * G.pal_cap;
+            if (pal && lane == 0) pal[0] = root;
+            for (uint32_t k0 = 0; k0 < n_need; k0 += 32) {
+                const uint32_t kn = min(32u, n_need - k0);
+                const uint2 mine2 = lane < kn ? S.plist[k0 + lane] : make_uint2(0u, 0u);
+                uint32_t res = 0;
+                for (uint32_t k = 0; k < kn; k++) {
+                    const uint32_t vk = __shfl_sync(kFull, mine2.y, k);
+                    const bool match = lane <= 16 && lane <= ip && win == vk;
+                    const uint32_t mm = __ballot_sync(kFull, match);
+                    uint32_t r;
+                    if (mm) {
+                        const uint32_t f = __ffs(mm) - 1;
+                        r = f == 0 ? OP_P0 : (OP_PD | ((f - 1) << 4));
+                    } else {
+                        r = OP_PA;
+                        const uint32_t up = __shfl_up_sync(kFull, win, 1);
+                        win = lane == 0 ? vk : up;
+                        if (pal && lane == 0) pal[np] = vk;
+                        ip += 1;
+                        np += 1;
+                    }
+                    res = lane == k ? r : res;
+                }
+                if (lane < kn) {
+                    ops[mine2.x] = (uint8_t)((ops[mine2.x] & 8u) | res);
+                    if ((res & 7u) == OP_PD)
+                        atomicAdd(&sh_pd[(mine2.x >= n_int_ops ? kEncWarps : 0u) + mine2.x / per], 1u);
+                }
+            }
+            if (lane == 0) sh_np = np;
+        }
+        __syncthreads();
+    } else     {
         uint32_t cnt = 0;
         for (uint32_t g = j0; g < j1; g += 32) {
             const uint32_t j = g + lane;
@@ -419,21 +477,25 @@ __global__ void __launch_bounds__(kEncThreads)
     // ---- D. nibble positions: an op's index in its stream plus the P_delta ops before it in that stream
     uint32_t sym_tot[2];
     {
-        uint32_t pdi = 0, pdl = 0;
-        for (uint32_t g = j0; g < j1; g += 32) {
-            const uint32_t j = g + lane;
-            const bool pd = j < j1 && (ops[j] & 7u) == OP_PD;
-            pdi += __popc(__ballot_sync(kFull, pd && j < n_int_ops));
-            pdl += __popc(__ballot_sync(kFull, pd && j >= n_int_ops));
+        const uint32_t *pdc = sh_pd;  // P_delta per warp range: counted by the walk, or here
+        if (!fast) {
+            uint32_t pdi = 0, pdl = 0;
+            for (uint32_t g = j0; g < j1; g += 32) {
+                const uint32_t j = g + lane;
+                const bool pd = j < j1 && (ops[j] & 7u) == OP_PD;
+                pdi += __popc(__ballot_sync(kFull, pd && j < n_int_ops));
+                pdl += __popc(__ballot_sync(kFull, pd && j >= n_int_ops));
+            }
+            if (lane == 0) {
+                S.red[warp] = pdi;
+                S.red[kEncWarps + warp] = pdl;
+            }
+            __syncthreads();
+            pdc = S.red;
         }
-        if (lane == 0) {
-            S.red[warp] = pdi;
-            S.red[kEncWarps + warp] = pdl;
-        }
-        __syncthreads();
         uint32_t bi = 0, bl = 0, toti = 0, totl = 0;
         for (uint32_t w2 = 0; w2 < kEncWarps; w2++) {
-            const uint32_t vi = S.red[w2], vl = S.red[kEncWarps + w2];
+            const uint32_t vi = pdc[w2], vl = pdc[kEncWarps + w2];
             bi += w2 < warp ? vi : 0u;
             bl += w2 < warp ? vl : 0u;
             toti += vi;
