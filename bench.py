@@ -31,7 +31,7 @@ STRIDE = 512
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--b", type=int, default=B)
@@ -68,7 +68,7 @@ class ClockSampler:
         self.t0 = time.time()
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -81,7 +81,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        """Wall-clock bounds of the timed region (to count the samples taken inside it)."""
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -94,7 +98,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        w = getattr(self, "window", None)
+        inside = sum(1 for t, _ in self.lines if w and w[0] <= t <= w[1])
+        for _, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -107,7 +113,8 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm), "window": "warm-up through the timed region"}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": inside,
+                "window": "warm-up through the timed region, every 200 ms"}
 
 
 def measured_peak_hbm():
@@ -256,11 +263,13 @@ def run_cells1024(args):
         graph.replay()
     torch.cuda.synchronize(dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    w0 = time.time()
     for a, z in evs:
         a.record(stream)
         graph.replay()
         z.record(stream)
     torch.cuda.synchronize(dev)
+    clk.mark(w0, time.time())
     clk.__exit__()
     ms = float(np.median([a.elapsed_time(z) for a, z in evs]))
     assert bool((status == 0).all())
@@ -397,6 +406,7 @@ def run_worley2048(args):
     rc, _ = srv.poll(tickets[-1], timeout_us=30_000_000)
     assert rc == csgv.CSGV_OK
     wall = time.perf_counter() - t0
+    clk.mark(time.time() - wall, time.time())
     clk.__exit__()
     st, lat = srv.stats(with_latencies=True)
     for t in tickets[-2:]:
@@ -462,22 +472,24 @@ def main():
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        table = csgv.csgv_build_freq_table(vol, b, STRIDE)
+        # prepass counts taken from this encode's own nibble streams of every STRIDE-th brick
+        v, _ = csgv.csgv_encode_bricks_sampled(vol, b, STRIDE, K_max=args.k_max, S_min=args.s_min)
         if ev:
             ev[1].record(stream)
-        v = csgv.csgv_encode_bricks(vol, b, table, K_max=args.k_max, S_min=args.s_min)
-        if ev:
-            ev[2].record(stream)
         csgv.csgv_decode_bricks(v, ids, lods, out, offs, status)
         if ev:
-            ev[3].record(stream)
+            ev[2].record(stream)
         return v
 
     clk = ClockSampler(local).__enter__()
+    prev = None
     for _ in range(args.warmup):
-        step()
+        v = step()
+        if prev is not None:
+            prev.close_async(stream.cuda_stream)
+        prev = v
     torch.cuda.synchronize(dev)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     vols = []
     if world > 1:
         torch.distributed.barrier()
@@ -487,13 +499,17 @@ def main():
         csgv.profile_enable(True)  # per-kernel CUDA events on the launching stream
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
         t_start.record(stream)
         for s in range(args.steps):
-            vols.append(step(evs[s]))
-            if len(vols) > 2:
-                vols.pop(0).close()
+            v = step(evs[s])
+            if prev is not None:
+                prev.close_async(stream.cuda_stream)  # in stream order, after the decode that used it
+            prev = v
         t_end.record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark(w0, time.time())
+        vols = [prev]
         csgv.profile_enable(False)
         prof = csgv.profile_read()
     clk.__exit__()
@@ -505,8 +521,8 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
-    ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
-    prep_ms, enc_ms, dec_ms = (float(np.median(ph[:, i])) for i in range(3))
+    ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])] for e in evs])
+    enc_ms, dec_ms = (float(np.median(ph[:, i])) for i in range(2))
     assert bool((status == 0).all()), "decode reported errors"
     v = vols[-1]
     inf = v.info()
@@ -570,7 +586,7 @@ def main():
     host_leaves = {"decode_gbs": out_bytes / (float(np.median(hl)) / 1e3) / 1e9,
                    "device_bytes_saved": int(inf.leaf_words) * 2}
 
-    # end to end through the public API with host buffers: H2D volume, prepass, encode, decode, D2H labels
+    # end to end through the public API with host buffers: H2D volume, encode with tables, decode, D2H labels
     host_vol = torch.from_numpy(vol_np.view(np.int32)).pin_memory()
     host_out = torch.empty(n * b ** 3, dtype=torch.int32).pin_memory()
     e2e = []
@@ -595,12 +611,12 @@ def main():
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD} 512^3 warped Voronoi, 20000 cells, 30% background, b={b}",
-                   "bricks": n, "lod": 0, "step": "prepass(stride 512)+encode+batched decode",
+                   "bricks": n, "lod": 0, "step": "encode with sampled tables (stride 512) + batched decode",
                    "K_max": args.k_max, "S_min": args.s_min,
                    "l2": "inputs and outputs (512 MiB each) larger than L2", "parallelism": f"replicas x{world}"},
-        "phases_ms": {"prepass": prep_ms, "encode": enc_ms, "decode": dec_ms},
+        "phases_ms": {"encode_with_tables": enc_ms, "decode": dec_ms},
         "decode_gbs": out_bytes / (dec_alone_ms / 1e3) / 1e9,
-        "encode_gbs": out_bytes / ((prep_ms + enc_ms) / 1e3) / 1e9,
+        "encode_gbs": out_bytes / (enc_ms / 1e3) / 1e9,
         "plain_decode_gbs": plain_gbs,
         "leaves_on_host": host_leaves,
         "batched_vs_plain": (out_bytes / (dec_alone_ms / 1e3) / 1e9) / plain_gbs if plain_gbs else None,

@@ -106,10 +106,31 @@ CSGV_API int csgv_freq_table_from_counts(const uint64_t counts[32], csgv_freq_ta
  * Brick encoder (Alg. 2, Sec. 3.2-3.4) for every brick of the volume, then
  * entropy coding and packing.  The library allocates the compressed arrays;
  * the returned volume owns them until csgv_volume_destroy.  cfg may be NULL
- * (defaults).  Synchronises `stream` (reads sizes back to allocate).
+ * (defaults).  Synchronises `stream` once per encode batch (reads the sizes
+ * back to allocate), then packs asynchronously on it: the volume is complete
+ * in the order of `stream`.  Decodes on other streams wait for it through an
+ * event the library records (except inside a stream capture, which cannot
+ * depend on uncaptured work: launch such a graph once the volume is complete);
+ * csgv_volume_export and csgv_volume_destroy synchronise the device.
  */
 CSGV_API int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
                        const csgv_config *cfg, csgv_volume **out, void *stream);
+
+/*
+ * Prepass and encode in one call: the op streams of every brick are made first
+ * (they do not depend on the tables), the nibbles of every sample_stride-th
+ * brick are counted from them, the tables are normalised from those counts as
+ * csgv_build_freq_table does, and the streams are then entropy-coded.  The
+ * result is byte-identical to csgv_build_freq_table followed by
+ * csgv_encode_bricks, without coding the sampled bricks twice.  *table_out
+ * (if not NULL) receives the tables.  The counts, the tables and the coding
+ * stay on the device; the call synchronises `stream` once, like
+ * csgv_encode_bricks.  Volumes larger than one encode batch take the two-call
+ * path internally.
+ */
+CSGV_API int csgv_encode_bricks_sampled(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b,
+                                        uint32_t sample_stride, const csgv_config *cfg, csgv_freq_table *table_out,
+                                        csgv_volume **out, void *stream);
 
 /*
  * Batched decoding (Alg. 1, Sec. 4.1: "the decompression is executed in
@@ -248,6 +269,18 @@ CSGV_API void csgv_serve_destroy(csgv_server *s);
 
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
+
+/*
+ * Free a volume in stream order, without synchronising: its device arrays are
+ * released on `stream` once the work queued there before this call is done
+ * (and once the volume itself is complete, if it was made on another stream).
+ * Every call that uses the volume must already be queued on `stream`, or be
+ * ordered before it; the handle is invalid on return.  A volume whose leaf
+ * words are in host memory (csgv_volume_leaves_to_host) is freed as by
+ * csgv_volume_destroy.  Returns CSGV_ERR_CUDA if a free could not be queued
+ * (the volume is freed all the same).
+ */
+CSGV_API int csgv_volume_destroy_async(csgv_volume *vol, void *stream);
 
 /*
  * Detail separation (Sec. 4.2 of the paper): move the leaf streams (the data of

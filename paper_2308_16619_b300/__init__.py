@@ -21,7 +21,8 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
            "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune",
-           "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device")
+           "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device",
+           "csgv_encode_bricks_sampled", "csgv_volume_destroy_async")
 
 
 class CsgvError(RuntimeError):
@@ -78,6 +79,8 @@ def lib():
         vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
         L.csgv_decode_autotune.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, C.POINTER(DecodeTuning)]
         L.csgv_volume_leaves_to_host.argtypes = [vp]
+        L.csgv_encode_bricks_sampled.argtypes = [vp, vp, u32, u32, C.POINTER(Config), C.POINTER(FreqTable),
+                                                 C.POINTER(vp), vp]
         L.csgv_volume_leaves_to_device.argtypes = [vp]
         L.csgv_profile_enable.argtypes = [C.c_int]
         L.csgv_profile_read.argtypes = [u32, vp, vp, vp, vp]
@@ -91,6 +94,7 @@ def lib():
         L.csgv_volume_import.argtypes = [u32, vp, u32, u32, vp] + [vp] * 8 + [C.POINTER(vp)]
         L.csgv_volume_destroy.argtypes = [vp]
         L.csgv_volume_destroy.restype = None
+        L.csgv_volume_destroy_async.argtypes = [vp, vp]
         L.csgv_encode_bricks_noalloc.argtypes = [vp, vp, u32, C.POINTER(FreqTable), C.POINTER(Config),
                                                  vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]
         L.csgv_serve_create.argtypes = [vp, C.POINTER(ServeConfig), C.POINTER(vp)]
@@ -169,6 +173,12 @@ class Volume:
             lib().csgv_volume_destroy(self._h)
             self._h = C.c_void_p(0)
 
+    def close_async(self, stream=None):
+        """Free in stream order on `stream` (default: the current stream), without synchronising."""
+        if self._h and self._h.value:
+            h, self._h = self._h, C.c_void_p(0)
+            _check(lib().csgv_volume_destroy_async(h, _stream(stream)))
+
     def __del__(self):
         try:
             self.close()
@@ -200,6 +210,18 @@ def csgv_encode_bricks(vol, b, table, K_max=32, S_min=256, stream=None):
     _check(lib().csgv_encode_bricks(_ptr(vol), _dims3(vol), b, C.byref(table), C.byref(cfg), C.byref(h),
                                     _stream(stream)))
     return Volume(h.value)
+
+
+def csgv_encode_bricks_sampled(vol, b, sample_stride=1, K_max=32, S_min=256, stream=None):
+    """Prepass and encode in one call (tables from the nibbles of every sample_stride-th brick of this encode).
+    Returns (Volume, FreqTable)."""
+    assert vol.is_cuda and vol.element_size() == 4 and vol.is_contiguous()
+    cfg = Config(K_max, S_min)
+    t = FreqTable()
+    h = C.c_void_p()
+    _check(lib().csgv_encode_bricks_sampled(_ptr(vol), _dims3(vol), b, sample_stride, C.byref(cfg), C.byref(t),
+                                            C.byref(h), _stream(stream)))
+    return Volume(h.value), t
 
 
 def csgv_decode_bricks(volume, brick_ids, lods, out, out_offsets, status, stream=None, plain=False):

@@ -44,6 +44,7 @@ struct csgv_volume {
     uint16_t *leaf_host = nullptr;        // leaf words in mapped host memory (csgv_volume_leaves_to_host)
     uint64_t dec_ws_bytes = 192ull << 20;  // decode configuration (csgv_decode_autotune)
     uint32_t dec_rec_per_sm = 3;
+    cudaEvent_t ready = nullptr;  // recorded when the arrays are complete on the stream that made them
 };
 
 namespace {
@@ -122,26 +123,61 @@ bool valid_table(const uint32_t *f) {
 
 // Volume arrays come from a per-device stream-ordered pool (see dev_pool), so encoding a volume costs no
 // device-wide synchronisation; they are returned when the volume is destroyed.
-void vol_free_arrays(csgv_volume *v) {
+cudaError_t vol_free_arrays(csgv_volume *v, cudaStream_t st = 0) {
+    if (v->ready) cudaEventDestroy(v->ready);
+    v->ready = nullptr;
     void *arr[] = {v->pal_off, v->int_off, v->leaf_off, v->pal,       v->int_words,
                    v->leaf_host ? nullptr : v->leaf_words, v->n_int_sym, v->n_leaf_sym, v->lut};
+    cudaError_t err = cudaSuccess;
     for (void *a : arr)
-        if (a) cudaFreeAsync(a, 0);
+        if (a) {
+            const cudaError_t e = cudaFreeAsync(a, st);
+            if (e != cudaSuccess && err == cudaSuccess) err = e;
+        }
     if (v->leaf_host) cudaFreeHost(v->leaf_host);
     v->leaf_host = nullptr;
+    return err;
 }
 
-// decode table (2 x 4096 packed entries) from the frequencies, on the device
-__global__ void build_lut_kernel(csgv_freq_table t, uint32_t *lut) {
+// decode table (2 x 4096 packed entries) from the frequencies (freq_dev when given, else t), on the device
+__global__ void build_lut_kernel(csgv_freq_table t, const uint32_t *freq_dev, uint32_t *lut) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 2 * csgv::kM) return;
     const uint32_t tb = i / csgv::kM, slot = i % csgv::kM;
+    const uint32_t *f = (freq_dev ? freq_dev : t.freq) + 16 * tb;
     uint32_t cum = 0, s = 0;
-    while (s < 15 && cum + t.freq[16 * tb + s] <= slot) cum += t.freq[16 * tb + s++];
-    lut[i] = csgv::lut_pack(s, t.freq[16 * tb + s], slot - cum);
+    while (s < 15 && cum + f[s] <= slot) cum += f[s++];
+    lut[i] = csgv::lut_pack(s, f[s], slot - cum);
 }
 
-int vol_finish(csgv_volume *v, cudaStream_t st) {
+// Both tables from the nibble counts on the device, one warp: lane 16t + s holds symbol s of table t.  Same
+// result as normalise_table: f = 1 + floor(c (M - 16) / total), and the r leftover units go to the symbols of
+// rank < r, rank = the number of symbols with a larger count or an equal count and a lower index (the order
+// in which normalise_table hands them out).
+__global__ void __launch_bounds__(32) freq_from_counts_kernel(const unsigned long long *cnt, uint32_t *freq) {
+    const uint32_t lane = threadIdx.x, s = lane & 15;
+    const unsigned long long c = cnt[lane];
+    unsigned long long total = c;
+    for (int d = 1; d < 16; d <<= 1) total += __shfl_xor_sync(csgv::kFull, total, d);
+    const unsigned long long lim = ~0ull / (csgv::kM - 16);
+    unsigned long long q = 0;
+    if (total != 0)
+        q = c <= lim ? c * (csgv::kM - 16) / total
+                     : (unsigned long long)((unsigned __int128)c * (csgv::kM - 16) / total);
+    uint32_t f = 1u + (uint32_t)q;
+    uint32_t sum = f;
+    for (int d = 1; d < 16; d <<= 1) sum += __shfl_xor_sync(csgv::kFull, sum, d);
+    uint32_t rank = 0;
+    for (uint32_t o = 0; o < 16; o++) {
+        const unsigned long long co = __shfl_sync(csgv::kFull, c, (lane & 16u) | o);
+        rank += (co > c || (co == c && o < s)) ? 1u : 0u;
+    }
+    f += rank < csgv::kM - sum ? 1u : 0u;
+    freq[lane] = total == 0 ? csgv::kM / 16 : f;
+}
+
+// allocate and fill the volume's decode table on `st` from v->freq, or from freq_dev (device) when given
+int vol_lut(csgv_volume *v, const uint32_t *freq_dev, cudaStream_t st) {
     cudaMemPool_t pool;
     int rc = dev_pool(&pool);
     if (rc) return rc;
@@ -150,10 +186,16 @@ int vol_finish(csgv_volume *v, cudaStream_t st) {
     memcpy(t.freq, v->freq, sizeof t.freq);
     {
         csgv::ProfScope ps("build_lut", st);
-        build_lut_kernel<<<2 * csgv::kM / 256, 256, 0, st>>>(t, v->lut);
+        build_lut_kernel<<<2 * csgv::kM / 256, 256, 0, st>>>(t, freq_dev, v->lut);
     }
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(st));
+    return CSGV_OK;
+}
+
+// mark the volume complete in the order of `st`: calls on other streams wait for this event
+int vol_ready(csgv_volume *v, cudaStream_t st) {
+    if (!v->ready) CK(cudaEventCreateWithFlags(&v->ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(v->ready, st));
     return CSGV_OK;
 }
 
@@ -179,7 +221,8 @@ int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
 
 // Encoder scratch, kept per device between calls so that encoding does not allocate and free
 // gigabytes (cudaFree synchronises the whole device) on every call.  Guarded by g_arena_mu for the
-// whole encode call; the call synchronises its stream before it returns, so the next call may reuse it.
+// whole encode call; the next call's stream waits for g_arena_done (the previous call's last kernel
+// on the arena) before it writes the arena again.
 constexpr int kArenaDevices = 64;
 struct Arena {
     void *p = nullptr;
@@ -187,6 +230,8 @@ struct Arena {
 };
 Arena g_arena[kArenaDevices];
 std::mutex g_arena_mu;
+cudaEvent_t g_arena_done[kArenaDevices];  // recorded after the last kernel of an encode that read the arena
+void *g_readback[kArenaDevices];          // pinned host copy of an encode's per-batch results
 
 cudaError_t arena_get(int dev, size_t bytes, void **out) {
     Arena &A = g_arena[dev];
@@ -233,13 +278,33 @@ std::atomic<bool> g_prof_on{false};
 struct ProfRec {
     const char *name;
     cudaEvent_t e0, e1;
+    int dev;  // device the events belong to
 };
 std::vector<ProfRec> g_prof;
+std::vector<std::pair<int, cudaEvent_t>> g_prof_free;  // (device, event) ready for reuse
 }  // namespace
 bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
+cudaEvent_t prof_event() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (size_t i = g_prof_free.size(); i-- > 0;)
+            if (g_prof_free[i].first == dev) {
+                cudaEvent_t e = g_prof_free[i].second;
+                g_prof_free[i] = g_prof_free.back();
+                g_prof_free.pop_back();
+                return e;
+            }
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
 void prof_record(const char *name, cudaEvent_t e0, cudaEvent_t e1) {
+    int dev = 0;
+    cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof.push_back({name, e0, e1});
+    g_prof.push_back({name, e0, e1, dev});
 }
 }  // namespace csgv
 
@@ -249,33 +314,9 @@ const char *csgv_last_error(void) { return g_err.c_str(); }
 
 int csgv_freq_table_from_counts(const uint64_t counts[32], csgv_freq_table *out) {
     if (!counts || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
-    uint64_t c[32];
+    unsigned long long c[32];
     memcpy(c, counts, sizeof c);  // counts may alias out->counts
-    for (int t = 0; t < 2; t++) {
-        const uint64_t *ct = c + 16 * t;
-        uint32_t *f = out->freq + 16 * t;
-        uint64_t total = 0;
-        for (int s = 0; s < 16; s++) total += ct[s];
-        if (total == 0) {
-            for (int s = 0; s < 16; s++) f[s] = csgv::kM / 16;
-            continue;
-        }
-        // f = 1 + floor(c * (M - 16) / total); the r < 16 leftover units go +1 to the largest counts
-        uint32_t sum = 0;
-        for (int s = 0; s < 16; s++) {
-            const unsigned __int128 q = (unsigned __int128)ct[s] * (csgv::kM - 16) / total;
-            f[s] = 1u + (uint32_t)q;
-            sum += f[s];
-        }
-        bool used[16] = {false};
-        for (uint32_t k = 0; k < csgv::kM - sum; k++) {
-            int best = -1;
-            for (int s = 0; s < 16; s++)
-                if (!used[s] && (best < 0 || ct[s] > ct[best])) best = s;
-            used[best] = true;
-            f[best] += 1;
-        }
-    }
+    for (int t = 0; t < 2; t++) csgv::normalise_table(c + 16 * t, out->freq + 16 * t);
     memcpy(out->counts, c, sizeof c);
     return CSGV_OK;
 }
@@ -324,13 +365,17 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
     return csgv_freq_table_from_counts(out->counts, out);
 }
 
-int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
-                       const csgv_config *cfg, csgv_volume **out, void *stream) {
+// Encode with the given tables, or (table == NULL) with tables normalised from the nibble counts of every
+// sample_stride-th brick of this encode (written to *table_out when given).
+static int encode_impl(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
+                       uint32_t sample_stride, const csgv_config *cfg, csgv_freq_table *table_out,
+                       csgv_volume **out, void *stream) {
     uint32_t N;
     int rc = check_dims(dims, b, N);
     if (rc) return rc;
-    if (!vol_dev || !table || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
-    if (!valid_table(table->freq)) return fail(CSGV_ERR_INVALID_ARG, "frequency tables must sum to 4096 with f >= 1");
+    if (!vol_dev || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    if (table && !valid_table(table->freq)) return fail(CSGV_ERR_INVALID_ARG, "frequency tables must sum to 4096 with f >= 1");
+    if (!table && sample_stride == 0) return fail(CSGV_ERR_INVALID_ARG, "sample_stride must be >= 1");
     const uint32_t K_max = cfg ? cfg->K_max : 32, S_min = cfg ? cfg->S_min : 256;
     if (K_max < 1 || K_max > 32 || S_min < 1) return fail(CSGV_ERR_INVALID_ARG, "K_max must be 1..32, S_min >= 1");
     cudaStream_t st = (cudaStream_t)stream;
@@ -340,7 +385,6 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     v->N = N;
     v->K_max = K_max;
     v->S_min = S_min;
-    memcpy(v->freq, table->freq, sizeof v->freq);
     csgv::EncVol EV;
     EV.vol = vol_dev;
     v->n_bricks = 1;
@@ -358,15 +402,30 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     size_t budget = std::min<size_t>(free_b / 4, (size_t)6 << 30);
     uint64_t C = std::max<uint64_t>(1, std::min<uint64_t>(n, budget / per));
     C = std::min<uint64_t>(C, 65535);
+    csgv_freq_table made;
+    if (!table && C < n) {  // more than one batch: the tables are needed before the first one is coded
+        delete v;
+        rc = csgv_build_freq_table(vol_dev, dims, b, sample_stride, &made, stream);
+        if (rc) return rc;
+        if (table_out) *table_out = made;
+        return encode_impl(vol_dev, dims, b, &made, 1, cfg, nullptr, out, stream);
+    }
+    if (table) memcpy(v->freq, table->freq, sizeof v->freq);
 
+    int dev = -1;
     auto cleanup = [&](int code) {
+        // kernels already queued may still use the arena: the next encode waits for them
+        if (dev >= 0 && g_arena_done[dev]) cudaEventRecord(g_arena_done[dev], st);
         vol_free_arrays(v);
         delete v;
         return code;
     };
     csgv::EncScratch SC{};
-    uint32_t *freq_d = nullptr, *maxpal_d = nullptr;
-    uint64_t *tot_d = nullptr;
+    // what the host reads back after each batch, in one copy: running totals, prepass counts, maxima, tables
+    struct Readback {
+        unsigned long long tot[3], cnt[32];
+        uint32_t maxes[4], freq[32];
+    };
     auto free_tmp = [&]() {};  // scratch lives in the per-device arena
 #define CKE(call)                                                  \
     do {                                                           \
@@ -377,9 +436,10 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
         }                                                          \
     } while (0)
     std::lock_guard<std::mutex> arena_lock(g_arena_mu);
-    int dev = 0;
-    CKE(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kArenaDevices) return cleanup(fail(CSGV_ERR_INVALID_ARG, "device index %d too large", dev));
+    int d_ = 0;
+    CKE(cudaGetDevice(&d_));
+    if (d_ < 0 || d_ >= kArenaDevices) return cleanup(fail(CSGV_ERR_INVALID_ARG, "device index %d too large", d_));
+    dev = d_;
     // carve the batch scratch out of the arena (256-byte aligned pieces)
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -389,8 +449,7 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     };
     const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
     const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
-    const size_t o_sz = take(C * 8 * 4), o_f = take(32 * 4), o_t = take(3 * 8), o_m = take(3 * 4);
-    const size_t o_ops = take(C * G.ops_cap);
+    const size_t o_sz = take(C * 8 * 4), o_rb = take(sizeof(Readback)), o_ops = take(C * G.ops_cap);
     void *arena = nullptr;
     CKE(arena_get(dev, off, &arena));
     unsigned char *A = (unsigned char *)arena;
@@ -401,9 +460,11 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     SC.w_leaf = (uint16_t *)(A + o_wl);
     SC.sizes = (uint32_t *)(A + o_sz);
     SC.ops = A + o_ops;
-    freq_d = (uint32_t *)(A + o_f);
-    tot_d = (uint64_t *)(A + o_t);
-    maxpal_d = (uint32_t *)(A + o_m);
+    Readback *rb_d = (Readback *)(A + o_rb);
+    if (!g_readback[dev]) CKE(cudaMallocHost(&g_readback[dev], sizeof(Readback)));
+    Readback &rb = *(Readback *)g_readback[dev];
+    if (g_arena_done[dev]) CKE(cudaStreamWaitEvent(st, g_arena_done[dev], 0));  // the previous encode is done with it
+    else CKE(cudaEventCreateWithFlags(&g_arena_done[dev], cudaEventDisableTiming));
     cudaMemPool_t pool;
     if ((rc = dev_pool(&pool))) return cleanup(rc);
     CKE(cudaMallocFromPoolAsync((void **)&v->pal_off, (n + 1) * 8, pool, st));
@@ -411,18 +472,44 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
     CKE(cudaMallocFromPoolAsync((void **)&v->leaf_off, (n + 1) * 8, pool, st));
     CKE(cudaMallocFromPoolAsync((void **)&v->n_int_sym, n * 4, pool, st));
     CKE(cudaMallocFromPoolAsync((void **)&v->n_leaf_sym, n * 4, pool, st));
-    CKE(cudaMemcpyAsync(freq_d, table->freq, 32 * 4, cudaMemcpyHostToDevice, st));
-    CKE(cudaMemsetAsync(tot_d, 0, 3 * 8, st));
-    CKE(cudaMemsetAsync(maxpal_d, 0, 3 * 4, st));
+    if (table) {
+        memset(&rb, 0, sizeof rb);
+        memcpy(rb.freq, table->freq, sizeof rb.freq);
+        CKE(cudaMemcpyAsync(rb_d, &rb, sizeof rb, cudaMemcpyHostToDevice, st));
+    } else {
+        CKE(cudaMemsetAsync(rb_d, 0, sizeof(Readback), st));
+    }
     uint64_t cap_p = 0, cap_i = 0, cap_l = 0;
     uint64_t tot[3] = {0, 0, 0};
     for (uint64_t first = 0; first < n; first += C) {
         const uint32_t m = (uint32_t)std::min<uint64_t>(C, n - first);
-        CKE(csgv::launch_encode(EV, G, first, 1, m, freq_d, SC, nullptr, st));
-        CKE(csgv::launch_scan(SC.sizes, m, first, v->pal_off, v->int_off, v->leaf_off, tot_d, st));
+        if (table) {
+            CKE(csgv::launch_encode(EV, G, first, 1, m, rb_d->freq, SC, nullptr, st));
+        } else {
+            // op streams first (they do not depend on the tables), then the prepass counts from them, the
+            // tables from the counts, and the entropy coding, all on the device
+            CKE(csgv::launch_encode(EV, G, first, 1, m, nullptr, SC, nullptr, st));
+            CKE(csgv::launch_nibble_hist(G, SC, m, sample_stride, rb_d->cnt, st));
+            {
+                csgv::ProfScope ps("freq_tables", st);
+                freq_from_counts_kernel<<<1, 32, 0, st>>>(rb_d->cnt, rb_d->freq);
+            }
+            CKE(cudaGetLastError());
+            CKE(csgv::launch_rans_encode(G, SC, m, rb_d->freq, st));
+        }
+        CKE(csgv::launch_scan(SC.sizes, m, first, v->pal_off, v->int_off, v->leaf_off,
+                              (uint64_t *)rb_d->tot, rb_d->maxes, st));
+        if (first + m >= n && (rc = vol_lut(v, rb_d->freq, st))) return cleanup(rc);  // tables are final
         const uint64_t prev[3] = {tot[0], tot[1], tot[2]};
-        CKE(cudaMemcpyAsync(tot, tot_d, 3 * 8, cudaMemcpyDeviceToHost, st));
+        CKE(cudaMemcpyAsync(&rb, rb_d, sizeof rb, cudaMemcpyDeviceToHost, st));
         CKE(cudaStreamSynchronize(st));
+        for (int a = 0; a < 3; a++) tot[a] = rb.tot[a];
+        if (!table) {  // the sampled tables (one batch only)
+            memcpy(made.counts, rb.cnt, sizeof made.counts);
+            memcpy(made.freq, rb.freq, sizeof made.freq);
+            memcpy(v->freq, made.freq, sizeof v->freq);
+            if (table_out) *table_out = made;
+        }
         int g;
         const bool last = first + m >= n;  // a single batch is sized exactly
         if ((g = grow((void **)&v->pal, cap_p, std::max<uint64_t>(tot[0], 1), 4, prev[0], st, last && first == 0)) ||
@@ -432,23 +519,32 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
             return cleanup(g);
         }
         CKE(csgv::launch_compact(G, SC, first, m, v->pal_off, v->int_off, v->leaf_off, v->pal, v->int_words,
-                                 v->leaf_words, v->n_int_sym, v->n_leaf_sym, maxpal_d, st));
+                                 v->leaf_words, v->n_int_sym, v->n_leaf_sym, st));
     }
-    uint32_t maxes[3] = {0, 0, 0};
-    CKE(cudaMemcpyAsync(maxes, maxpal_d, 3 * 4, cudaMemcpyDeviceToHost, st));
-    CKE(cudaStreamSynchronize(st));
-    v->max_palette = maxes[0];
-    v->max_int_sym = maxes[1];
-    v->max_leaf_sym = maxes[2];
+    CKE(cudaEventRecord(g_arena_done[dev], st));
+    v->max_palette = rb.maxes[0];  // maxima over every batch (raised by each scan)
+    v->max_int_sym = rb.maxes[1];
+    v->max_leaf_sym = rb.maxes[2];
     free_tmp();
 #undef CKE
     v->n_pal = tot[0];
     v->n_iw = tot[1];
     v->n_lw = tot[2];
-    rc = vol_finish(v, st);
+    rc = vol_ready(v, st);
     if (rc) return cleanup(rc);
     *out = v;
     return CSGV_OK;
+}
+
+int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
+                       const csgv_config *cfg, csgv_volume **out, void *stream) {
+    if (!table) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    return encode_impl(vol_dev, dims, b, table, 1, cfg, nullptr, out, stream);
+}
+
+int csgv_encode_bricks_sampled(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, uint32_t sample_stride,
+                               const csgv_config *cfg, csgv_freq_table *table_out, csgv_volume **out, void *stream) {
+    return encode_impl(vol_dev, dims, b, nullptr, sample_stride, cfg, table_out, out, stream);
 }
 
 static int decode_args(const csgv_volume *vol, const uint32_t *ids, const uint8_t *lods, uint32_t n, uint32_t *out,
@@ -479,6 +575,11 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, v->dec_ws_bytes / stride));
     const size_t info_bytes = ((size_t)S * 8 + 255) & ~(size_t)255;
     const size_t bytes = 256 + info_bytes + (size_t)S * stride;
+    // the volume may come from another stream; a captured graph cannot depend on uncaptured work, so a
+    // decode being captured does not wait (the graph is launched once the volume is complete)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (v->ready && cap == cudaStreamCaptureStatusNone) CK(cudaStreamWaitEvent(st, v->ready, 0));
     void *ws = nullptr;
     CK(cudaMallocFromPoolAsync(&ws, bytes, pool, st));
     csgv::RecJob J;
@@ -710,7 +811,9 @@ int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint3
         delete v;
         return cuda_fail(e, "volume import");
     }
-    rc = vol_finish(v, 0);
+    rc = vol_lut(v, nullptr, 0);
+    if (!rc) rc = vol_ready(v, 0);
+    if (!rc && cudaStreamSynchronize(0) != cudaSuccess) rc = fail(CSGV_ERR_CUDA, "volume import: decode table");
     if (rc) {
         vol_free_arrays(v);
         delete v;
@@ -737,8 +840,8 @@ int csgv_profile_read(uint32_t max_kernels, char *names, double *total_ms, uint3
         float t = 0.f;
         cudaError_t e = cudaEventElapsedTime(&t, r.e0, r.e1);
         if (e != cudaSuccess && err == cudaSuccess) err = e;
-        cudaEventDestroy(r.e0);
-        cudaEventDestroy(r.e1);
+        csgv::g_prof_free.push_back({r.dev, r.e0});
+        csgv::g_prof_free.push_back({r.dev, r.e1});
         size_t k = 0;
         while (k < keys.size() && keys[k] != r.name) k++;
         if (k == keys.size()) {
@@ -759,6 +862,20 @@ int csgv_profile_read(uint32_t max_kernels, char *names, double *total_ms, uint3
     }
     *n_kernels = nk;
     return CSGV_OK;
+}
+
+int csgv_volume_destroy_async(csgv_volume *vol, void *stream) {
+    if (!vol) return CSGV_OK;
+    if (vol->leaf_host) {  // freeing page-locked host memory synchronises anyway
+        csgv_volume_destroy(vol);
+        return CSGV_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = vol->ready ? cudaStreamWaitEvent(st, vol->ready, 0) : cudaSuccess;
+    const cudaError_t ef = vol_free_arrays(vol, st);
+    delete vol;
+    if (e == cudaSuccess) e = ef;
+    return e == cudaSuccess ? CSGV_OK : cuda_fail(e, "csgv_volume_destroy_async");
 }
 
 void csgv_volume_destroy(csgv_volume *vol) {

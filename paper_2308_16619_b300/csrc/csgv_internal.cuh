@@ -41,6 +41,32 @@ __host__ __device__ inline uint32_t lut_pack(uint32_t sym, uint32_t f, uint32_t 
     return sym | (f << 4) | (bias << 17);
 }
 
+// One frequency table (16 symbols) normalised to M from nibble counts (Sec. 3.3; reading R11):
+// f = 1 + floor(c * (M - 16) / total), and the fewer than 16 units left over go one each to the largest
+// counts (ties to the lower symbol).  All-zero counts give the uniform table.  Host and device.
+__host__ __device__ inline void normalise_table(const unsigned long long *ct, uint32_t *f) {
+    unsigned long long total = 0;
+    for (int s = 0; s < 16; s++) total += ct[s];
+    if (total == 0) {
+        for (int s = 0; s < 16; s++) f[s] = kM / 16;
+        return;
+    }
+    uint32_t sum = 0;
+    for (int s = 0; s < 16; s++) {
+        const unsigned __int128 q = (unsigned __int128)ct[s] * (kM - 16) / total;
+        f[s] = 1u + (uint32_t)q;
+        sum += f[s];
+    }
+    uint32_t used = 0;
+    for (uint32_t k = 0; k < kM - sum; k++) {
+        int best = -1;
+        for (int s = 0; s < 16; s++)
+            if (!((used >> s) & 1u) && (best < 0 || ct[s] > ct[best])) best = s;
+        used |= 1u << best;
+        f[best] += 1;
+    }
+}
+
 // number of interleaved states for a stream of n symbols (R10)
 __host__ __device__ inline uint32_t lanes_for(uint32_t n, uint32_t K_max, uint32_t S_min) {
     if (n == 0) return 0;
@@ -52,23 +78,22 @@ __host__ __device__ inline uint32_t lanes_for(uint32_t n, uint32_t K_max, uint32
 
 // Kernel timing (csgv_profile_*): while enabled, a ProfScope around a launch records CUDA events on the
 // launching stream before and after it (api.cu keeps the records).
+// Events come from a per-device free list that csgv_profile_read refills, so that timing a launch costs
+// two event records and no event creation.
 bool prof_on();
+cudaEvent_t prof_event();  // nullptr if no event could be made
 void prof_record(const char *name, cudaEvent_t e0, cudaEvent_t e1);
 struct ProfScope {
     const char *name;
     cudaStream_t st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ProfScope(const char *n, cudaStream_t s) : name(n), st(s) {
-        if (prof_on() && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, st);
+        if (prof_on() && (e0 = prof_event()) && (e1 = prof_event())) cudaEventRecord(e0, st);
     }
     ~ProfScope() {
-        if (!e0) return;
-        if (cudaEventCreate(&e1) == cudaSuccess) {
-            cudaEventRecord(e1, st);
-            prof_record(name, e0, e1);
-        } else {
-            cudaEventDestroy(e0);
-        }
+        if (!e0 || !e1) return;
+        cudaEventRecord(e1, st);
+        prof_record(name, e0, e1);
     }
 };
 

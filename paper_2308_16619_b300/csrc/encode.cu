@@ -619,54 +619,129 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     }
 }
 
+// Nibble counts (interior then leaf) of the bricks of a batch whose slot is a multiple of `stride`, from
+// the nibbles in scratch: the counts of the frequency prepass (Sec. 3.3), taken from an encode.  Grid
+// (sampled bricks, kHistSplit): each CTA counts a share of one brick's nibbles, 16 bytes per load.  Counts
+// are packed 8 bits per bin in four 64-bit words per thread (bins 0-7, 8-15 interior; 16-23, 24-31 leaf):
+// a thread sees at most 2 x 16 bytes of each stream for b <= 32, far below 255.
+constexpr uint32_t kHistSplit = 8;
+
+__device__ __forceinline__ void hist16(uint4 v, uint32_t nb, unsigned long long &lo, unsigned long long &hi) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 16; k++) {
+        const uint32_t nib = (w[k >> 2] >> (8 * (k & 3))) & 15u;
+        const unsigned long long inc = k < nb ? 1ull << (8 * (nib & 7u)) : 0ull;
+        if (nib & 8u) hi += inc;
+        else lo += inc;
+    }
+}
+
+__global__ void __launch_bounds__(256) nibble_hist_kernel(EncGeom G, EncScratch SC, uint32_t stride,
+                                                          unsigned long long *counts) {
+    __shared__ uint32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t slot = blockIdx.x * stride;
+    const uint32_t *sz = SC.sizes + (size_t)slot * 8;
+    const uint32_t n_of[2] = {sz[1], sz[2]};
+    const uint4 *src[2] = {(const uint4 *)(SC.nib_int + (size_t)slot * G.int_cap),
+                           (const uint4 *)(SC.nib_leaf + (size_t)slot * G.leaf_cap)};
+    unsigned long long w[4] = {0, 0, 0, 0};
+    const uint32_t t0 = blockIdx.y * blockDim.x + threadIdx.x, step = kHistSplit * blockDim.x;
+#pragma unroll
+    for (int part = 0; part < 2; part++) {
+        const uint32_t n = n_of[part];
+        for (uint32_t i = t0; 16 * i < n; i += step)
+            hist16(src[part][i], min(16u, n - 16 * i), w[2 * part], w[2 * part + 1]);
+    }
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (uint32_t bin = 0; bin < 32; bin++) {
+        const uint32_t c = __reduce_add_sync(kFull, (uint32_t)(w[bin >> 3] >> (8 * (bin & 7))) & 255u);
+        if (lane == 0 && c) atomicAdd(&h[bin], c);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(counts + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
 // Exclusive scan of per-brick sizes (palette labels, interior words, leaf words) of one batch into the
-// volume's offset arrays, continuing from the running totals in tot[0..2]; writes the new totals.
+// volume's offset arrays, continuing from the running totals in tot[0..2]; writes the new totals.  Also
+// raises maxes[0..2] (when given) to the batch's largest palette, interior and leaf symbol counts.  One CTA:
+// thread t takes the contiguous run of bricks [t * per, (t + 1) * per), sums it, and the block scans the
+// 1024 sums.
 __global__ void __launch_bounds__(1024) scan_sizes_kernel(const uint32_t *sizes, uint32_t n, uint64_t first,
                                                           uint64_t *pal_off, uint64_t *int_off, uint64_t *leaf_off,
-                                                          uint64_t *tot) {
+                                                          uint64_t *tot, uint32_t *maxes) {
     __shared__ unsigned long long part[3][32];
+    __shared__ uint32_t mx[3][32];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned long long run[3] = {tot[0], tot[1], tot[2]};
-    for (uint32_t g = 0; g < n; g += 1024) {
-        const uint32_t i = g + tid;
-        unsigned long long v[3] = {0, 0, 0};
-        if (i < n) {
-            v[0] = sizes[8 * (size_t)i + 0];
-            v[1] = sizes[8 * (size_t)i + 3];
-            v[2] = sizes[8 * (size_t)i + 4];
-        }
-        unsigned long long inc[3] = {v[0], v[1], v[2]};
+    const uint32_t per = (n + 1023) / 1024, i0 = min(n, tid * per), i1 = min(n, i0 + per);
+    unsigned long long sum[3] = {0, 0, 0};
+    uint32_t big[3] = {0, 0, 0};
+#pragma unroll 4
+    for (uint32_t i = i0; i < i1; i++) {
+        const uint4 q = *(const uint4 *)(sizes + 8 * (size_t)i);  // n_pal, n_int_sym, n_leaf_sym, n_int_words
+        const uint32_t nwl = sizes[8 * (size_t)i + 4];
+        sum[0] += q.x;
+        sum[1] += q.w;
+        sum[2] += nwl;
+        big[0] = max(big[0], q.x);
+        big[1] = max(big[1], q.y);
+        big[2] = max(big[2], q.z);
+    }
+    unsigned long long inc[3] = {sum[0], sum[1], sum[2]};
 #pragma unroll
-        for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 3; a++) {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long u = __shfl_up_sync(kFull, inc[a], d);
+            if (lane >= (uint32_t)d) inc[a] += u;
+        }
+        big[a] = __reduce_max_sync(kFull, big[a]);
+    }
+    if (lane == 31)
+        for (int a = 0; a < 3; a++) part[a][warp] = inc[a];
+    if (lane == 0)
+        for (int a = 0; a < 3; a++) mx[a][warp] = big[a];
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the 32 warp totals, in place
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const unsigned long long t = part[a][lane];
+            unsigned long long x = t;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long u = __shfl_up_sync(kFull, inc[a], d);
-                if (lane >= (uint32_t)d) inc[a] += u;
+                const unsigned long long u = __shfl_up_sync(kFull, x, d);
+                if (lane >= (uint32_t)d) x += u;
             }
-        if (lane == 31)
-            for (int a = 0; a < 3; a++) part[a][warp] = inc[a];
-        __syncthreads();
-        unsigned long long wo[3] = {0, 0, 0}, bt[3] = {0, 0, 0};
-        for (uint32_t w = 0; w < 32; w++)
-            for (int a = 0; a < 3; a++) {
-                if (w < warp) wo[a] += part[a][w];
-                bt[a] += part[a][w];
-            }
-        if (i < n) {
-            pal_off[first + i] = run[0] + wo[0] + inc[0] - v[0];
-            int_off[first + i] = run[1] + wo[1] + inc[1] - v[1];
-            leaf_off[first + i] = run[2] + wo[2] + inc[2] - v[2];
+            part[a][lane] = x - t;
         }
-        for (int a = 0; a < 3; a++) run[a] += bt[a];
-        __syncthreads();
     }
-    if (tid == 0) {
-        tot[0] = run[0];
-        tot[1] = run[1];
-        tot[2] = run[2];
+    __syncthreads();
+    unsigned long long run[3];
+    for (int a = 0; a < 3; a++) run[a] = tot[a] + part[a][warp] + inc[a] - sum[a];  // before this thread's first brick
+    for (uint32_t i = i0; i < i1; i++) {
+        const uint4 q = *(const uint4 *)(sizes + 8 * (size_t)i);
+        const uint32_t nwl = sizes[8 * (size_t)i + 4];
+        pal_off[first + i] = run[0];
+        int_off[first + i] = run[1];
+        leaf_off[first + i] = run[2];
+        run[0] += q.x;
+        run[1] += q.w;
+        run[2] += nwl;
+    }
+    __syncthreads();  // every thread has read tot[] before thread 1023 moves it
+    if (tid == 1023) {  // holds the batch's inclusive totals
+        for (int a = 0; a < 3; a++) tot[a] = run[a];
         pal_off[first + n] = run[0];
         int_off[first + n] = run[1];
         leaf_off[first + n] = run[2];
+    }
+    if (tid < 3 && maxes) {
+        uint32_t m = maxes[tid];
+        for (uint32_t w = 0; w < 32; w++) m = max(m, mx[tid][w]);
+        maxes[tid] = m;
     }
 }
 
@@ -674,7 +749,7 @@ __global__ void __launch_bounds__(1024) scan_sizes_kernel(const uint32_t *sizes,
 __global__ void __launch_bounds__(256) compact_kernel(EncGeom G, EncScratch SC, uint64_t first, const uint64_t *pal_off,
                                                       const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal,
                                                       uint16_t *int_words, uint16_t *leaf_words, uint32_t *n_int_sym,
-                                                      uint32_t *n_leaf_sym, uint32_t *max_pal) {
+                                                      uint32_t *n_leaf_sym) {
     const uint32_t slot = blockIdx.x;
     const uint32_t *sz = SC.sizes + (size_t)slot * 8;
     const uint64_t id = first + slot;
@@ -690,9 +765,6 @@ __global__ void __launch_bounds__(256) compact_kernel(EncGeom G, EncScratch SC, 
     if (threadIdx.x == 0) {
         n_int_sym[id] = sz[1];
         n_leaf_sym[id] = sz[2];
-        atomicMax(max_pal, np);  // max_pal[0..2]: largest palette, interior and leaf symbol counts
-        atomicMax(max_pal + 1, sz[1]);
-        atomicMax(max_pal + 2, sz[2]);
     }
 }
 
@@ -736,7 +808,14 @@ cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, u
         encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess || count) return e;
+    if (e != cudaSuccess || count || !freq) return e;  // no tables yet: the caller codes later
+    return launch_rans_encode(G, SC, n, freq, st);
+}
+
+cudaError_t launch_rans_encode(const EncGeom &G, const EncScratch &SC, uint32_t n, const uint32_t *freq,
+                               cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e;
     const uint32_t smem_e = kRansEncWarps * kRansEncWin;
     e = cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
     if (e != cudaSuccess) return e;
@@ -747,24 +826,34 @@ cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, u
     return cudaGetLastError();
 }
 
+cudaError_t launch_nibble_hist(const EncGeom &G, const EncScratch &SC, uint32_t n, uint32_t stride,
+                               unsigned long long *counts, cudaStream_t st) {
+    const uint32_t sampled = (n + stride - 1) / stride;
+    if (sampled == 0) return cudaSuccess;
+    {
+        ProfScope ps("nibble_hist", st);
+        nibble_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan(const uint32_t *sizes, uint32_t n, uint64_t first, uint64_t *pal_off, uint64_t *int_off,
-                        uint64_t *leaf_off, uint64_t *tot, cudaStream_t st) {
+                        uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes, cudaStream_t st) {
     {
         ProfScope ps("scan_sizes", st);
-        scan_sizes_kernel<<<1, 1024, 0, st>>>(sizes, n, first, pal_off, int_off, leaf_off, tot);
+        scan_sizes_kernel<<<1, 1024, 0, st>>>(sizes, n, first, pal_off, int_off, leaf_off, tot, maxes);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t first, uint32_t n, const uint64_t *pal_off,
                            const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal, uint16_t *int_words,
-                           uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, uint32_t *max_pal,
-                           cudaStream_t st) {
+                           uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps("compact", st);
         compact_kernel<<<n, 256, 0, st>>>(G, SC, first, pal_off, int_off, leaf_off, pal, int_words, leaf_words, n_int_sym,
-                                          n_leaf_sym, max_pal);
+                                          n_leaf_sym);
     }
     return cudaGetLastError();
 }

@@ -36,11 +36,14 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min);
 size_t scratch_bytes_per_brick(const EncGeom &G);
 cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, uint64_t stride, uint32_t n,
                           const uint32_t *freq, const EncScratch &SC, unsigned long long *count, cudaStream_t st);
+cudaError_t launch_rans_encode(const EncGeom &G, const EncScratch &SC, uint32_t n, const uint32_t *freq,
+                               cudaStream_t st);
+cudaError_t launch_nibble_hist(const EncGeom &G, const EncScratch &SC, uint32_t n, uint32_t stride,
+                               unsigned long long *counts, cudaStream_t st);
 cudaError_t launch_scan(const uint32_t *sizes, uint32_t n, uint64_t first, uint64_t *pal_off, uint64_t *int_off,
-                        uint64_t *leaf_off, uint64_t *tot, cudaStream_t st);
+                        uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes, cudaStream_t st);
 cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t first, uint32_t n, const uint64_t *pal_off,
                            const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal, uint16_t *int_words,
-                           uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, uint32_t *max_pal,
-                           cudaStream_t st);
+                           uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, cudaStream_t st);
 
 }  // namespace csgv

@@ -164,7 +164,7 @@ int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], 
     if (e == cudaSuccess) e = cudaMemsetAsync(maxpal_d, 0, 3 * 4, st);
     if (e == cudaSuccess) e = csgv::launch_encode(EV, G, 0, 1, (uint32_t)n, freq_d, SC, nullptr, st);
     if (e == cudaSuccess)
-        e = csgv::launch_scan(SC.sizes, (uint32_t)n, 0, pal_off_dev, int_off_dev, leaf_off_dev, tot_d, st);
+        e = csgv::launch_scan(SC.sizes, (uint32_t)n, 0, pal_off_dev, int_off_dev, leaf_off_dev, tot_d, maxpal_d, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(totals, tot_d, 3 * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -178,7 +178,7 @@ int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], 
         return err(CSGV_ERR_INVALID_ARG, msg);
     }
     e = csgv::launch_compact(G, SC, 0, (uint32_t)n, pal_off_dev, int_off_dev, leaf_off_dev, pal_dev, int_words_dev,
-                             leaf_words_dev, n_int_sym_dev, n_leaf_sym_dev, maxpal_d, st);
+                             leaf_words_dev, n_int_sym_dev, n_leaf_sym_dev, st);
     if (e != cudaSuccess) {
         snprintf(msg, sizeof msg, "compact: %s", cudaGetErrorString(e));
         return err(CSGV_ERR_CUDA, msg);

@@ -305,3 +305,74 @@ def test_one_table_and_single_state_variants_round_trip():
         got = out.cpu().numpy().view(np.uint32).reshape(4, 6, 8, 16, 16, 16).transpose(0, 3, 1, 4, 2, 5)
         assert np.array_equal(got.reshape(vol.shape), vol)
         v.close()
+
+
+@pytest.mark.parametrize("b,shape,stride", [(32, (128, 128, 128), 1), (32, (128, 128, 128), 5),
+                                            (2, (64, 64, 128), 512)])
+def test_sampled_encode_equals_prepass_then_encode(b, shape, stride):
+    """csgv_encode_bricks_sampled (tables from the encode's own nibbles of every stride-th brick) gives the
+    same tables and byte-identical streams as csgv_build_freq_table followed by csgv_encode_bricks; the
+    2^3 case has more bricks than one encode batch and takes the two-call path inside."""
+    import torch
+    csgv = _csgv()
+    vol = synth.voronoi(shape, 300, seed=37, warp_amp=4, bg_permille=300)
+    d = torch.from_numpy(vol.view(np.int32)).cuda()
+    t1 = csgv.csgv_build_freq_table(d, b, stride)
+    v1 = csgv.csgv_encode_bricks(d, b, t1)
+    v2, t2 = csgv.csgv_encode_bricks_sampled(d, b, stride)
+    assert list(t1.freq) == list(t2.freq) and list(t1.counts) == list(t2.counts)
+    e1, e2 = v1.export(), v2.export()
+    for k in e1:
+        assert np.array_equal(e1[k], e2[k]), k
+    v1.close()
+    v2.close()
+
+
+@pytest.mark.parametrize("kind", ["constant", "halves", "stripes"])
+def test_sampled_tables_degenerate_counts(kind):
+    """Tables normalised on the device from sampled counts equal the host normalisation when the counts
+    are all zero (constant volume: uniform tables) or concentrated on one or two symbols (many zero-count
+    ties, leftover units going to the largest counts)."""
+    import torch
+    csgv = _csgv()
+    vol = np.full((64, 64, 64), 7, np.uint32)
+    if kind == "halves":
+        vol[:, :, 37:] = 9
+    elif kind == "stripes":
+        vol[:, :, ::2] = 3
+    d = torch.from_numpy(vol.view(np.int32)).cuda()
+    t1 = csgv.csgv_build_freq_table(d, 32, 1)
+    v2, t2 = csgv.csgv_encode_bricks_sampled(d, 32, 1)
+    hostt = csgv.csgv_freq_table_from_counts(list(t1.counts))
+    assert list(t1.freq) == list(hostt.freq) == list(t2.freq)
+    if kind == "constant":
+        assert list(t2.freq) == [256] * 32
+    v2.close()
+
+
+def test_destroy_async_then_reuse_memory():
+    """A volume freed in stream order right after its decode is queued decodes correctly, and a volume
+    encoded next (reusing the freed pool memory) decodes correctly too."""
+    import torch
+    csgv = _csgv()
+    outs = []
+    for seed in (41, 42, 43):
+        vol = synth.voronoi((64, 64, 96), 150, seed=seed, warp_amp=3, bg_permille=200)
+        d = torch.from_numpy(vol.view(np.int32)).cuda()
+        v, _ = csgv.csgv_encode_bricks_sampled(d, 16, 3)
+        n = v.info().n_bricks
+        ids = torch.arange(n, dtype=torch.int32, device="cuda")
+        lods = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        offs = torch.arange(n, dtype=torch.int64, device="cuda") * 16 ** 3
+        out = torch.empty(n * 16 ** 3, dtype=torch.int32, device="cuda")
+        status = torch.empty(n, dtype=torch.int32, device="cuda")
+        csgv.csgv_decode_bricks(v, ids, lods, out, offs, status)
+        v.close_async()
+        outs.append((vol, out, status))
+    torch.cuda.synchronize()
+    for vol, out, status in outs:
+        assert bool((status == 0).all())
+        got = out.view(-1, 16, 16, 16).cpu().numpy().view(np.uint32)
+        bz, by, bx = (s // 16 for s in vol.shape)
+        want = vol.reshape(bz, 16, by, 16, bx, 16).transpose(0, 2, 4, 1, 3, 5).reshape(-1, 16, 16, 16)
+        assert np.array_equal(got, want)
