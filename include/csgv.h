@@ -188,7 +188,7 @@ CSGV_API int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_m
  * offsets with n_bricks + 1 entries (u64), palettes (u32), interior and leaf
  * words (u16), symbol counts (u32, n_bricks).  *_capacity give the sizes of
  * pal_dev, int_words_dev and leaf_words_dev in elements.
- * Limits: at most 81 bricks of 32^3 (647 of 16^3, 4960 of 8^3, 25496 of 4^3,
+ * Limits: at most 81 bricks of 32^3 (647 of 16^3, 4954 of 8^3, 25496 of 4^3,
  * 49634 of 2^3) per call; larger volumes are rejected with
  * CSGV_ERR_INVALID_ARG and a message.  totals[3] (host) receives the number of
  * palette labels, interior words and leaf words; if an output array is too

@@ -116,8 +116,11 @@ struct EncSmem {
     __host__ __device__ static uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
 };
 
+// phase D reuses the whole dynamic area as per-warp op staging, at least 512 bytes per warp
+constexpr uint32_t kStageMin = 512;
 __host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes) {
-    return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + 64 * 4 + 256 * 8;
+    const uint32_t a = EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + 64 * 4 + 256 * 8;
+    return a > kEncWarps * kStageMin ? a : kEncWarps * kStageMin;
 }
 
 // exclusive block scan of one value per warp (warp totals in `red`), returns warp's offset and the total
@@ -150,6 +153,67 @@ __device__ __forceinline__ uint32_t node_label(const Brick &B, const EncSmem &S,
                                                uint32_t q) {
     if (l == 0) return B.at(compact5(q), compact5(q >> 1), compact5(q >> 2));
     return S.lab[loff(G.N, l) + q];
+}
+
+// Palette operations (Sec. 3.2) of up to 32 children in stream order, one per lane (lane k < kn: child k with
+// label `lab`), for warp 0 of the encoder.  The window `win` holds palette[i_p - f] in lane f (f <= 16; valid
+// for f <= ip).  Returns lane k's op (P_0, P_delta | delta << 4 or P_a), writes the P_a labels to pal (if
+// given) at np, np + 1, ..., and moves the window, ip and np past the chunk.
+// The chunk is resolved at once: a child whose label is neither in the window nor carried by an earlier child
+// of the chunk is a P_a; every other child finds its label at depth f = (the label's depth in the window, or
+// the appends since the label's first child in the chunk) plus the P_a before it.  If some f exceeds 16 (appends
+// in this chunk pushed a label out of the window) the chunk is walked child by child instead.  tmp: 32 words of
+// shared memory.
+__device__ __forceinline__ uint32_t palette_chunk(uint32_t lab, uint32_t kn, uint32_t &win, uint32_t &ip,
+                                                  uint32_t &np, uint32_t *pal, uint32_t *tmp) {
+    const uint32_t lane = threadIdx.x & 31;
+    const bool valid = lane < kn;
+    uint32_t pw = 32;  // depth of this child's label in the window (32: not in it)
+#pragma unroll
+    for (uint32_t f = 0; f <= 16; f++) {
+        const uint32_t w = __shfl_sync(kFull, win, f);
+        pw = (pw == 32 && f <= ip && w == lab) ? f : pw;
+    }
+    const uint32_t vmask = __ballot_sync(kFull, valid);
+    const uint32_t same = __match_any_sync(kFull, lab) & vmask;
+    const uint32_t first = __ffs(same) - 1;  // first child of the chunk with this label
+    const bool app = valid && pw == 32 && first == lane;
+    const uint32_t amask = __ballot_sync(kFull, app);
+    const uint32_t a_before = __popc(amask & lanemask_lt());
+    uint32_t f = 0;
+    if (valid && !app) f = pw != 32 ? a_before + pw : a_before - __popc(amask & ((1u << first) - 1u)) - 1u;
+    if (__ballot_sync(kFull, valid && !app && f > 16) == 0) {
+        const uint32_t A = __popc(amask);
+        if (pal && app) pal[np + a_before] = lab;
+        if (app && A - 1u - a_before < 17u) tmp[A - 1u - a_before] = lab;
+        __syncwarp();
+        const uint32_t old = __shfl_sync(kFull, win, (lane - A) & 31u);
+        win = lane < A ? tmp[lane & 31u] : old;
+        __syncwarp();
+        ip += A;
+        np += A;
+        return app ? OP_PA : (f == 0 ? OP_P0 : (OP_PD | ((f - 1u) << 4)));
+    }
+    uint32_t res = 0;
+    for (uint32_t k = 0; k < kn; k++) {
+        const uint32_t vk = __shfl_sync(kFull, lab, k);
+        const bool match = lane <= 16 && lane <= ip && win == vk;
+        const uint32_t mm = __ballot_sync(kFull, match);
+        uint32_t r;
+        if (mm) {
+            const uint32_t fm = __ffs(mm) - 1;
+            r = fm == 0 ? OP_P0 : (OP_PD | ((fm - 1) << 4));
+        } else {
+            r = OP_PA;
+            const uint32_t up = __shfl_up_sync(kFull, win, 1);
+            win = lane == 0 ? vk : up;
+            if (pal && lane == 0) pal[np] = vk;
+            ip += 1;
+            np += 1;
+        }
+        res = lane == k ? r : res;
+    }
+    return res;
 }
 
 // Encode (or, when count != nullptr, only count the nibbles of) one brick: phases A-D.
@@ -371,25 +435,7 @@ __global__ void __launch_bounds__(kEncThreads)
             for (uint32_t k0 = 0; k0 < n_need; k0 += 32) {
                 const uint32_t kn = min(32u, n_need - k0);
                 const uint2 mine2 = lane < kn ? S.plist[k0 + lane] : make_uint2(0u, 0u);
-                uint32_t res = 0;
-                for (uint32_t k = 0; k < kn; k++) {
-                    const uint32_t vk = __shfl_sync(kFull, mine2.y, k);
-                    const bool match = lane <= 16 && lane <= ip && win == vk;
-                    const uint32_t mm = __ballot_sync(kFull, match);
-                    uint32_t r;
-                    if (mm) {
-                        const uint32_t f = __ffs(mm) - 1;
-                        r = f == 0 ? OP_P0 : (OP_PD | ((f - 1) << 4));
-                    } else {
-                        r = OP_PA;
-                        const uint32_t up = __shfl_up_sync(kFull, win, 1);
-                        win = lane == 0 ? vk : up;
-                        if (pal && lane == 0) pal[np] = vk;
-                        ip += 1;
-                        np += 1;
-                    }
-                    res = lane == k ? r : res;
-                }
+                const uint32_t res = palette_chunk(mine2.y, kn, win, ip, np, pal, S.red);
                 if (lane < kn) {
                     ops[mine2.x] = (uint8_t)((ops[mine2.x] & 8u) | res);
                     if ((res & 7u) == OP_PD)
@@ -446,25 +492,7 @@ __global__ void __launch_bounds__(kEncThreads)
                 for (uint32_t k0 = 0; k0 < nk; k0 += 32) {
                     const uint32_t kn = min(32u, nk - k0);
                     const uint2 mine = lane < kn ? S.plist[k0 + lane] : make_uint2(0u, 0u);
-                    uint32_t res = 0;
-                    for (uint32_t k = 0; k < kn; k++) {
-                        const uint32_t vk = __shfl_sync(kFull, mine.y, k);
-                        const bool match = lane <= 16 && lane <= ip && win == vk;
-                        const uint32_t mm = __ballot_sync(kFull, match);
-                        uint32_t r;
-                        if (mm) {
-                            const uint32_t f = __ffs(mm) - 1;
-                            r = f == 0 ? OP_P0 : (OP_PD | ((f - 1) << 4));
-                        } else {
-                            r = OP_PA;
-                            const uint32_t up = __shfl_up_sync(kFull, win, 1);
-                            win = lane == 0 ? vk : up;
-                            if (pal && lane == 0) pal[np] = vk;
-                            ip += 1;
-                            np += 1;
-                        }
-                        res = lane == k ? r : res;
-                    }
+                    const uint32_t res = palette_chunk(mine.y, kn, win, ip, np, pal, S.red);
                     if (lane < kn) ops[mine.x] = (uint8_t)((ops[mine.x] & 8u) | res);
                 }
             }
@@ -487,11 +515,10 @@ __global__ void __launch_bounds__(kEncThreads)
                 pdl += __popc(__ballot_sync(kFull, pd && j >= n_int_ops));
             }
             if (lane == 0) {
-                S.red[warp] = pdi;
-                S.red[kEncWarps + warp] = pdl;
+                sh_pd[warp] = pdi;
+                sh_pd[kEncWarps + warp] = pdl;
             }
             __syncthreads();
-            pdc = S.red;
         }
         uint32_t bi = 0, bl = 0, toti = 0, totl = 0;
         for (uint32_t w2 = 0; w2 < kEncWarps; w2++) {
@@ -505,10 +532,18 @@ __global__ void __launch_bounds__(kEncThreads)
         sym_tot[1] = n_ops - n_int_ops + totl;
         uint8_t *nib_i = count ? nullptr : SC.nib_int + (size_t)slot * G.int_cap;
         uint8_t *nib_l = count ? nullptr : SC.nib_leaf + (size_t)slot * G.leaf_cap;
-        for (uint32_t g = j0; g < j1; g += 32) {
+        // this warp's ops are staged in shared memory (the pyramid and lists are dead now), stage bytes at a
+        // time with 16-byte loads: one round trip to L2 instead of one per 32 ops
+        const uint32_t stage = (G.smem / kEncWarps) & ~(kStageMin - 1u);
+        uint8_t *stg = smem_raw + warp * stage;
+        for (uint32_t js = j0; js < j1; js += stage) {
+            const uint32_t len = min(stage, j1 - js), nv = (len + 15u) >> 4;  // j0, js: multiples of 16
+            for (uint32_t q = lane; q < nv; q += 32) *(uint4 *)(stg + 16 * q) = *(const uint4 *)(ops + js + 16 * q);
+            __syncwarp();
+        for (uint32_t g = js; g < js + len; g += 32) {
             const uint32_t j = g + lane;
-            const bool in = j < j1;
-            const uint32_t o = in ? ops[j] : 0u;
+            const bool in = j < js + len;
+            const uint32_t o = in ? stg[j - js] : 0u;
             const uint32_t op = o & 7u;
             const bool pd = in && op == OP_PD;
             const bool leaf = j >= n_int_ops;
@@ -528,6 +563,8 @@ __global__ void __launch_bounds__(kEncThreads)
             }
             bi += __popc(mi);
             bl += __popc(ml);
+        }
+            __syncwarp();
         }
     }
     if (count) {
@@ -783,7 +820,9 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
     }
     G.up_nodes = u;
     const uint32_t b3 = G.b * G.b * G.b;
-    G.ops_cap = u + b3 - 1 > 256u ? u + b3 - 1 : 256u;  // every node but the root can be coded (>= 256: rANS staging)
+    // every node but the root can be coded (>= 256: rANS staging); a multiple of 16 so that each brick's op
+    // array starts on a 16-byte boundary (phase D stages it with 16-byte loads)
+    G.ops_cap = ((u + b3 - 1 > 256u ? u + b3 - 1 : 256u) + 15u) & ~15u;
     G.pal_cap = u + b3;             // palette: root + one per P_a
     G.int_cap = (2 * (u - 1) + 2 + 15) & ~15u;  // interior nibbles (op + delta each), 16-byte pitch
     G.leaf_cap = (2 * b3 + 15) & ~15u;

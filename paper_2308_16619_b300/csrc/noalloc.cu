@@ -13,7 +13,7 @@
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes
 // (32 MiB), present on every GPU that loads the library until the process
 // exits.  It holds the per-brick buffers of the encoder, so a call accepts at
-// most a fixed number of bricks (b = 32: 81, b = 16: 647, b = 8: 4960,
+// most a fixed number of bricks (b = 32: 81, b = 16: 647, b = 8: 4954,
 // b = 4: 25496, b = 2: 49634) and rejects larger volumes with
 // CSGV_ERR_INVALID_ARG.  Every call shares the array and it keeps the last
 // call's contents: the counters that must start at zero are cleared at the

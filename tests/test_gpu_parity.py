@@ -376,3 +376,24 @@ def test_destroy_async_then_reuse_memory():
         bz, by, bx = (s // 16 for s in vol.shape)
         want = vol.reshape(bz, 16, by, 16, bx, 16).transpose(0, 2, 4, 1, 3, 5).reshape(-1, 16, 16, 16)
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("block,n_labels", [(8, 18), (8, 23), (8, 40), (4, 23), (2, 19)])
+def test_palette_churn_byte_identical(block, n_labels):
+    """Blocks of block^3 voxels with labels drawn from 18-40 values: many palette ops per brick, labels that
+    leave the 17-entry window and come back, and P_delta at every depth; the encoder's streams are
+    byte-identical to the oracle's (8^3 blocks: up to a few hundred palette children per brick, 4^3 and
+    2^3: thousands)."""
+    torch = _torch()
+    csgv = _csgv()
+    rng = np.random.default_rng(block * 100 + n_labels)
+    shape = (32, 32, 64)
+    g = rng.integers(0, n_labels, size=(shape[0] // block, shape[1] // block, shape[2] // block))
+    vol = np.repeat(np.repeat(np.repeat(g, block, 0), block, 1), block, 2).astype(np.uint32) * 131 + 9
+    V = O.encode_volume(vol, 5, stride=1)
+    d = to_dev(vol)
+    t = csgv.csgv_build_freq_table(d, 32, 1)
+    assert np.array_equal(t.freq_array(), V.freq)
+    gv = csgv.csgv_encode_bricks(d, 32, t)
+    torch.cuda.synchronize()
+    assert_same_arrays(gv.export(), V)
