@@ -226,7 +226,9 @@ __global__ void __launch_bounds__(kEncThreads)
     __shared__ uint32_t sh_np;
     __shared__ uint32_t sh_npc;                 // children that need a palette op (phase B)
     __shared__ uint32_t sh_pd[2 * kEncWarps];   // P_delta ops per warp range of phase D, per stream (phase C)
-    __shared__ uint32_t lvl_base[kMaxN + 2], lvl_nact[kMaxN + 2];  // ops of children of parent level l
+    __shared__ uint32_t lvl_rank[kMaxN + 2];  // rank of the first active parent of level l; [0]: all of them
+    __shared__ uint32_t lvl_sp[kMaxN + 2];    // active parents stored before level l (level 1 first)
+    uint32_t n_act_total;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t slot = blockIdx.x;
     if (slot >= n_in_batch) return;
@@ -284,9 +286,12 @@ __global__ void __launch_bounds__(kEncThreads)
             }
         }
         __syncthreads();
+        // levels of more than 64 nodes by the whole CTA, the smaller ones by warp 0 alone (no CTA barriers)
         for (uint32_t l = 2; l <= N; l++) {
             const uint32_t nl = 1u << (3 * (N - l));
-            for (uint32_t i = tid; i < nl; i += kEncThreads) {
+            const bool big = nl > 64;
+            if (!big && warp != 0) break;
+            for (uint32_t i = big ? tid : lane; i < nl; i += big ? kEncThreads : 32u) {
                 const uint4 wa = *(const uint4 *)(S.lab + loff(G.N, l - 1) + 8 * i),
                             wb = *(const uint4 *)(S.lab + loff(G.N, l - 1) + 8 * i + 4);
                 const uint2 cs = *(const uint2 *)(S.cst + loff(G.N, l - 1) + 8 * i);  // 8 flags, 0 or 1 each
@@ -295,46 +300,102 @@ __global__ void __launch_bounds__(kEncThreads)
                 S.lab[loff(G.N, l) + i] = mode8(wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w, eq);
                 S.cst[loff(G.N, l) + i] = eq && allc;
             }
-            __syncthreads();
-        }
-    }
-
-    // ---- B. active parent lists and reuse operations, level by level (Alg. 2 traversal)
-    uint32_t n_ops = 0, n_int_ops = 0;
-    for (uint32_t l = N; l >= 1; l--) {
-        const uint32_t nl = 1u << (3 * (N - l));
-        // compact the active parents of level l (Morton order): each warp a contiguous range of 32-blocks
-        const uint32_t nblk = (nl + 31) / 32, bpw = (nblk + kEncWarps - 1) / kEncWarps;
-        const uint32_t b0 = min(warp * bpw, nblk), b1 = min(b0 + bpw, nblk);
-        uint32_t cnt = 0;
-        for (uint32_t bk = b0; bk < b1; bk++) {
-            const uint32_t i = 32 * bk + lane;
-            cnt += __popc(__ballot_sync(kFull, i < nl && !S.cst[loff(G.N, l) + i]));
-        }
-        uint32_t n_act;
-        uint32_t wb = block_excl_warp(S.red, cnt, n_act);
-        for (uint32_t bk = b0; bk < b1; bk++) {
-            const uint32_t i = 32 * bk + lane;
-            const bool act = i < nl && !S.cst[loff(G.N, l) + i];
-            const uint32_t m = __ballot_sync(kFull, act);
-            if (act) S.list[loff(G.N, l) + wb + __popc(m & lanemask_lt())] = (uint16_t)i;
-            wb += __popc(m);
+            if (big) __syncthreads();
+            else __syncwarp();
         }
         __syncthreads();
-        const uint32_t lc = l - 1;
-        const uint32_t nops_l = 8 * n_act;
-        if (tid == 0) {
-            lvl_base[l] = n_ops;
-            lvl_nact[l] = n_act;
+    }
+
+    // ---- B. active parents and reuse operations (Alg. 2 traversal).  The op array lists the children of the
+    // active (non-constant) parents level by level from the root down, 8 per parent, parents in Morton order
+    // within a level.  Ranking the active parents in that order (rank of a parent of level l = the active
+    // parents of the levels above plus those before it on level l) puts its children's ops at 8r .. 8r + 7,
+    // so every level is coded in one pass.  The flags are counted in their storage order (level 1 first),
+    // 16 per 16-byte load, by contiguous runs of chunks per thread.
+    {
+        const uint32_t ne = G.up_nodes, nq = (ne + 15) >> 4, cpt = (nq + kEncThreads - 1) / kEncThreads;
+        const uint32_t q0 = min(tid * cpt, nq), q1 = min(q0 + cpt, nq);
+        // active (flag 0) bytes of chunk q as a 16-bit mask, bytes at or past ne excluded
+        auto act_mask = [&](uint32_t q) {
+            const uint4 f = *(const uint4 *)(S.cst + 16 * q);
+            const uint32_t w[4] = {f.x, f.y, f.z, f.w};
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) m |= (((~w[k] & 0x01010101u) * 0x00204081u) >> 21 & 15u) << (4 * k);  // byte i -> bit i
+            const uint32_t valid = 16 * q + 16 <= ne ? 0xFFFFu : (1u << (ne - 16 * q)) - 1u;
+            return m & valid;
+        };
+        uint32_t cnt = 0;
+        for (uint32_t q = q0; q < q1; q++) cnt += __popc(act_mask(q));
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += u;
         }
+        uint32_t n_act_all;
+        const uint32_t wb = block_excl_warp(S.red, __shfl_sync(kFull, incl, 31), n_act_all);
+        const uint32_t base = wb + incl - cnt;  // active flags before this thread's first chunk
+        // level starts in storage order (levels 2..N); lvl_sp[l]: active flags before level l's first node
+        uint32_t bnd[kMaxN + 1];
+#pragma unroll
+        for (uint32_t l = 1; l <= (uint32_t)kMaxN; l++) bnd[l] = l <= N ? loff(G.N, l) : ne;
+        {
+            uint32_t run = base;
+            for (uint32_t q = q0; q < q1; q++) {
+                const uint32_t m = act_mask(q);
+#pragma unroll
+                for (uint32_t l = 2; l <= (uint32_t)kMaxN; l++)
+                    if (l <= N && bnd[l] >= 16 * q && bnd[l] < 16 * q + 16)
+                        lvl_sp[l] = run + __popc(m & ((1u << (bnd[l] - 16 * q)) - 1u));
+                run += __popc(m);
+            }
+        }
+        if (tid == 0) {
+            lvl_sp[1] = 0;
+            lvl_sp[N + 1] = n_act_all;
+        }
+        __syncthreads();
+        // stream rank of each active parent: S.list[rank] = its index within its level
+        uint32_t run = base;
+        for (uint32_t q = q0; q < q1; q++) {
+            uint32_t m = act_mask(q);
+            while (m) {
+                const uint32_t k = __ffs(m) - 1, e = 16 * q + k;
+                m &= m - 1;
+                uint32_t l = 1, lb = 0;
+#pragma unroll
+                for (uint32_t L = 2; L <= (uint32_t)kMaxN; L++)
+                    if (L <= N && e >= bnd[L]) {
+                        l = L;
+                        lb = bnd[L];
+                    }
+                const uint32_t r = n_act_all - lvl_sp[l + 1] + run - lvl_sp[l];
+                S.list[r] = (uint16_t)(e - lb);
+                run++;
+            }
+        }
+        if (tid <= N) lvl_rank[tid] = tid == 0 ? n_act_all : n_act_all - lvl_sp[tid + 1];  // first rank of level
+        __syncthreads();
+        n_act_total = n_act_all;
+    }
+    const uint32_t n_ops = 8 * n_act_total, n_int_ops = 8 * lvl_rank[1];
+    for (uint32_t r = tid; r < n_act_total; r += kEncThreads) {
+        uint32_t l = N;
+        for (uint32_t L = 1; L < N; L++)
+            if (r >= lvl_rank[L]) {
+                l = L;
+                break;
+            }
+        const uint32_t lc = l - 1;
+        const uint32_t p = S.list[r];
         // one thread per active parent: its 8 children, the parents next to it toward +axis, and the nodes
         // before its children toward -axis (children of the parent before it along that axis) are loaded
         // once; the 8 ops are chosen in registers and stored as one 8-byte word
         const uint32_t pbits = (1u << (3 * (N - l))) - 1u;  // Morton code bits of the parent level
         const uint32_t pmx = kMX & pbits, pmy = kMY & pbits, pmz = kMZ & pbits;
         const uint32_t *Lp = S.lab + loff(G.N, l);
-        for (uint32_t jj = tid; jj < n_act; jj += kEncThreads) {
-            const uint32_t p = S.list[loff(G.N, l) + jj];
+        {
             const uint32_t pl = Lp[p];
             // faces of the brick: no -axis neighbour on the low face, no +axis neighbour on the high face
             const bool lox = (p & pmx) == 0, loy = (p & pmy) == 0, loz = (p & pmz) == 0;
@@ -395,18 +456,16 @@ __global__ void __launch_bounds__(kEncThreads)
                 w[c >> 2] |= (op | (stop << 3)) << (8 * (c & 3u));
                 if (op == kNeedPal) {  // gathered with its label for the palette pass (first 256)
                     const uint32_t at = atomicAdd(&sh_npc, 1u);
-                    if (at < 256) S.plist[at] = make_uint2(n_ops + 8 * jj + c, v[c]);
+                    if (at < 256) S.plist[at] = make_uint2(8 * r + c, v[c]);
                 }
             }
-            *(uint2 *)(ops + n_ops + 8 * jj) = make_uint2(w[0], w[1]);
+            *(uint2 *)(ops + 8 * r) = make_uint2(w[0], w[1]);
         }
-        n_ops += nops_l;
-        if (lc >= 1) n_int_ops = n_ops;
-        __syncthreads();
     }
+    __syncthreads();
 
     // each warp takes a contiguous range of the op array in phases C and D
-    const uint32_t per = ((n_ops + kEncWarps - 1) / kEncWarps + 31) & ~31u;
+    const uint32_t per = ((n_ops + kEncWarps - 1) / kEncWarps + 127) & ~127u;  // phase D: 128 ops per warp step
     const uint32_t j0 = min(warp * per, n_ops), j1 = min(j0 + per, n_ops);
 
     // ---- C. palette pass in stream order: warp 0 walks the children no reuse fits, with the last 17 palette
@@ -477,13 +536,15 @@ __global__ void __launch_bounds__(kEncThreads)
             // ... then their labels, one child per lane (the loads overlap)
             const uint32_t e0 = max(wbase, r0), e1 = min(wbase + cnt, r0 + 256);
             for (uint32_t e = e0 + lane; e < e1; e += 32) {
-                const uint32_t j = S.plist[e - r0].x;
-                uint32_t l = 1;
-                for (uint32_t L = N; L >= 2; L--)
-                    if (j >= lvl_base[L] && j < lvl_base[L] + 8 * lvl_nact[L]) l = L;
-                const uint32_t base = lvl_base[l];
-                const uint32_t p = S.list[loff(G.N, l) + ((j - base) >> 3)];
-                S.plist[e - r0].y = node_label(B, S, G, l - 1, 8 * p + ((j - base) & 7u));
+                const uint32_t j = S.plist[e - r0].x, r = j >> 3;
+                uint32_t l = N;
+                for (uint32_t L = 1; L < N; L++)
+                    if (r >= lvl_rank[L]) {
+                        l = L;
+                        break;
+                    }
+                const uint32_t p = S.list[r];
+                S.plist[e - r0].y = node_label(B, S, G, l - 1, 8 * p + (j & 7u));
             }
             __syncthreads();
             if (warp == 0) {
@@ -530,6 +591,8 @@ __global__ void __launch_bounds__(kEncThreads)
         }
         sym_tot[0] = n_int_ops + toti;
         sym_tot[1] = n_ops - n_int_ops + totl;
+        // next nibble position of this warp's range in each stream: index in the stream plus the P_delta before
+        uint32_t oi = j0 + bi, ol = (j0 > n_int_ops ? j0 - n_int_ops : 0u) + bl;
         uint8_t *nib_i = count ? nullptr : SC.nib_int + (size_t)slot * G.int_cap;
         uint8_t *nib_l = count ? nullptr : SC.nib_leaf + (size_t)slot * G.leaf_cap;
         // this warp's ops are staged in shared memory (the pyramid and lists are dead now), stage bytes at a
@@ -540,30 +603,48 @@ __global__ void __launch_bounds__(kEncThreads)
             const uint32_t len = min(stage, j1 - js), nv = (len + 15u) >> 4;  // j0, js: multiples of 16
             for (uint32_t q = lane; q < nv; q += 32) *(uint4 *)(stg + 16 * q) = *(const uint4 *)(ops + js + 16 * q);
             __syncwarp();
-        for (uint32_t g = js; g < js + len; g += 32) {
-            const uint32_t j = g + lane;
-            const bool in = j < js + len;
-            const uint32_t o = in ? stg[j - js] : 0u;
-            const uint32_t op = o & 7u;
-            const bool pd = in && op == OP_PD;
-            const bool leaf = j >= n_int_ops;
-            const uint32_t mi = __ballot_sync(kFull, pd && !leaf), ml = __ballot_sync(kFull, pd && leaf);
-            const uint32_t pos = leaf ? j - n_int_ops + bl + __popc(ml & lanemask_lt()) : j + bi + __popc(mi & lanemask_lt());
-            const uint32_t nibble = op | (o & 8u);
-            const uint32_t delta = o >> 4;
-            if (in) {
-                if (count) {
-                    atomicAdd(&hist[16 * leaf + nibble], 1u);
-                    if (pd) atomicAdd(&hist[16 * leaf + delta], 1u);
-                } else {
-                    uint8_t *nb = leaf ? nib_l : nib_i;
-                    nb[pos] = (uint8_t)nibble;
-                    if (pd) nb[pos + 1] = (uint8_t)delta;
+            // 4 consecutive ops per lane (groups never straddle the interior / leaf boundary, a multiple of 8);
+            // a lane emits one nibble per op plus the delta nibble of a P_delta, at consecutive positions found
+            // by a warp scan of the nibble counts (interior in the low half, leaf in the high half)
+            for (uint32_t g = js; g < js + len; g += 128) {
+                const uint32_t j = g + 4 * lane;
+                const uint32_t nin = j < js + len ? min(4u, js + len - j) : 0u;
+                const uint32_t w = nin ? *(const uint32_t *)(stg + (j - js)) : 0u;
+                const bool leaf = j >= n_int_ops;
+                uint32_t pdm = 0;
+#pragma unroll
+                for (uint32_t k = 0; k < 4; k++)
+                    pdm |= (k < nin && ((w >> (8 * k)) & 7u) == OP_PD) ? 1u << k : 0u;
+                const uint32_t outn = nin + __popc(pdm);
+                const uint32_t v = leaf ? outn << 16 : outn;
+                uint32_t incl = v;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t u = __shfl_up_sync(kFull, incl, d);
+                    if (lane >= (uint32_t)d) incl += u;
                 }
+                const uint32_t excl = incl - v, tot = __shfl_sync(kFull, incl, 31);
+                if (count) {
+#pragma unroll
+                    for (uint32_t k = 0; k < 4; k++)
+                        if (k < nin) {
+                            const uint32_t o = (w >> (8 * k)) & 255u;
+                            atomicAdd(&hist[16 * leaf + (o & 15u)], 1u);
+                            if ((pdm >> k) & 1u) atomicAdd(&hist[16 * leaf + (o >> 4)], 1u);
+                        }
+                } else if (nin) {
+                    uint8_t *nb = leaf ? nib_l + ol + (excl >> 16) : nib_i + oi + (excl & 0xFFFFu);
+#pragma unroll
+                    for (uint32_t k = 0; k < 4; k++)
+                        if (k < nin) {
+                            const uint32_t o = (w >> (8 * k)) & 255u;
+                            *nb++ = (uint8_t)(o & 15u);
+                            if ((pdm >> k) & 1u) *nb++ = (uint8_t)(o >> 4);
+                        }
+                }
+                oi += tot & 0xFFFFu;
+                ol += tot >> 16;
             }
-            bi += __popc(mi);
-            bl += __popc(ml);
-        }
             __syncwarp();
         }
     }
