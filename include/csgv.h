@@ -178,6 +178,45 @@ CSGV_API int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_m
                        const uint32_t *n_int_sym_host, const uint32_t *n_leaf_sym_host, csgv_volume **out);
 
 /*
+ * Streaming encoder: the volume's bricks arrive in batches from any source
+ * (a procedural generator, a file read in pieces) and the raw volume never has
+ * to exist in device memory as a whole.  A batch is m whole bricks in
+ * brick-major order: brick i of the batch is b^3 uint32 labels at
+ * bricks_dev + i * b^3, x fastest within the brick, already padded (voxels
+ * past the volume's edge carry the clamp-to-edge labels).  Batches must come
+ * in brick-id order (first = the number of bricks added so far) and cover all
+ * bricks before csgv_stream_encoder_finish.  The result is the same volume
+ * csgv_encode_bricks makes from the whole raw volume with the same tables and
+ * configuration.
+ *
+ * csgv_stream_encoder_create: dims, b and cfg as for csgv_encode_bricks; the
+ * tables are required (see csgv_count_bricks for a prepass over sampled
+ * bricks).  Asynchronous on `stream`.
+ * csgv_stream_encoder_add: encodes the batch; the caller may reuse bricks_dev
+ * once the call returns (it synchronises `stream` once per internal batch).
+ * csgv_stream_encoder_finish: hands over the completed volume (complete in the
+ * order of `stream`) and frees the encoder.
+ * csgv_stream_encoder_destroy: abandons an unfinished encoder (synchronises the
+ * device).
+ */
+typedef struct csgv_stream_encoder csgv_stream_encoder;
+CSGV_API int csgv_stream_encoder_create(const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
+                                        const csgv_config *cfg, csgv_stream_encoder **out, void *stream);
+CSGV_API int csgv_stream_encoder_add(csgv_stream_encoder *enc, const uint32_t *bricks_dev, uint64_t first,
+                                     uint32_t m, void *stream);
+CSGV_API int csgv_stream_encoder_finish(csgv_stream_encoder *enc, csgv_volume **out, void *stream);
+CSGV_API void csgv_stream_encoder_destroy(csgv_stream_encoder *enc);
+
+/*
+ * Frequency prepass over a batch of bricks in the layout of
+ * csgv_stream_encoder_add (m bricks of b^3 labels, brick-major): adds the
+ * batch's 2 x 16 nibble counts to counts[0..31] (host, in/out), for
+ * csgv_freq_table_from_counts.  Synchronises `stream`.
+ */
+CSGV_API int csgv_count_bricks(const uint32_t *bricks_dev, uint32_t m, uint32_t b, uint64_t counts[32],
+                               void *stream);
+
+/*
  * Allocation-free brick encoder, for callers that cannot call cudaMalloc:
  * programs whose device memory belongs to their own pool allocator, and
  * loops that cannot afford cudaFree's device-wide synchronisation.  The

@@ -22,7 +22,9 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
            "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune",
            "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device",
-           "csgv_encode_bricks_sampled", "csgv_volume_destroy_async")
+           "csgv_encode_bricks_sampled", "csgv_volume_destroy_async", "csgv_stream_encoder_create",
+           "csgv_stream_encoder_add", "csgv_stream_encoder_finish", "csgv_stream_encoder_destroy",
+           "csgv_count_bricks")
 
 
 class CsgvError(RuntimeError):
@@ -95,6 +97,12 @@ def lib():
         L.csgv_volume_destroy.argtypes = [vp]
         L.csgv_volume_destroy.restype = None
         L.csgv_volume_destroy_async.argtypes = [vp, vp]
+        L.csgv_stream_encoder_create.argtypes = [vp, u32, C.POINTER(FreqTable), C.POINTER(Config), C.POINTER(vp), vp]
+        L.csgv_stream_encoder_add.argtypes = [vp, vp, u64, u32, vp]
+        L.csgv_stream_encoder_finish.argtypes = [vp, C.POINTER(vp), vp]
+        L.csgv_stream_encoder_destroy.argtypes = [vp]
+        L.csgv_stream_encoder_destroy.restype = None
+        L.csgv_count_bricks.argtypes = [vp, u32, u32, vp, vp]
         L.csgv_encode_bricks_noalloc.argtypes = [vp, vp, u32, C.POINTER(FreqTable), C.POINTER(Config),
                                                  vp, vp, u64, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]
         L.csgv_serve_create.argtypes = [vp, C.POINTER(ServeConfig), C.POINTER(vp)]
@@ -301,6 +309,52 @@ class DeviceView:
     def __init__(self, ptr, n):
         self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<u4", "data": (int(ptr), False),
                                          "version": 3}
+
+
+class StreamEncoder:
+    """Encoder fed with batches of whole bricks in brick-id order (brick-major device tensors of b^3 labels
+    per brick); finish() returns the Volume."""
+
+    def __init__(self, dims_xyz, b, table, K_max=32, S_min=256, stream=None):
+        self.b = b
+        cfg = Config(K_max, S_min)
+        h = C.c_void_p()
+        dims = (C.c_uint64 * 3)(*dims_xyz)
+        _check(lib().csgv_stream_encoder_create(dims, b, C.byref(table), C.byref(cfg), C.byref(h), _stream(stream)))
+        self._h = h
+
+    def add(self, bricks, first, stream=None):
+        assert bricks.is_cuda and bricks.element_size() == 4 and bricks.is_contiguous()
+        m = bricks.numel() // self.b ** 3
+        assert m * self.b ** 3 == bricks.numel()
+        _check(lib().csgv_stream_encoder_add(self._h, _ptr(bricks), first, m, _stream(stream)))
+
+    def finish(self, stream=None):
+        v = C.c_void_p()
+        _check(lib().csgv_stream_encoder_finish(self._h, C.byref(v), _stream(stream)))
+        self._h = C.c_void_p(0)
+        return Volume(v.value)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().csgv_stream_encoder_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def csgv_count_bricks(bricks, b, counts=None, stream=None):
+    """Add the nibble counts of a brick-major batch to counts (32 uint64, host); returns counts."""
+    assert bricks.is_cuda and bricks.element_size() == 4 and bricks.is_contiguous()
+    counts = np.zeros(32, np.uint64) if counts is None else counts
+    assert counts.dtype == np.uint64 and counts.shape == (32,) and counts.flags.c_contiguous
+    _check(lib().csgv_count_bricks(_ptr(bricks), bricks.numel() // b ** 3, b, counts.ctypes.data_as(C.c_void_p),
+                                   _stream(stream)))
+    return counts
 
 
 class Server:

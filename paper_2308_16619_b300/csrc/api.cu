@@ -365,6 +365,159 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
     return csgv_freq_table_from_counts(out->counts, out);
 }
 
+// What the host reads back after each encode batch, in one copy: running totals, prepass counts, maxima,
+// tables.  Lives in the arena (device) and in pinned memory (host).
+struct Readback {
+    unsigned long long tot[3], cnt[32];
+    uint32_t maxes[4], freq[32];
+};
+
+// A volume being encoded: its bricks are appended batch by batch (one call, or a stream encoder across calls).
+struct EncRun {
+    csgv_volume *v = nullptr;
+    csgv::EncGeom G{};
+    uint64_t cap_p = 0, cap_i = 0, cap_l = 0;  // allocated palette labels / interior words / leaf words
+    uint64_t tot[3] = {0, 0, 0};               // used so far
+    uint32_t maxes[3] = {0, 0, 0};             // largest palette, interior and leaf symbol counts so far
+};
+
+// bricks per encode batch: the scratch of a batch takes at most a quarter of free memory (6 GB at most)
+static uint64_t enc_batch_bricks(const csgv::EncGeom &G, uint64_t n) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t budget = std::min<size_t>(free_b / 4, (size_t)6 << 30);
+    const uint64_t C = std::max<uint64_t>(1, std::min<uint64_t>(n, budget / csgv::scratch_bytes_per_brick(G)));
+    return std::min<uint64_t>(C, 65535);
+}
+
+// the per-brick index arrays of a volume (offsets, symbol counts), from the pool
+static int vol_alloc_index(csgv_volume *v, cudaStream_t st) {
+    cudaMemPool_t pool;
+    int rc = dev_pool(&pool);
+    if (rc) return rc;
+    const uint64_t n = v->n_bricks;
+    CK(cudaMallocFromPoolAsync((void **)&v->pal_off, (n + 1) * 8, pool, st));
+    CK(cudaMallocFromPoolAsync((void **)&v->int_off, (n + 1) * 8, pool, st));
+    CK(cudaMallocFromPoolAsync((void **)&v->leaf_off, (n + 1) * 8, pool, st));
+    CK(cudaMallocFromPoolAsync((void **)&v->n_int_sym, n * 4, pool, st));
+    CK(cudaMallocFromPoolAsync((void **)&v->n_leaf_sym, n * 4, pool, st));
+    return CSGV_OK;
+}
+
+// Encode bricks ev_first .. ev_first + m - 1 of EV (brick ids of EV's grid) as the volume's bricks glob_first ..,
+// in batches of C.  table: the tables; NULL: tables normalised on the device from the nibbles of every
+// sample_stride-th brick of this run (a single batch; they are returned in *made and set in the volume).
+// build_lut: build the volume's decode table once the tables are final.  Synchronises st once per batch.
+static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint64_t glob_first, uint64_t m,
+                      uint64_t C, const csgv_freq_table *table, uint32_t sample_stride, csgv_freq_table *made,
+                      bool build_lut, cudaStream_t st) {
+    csgv_volume *v = R.v;
+    const csgv::EncGeom &G = R.G;
+    int rc = CSGV_OK, dev = -1;
+    auto bail = [&](int code) {
+        // kernels already queued may still use the arena: the next encode waits for them
+        if (dev >= 0 && g_arena_done[dev]) cudaEventRecord(g_arena_done[dev], st);
+        return code;
+    };
+#define CKE(call)                                          \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call)); \
+    } while (0)
+    std::lock_guard<std::mutex> arena_lock(g_arena_mu);
+    int d_ = 0;
+    CKE(cudaGetDevice(&d_));
+    if (d_ < 0 || d_ >= kArenaDevices) return fail(CSGV_ERR_INVALID_ARG, "device index %d too large", d_);
+    dev = d_;
+    // carve the batch scratch out of the arena (256-byte aligned pieces)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
+    const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
+    const size_t o_sz = take(C * 8 * 4), o_rb = take(sizeof(Readback)), o_ops = take(C * G.ops_cap);
+    void *arena = nullptr;
+    CKE(arena_get(dev, off, &arena));
+    unsigned char *A = (unsigned char *)arena;
+    csgv::EncScratch SC{};
+    SC.pal = (uint32_t *)(A + o_pal);
+    SC.nib_int = A + o_ni;
+    SC.nib_leaf = A + o_nl;
+    SC.w_int = (uint16_t *)(A + o_wi);
+    SC.w_leaf = (uint16_t *)(A + o_wl);
+    SC.sizes = (uint32_t *)(A + o_sz);
+    SC.ops = A + o_ops;
+    Readback *rb_d = (Readback *)(A + o_rb);
+    if (!g_readback[dev]) CKE(cudaMallocHost(&g_readback[dev], sizeof(Readback)));
+    Readback &rb = *(Readback *)g_readback[dev];
+    if (g_arena_done[dev]) CKE(cudaStreamWaitEvent(st, g_arena_done[dev], 0));  // the previous encode is done with it
+    else CKE(cudaEventCreateWithFlags(&g_arena_done[dev], cudaEventDisableTiming));
+    memset(&rb, 0, sizeof rb);
+    for (int a = 0; a < 3; a++) rb.tot[a] = R.tot[a];  // the scan continues from the running totals
+    if (table) memcpy(rb.freq, table->freq, sizeof rb.freq);
+    CKE(cudaMemcpyAsync(rb_d, &rb, sizeof rb, cudaMemcpyHostToDevice, st));
+    for (uint64_t j = 0; j < m; j += C) {
+        const uint32_t mm = (uint32_t)std::min<uint64_t>(C, m - j);
+        const uint64_t gfirst = glob_first + j;
+        if (table) {
+            CKE(csgv::launch_encode(EV, G, ev_first + j, 1, mm, rb_d->freq, SC, nullptr, st));
+        } else {
+            // op streams first (they do not depend on the tables), then the prepass counts from them, the
+            // tables from the counts, and the entropy coding, all on the device
+            CKE(csgv::launch_encode(EV, G, ev_first + j, 1, mm, nullptr, SC, nullptr, st));
+            CKE(csgv::launch_nibble_hist(G, SC, mm, sample_stride, rb_d->cnt, st));
+            {
+                csgv::ProfScope ps("freq_tables", st);
+                freq_from_counts_kernel<<<1, 32, 0, st>>>(rb_d->cnt, rb_d->freq);
+            }
+            CKE(cudaGetLastError());
+            CKE(csgv::launch_rans_encode(G, SC, mm, rb_d->freq, st));
+        }
+        CKE(csgv::launch_scan(SC.sizes, mm, gfirst, v->pal_off, v->int_off, v->leaf_off, (uint64_t *)rb_d->tot,
+                              rb_d->maxes, st));
+        const bool final_batch = j + mm >= m;
+        if (build_lut && final_batch && (rc = vol_lut(v, rb_d->freq, st))) return bail(rc);  // tables are final
+        const uint64_t prev[3] = {R.tot[0], R.tot[1], R.tot[2]};
+        CKE(cudaMemcpyAsync(&rb, rb_d, sizeof rb, cudaMemcpyDeviceToHost, st));
+        CKE(cudaStreamSynchronize(st));
+        for (int a = 0; a < 3; a++) {
+            R.tot[a] = rb.tot[a];
+            R.maxes[a] = std::max(R.maxes[a], rb.maxes[a]);
+        }
+        if (!table) {  // the sampled tables (one batch only)
+            memcpy(made->counts, rb.cnt, sizeof made->counts);
+            memcpy(made->freq, rb.freq, sizeof made->freq);
+            memcpy(v->freq, made->freq, sizeof v->freq);
+        }
+        // the whole volume in one batch: arrays sized exactly; otherwise grown geometrically
+        const bool exact = gfirst == 0 && mm == v->n_bricks;
+        int g;
+        if ((g = grow((void **)&v->pal, R.cap_p, std::max<uint64_t>(R.tot[0], 1), 4, prev[0], st, exact)) ||
+            (g = grow((void **)&v->int_words, R.cap_i, R.tot[1] + kWordPad, 2, prev[1], st, exact)) ||
+            (g = grow((void **)&v->leaf_words, R.cap_l, R.tot[2] + kWordPad, 2, prev[2], st, exact)))
+            return bail(g);
+        CKE(csgv::launch_compact(G, SC, gfirst, mm, v->pal_off, v->int_off, v->leaf_off, v->pal, v->int_words,
+                                 v->leaf_words, v->n_int_sym, v->n_leaf_sym, st));
+    }
+    CKE(cudaEventRecord(g_arena_done[dev], st));
+#undef CKE
+    return CSGV_OK;
+}
+
+// the volume's totals and maxima from a finished run
+static void run_finish(EncRun &R) {
+    csgv_volume *v = R.v;
+    v->max_palette = R.maxes[0];
+    v->max_int_sym = R.maxes[1];
+    v->max_leaf_sym = R.maxes[2];
+    v->n_pal = R.tot[0];
+    v->n_iw = R.tot[1];
+    v->n_lw = R.tot[2];
+}
+
 // Encode with the given tables, or (table == NULL) with tables normalised from the nibble counts of every
 // sample_stride-th brick of this encode (written to *table_out when given).
 static int encode_impl(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
@@ -395,13 +548,10 @@ static int encode_impl(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
         v->n_bricks *= v->grid[a];
     }
     const uint64_t n = v->n_bricks;
-    csgv::EncGeom G = csgv::make_geom(N, K_max, S_min);
-    const size_t per = csgv::scratch_bytes_per_brick(G);
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    size_t budget = std::min<size_t>(free_b / 4, (size_t)6 << 30);
-    uint64_t C = std::max<uint64_t>(1, std::min<uint64_t>(n, budget / per));
-    C = std::min<uint64_t>(C, 65535);
+    EncRun R;
+    R.v = v;
+    R.G = csgv::make_geom(N, K_max, S_min);
+    const uint64_t C = enc_batch_bricks(R.G, n);
     csgv_freq_table made;
     if (!table && C < n) {  // more than one batch: the tables are needed before the first one is coded
         delete v;
@@ -411,127 +561,18 @@ static int encode_impl(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
         return encode_impl(vol_dev, dims, b, &made, 1, cfg, nullptr, out, stream);
     }
     if (table) memcpy(v->freq, table->freq, sizeof v->freq);
-
-    int dev = -1;
-    auto cleanup = [&](int code) {
-        // kernels already queued may still use the arena: the next encode waits for them
-        if (dev >= 0 && g_arena_done[dev]) cudaEventRecord(g_arena_done[dev], st);
+    rc = vol_alloc_index(v, st);
+    if (!rc) rc = encode_run(R, EV, 0, 0, n, C, table, sample_stride, &made, true, st);
+    if (!rc) {
+        run_finish(R);
+        if (!table && table_out) *table_out = made;
+        rc = vol_ready(v, st);
+    }
+    if (rc) {
         vol_free_arrays(v);
         delete v;
-        return code;
-    };
-    csgv::EncScratch SC{};
-    // what the host reads back after each batch, in one copy: running totals, prepass counts, maxima, tables
-    struct Readback {
-        unsigned long long tot[3], cnt[32];
-        uint32_t maxes[4], freq[32];
-    };
-    auto free_tmp = [&]() {};  // scratch lives in the per-device arena
-#define CKE(call)                                                  \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) {                                   \
-            free_tmp();                                            \
-            return cleanup(cuda_fail(e_, #call));                  \
-        }                                                          \
-    } while (0)
-    std::lock_guard<std::mutex> arena_lock(g_arena_mu);
-    int d_ = 0;
-    CKE(cudaGetDevice(&d_));
-    if (d_ < 0 || d_ >= kArenaDevices) return cleanup(fail(CSGV_ERR_INVALID_ARG, "device index %d too large", d_));
-    dev = d_;
-    // carve the batch scratch out of the arena (256-byte aligned pieces)
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        const size_t o = off;
-        off = (off + bytes + 255) & ~(size_t)255;
-        return o;
-    };
-    const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
-    const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
-    const size_t o_sz = take(C * 8 * 4), o_rb = take(sizeof(Readback)), o_ops = take(C * G.ops_cap);
-    void *arena = nullptr;
-    CKE(arena_get(dev, off, &arena));
-    unsigned char *A = (unsigned char *)arena;
-    SC.pal = (uint32_t *)(A + o_pal);
-    SC.nib_int = A + o_ni;
-    SC.nib_leaf = A + o_nl;
-    SC.w_int = (uint16_t *)(A + o_wi);
-    SC.w_leaf = (uint16_t *)(A + o_wl);
-    SC.sizes = (uint32_t *)(A + o_sz);
-    SC.ops = A + o_ops;
-    Readback *rb_d = (Readback *)(A + o_rb);
-    if (!g_readback[dev]) CKE(cudaMallocHost(&g_readback[dev], sizeof(Readback)));
-    Readback &rb = *(Readback *)g_readback[dev];
-    if (g_arena_done[dev]) CKE(cudaStreamWaitEvent(st, g_arena_done[dev], 0));  // the previous encode is done with it
-    else CKE(cudaEventCreateWithFlags(&g_arena_done[dev], cudaEventDisableTiming));
-    cudaMemPool_t pool;
-    if ((rc = dev_pool(&pool))) return cleanup(rc);
-    CKE(cudaMallocFromPoolAsync((void **)&v->pal_off, (n + 1) * 8, pool, st));
-    CKE(cudaMallocFromPoolAsync((void **)&v->int_off, (n + 1) * 8, pool, st));
-    CKE(cudaMallocFromPoolAsync((void **)&v->leaf_off, (n + 1) * 8, pool, st));
-    CKE(cudaMallocFromPoolAsync((void **)&v->n_int_sym, n * 4, pool, st));
-    CKE(cudaMallocFromPoolAsync((void **)&v->n_leaf_sym, n * 4, pool, st));
-    if (table) {
-        memset(&rb, 0, sizeof rb);
-        memcpy(rb.freq, table->freq, sizeof rb.freq);
-        CKE(cudaMemcpyAsync(rb_d, &rb, sizeof rb, cudaMemcpyHostToDevice, st));
-    } else {
-        CKE(cudaMemsetAsync(rb_d, 0, sizeof(Readback), st));
+        return rc;
     }
-    uint64_t cap_p = 0, cap_i = 0, cap_l = 0;
-    uint64_t tot[3] = {0, 0, 0};
-    for (uint64_t first = 0; first < n; first += C) {
-        const uint32_t m = (uint32_t)std::min<uint64_t>(C, n - first);
-        if (table) {
-            CKE(csgv::launch_encode(EV, G, first, 1, m, rb_d->freq, SC, nullptr, st));
-        } else {
-            // op streams first (they do not depend on the tables), then the prepass counts from them, the
-            // tables from the counts, and the entropy coding, all on the device
-            CKE(csgv::launch_encode(EV, G, first, 1, m, nullptr, SC, nullptr, st));
-            CKE(csgv::launch_nibble_hist(G, SC, m, sample_stride, rb_d->cnt, st));
-            {
-                csgv::ProfScope ps("freq_tables", st);
-                freq_from_counts_kernel<<<1, 32, 0, st>>>(rb_d->cnt, rb_d->freq);
-            }
-            CKE(cudaGetLastError());
-            CKE(csgv::launch_rans_encode(G, SC, m, rb_d->freq, st));
-        }
-        CKE(csgv::launch_scan(SC.sizes, m, first, v->pal_off, v->int_off, v->leaf_off,
-                              (uint64_t *)rb_d->tot, rb_d->maxes, st));
-        if (first + m >= n && (rc = vol_lut(v, rb_d->freq, st))) return cleanup(rc);  // tables are final
-        const uint64_t prev[3] = {tot[0], tot[1], tot[2]};
-        CKE(cudaMemcpyAsync(&rb, rb_d, sizeof rb, cudaMemcpyDeviceToHost, st));
-        CKE(cudaStreamSynchronize(st));
-        for (int a = 0; a < 3; a++) tot[a] = rb.tot[a];
-        if (!table) {  // the sampled tables (one batch only)
-            memcpy(made.counts, rb.cnt, sizeof made.counts);
-            memcpy(made.freq, rb.freq, sizeof made.freq);
-            memcpy(v->freq, made.freq, sizeof v->freq);
-            if (table_out) *table_out = made;
-        }
-        int g;
-        const bool last = first + m >= n;  // a single batch is sized exactly
-        if ((g = grow((void **)&v->pal, cap_p, std::max<uint64_t>(tot[0], 1), 4, prev[0], st, last && first == 0)) ||
-            (g = grow((void **)&v->int_words, cap_i, tot[1] + kWordPad, 2, prev[1], st, last && first == 0)) ||
-            (g = grow((void **)&v->leaf_words, cap_l, tot[2] + kWordPad, 2, prev[2], st, last && first == 0))) {
-            free_tmp();
-            return cleanup(g);
-        }
-        CKE(csgv::launch_compact(G, SC, first, m, v->pal_off, v->int_off, v->leaf_off, v->pal, v->int_words,
-                                 v->leaf_words, v->n_int_sym, v->n_leaf_sym, st));
-    }
-    CKE(cudaEventRecord(g_arena_done[dev], st));
-    v->max_palette = rb.maxes[0];  // maxima over every batch (raised by each scan)
-    v->max_int_sym = rb.maxes[1];
-    v->max_leaf_sym = rb.maxes[2];
-    free_tmp();
-#undef CKE
-    v->n_pal = tot[0];
-    v->n_iw = tot[1];
-    v->n_lw = tot[2];
-    rc = vol_ready(v, st);
-    if (rc) return cleanup(rc);
     *out = v;
     return CSGV_OK;
 }
@@ -545,6 +586,111 @@ int csgv_encode_bricks(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t
 int csgv_encode_bricks_sampled(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, uint32_t sample_stride,
                                const csgv_config *cfg, csgv_freq_table *table_out, csgv_volume **out, void *stream) {
     return encode_impl(vol_dev, dims, b, nullptr, sample_stride, cfg, table_out, out, stream);
+}
+
+struct csgv_stream_encoder {
+    EncRun R;
+    csgv_freq_table table;
+    uint32_t b = 0;
+    uint64_t next = 0;  // bricks added so far
+};
+
+int csgv_stream_encoder_create(const uint64_t dims[3], uint32_t b, const csgv_freq_table *table,
+                               const csgv_config *cfg, csgv_stream_encoder **out, void *stream) {
+    uint32_t N;
+    int rc = check_dims(dims, b, N);
+    if (rc) return rc;
+    if (!table || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    if (!valid_table(table->freq)) return fail(CSGV_ERR_INVALID_ARG, "frequency tables must sum to 4096 with f >= 1");
+    const uint32_t K_max = cfg ? cfg->K_max : 32, S_min = cfg ? cfg->S_min : 256;
+    if (K_max < 1 || K_max > 32 || S_min < 1) return fail(CSGV_ERR_INVALID_ARG, "K_max must be 1..32, S_min >= 1");
+    *out = nullptr;
+    csgv_volume *v = new csgv_volume();
+    v->N = N;
+    v->K_max = K_max;
+    v->S_min = S_min;
+    v->n_bricks = 1;
+    for (int a = 0; a < 3; a++) {
+        v->dims[a] = dims[a];
+        v->grid[a] = (dims[a] + b - 1) / b;
+        v->n_bricks *= v->grid[a];
+    }
+    memcpy(v->freq, table->freq, sizeof v->freq);
+    rc = vol_alloc_index(v, (cudaStream_t)stream);
+    if (rc) {
+        vol_free_arrays(v);
+        delete v;
+        return rc;
+    }
+    csgv_stream_encoder *e = new csgv_stream_encoder();
+    e->R.v = v;
+    e->R.G = csgv::make_geom(N, K_max, S_min);
+    e->table = *table;
+    e->b = b;
+    *out = e;
+    return CSGV_OK;
+}
+
+int csgv_stream_encoder_add(csgv_stream_encoder *enc, const uint32_t *bricks_dev, uint64_t first, uint32_t m,
+                            void *stream) {
+    if (!enc || !enc->R.v) return fail(CSGV_ERR_INVALID_ARG, "NULL or finished encoder");
+    if (m == 0) return CSGV_OK;
+    if (!bricks_dev) return fail(CSGV_ERR_INVALID_ARG, "NULL bricks");
+    if (first != enc->next) return fail(CSGV_ERR_INVALID_ARG, "bricks must come in order: expected brick %llu, got %llu",
+                                        (unsigned long long)enc->next, (unsigned long long)first);
+    if (first + m > enc->R.v->n_bricks) return fail(CSGV_ERR_INVALID_ARG, "bricks past the end of the volume");
+    if (((uintptr_t)bricks_dev & 15u) != 0) return fail(CSGV_ERR_INVALID_ARG, "bricks_dev must be 16-byte aligned");
+    // the batch seen as a volume of m bricks stacked along z: its brick i is the batch's brick i
+    csgv::EncVol EV;
+    EV.vol = bricks_dev;
+    EV.dims[0] = EV.dims[1] = enc->b;
+    EV.dims[2] = (uint64_t)enc->b * m;
+    EV.nb[0] = EV.nb[1] = 1;
+    EV.nb[2] = m;
+    const uint64_t C = enc_batch_bricks(enc->R.G, m);
+    const int rc = encode_run(enc->R, EV, 0, first, m, C, &enc->table, 1, nullptr, false, (cudaStream_t)stream);
+    if (rc) return rc;
+    enc->next += m;
+    return CSGV_OK;
+}
+
+int csgv_stream_encoder_finish(csgv_stream_encoder *enc, csgv_volume **out, void *stream) {
+    if (!enc || !enc->R.v || !out) return fail(CSGV_ERR_INVALID_ARG, "NULL argument or finished encoder");
+    csgv_volume *v = enc->R.v;
+    if (enc->next != v->n_bricks)
+        return fail(CSGV_ERR_INVALID_ARG, "%llu of %llu bricks added", (unsigned long long)enc->next,
+                    (unsigned long long)v->n_bricks);
+    run_finish(enc->R);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = vol_lut(v, nullptr, st);
+    if (!rc) rc = vol_ready(v, st);
+    if (rc) return rc;
+    enc->R.v = nullptr;
+    delete enc;
+    *out = v;
+    return CSGV_OK;
+}
+
+void csgv_stream_encoder_destroy(csgv_stream_encoder *enc) {
+    if (!enc) return;
+    if (enc->R.v) {
+        cudaDeviceSynchronize();
+        vol_free_arrays(enc->R.v);
+        delete enc->R.v;
+    }
+    delete enc;
+}
+
+int csgv_count_bricks(const uint32_t *bricks_dev, uint32_t m, uint32_t b, uint64_t counts[32], void *stream) {
+    if (!counts) return fail(CSGV_ERR_INVALID_ARG, "NULL counts");
+    if (m == 0) return CSGV_OK;
+    if (!bricks_dev) return fail(CSGV_ERR_INVALID_ARG, "NULL bricks");
+    const uint64_t dims[3] = {b, b, (uint64_t)b * m};  // the bricks stacked along z
+    csgv_freq_table t;
+    const int rc = csgv_build_freq_table(bricks_dev, dims, b, 1, &t, stream);
+    if (rc) return rc;
+    for (int k = 0; k < 32; k++) counts[k] += t.counts[k];
+    return CSGV_OK;
 }
 
 static int decode_args(const csgv_volume *vol, const uint32_t *ids, const uint8_t *lods, uint32_t n, uint32_t *out,

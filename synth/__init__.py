@@ -37,6 +37,9 @@ def gpu_lib():
         _gpu_lib = C.CDLL(build_gpu())
         _gpu_lib.synth_worley_dev.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
                                               C.c_uint64, C.c_void_p]
+        _gpu_lib.synth_fiber_bricks_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint64,
+                                                    C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                                    C.c_uint64, C.c_void_p]
     return _gpu_lib
 
 
@@ -62,6 +65,8 @@ def lib():
                                           C.c_double, C.c_double, C.c_double, C.c_uint64]
         _lib.synth_worley.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint64,
                                       C.c_int]
+        _lib.synth_fibers.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                                      C.c_uint64]
         _lib.synth_label.restype = C.c_uint32
         _lib.synth_label.argtypes = [C.c_uint64, C.c_uint64]
     return _lib
@@ -105,6 +110,32 @@ def worley_device(shape_zyx, cell, seed):
                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0
     return vol
+
+
+def fibers(shape_zyx, cell, tubes, seed):
+    """Fiber volume (host, small volumes): tubes along Catmull-Rom splines, `tubes` per cell of cell^3 voxels
+    (gen.c, synth_fibers)."""
+    Z, Y, X = shape_zyx
+    vol = np.empty((Z, Y, X), np.uint32)
+    assert lib().synth_fibers(vol.ctypes.data_as(C.c_void_p), X, Y, Z, cell, tubes, seed) == 0
+    return vol
+
+
+def fiber_bricks_device(dims_xyz, b, cell, tubes, seed, first=0, m=None, ids=None, out=None):
+    """Bricks of the same fiber volume made on the current CUDA device without the volume: brick ids
+    first .. first + m - 1 (or the int64 device tensor `ids`), each b^3 labels x fastest, brick-major, in an
+    int32-typed torch tensor (out, if given)."""
+    import torch
+    X, Y, Z = dims_xyz
+    if ids is not None:
+        m = ids.numel()
+    if out is None:
+        out = torch.empty(m * b ** 3, dtype=torch.int32, device="cuda")
+    rc = gpu_lib().synth_fiber_bricks_dev(C.c_void_p(out.data_ptr()),
+                                          C.c_void_p(ids.data_ptr() if ids is not None else 0), first, m, X, Y, Z,
+                                          b, cell, tubes, seed, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, rc
+    return out
 
 
 def camera_trace(dims_xyz, b, n_frames, seed, width=1920, height=1080, fov_deg=45.0, device=None,
@@ -183,6 +214,8 @@ WORKLOADS = {
     "voronoi512": dict(shape=(512, 512, 512),
                        make=lambda: voronoi((512, 512, 512), 20000, seed=2, warp_amp=4, bg_permille=300)),
     "cells1024": dict(shape=(1024, 1024, 1024), make=lambda: ellipsoids((1024, 1024, 1024), 200000, seed=3)[0]),
+    # 4096 x 4096 x 2048 fibers: 1M tubes (8 per 64^3 cell), made brick by brick on the device, never whole
+    "fiber4096": dict(shape=(2048, 4096, 4096), cell=64, tubes=8, seed=5, make=None),
     # 2048 x 2048 x 1024 Worley cells on a 24-voxel jittered grid (made on the device: 16 GB)
     "worley2048": dict(shape=(1024, 2048, 2048), make=lambda: worley_device((1024, 2048, 2048), 24, seed=4)),
 }

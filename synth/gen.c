@@ -376,3 +376,109 @@ int synth_worley(uint32_t *vol, uint64_t X, uint64_t Y, uint64_t Z, uint32_t cel
     run_slabs(worley_slab, &W, Z, n_threads);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Fibers (stand-in for the paper's Fiber data set, the stress volume) */
+/* ------------------------------------------------------------------ */
+/*
+ * Tubes along Catmull-Rom splines.  The volume is cut into cells of G^3 voxels;
+ * cell (cx, cy, cz) owns T tubes, tube id t = cell * T + k with cell = cx + ncx *
+ * (cy + ncy * cz).  A tube has 5 control points: P0 uniform in the cell, then
+ * P_i = P_{i-1} + D + J_i per axis (D in [-8, 7] fixed per tube, J_i in [-4, 3]),
+ * clamped to the cell box grown by 32 voxels; radius r in {2..6} voxels.  Its
+ * two spans (P1 -> P2, P2 -> P3) are sampled at t = q / 16, q = 0..15, as balls
+ * of radius r: the centre in 1/8-voxel units is floor(num / 1024) with num =
+ * 8192 p1 + 256 A q + 16 B q^2 + C q^3 (A, B, C the Catmull-Rom coefficients:
+ * exact integers).  Voxel v (centre 8 v + 4 in those units) belongs to a ball
+ * iff sum_a (8 v_a + 4 - c_a)^2 <= (8 r)^2.  A voxel takes the label of the
+ * lowest tube id among the balls that hold it (synth_label of that id under
+ * seed ^ 0xF1BE5), else 0.  Every ball lies within 48 voxels of its cell box
+ * (clamp margin 32, spline overshoot below 5, radius 6), which is what a
+ * per-brick generator needs to find the tubes that reach a brick.
+ */
+#define FIB_BALLS 16
+#define FIB_MARGIN 32
+#define FIB_REACH 48
+
+static int64_t floor_div(int64_t a, int64_t d) { return a >= 0 ? a / d : -((-a + d - 1) / d); }
+
+static uint64_t fib_hash(uint64_t seed, uint64_t t, uint64_t j) { return hash2(seed ^ 0xF1BE5ull, t * 16 + j); }
+
+static void fib_tube(uint64_t seed, uint64_t t, const int64_t O[3], int64_t G, int64_t P[5][3], int64_t *R) {
+    const uint64_t h0 = fib_hash(seed, t, 0), h1 = fib_hash(seed, t, 1);
+    int64_t D[3];
+    for (int a = 0; a < 3; a++) {
+        P[0][a] = O[a] + (int64_t)(((h0 >> (16 * a)) & 0xFFFFull) % (uint64_t)G);
+        D[a] = (int64_t)((h1 >> (8 * a)) & 15ull) - 8;
+    }
+    for (int i = 1; i < 5; i++) {
+        const uint64_t h = fib_hash(seed, t, 1 + i);
+        for (int a = 0; a < 3; a++) {
+            int64_t p = P[i - 1][a] + D[a] + (int64_t)((h >> (8 * a)) & 7ull) - 4;
+            const int64_t lo = O[a] - FIB_MARGIN, hi = O[a] + G + FIB_MARGIN - 1;
+            P[i][a] = p < lo ? lo : (p > hi ? hi : p);
+        }
+    }
+    *R = 8 * (2 + (int64_t)(fib_hash(seed, t, 6) % 5));
+}
+
+static void fib_ball(const int64_t P[5][3], int span, int64_t q, int64_t c[3]) {
+    for (int a = 0; a < 3; a++) {
+        const int64_t p0 = P[span - 1][a], p1 = P[span][a], p2 = P[span + 1][a], p3 = P[span + 2][a];
+        const int64_t A = p2 - p0, B = 2 * p0 - 5 * p1 + 4 * p2 - p3, Cc = -p0 + 3 * p1 - 3 * p2 + p3;
+        c[a] = floor_div(8192 * p1 + 256 * A * q + 16 * B * q * q + Cc * q * q * q, 1024);
+    }
+}
+
+static int64_t isqrt64(int64_t n) {
+    int64_t w = (int64_t)sqrt((double)n);
+    while (w * w > n) w--;
+    while ((w + 1) * (w + 1) <= n) w++;
+    return w;
+}
+
+/* the whole volume, on the host (small volumes: tests and the oracle's inputs) */
+int synth_fibers(uint32_t *vol, uint64_t X, uint64_t Y, uint64_t Z, uint32_t cell, uint32_t tubes, uint64_t seed) {
+    if (!vol || !cell || !X || !Y || !Z) return 1;
+    const int64_t G = cell, dims[3] = {(int64_t)X, (int64_t)Y, (int64_t)Z};
+    const uint64_t ncx = (X + G - 1) / G, ncy = (Y + G - 1) / G, ncz = (Z + G - 1) / G;
+    const uint64_t nv = X * Y * Z;
+    for (uint64_t i = 0; i < nv; i++) vol[i] = 0xFFFFFFFFu;  /* lowest tube id so far */
+    for (uint64_t cz = 0; cz < ncz; cz++)
+        for (uint64_t cy = 0; cy < ncy; cy++)
+            for (uint64_t cx = 0; cx < ncx; cx++)
+                for (uint32_t k = 0; k < tubes; k++) {
+                    const uint64_t t = (cx + ncx * (cy + ncy * cz)) * tubes + k;
+                    const int64_t O[3] = {(int64_t)cx * G, (int64_t)cy * G, (int64_t)cz * G};
+                    int64_t P[5][3], R;
+                    fib_tube(seed, t, O, G, P, &R);
+                    for (int span = 1; span <= 2; span++)
+                        for (int64_t q = 0; q < FIB_BALLS; q++) {
+                            int64_t c[3];
+                            fib_ball(P, span, q, c);
+                            int64_t lo[3], hi[3];
+                            for (int a = 0; a < 3; a++) {
+                                lo[a] = -floor_div(-(c[a] - 4 - R), 8);  /* ceil */
+                                hi[a] = floor_div(c[a] - 4 + R, 8);
+                                if (lo[a] < 0) lo[a] = 0;
+                                if (hi[a] > dims[a] - 1) hi[a] = dims[a] - 1;
+                            }
+                            for (int64_t z = lo[2]; z <= hi[2]; z++) {
+                                const int64_t dz = 8 * z + 4 - c[2];
+                                for (int64_t y = lo[1]; y <= hi[1]; y++) {
+                                    const int64_t dy = 8 * y + 4 - c[1], rem = R * R - dz * dz - dy * dy;
+                                    if (rem < 0) continue;
+                                    const int64_t w = isqrt64(rem);
+                                    int64_t x0 = -floor_div(-(c[0] - 4 - w), 8), x1 = floor_div(c[0] - 4 + w, 8);
+                                    if (x0 < lo[0]) x0 = lo[0];
+                                    if (x1 > hi[0]) x1 = hi[0];
+                                    uint32_t *row = vol + (uint64_t)y * X + (uint64_t)z * X * Y;
+                                    for (int64_t x = x0; x <= x1; x++)
+                                        if ((uint32_t)t < row[x]) row[x] = (uint32_t)t;
+                                }
+                            }
+                        }
+                }
+    for (uint64_t i = 0; i < nv; i++) vol[i] = vol[i] == 0xFFFFFFFFu ? 0u : synth_label(seed ^ 0xF1BE5ull, vol[i]);
+    return 0;
+}
