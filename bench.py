@@ -312,8 +312,8 @@ def run_cells1024(args):
 
 def run_variants(args):
     """Coding variants on voronoi512 b=32 (compression ratio and decode speed): two tables with K_max = 32
-    (default), 16 and 1 (the paper's single rANS state), one table for both streams, and no rANS (raw
-    nibbles, two per byte; size from the symbol counts)."""
+    (default), 16 and 1 (the paper's single rANS state), one table for both streams, no rANS (raw nibbles,
+    two per byte; size from the symbol counts), and brick size 64."""
     import torch
     import synth
     import paper_2308_16619_b300 as csgv
@@ -360,6 +360,35 @@ def run_variants(args):
                 "cr_percent": 100.0 * (len(ex["pal"]) * 4 + raw_nibbles + n * (3 * 8 + 2 * 4)) / raw,
                 "decode_gbs": None}
         v.close()
+    # brick size 64 (the level arrays in global memory): its own tables, the default K_max
+    b64 = 64
+    n64 = vol_np.size // b64 ** 3
+    t64 = csgv.csgv_build_freq_table(vol, b64, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    v = csgv.csgv_encode_bricks(vol, b64, t64, S_min=args.s_min)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    enc64_ms = e0.elapsed_time(e1)
+    ids64 = torch.arange(n64, dtype=torch.int32, device=dev)
+    lods64 = torch.zeros(n64, dtype=torch.uint8, device=dev)
+    offs64 = torch.arange(n64, dtype=torch.int64, device=dev) * b64 ** 3
+    st64 = torch.empty(n64, dtype=torch.int32, device=dev)
+    ts = []
+    for r in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        csgv.csgv_decode_bricks(v, ids64, lods64, out, offs64, st64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if r >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+    assert bool((st64 == 0).all())
+    assert torch.equal(out.view(n64, b64, b64, b64)[0].cpu(), vol[:b64, :b64, :b64].cpu())
+    rows["b=64, two tables, K_max=32"] = {"cr_percent": 100.0 * v.info().compressed_bytes / raw,
+                                          "decode_gbs": raw / (float(np.median(ts)) / 1e3) / 1e9,
+                                          "encode_gbs": raw / (enc64_ms / 1e3) / 1e9}
+    v.close()
     line = {"metric": "compression ratio and decoded GB/s of coding variants", "value": rows["two tables, K_max=32"]["cr_percent"],
             "unit": "% of raw", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
             "dtype": "u32", "data": "synthetic",

@@ -16,7 +16,7 @@
  *     corrupt data is reported through status words.
  *
  * Stream format (fixed readings of the paper, Sec. 3):
- *   brick b = 2^N (N = 1..5), clamp-to-edge padding, brick id
+ *   brick b = 2^N (N = 1..6), clamp-to-edge padding, brick id
  *   bx + nbx * (by + nby * bz); per brick a palette of uint32 labels and two
  *   rANS-coded nibble streams (interior: children on levels N-1..1; leaf:
  *   children on level 0).  Nibble = op | stop << 3 with R_p=0 R_x=1 R_y=2
@@ -88,7 +88,7 @@ CSGV_API const char *csgv_last_error(void);
  * encoder in count-only mode over every brick whose id is a multiple of
  * sample_stride, counts interior and leaf nibbles, and normalises each
  * table to 4096 (f = 1 + floor(c * 4080 / total), remainder to the largest
- * counts).  vol_dev: dims[0]*dims[1]*dims[2] labels.  b: 2..32, a power of
+ * counts).  vol_dev: dims[0]*dims[1]*dims[2] labels.  b: 2..64, a power of
  * two.  Synchronises `stream` (reads 32 counters back).
  */
 CSGV_API int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint32_t b, uint32_t sample_stride,
@@ -227,8 +227,8 @@ CSGV_API int csgv_count_bricks(const uint32_t *bricks_dev, uint32_t m, uint32_t 
  * offsets with n_bricks + 1 entries (u64), palettes (u32), interior and leaf
  * words (u16), symbol counts (u32, n_bricks).  *_capacity give the sizes of
  * pal_dev, int_words_dev and leaf_words_dev in elements.
- * Limits: at most 81 bricks of 32^3 (647 of 16^3, 4954 of 8^3, 25496 of 4^3,
- * 49634 of 2^3) per call; larger volumes are rejected with
+ * Limits: at most 81 bricks of 32^3 (9 of 64^3, 647 of 16^3, 4954 of 8^3,
+ * 25496 of 4^3, 49634 of 2^3) per call; larger volumes are rejected with
  * CSGV_ERR_INVALID_ARG and a message.  totals[3] (host) receives the number of
  * palette labels, interior words and leaf words; if an output array is too
  * small the call returns CSGV_ERR_INVALID_ARG with totals filled and writes

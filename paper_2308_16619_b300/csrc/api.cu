@@ -14,15 +14,6 @@
 
 // kernels' launchers (decode.cu, encode.cu)
 namespace csgv {
-struct RecJob {
-    const uint32_t *ids;
-    const uint8_t *lods;
-    uint32_t n;
-    uint8_t *recs;
-    uint64_t stride, leaf_at, t8_at, t8_leaf_at;
-    uint32_t *info;
-    uint32_t *counter;
-};
 cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uint32_t *out, const uint64_t *out_off,
                                 int32_t *status, uint32_t rec_blocks, cudaStream_t st);
 }  // namespace csgv
@@ -213,7 +204,7 @@ csgv::VolDev dev_view(const csgv_volume *v) {
 
 int check_dims(const uint64_t dims[3], uint32_t b, uint32_t &N) {
     if (!dims) return fail(CSGV_ERR_INVALID_ARG, "dims is NULL");
-    if (!pow2_brick(b, N)) return fail(CSGV_ERR_INVALID_ARG, "brick size %u is not a power of two in [2, 32]", b);
+    if (!pow2_brick(b, N)) return fail(CSGV_ERR_INVALID_ARG, "brick size %u is not a power of two in [2, 64]", b);
     for (int a = 0; a < 3; a++)
         if (dims[a] == 0 || dims[a] > (1ull << 31)) return fail(CSGV_ERR_INVALID_ARG, "bad dimension %d", a);
     return CSGV_OK;
@@ -346,18 +337,23 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
     CK(cudaMallocFromPoolAsync((void **)&cnt, 32 * 8, pool, st));
     CK(cudaMemsetAsync(cnt, 0, 32 * 8, st));
     csgv::EncScratch SC{};
-    const uint64_t per_batch = 4096;  // sampled bricks per count-mode launch (op scratch: ops_cap bytes each)
-    CK(cudaMallocFromPoolAsync((void **)&SC.ops, std::min<uint64_t>(per_batch, n_sampled) * G.ops_cap, pool, st));
+    // sampled bricks per count-mode launch (op scratch, and for b = 64 the level arrays, per brick)
+    const uint64_t per_batch = std::min<uint64_t>(4096, ((uint64_t)1 << 31) / (G.ops_cap + G.lvl_bytes));
+    const uint64_t nb = std::min<uint64_t>(per_batch, n_sampled);
+    CK(cudaMallocFromPoolAsync((void **)&SC.ops, nb * G.ops_cap, pool, st));
+    if (G.lvl_bytes) CK(cudaMallocFromPoolAsync((void **)&SC.lvl, nb * G.lvl_bytes, pool, st));
     for (uint64_t first = 0; first < n_sampled; first += per_batch) {
         const uint32_t m = (uint32_t)std::min<uint64_t>(per_batch, n_sampled - first);
         cudaError_t e = csgv::launch_encode(EV, G, first * sample_stride, sample_stride, m, nullptr, SC, cnt, st);
         if (e != cudaSuccess) {
             cudaFreeAsync(SC.ops, st);
+            if (SC.lvl) cudaFreeAsync(SC.lvl, st);
             cudaFreeAsync(cnt, st);
             return cuda_fail(e, "encode (count mode)");
         }
     }
     cudaFreeAsync(SC.ops, st);
+    if (SC.lvl) cudaFreeAsync(SC.lvl, st);
     cudaError_t e = cudaMemcpyAsync(out->counts, cnt, 32 * 8, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(cnt, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -439,6 +435,7 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
     const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
     const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
     const size_t o_sz = take(C * 8 * 4), o_rb = take(sizeof(Readback)), o_ops = take(C * G.ops_cap);
+    const size_t o_lvl = take(C * G.lvl_bytes);
     void *arena = nullptr;
     CKE(arena_get(dev, off, &arena));
     unsigned char *A = (unsigned char *)arena;
@@ -450,6 +447,7 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
     SC.w_leaf = (uint16_t *)(A + o_wl);
     SC.sizes = (uint32_t *)(A + o_sz);
     SC.ops = A + o_ops;
+    SC.lvl = A + o_lvl;
     Readback *rb_d = (Readback *)(A + o_rb);
     if (!g_readback[dev]) CKE(cudaMallocHost(&g_readback[dev], sizeof(Readback)));
     Readback &rb = *(Readback *)g_readback[dev];
@@ -717,8 +715,21 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     const uint64_t leaf_at = ((uint64_t)v->max_int_sym + 7) & ~7ull;
     const uint64_t t8_at = a16(leaf_at + (((uint64_t)v->max_leaf_sym + 7) & ~7ull));
     const uint64_t t8_leaf_at = t8_at + a16((leaf_at / 8 + 1) * 2);
-    const uint64_t stride = t8_leaf_at + a16(((t8_at - leaf_at) / 8 + 1) * 2);
-    uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, v->dec_ws_bytes / stride));
+    uint64_t stride = t8_leaf_at + a16(((t8_at - leaf_at) / 8 + 1) * 2);
+    // b = 64: the request's level arrays (uint32 palette indices, constant flags) and parent list too
+    uint64_t lev_at = 0, flag_at = 0, list_at = 0;
+    if (v->N >= 6) {
+        uint64_t nodes = 0;
+        for (uint32_t l = 0; l <= v->N; l++) nodes += 1ull << (3 * (v->N - l));
+        lev_at = stride;
+        flag_at = lev_at + a16(nodes * 4);
+        list_at = flag_at + a16(nodes);
+        stride = list_at + a16((1ull << (3 * (v->N - 1))) * 4);
+    }
+    // b = 64 requests carry their level arrays (about 2 MB each): a larger budget keeps a slice above the
+    // SM count
+    const uint64_t budget = v->N >= 6 ? std::max<uint64_t>(v->dec_ws_bytes, 2ull << 30) : v->dec_ws_bytes;
+    uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, budget / stride));
     const size_t info_bytes = ((size_t)S * 8 + 255) & ~(size_t)255;
     const size_t bytes = 256 + info_bytes + (size_t)S * stride;
     // the volume may come from another stream; a captured graph cannot depend on uncaptured work, so a
@@ -736,6 +747,9 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     J.leaf_at = leaf_at;
     J.t8_at = t8_at;
     J.t8_leaf_at = t8_leaf_at;
+    J.lev_at = lev_at;
+    J.flag_at = flag_at;
+    J.list_at = list_at;
     cudaError_t e = cudaSuccess;
     for (uint64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += S) {
         J.n = (uint32_t)std::min<uint64_t>(S, n - r0);
@@ -899,7 +913,7 @@ int csgv_volume_import(uint32_t N, const uint64_t dims[3], uint32_t K_max, uint3
                        const uint16_t *int_words_host, const uint64_t *leaf_off_host, const uint16_t *leaf_words_host,
                        const uint32_t *n_int_sym_host, const uint32_t *n_leaf_sym_host, csgv_volume **out) {
     uint32_t NN;
-    int rc = check_dims(dims, N >= 1 && N <= 5 ? (1u << N) : 0u, NN);
+    int rc = check_dims(dims, N >= 1 && N <= (uint32_t)csgv::kMaxN ? (1u << N) : 0u, NN);
     if (rc) return rc;
     if (!out || !freq || !pal_off_host || !int_off_host || !leaf_off_host || !n_int_sym_host || !n_leaf_sym_host)
         return fail(CSGV_ERR_INVALID_ARG, "NULL argument");

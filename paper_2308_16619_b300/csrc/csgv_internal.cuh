@@ -15,14 +15,30 @@ constexpr uint32_t kL = 1u << 16;
 // operation codes (reading R6)
 enum : uint32_t { OP_RP = 0, OP_RX = 1, OP_RY = 2, OP_RZ = 3, OP_P0 = 4, OP_PD = 5, OP_PA = 6 };
 
-constexpr int kMaxN = 5;         // b <= 32
+constexpr int kMaxN = 6;         // b <= 64 (b = 64 keeps its level arrays in global memory)
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // per-request status codes written by the decoder (same values as the ABI)
 constexpr int32_t kStOk = 0, kStCorrupt = 4, kStRange = 7;
 
-// Morton masks of the x / y / z bits (x = bit 0, R5), up to 5 bits per axis
-constexpr uint32_t kMX = 0x1249u, kMY = 0x2492u, kMZ = 0x4924u;
+// Morton masks of the x / y / z bits (x = bit 0, R5), up to 6 bits per axis; every use masks them with the
+// bits of the level at hand
+constexpr uint32_t kMX = 0x9249u, kMY = 0x12492u, kMZ = 0x24924u;
+
+// Decode workspace of one slice of requests.  Request i owns recs + i * stride: interior records at 0, leaf
+// records at leaf_at, the P_a counts before every 8th record (uint16) of the two streams at t8_at and
+// t8_leaf_at, and for b = 64 its level arrays (uint32 palette indices at lev_at, constant flags at flag_at,
+// the listed parents at list_at); info[2i + s] = record count of stream s | a flag if malformed.
+struct RecJob {
+    const uint32_t *ids;
+    const uint8_t *lods;
+    uint32_t n;
+    uint8_t *recs;
+    uint64_t stride, leaf_at, t8_at, t8_leaf_at;
+    uint64_t lev_at, flag_at, list_at;  // b = 64 only
+    uint32_t *info;
+    uint32_t *counter;
+};
 
 // Device view of a compressed volume (passed to kernels by value).
 struct VolDev {

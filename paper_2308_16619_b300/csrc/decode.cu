@@ -31,18 +31,6 @@
 
 namespace csgv {
 
-// Workspace of one slice.  Request i owns recs + i * stride: interior records at 0, leaf records at
-// leaf_at, and the P_a counts before every 8th record (uint16) of the two streams at t8_at and
-// t8_leaf_at; info[2i + s] = record count of stream s | kRecBad if the stream is malformed.
-struct RecJob {
-    const uint32_t *ids;
-    const uint8_t *lods;
-    uint32_t n;
-    uint8_t *recs;
-    uint64_t stride, leaf_at, t8_at, t8_leaf_at;
-    uint32_t *info;
-    uint32_t *counter;
-};
 
 namespace {
 
@@ -673,6 +661,194 @@ __global__ void __launch_bounds__(kRbThreads) rebuild(VolDev V, RecJob J, uint32
     if (threadIdx.x == 0) status[i] = st;
 }
 
+// ------------------------------------------------------------------ rebuild for b = 64 (global memory)
+//
+// The levels of a 64^3 brick (299 593 palette indices, uint32: a palette may pass 2^16 entries) do not fit in
+// shared memory: they live in the request's workspace (lev_at), with one constant flag per node (flag_at)
+// and the listed parents of the level being rebuilt (list_at).  One CTA of kGwThreads threads per request,
+// level by level: the non-constant parents are listed by a block scan; every record of the level is decoded
+// by the thread owning its run of records, with i_p from a block scan of the P_a counts (so no sampled P_a
+// counts are needed); children of constant parents copy their parent; -axis sentinels are then followed (at
+// most 3 hops, as in the shared-memory kernel).  Same results and status codes as rebuild.
+
+constexpr uint32_t kGwThreads = 1024;
+constexpr uint32_t kGwSent = 0xFFFFFFFDu;  // 0xFFFFFFFD..F: unresolved R_x-, R_y-, R_z-
+
+__host__ __device__ __forceinline__ uint32_t spread6(uint32_t v) {
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8) | ((v & 32u) << 10);
+}
+
+// exclusive block scan of one value per thread; red: 33 words of shared memory
+__device__ __forceinline__ uint32_t gw_scan(uint32_t v, uint32_t *red, uint32_t &total) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += u;
+    }
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nw ? red[lane] : 0u;
+        uint32_t x = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(kFull, x, d);
+            if (lane >= (uint32_t)d) x += u;
+        }
+        red[lane] = x - w;
+        if (lane == 31) red[32] = x;
+    }
+    __syncthreads();
+    const uint32_t r = red[warp] + incl - v;
+    total = red[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint32_t i, uint32_t *out,
+                                          uint32_t *red, uint32_t &sh_bad) {
+    const uint32_t N = V.N, nt = blockDim.x, tid = threadIdx.x;
+    const uint32_t id = J.ids[i], t = J.lods[i];
+    if (id >= V.n_bricks || t > N) return kStRange;
+    const uint64_t p0 = V.pal_off[id], np64 = V.pal_off[id + 1] - p0;
+    if (np64 == 0 || np64 >= kGwSent) return kStCorrupt;
+    const uint32_t np = (uint32_t)np64;
+    const uint32_t *pal = V.pal + p0;
+    const uint32_t n_int = V.n_int_sym[id], n_leaf = V.n_leaf_sym[id];
+    const uint32_t s = N - t, side = 1u << s, nvox = side * side * side;
+    if (n_int == 0 && n_leaf == 0) {  // homogeneous brick (reading R2)
+        if (V.int_off[id + 1] != V.int_off[id] || V.leaf_off[id + 1] != V.leaf_off[id]) return kStCorrupt;
+        const uint32_t l0 = __ldg(pal);
+        for (uint32_t q = tid; q < nvox; q += nt) out[q] = l0;
+        return kStOk;
+    }
+    if (t == N) {
+        if (tid == 0) out[0] = __ldg(pal);
+        return kStOk;
+    }
+    const uint32_t info_int = J.info[2 * i], info_leaf = t == 0 ? J.info[2 * i + 1] : 0u;
+    if ((info_int | info_leaf) & kRecBad) return kStCorrupt;
+    uint8_t *base = J.recs + (uint64_t)i * J.stride;
+    uint32_t *lev = (uint32_t *)(base + J.lev_at);
+    uint8_t *flg = base + J.flag_at;
+    uint32_t *lst = (uint32_t *)(base + J.list_at);
+    if (tid == 0) {
+        lev[lev_off(N, N)] = 0;  // the root: palette index 0, not constant (the brick has symbols)
+        flg[lev_off(N, N)] = 0;
+    }
+    __syncthreads();
+    uint32_t used = 0, ip = 0;
+    for (int li = (int)N - 1; li >= (int)t; li--) {
+        const uint32_t l = (uint32_t)li;
+        const uint32_t npar = 1u << (3 * (N - l - 1)), nch = 8 * npar, pbits = npar - 1, cbits = nch - 1;
+        const uint32_t *P = lev + lev_off(N, l + 1);
+        uint32_t *C = lev + lev_off(N, l);
+        const uint8_t *fP = flg + lev_off(N, l + 1);
+        uint8_t *fC = flg + lev_off(N, l);
+        const uint8_t *R = base + used;
+        uint32_t n_left = info_int - used;
+        if (l == 0) {  // the leaf stream follows the complete interior stream
+            if (used != info_int) return kStCorrupt;
+            R = base + J.leaf_at;
+            n_left = info_leaf;
+            used = 0;
+        }
+        // the non-constant parents, in Morton order
+        uint32_t n_act;
+        {
+            const uint32_t per = (npar + nt - 1) / nt, k0 = min(tid * per, npar), k1 = min(k0 + per, npar);
+            uint32_t c = 0;
+            for (uint32_t k = k0; k < k1; k++) c += fP[k] == 0 ? 1u : 0u;
+            uint32_t j = gw_scan(c, red, n_act);
+            for (uint32_t k = k0; k < k1; k++)
+                if (fP[k] == 0) lst[j++] = k;
+        }
+        if (8 * n_act > n_left) return kStCorrupt;
+        if (tid == 0) sh_bad = 0;
+        __syncthreads();
+        // every record of the level: i_p before it = ip + the P_a records before it in this level
+        const uint32_t nrec = 8 * n_act;
+        bool bad = false;
+        uint32_t n_pa;
+        {
+            const uint32_t per = (nrec + nt - 1) / nt, r0 = min(tid * per, nrec), r1 = min(r0 + per, nrec);
+            uint32_t c = 0;
+            for (uint32_t r = r0; r < r1; r++) c += (R[r] & 7u) == OP_PA ? 1u : 0u;
+            uint32_t ipc = ip + gw_scan(c, red, n_pa);
+            for (uint32_t r = r0; r < r1; r++) {
+                const uint32_t o = R[r], op = o & 7u, stop = (o >> 3) & 1u, delta = o >> 4;
+                const uint32_t k = lst[r >> 3], c8 = r & 7u, q = 8 * k + c8;
+                uint32_t v = P[k];  // R_p
+                if (op >= OP_RX && op <= OP_RZ) {
+                    const uint32_t a = op - OP_RX, ma = kMX << a;
+                    if ((c8 >> a) & 1u) {  // +axis: the neighbour's parent (R4)
+                        if ((k & ma & pbits) == (ma & pbits)) bad = true;
+                        else v = P[minc(k, ma) & pbits];
+                    } else {  // -axis: the node before it on this level, resolved below
+                        if ((q & ma & cbits) == 0) bad = true;
+                        v = kGwSent + a;
+                    }
+                } else if (op >= OP_P0) {
+                    if (op == 7u || (op == OP_PD && ipc < 1 + delta) || (op == OP_PA && ipc + 1 >= np)) bad = true;
+                    v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);
+                }
+                if (l == 0 && stop) bad = true;  // leaf records carry no stop bit
+                C[q] = v;
+                if (l >= 1) fC[q] = (uint8_t)stop;
+                ipc += op == OP_PA ? 1u : 0u;
+            }
+        }
+        // children of constant parents repeat their parent
+        for (uint32_t k = tid; k < npar; k += nt)
+            if (fP[k]) {
+                const uint32_t v = P[k];
+                for (uint32_t c8 = 0; c8 < 8; c8++) {
+                    C[8 * k + c8] = v;
+                    if (l >= 1) fC[8 * k + c8] = 1;
+                }
+            }
+        if (bad) sh_bad = 1;
+        __syncthreads();
+        volatile uint32_t *Cv = C;
+        for (uint32_t q = tid; q < nch; q += nt) {
+            uint32_t w = Cv[q];
+            if (w >= kGwSent) {
+                uint32_t qq = q;
+                for (int hop = 0; hop < 4 && w >= kGwSent; hop++) {
+                    qq = mdec(qq, kMX << (w - kGwSent)) & cbits;
+                    w = Cv[qq];
+                }
+                if (w >= kGwSent) sh_bad = 1;
+                else Cv[q] = w;
+            }
+        }
+        __syncthreads();
+        if (sh_bad) return kStCorrupt;
+        ip += n_pa;
+        used += nrec;
+    }
+    if ((t == 1 && used != info_int) || (t == 0 && used != info_leaf)) return kStCorrupt;
+    const uint32_t *Ct = lev + lev_off(N, t);
+    for (uint32_t q = tid; q < nvox; q += nt) {
+        const uint32_t x = q & (side - 1), y = (q >> s) & (side - 1), z = q >> (2 * s);
+        const uint32_t v = Ct[spread6(x) | (spread6(y) << 1) | (spread6(z) << 2)];
+        out[q] = __ldg(pal + min(v, np - 1));
+    }
+    return kStOk;
+}
+
+__global__ void __launch_bounds__(kGwThreads) rebuild_global(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                             const uint64_t *__restrict__ out_off,
+                                                             int32_t *__restrict__ status) {
+    __shared__ uint32_t red[33];
+    __shared__ uint32_t sh_bad;
+    const uint32_t i = blockIdx.x;
+    const int32_t st = rebuild_global_request(V, J, i, out + out_off[i], red, sh_bad);
+    if (threadIdx.x == 0) status[i] = st;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers (host)
@@ -699,6 +875,11 @@ cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uin
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (V.N >= 6) {  // b = 64: levels in the workspace
+        ProfScope ps("rebuild", st);
+        rebuild_global<<<J.n, kGwThreads, 0, st>>>(V, J, out, out_off, status);
+        return cudaGetLastError();
+    }
     const uint32_t smem_b = rebuild_smem_bytes(V.N, wide);
     if (wide) {
         e = cudaFuncSetAttribute(rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);

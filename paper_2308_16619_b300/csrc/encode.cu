@@ -42,14 +42,15 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
-__device__ __forceinline__ uint32_t spread5(uint32_t v) {
-    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8);
+// 6-bit coordinate <-> every third bit of a Morton code
+__device__ __forceinline__ uint32_t spread6(uint32_t v) {
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8) | ((v & 32u) << 10);
 }
 __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
-    return spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
+    return spread6(x) | (spread6(y) << 1) | (spread6(z) << 2);
 }
-__device__ __forceinline__ uint32_t compact5(uint32_t m) {
-    return (m & 1u) | ((m >> 2) & 2u) | ((m >> 4) & 4u) | ((m >> 6) & 8u) | ((m >> 8) & 16u);
+__device__ __forceinline__ uint32_t compact6(uint32_t m) {
+    return (m & 1u) | ((m >> 2) & 2u) | ((m >> 4) & 4u) | ((m >> 6) & 8u) | ((m >> 8) & 16u) | ((m >> 10) & 32u);
 }
 __device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m & ma) - 1u) & ma) | (m & ~ma); }
 __device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
@@ -99,27 +100,35 @@ struct Brick {
     }
 };
 
-// shared memory of the encoder CTA
+// Working arrays of the encoder CTA: the level arrays (labels, const flags and active parents of levels 1..N)
+// in shared memory, or for b = 64 (too large) in the brick's global scratch `lvl`; the scan scratch and the
+// palette gather list always in shared memory.
 struct EncSmem {
     uint32_t *lab;     // up_nodes labels, levels 1..N
     uint8_t *cst;      // up_nodes const flags
-    uint16_t *list;    // active parents per parent level (same offsets as lab)
+    uint16_t *list;    // active parents, ranked in stream order
     uint32_t *red;     // block scan scratch (64 words)
     uint2 *plist;      // children that need a palette op: (op index, label), 256 at a time
-    __device__ EncSmem(uint8_t *s, const EncGeom &G) {
-        lab = (uint32_t *)s;
-        cst = (uint8_t *)s + r16(G.up_nodes * 4);
+    __device__ EncSmem(uint8_t *s, const EncGeom &G, uint8_t *lvl) {
+        uint8_t *L = G.lvl_bytes ? lvl : s;
+        lab = (uint32_t *)L;
+        cst = L + r16(G.up_nodes * 4);
         list = (uint16_t *)(cst + r16(G.up_nodes));
-        red = (uint32_t *)((uint8_t *)list + r16(G.up_nodes * 2));
+        red = (uint32_t *)(G.lvl_bytes ? s : (uint8_t *)list + r16(G.up_nodes * 2));
         plist = (uint2 *)(red + 64);
     }
     __host__ __device__ static uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
 };
 
+// bytes of the level arrays of one brick
+__host__ __device__ inline uint32_t enc_level_bytes(uint32_t up_nodes) {
+    return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2);
+}
+
 // phase D reuses the whole dynamic area as per-warp op staging, at least 512 bytes per warp
 constexpr uint32_t kStageMin = 512;
-__host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes) {
-    const uint32_t a = EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2) + 64 * 4 + 256 * 8;
+__host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes, bool levels_in_global) {
+    const uint32_t a = (levels_in_global ? 0u : enc_level_bytes(up_nodes)) + 64 * 4 + 256 * 8;
     return a > kEncWarps * kStageMin ? a : kEncWarps * kStageMin;
 }
 
@@ -151,7 +160,7 @@ __device__ __forceinline__ uint32_t loff(uint32_t N, uint32_t l) {
 // label of node q (Morton) on level l of the brick
 __device__ __forceinline__ uint32_t node_label(const Brick &B, const EncSmem &S, const EncGeom &G, uint32_t l,
                                                uint32_t q) {
-    if (l == 0) return B.at(compact5(q), compact5(q >> 1), compact5(q >> 2));
+    if (l == 0) return B.at(compact6(q), compact6(q >> 1), compact6(q >> 2));
     return S.lab[loff(G.N, l) + q];
 }
 
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(kEncThreads)
     encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
                   EncScratch SC, unsigned long long *count) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    EncSmem S(smem_raw, G);
+    EncSmem S(smem_raw, G, SC.lvl + (size_t)blockIdx.x * G.lvl_bytes);
     __shared__ uint32_t hist[32];
     __shared__ uint32_t sh_np;
     __shared__ uint32_t sh_npc;                 // children that need a palette op (phase B)
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(kEncThreads)
 #pragma unroll 2
             for (uint32_t i = tid; i < npairs; i += kEncThreads) {
                 const uint32_t m2 = 2 * i;
-                const uint32_t x = compact5(m2), y = compact5(m2 >> 1), z = compact5(m2 >> 2);  // x even
+                const uint32_t x = compact6(m2), y = compact6(m2 >> 1), z = compact6(m2 >> 2);  // x even
                 const uint32_t *r = B.base + B.sz * (2 * z) + B.sy * (2 * y) + 2 * x;
                 const uint4 a = __ldg((const uint4 *)r), bb = __ldg((const uint4 *)(r + B.sy)),
                             c = __ldg((const uint4 *)(r + B.sz)), d = __ldg((const uint4 *)(r + B.sz + B.sy));
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(kEncThreads)
                     nz[c] = Lz[c | 4u];
                 }
             } else {
-                const uint32_t x0 = 2 * compact5(p), y0 = 2 * compact5(p >> 1), z0 = 2 * compact5(p >> 2);
+                const uint32_t x0 = 2 * compact6(p), y0 = 2 * compact6(p >> 1), z0 = 2 * compact6(p >> 2);
                 if (B.interior) {
                     const uint32_t *r = B.base + B.sz * z0 + B.sy * y0 + x0;
                     const int64_t sy = (int64_t)B.sy, sz = (int64_t)B.sz;
@@ -907,7 +916,8 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
     G.pal_cap = u + b3;             // palette: root + one per P_a
     G.int_cap = (2 * (u - 1) + 2 + 15) & ~15u;  // interior nibbles (op + delta each), 16-byte pitch
     G.leaf_cap = (2 * b3 + 15) & ~15u;
-    G.smem = enc_smem_bytes(G.up_nodes);
+    G.lvl_bytes = N >= 6 ? enc_level_bytes(G.up_nodes) : 0u;  // b = 64: level arrays in global scratch
+    G.smem = enc_smem_bytes(G.up_nodes, G.lvl_bytes != 0);
     G.K_max = K_max;
     G.S_min = S_min;
     return G;
@@ -915,7 +925,7 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
 
 size_t scratch_bytes_per_brick(const EncGeom &G) {
     return (size_t)G.pal_cap * 4 + G.int_cap + G.leaf_cap + (size_t)(G.int_cap + 64) * 2 +
-           (size_t)(G.leaf_cap + 64) * 2 + 8 * 4 + 64 + G.ops_cap;
+           (size_t)(G.leaf_cap + 64) * 2 + 8 * 4 + 64 + G.ops_cap + G.lvl_bytes;
 }
 
 cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, uint64_t stride, uint32_t n,

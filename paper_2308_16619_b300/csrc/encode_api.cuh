@@ -12,6 +12,7 @@ struct EncGeom {
     uint32_t ops_cap;         // coded children at most: nodes - 1
     uint32_t pal_cap, int_cap, leaf_cap;  // scratch capacities per brick (labels, nibbles, nibbles)
     uint32_t smem;            // dynamic shared memory bytes
+    uint32_t lvl_bytes;       // level arrays in global scratch per brick (b = 64), else 0
     uint32_t K_max, S_min;    // interleaving rule (R10)
 };
 
@@ -24,6 +25,7 @@ struct EncScratch {
     uint16_t *w_leaf;   // C x (leaf_cap + 64)
     uint32_t *sizes;    // C x 8: n_pal, n_int_sym, n_leaf_sym, n_int_words, n_leaf_words, int_start, leaf_start, 0
     uint8_t *ops;       // C x ops_cap: op bytes of the brick in stream order (encode kernel only)
+    uint8_t *lvl;       // C x lvl_bytes: level arrays (b = 64 only)
 };
 
 struct EncVol {

@@ -13,7 +13,7 @@
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes
 // (32 MiB), present on every GPU that loads the library until the process
 // exits.  It holds the per-brick buffers of the encoder, so a call accepts at
-// most a fixed number of bricks (b = 32: 81, b = 16: 647, b = 8: 4954,
+// most a fixed number of bricks (b = 64: 9, b = 32: 81, b = 16: 647, b = 8: 4954,
 // b = 4: 25496, b = 2: 49634) and rejects larger volumes with
 // CSGV_ERR_INVALID_ARG.  Every call shares the array and it keeps the last
 // call's contents: the counters that must start at zero are cleared at the
@@ -61,7 +61,7 @@ size_t carve(const csgv::EncGeom &G, size_t C, unsigned char *base, csgv::EncScr
     unsigned char *sz = take(C * 8 * 4), *pal = take(C * G.pal_cap * 4);
     unsigned char *ni = take(C * G.int_cap), *nl = take(C * G.leaf_cap);
     unsigned char *wi = take(C * (G.int_cap + 64) * 2), *wl = take(C * (G.leaf_cap + 64) * 2);
-    unsigned char *op = take(C * G.ops_cap);
+    unsigned char *op = take(C * G.ops_cap), *lv = take(C * G.lvl_bytes);
     if (base) {
         *freq = (uint32_t *)f;
         *tot = (uint64_t *)t;
@@ -73,6 +73,7 @@ size_t carve(const csgv::EncGeom &G, size_t C, unsigned char *base, csgv::EncScr
         SC->w_int = (uint16_t *)wi;
         SC->w_leaf = (uint16_t *)wl;
         SC->ops = op;
+        SC->lvl = lv;
     }
     return o;
 }
@@ -106,7 +107,7 @@ int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], 
     char msg[256];
     uint32_t N = 0;
     while (N <= (uint32_t)csgv::kMaxN && (1u << N) != b) N++;
-    if (N < 1 || N > (uint32_t)csgv::kMaxN) return err(CSGV_ERR_INVALID_ARG, "brick size must be 2, 4, 8, 16 or 32");
+    if (N < 1 || N > (uint32_t)csgv::kMaxN) return err(CSGV_ERR_INVALID_ARG, "brick size must be 2, 4, 8, 16, 32 or 64");
     if (!vol_dev || !dims || !table || !totals || !pal_off_dev || !pal_dev || !int_off_dev || !int_words_dev ||
         !leaf_off_dev || !leaf_words_dev || !n_int_sym_dev || !n_leaf_sym_dev)
         return err(CSGV_ERR_INVALID_ARG, "NULL argument");

@@ -397,3 +397,34 @@ def test_palette_churn_byte_identical(block, n_labels):
     gv = csgv.csgv_encode_bricks(d, 32, t)
     torch.cuda.synchronize()
     assert_same_arrays(gv.export(), V)
+
+
+@pytest.mark.parametrize("kind", ["voronoi", "small_alphabet", "noise_and_constant"])
+def test_b64_encode_byte_identical_and_decode_all_lods(kind):
+    """b = 64 (the level arrays in global memory on both sides): GPU streams byte-identical to the oracle's,
+    and every brick at every LOD 0..6 decodes to the oracle's labels.  The noise brick's palette (about
+    200 000 labels) is past 2^16 entries."""
+    csgv = _csgv()
+    if kind == "voronoi":
+        vol = synth.voronoi((64, 128, 192), 90, seed=61, warp_amp=3, bg_permille=250)
+    elif kind == "small_alphabet":
+        vol = structured_volume(62, (128, 64, 64), 150, 6)
+    else:
+        rng = np.random.default_rng(63)
+        vol = np.full((64, 64, 128), 41, np.uint32)
+        vol[:, :, :64] = rng.integers(0, 1 << 30, size=(64, 64, 64)).astype(np.uint32)
+    V = O.encode_volume(vol, 6, stride=1)
+    d = to_dev(vol)
+    t = csgv.csgv_build_freq_table(d, 64, 1)
+    assert np.array_equal(t.freq_array(), V.freq)
+    gv = csgv.csgv_encode_bricks(d, 64, t)
+    assert_same_arrays(gv.export(), V)
+    if kind == "noise_and_constant":
+        assert gv.info().max_palette > 65536
+    n = V.n_bricks
+    ids = np.repeat(np.arange(n, dtype=np.uint32), 7)
+    lods = np.tile(np.arange(7, dtype=np.uint8), n)
+    out, off, st = gpu_decode(gv, 6, ids, lods)
+    ref, roff, rst = O.decode_bricks(V, ids, lods)
+    assert (rst == 0).all() and (st == 0).all(), np.unique(st, return_counts=True)
+    assert np.array_equal(out[:len(ref)], ref)
