@@ -56,28 +56,27 @@ __device__ __forceinline__ uint32_t mdec(uint32_t m, uint32_t ma) { return (((m 
 __device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m | ~ma) + 1u) & ma) | (m & ~ma); }
 
 // Most frequent of 8 labels, ties to the first occurrence (Sec. 3.4): the distinct values are visited in
-// order of first occurrence and a later one wins only with a strictly larger count.
+// order of first occurrence and a later one wins only with a strictly larger count.  The positions are
+// visited in a fixed order (no selection of the value by index); a position already counted is skipped,
+// and the walk stops once the positions left cannot outnumber the best count.
 __device__ __forceinline__ uint32_t mode8(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t w4, uint32_t w5,
                                          uint32_t w6, uint32_t w7, bool &all_equal) {
+    const uint32_t w[8] = {w0, w1, w2, w3, w4, w5, w6, w7};
     uint32_t rem = 0xFFu, best = w0, bestc = 0;
-    while (rem) {
-        const uint32_t c = __ffs(rem) - 1;
-        uint32_t v = w0;
-        v = c == 1 ? w1 : v;
-        v = c == 2 ? w2 : v;
-        v = c == 3 ? w3 : v;
-        v = c == 4 ? w4 : v;
-        v = c == 5 ? w5 : v;
-        v = c == 6 ? w6 : v;
-        v = c == 7 ? w7 : v;
-        const uint32_t m = (w0 == v ? 1u : 0u) | (w1 == v ? 2u : 0u) | (w2 == v ? 4u : 0u) | (w3 == v ? 8u : 0u) |
-                           (w4 == v ? 16u : 0u) | (w5 == v ? 32u : 0u) | (w6 == v ? 64u : 0u) | (w7 == v ? 128u : 0u);
-        const uint32_t cnt = __popc(m);
-        if (cnt > bestc) {
-            bestc = cnt;
-            best = v;
+#pragma unroll
+    for (uint32_t c = 0; c < 8; c++) {
+        if (((rem >> c) & 1u) && __popc(rem) > bestc) {
+            const uint32_t v = w[c];
+            uint32_t m = 0;
+#pragma unroll
+            for (uint32_t j = c; j < 8; j++) m |= (w[j] == v ? 1u : 0u) << j;
+            const uint32_t cnt = __popc(m);
+            if (cnt > bestc) {
+                bestc = cnt;
+                best = v;
+            }
+            rem &= ~m;
         }
-        rem &= ~m;
     }
     all_equal = bestc == 8;
     return best;
