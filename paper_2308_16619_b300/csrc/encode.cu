@@ -32,7 +32,7 @@ namespace csgv {
 constexpr uint32_t kEncThreads = 256;
 constexpr uint32_t kEncWarps = kEncThreads / 32;
 constexpr uint32_t kNeedPal = 7;       // op placeholder: no reuse operation applies
-constexpr uint32_t kRansEncWarps = 16;  // rans_encode_kernel: one stream per warp
+constexpr uint32_t kRansEncWarps = 8;   // rans_encode_kernel: one stream per warp (8-warp CTAs spread evenly over the SMs)
 constexpr uint32_t kRansEncWin = 2048;  // staged symbols per warp (bytes)
 
 namespace {
