@@ -335,14 +335,14 @@ CSGV_API int csgv_volume_leaves_to_device(csgv_volume *vol);
 /* A decode configuration of a volume (csgv_decode_autotune). */
 typedef struct csgv_decode_tuning {
     uint64_t workspace_bytes;  /* op-record workspace per slice of requests (more: fewer, larger slices) */
-    uint32_t rans_ctas_per_sm; /* CTAs per SM of the rANS record kernel (1..3) */
+    uint32_t rans_ctas_per_sm; /* CTAs (8 warps each) per SM of the rANS record kernel (4 or 5) */
     uint32_t pad;
     double ms;                 /* measured time of the batch with this configuration */
 } csgv_decode_tuning;
 
 /*
  * Autotuner (batching at scale): time candidate decode configurations on this
- * batch (workspace 64 MiB .. 1 GiB per slice x rANS kernel 2 or 3 CTAs per SM;
+ * batch (workspace 64 MiB .. 1 GiB per slice x rANS kernel 4 or 5 CTAs per SM;
  * one warm-up and two timed runs each, CUDA events on the stream), keep the
  * fastest in the volume for later csgv_decode_bricks calls, and return it in
  * *best.  The batch's outputs are written (by every run).  Synchronises the

@@ -34,7 +34,7 @@ struct csgv_volume {
     uint32_t max_int_sym, max_leaf_sym;  // largest per-brick symbol counts: size the decode workspace
     uint16_t *leaf_host = nullptr;        // leaf words in mapped host memory (csgv_volume_leaves_to_host)
     uint64_t dec_ws_bytes = 192ull << 20;  // decode configuration (csgv_decode_autotune)
-    uint32_t dec_rec_per_sm = 3;
+    uint32_t dec_rec_per_sm = 5;
     cudaEvent_t ready = nullptr;  // recorded when the arrays are complete on the stream that made them
 };
 
@@ -839,7 +839,7 @@ int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const 
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const uint64_t ws[] = {64ull << 20, 192ull << 20, 512ull << 20, 1024ull << 20};
-    const uint32_t rec[] = {2, 3};
+    const uint32_t rec[] = {4, 5};
     for (uint64_t w : ws)
         for (uint32_t r : rec) {
             vol->dec_ws_bytes = w;

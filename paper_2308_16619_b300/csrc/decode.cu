@@ -36,7 +36,7 @@ namespace {
 
 constexpr uint32_t kRecBad = 0x80000000u;
 constexpr uint32_t kWinWords = 256;   // staged stream words per warp (uint16)
-constexpr uint32_t kRecWarps = 16;    // rans_records: warps per CTA
+constexpr uint32_t kRecWarps = 8;     // rans_records: warps per CTA (8-warp CTAs, 5 per SM: no register cap below 51)
 constexpr uint32_t kRbThreads = 256;  // rebuild: threads per CTA
 constexpr uint32_t kRbWarps = kRbThreads / 32;
 
@@ -160,7 +160,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     return ok ? otail : (otail | kRecBad);
 }
 
-__global__ void __launch_bounds__(kRecWarps * 32, 3) rans_records(VolDev V, RecJob J) {
+__global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records(VolDev V, RecJob J) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *lut_s = (uint32_t *)smem;
     for (uint32_t i = threadIdx.x; i < 2 * kM / 4; i += blockDim.x)
