@@ -366,6 +366,7 @@ int csgv_build_freq_table(const uint32_t *vol_dev, const uint64_t dims[3], uint3
 struct Readback {
     unsigned long long tot[3], cnt[32];
     uint32_t maxes[4], freq[32];
+    unsigned long long scan[csgv::kScanScratchBytes / 8];  // the size scan's block totals (device only)
 };
 
 // A volume being encoded: its bricks are appended batch by batch (one call, or a stream encoder across calls).
@@ -475,7 +476,7 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
             CKE(csgv::launch_rans_encode(G, SC, mm, rb_d->freq, st));
         }
         CKE(csgv::launch_scan(SC.sizes, mm, gfirst, v->pal_off, v->int_off, v->leaf_off, (uint64_t *)rb_d->tot,
-                              rb_d->maxes, st));
+                              rb_d->maxes, rb_d->scan, st));
         const bool final_batch = j + mm >= m;
         if (build_lut && final_batch && (rc = vol_lut(v, rb_d->freq, st))) return bail(rc);  // tables are final
         const uint64_t prev[3] = {R.tot[0], R.tot[1], R.tot[2]};

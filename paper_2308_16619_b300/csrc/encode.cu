@@ -871,6 +871,121 @@ __global__ void __launch_bounds__(1024) scan_sizes_kernel(const uint32_t *sizes,
     }
 }
 
+// Two-pass size scan for large batches (blocks of kScanBlock bricks, a thread per brick).  Pass 1: each block's
+// totals (palette labels, interior words, leaf words) and maxima (palette, interior and leaf symbol counts)
+// into blk[b]; block 0 also copies the running totals to blk[kScanMaxBlocks] (pass 2 reads that copy and its
+// last block writes the new totals).  Pass 2: each block starts from the running totals plus the blocks
+// before it and writes its offsets.  blk: (kScanMaxBlocks + 1) x 4 u64.
+constexpr uint32_t kScanBlock = 1024, kScanMaxBlocks = 64;
+
+__device__ __forceinline__ void scan_vals(const uint32_t *sizes, uint32_t i, uint32_t n, unsigned long long v[3],
+                                          uint32_t mx[3]) {
+    v[0] = v[1] = v[2] = 0;
+    mx[0] = mx[1] = mx[2] = 0;
+    if (i < n) {
+        const uint4 q = *(const uint4 *)(sizes + 8 * (size_t)i);  // n_pal, n_int_sym, n_leaf_sym, n_int_words
+        v[0] = q.x;
+        v[1] = q.w;
+        v[2] = sizes[8 * (size_t)i + 4];
+        mx[0] = q.x;
+        mx[1] = q.y;
+        mx[2] = q.z;
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_blocks_kernel(const uint32_t *sizes, uint32_t n,
+                                                                 const uint64_t *tot, unsigned long long *blk) {
+    __shared__ unsigned long long ps[3][32];
+    __shared__ uint32_t pm[3][32];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long v[3];
+    uint32_t mx[3];
+    scan_vals(sizes, blockIdx.x * kScanBlock + tid, n, v, mx);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v[a] += __shfl_xor_sync(kFull, v[a], d);
+        mx[a] = __reduce_max_sync(kFull, mx[a]);
+        if (lane == 0) {
+            ps[a][warp] = v[a];
+            pm[a][warp] = mx[a];
+        }
+    }
+    __syncthreads();
+    if (tid < 3) {
+        unsigned long long sum = 0;
+        uint32_t m = 0;
+        for (uint32_t w = 0; w < kScanBlock / 32; w++) {
+            sum += ps[tid][w];
+            m = max(m, pm[tid][w]);
+        }
+        blk[4 * blockIdx.x + tid] = sum;
+        blk[4 * (kScanMaxBlocks + 1) + 4 * blockIdx.x + tid] = m;  // maxima after the sums
+        if (blockIdx.x == 0) blk[4 * kScanMaxBlocks + tid] = tot[tid];
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_write_kernel(const uint32_t *sizes, uint32_t n, uint64_t first,
+                                                                uint64_t *pal_off, uint64_t *int_off,
+                                                                uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes,
+                                                                const unsigned long long *blk) {
+    __shared__ unsigned long long part[3][32], base[3];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, b = blockIdx.x;
+    if (tid < 3) {  // running totals plus the blocks before this one
+        unsigned long long s = blk[4 * kScanMaxBlocks + tid];
+        for (uint32_t k = 0; k < b; k++) s += blk[4 * k + tid];
+        base[tid] = s;
+    }
+    unsigned long long v[3], inc[3];
+    uint32_t mx[3];
+    const uint32_t i = b * kScanBlock + tid;
+    scan_vals(sizes, i, n, v, mx);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        inc[a] = v[a];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long u = __shfl_up_sync(kFull, inc[a], d);
+            if (lane >= (uint32_t)d) inc[a] += u;
+        }
+        if (lane == 31) part[a][warp] = inc[a];
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the warp totals, in place
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const unsigned long long t = part[a][lane];
+            unsigned long long x = t;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long u = __shfl_up_sync(kFull, x, d);
+                if (lane >= (uint32_t)d) x += u;
+            }
+            part[a][lane] = x - t;
+        }
+    }
+    __syncthreads();
+    unsigned long long o[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) o[a] = base[a] + part[a][warp] + inc[a] - v[a];
+    if (i < n) {
+        pal_off[first + i] = o[0];
+        int_off[first + i] = o[1];
+        leaf_off[first + i] = o[2];
+    }
+    if (b == gridDim.x - 1 && i == n - 1) {  // the batch's last brick: new totals and the end offsets
+        for (int a = 0; a < 3; a++) tot[a] = o[a] + v[a];
+        pal_off[first + n] = o[0] + v[0];
+        int_off[first + n] = o[1] + v[1];
+        leaf_off[first + n] = o[2] + v[2];
+    }
+    if (b == gridDim.x - 1 && tid < 3 && maxes) {
+        uint32_t m = maxes[tid];
+        for (uint32_t k = 0; k < gridDim.x; k++) m = max(m, (uint32_t)blk[4 * (kScanMaxBlocks + 1) + 4 * k + tid]);
+        maxes[tid] = m;
+    }
+}
+
 // Copy each brick's palette and words from scratch to the packed arrays.
 __global__ void __launch_bounds__(256) compact_kernel(EncGeom G, EncScratch SC, uint64_t first, const uint64_t *pal_off,
                                                       const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal,
@@ -967,10 +1082,21 @@ cudaError_t launch_nibble_hist(const EncGeom &G, const EncScratch &SC, uint32_t 
 }
 
 cudaError_t launch_scan(const uint32_t *sizes, uint32_t n, uint64_t first, uint64_t *pal_off, uint64_t *int_off,
-                        uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes, cudaStream_t st) {
-    {
+                        uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes, unsigned long long *blk, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t nblk = (n + kScanBlock - 1) / kScanBlock;
+    if (!blk || nblk > kScanMaxBlocks || nblk == 1) {  // one CTA
         ProfScope ps("scan_sizes", st);
         scan_sizes_kernel<<<1, 1024, 0, st>>>(sizes, n, first, pal_off, int_off, leaf_off, tot, maxes);
+        return cudaGetLastError();
+    }
+    {
+        ProfScope ps("scan_blocks", st);
+        scan_blocks_kernel<<<nblk, kScanBlock, 0, st>>>(sizes, n, tot, blk);
+    }
+    {
+        ProfScope ps("scan_sizes", st);
+        scan_write_kernel<<<nblk, kScanBlock, 0, st>>>(sizes, n, first, pal_off, int_off, leaf_off, tot, maxes, blk);
     }
     return cudaGetLastError();
 }

@@ -43,7 +43,9 @@ cudaError_t launch_rans_encode(const EncGeom &G, const EncScratch &SC, uint32_t 
 cudaError_t launch_nibble_hist(const EncGeom &G, const EncScratch &SC, uint32_t n, uint32_t stride,
                                unsigned long long *counts, cudaStream_t st);
 cudaError_t launch_scan(const uint32_t *sizes, uint32_t n, uint64_t first, uint64_t *pal_off, uint64_t *int_off,
-                        uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes, cudaStream_t st);
+                        uint64_t *leaf_off, uint64_t *tot, uint32_t *maxes, unsigned long long *blk, cudaStream_t st);
+// bytes of the scratch that launch_scan's two-pass scan needs (blk)
+constexpr size_t kScanScratchBytes = (64 + 1) * 4 * 8 * 2;
 cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t first, uint32_t n, const uint64_t *pal_off,
                            const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal, uint16_t *int_words,
                            uint16_t *leaf_words, uint32_t *n_int_sym, uint32_t *n_leaf_sym, cudaStream_t st);

@@ -165,7 +165,8 @@ int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], 
     if (e == cudaSuccess) e = cudaMemsetAsync(maxpal_d, 0, 3 * 4, st);
     if (e == cudaSuccess) e = csgv::launch_encode(EV, G, 0, 1, (uint32_t)n, freq_d, SC, nullptr, st);
     if (e == cudaSuccess)
-        e = csgv::launch_scan(SC.sizes, (uint32_t)n, 0, pal_off_dev, int_off_dev, leaf_off_dev, tot_d, maxpal_d, st);
+        e = csgv::launch_scan(SC.sizes, (uint32_t)n, 0, pal_off_dev, int_off_dev, leaf_off_dev, tot_d, maxpal_d, nullptr,
+                              st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(totals, tot_d, 3 * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
