@@ -428,3 +428,48 @@ def test_b64_encode_byte_identical_and_decode_all_lods(kind):
     ref, roff, rst = O.decode_bricks(V, ids, lods)
     assert (rst == 0).all() and (st == 0).all(), np.unique(st, return_counts=True)
     assert np.array_equal(out[:len(ref)], ref)
+
+
+def test_b64_range_and_corrupt_status():
+    """The b = 64 rebuild (levels in the workspace) reports the same statuses as the shared-memory kernel:
+    range errors for a bad id or LOD, corrupt for a truncated stream or a cut palette, and random word
+    flips never touch the other bricks of the batch."""
+    csgv = _csgv()
+    vol = synth.voronoi((64, 64, 128), 60, seed=64, warp_amp=2, bg_permille=200)
+    V = O.encode_volume(vol, 6, stride=1)
+    gv = import_oracle_volume(V)
+    out, off, st = gpu_decode(gv, 6, [0, 2, 1, 0, 1], [0, 0, 0, 7, 6])
+    assert st.tolist() == [0, 7, 0, 7, 0]
+    ids = np.array([0, 1], np.uint32)
+    lods = np.zeros(2, np.uint8)
+    ref, _, _ = O.decode_bricks(V, ids, lods)
+    lo = V.leaf_off.copy()
+    lw = np.delete(V.leaf_words, np.arange(int(lo[1]) - 5, int(lo[1])))
+    lo[1:] -= 5
+    bad = csgv.csgv_volume_import(6, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words, lo,
+                                  lw, V.n_int_sym, V.n_leaf_sym)
+    out, off, st = gpu_decode(bad, 6, ids, lods)
+    assert st[0] == 4 and st[1] == 0
+    assert np.array_equal(out[off[1]:], ref[off[1]:])
+    po = V.pal_off.copy()
+    cut = int(po[1]) - 1
+    pal = np.delete(V.pal, np.arange(1, 1 + cut))
+    po[1:] -= cut
+    bad = csgv.csgv_volume_import(6, V.dims, V.K_max, V.S_min, V.freq, po, pal, V.int_off, V.int_words, V.leaf_off,
+                                  V.leaf_words, V.n_int_sym, V.n_leaf_sym)
+    out, off, st = gpu_decode(bad, 6, ids, lods)
+    assert st[0] == 4 and st[1] == 0
+    assert np.array_equal(out[off[1]:], ref[off[1]:])
+    rng = np.random.default_rng(65)
+    for trial in range(4):
+        iw = V.int_words.copy()
+        lw = V.leaf_words.copy()
+        k = rng.integers(int(V.int_off[0]), int(V.int_off[1]), size=3)
+        iw[k] ^= rng.integers(1, 65535, size=3).astype(np.uint16)
+        k = rng.integers(int(V.leaf_off[0]), int(V.leaf_off[1]), size=3)
+        lw[k] ^= rng.integers(1, 65535, size=3).astype(np.uint16)
+        bad = csgv.csgv_volume_import(6, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, iw,
+                                      V.leaf_off, lw, V.n_int_sym, V.n_leaf_sym)
+        out, off, st = gpu_decode(bad, 6, ids, lods)
+        assert st[0] in (0, 4) and st[1] == 0
+        assert np.array_equal(out[off[1]:], ref[off[1]:])
