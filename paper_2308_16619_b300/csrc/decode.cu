@@ -5,7 +5,7 @@
 //
 //   rans_records (one warp per rANS stream; persistent CTAs hold both decode tables in shared memory).
 //     The K interleaved states of a stream live in lanes 0..K-1; a step decodes K symbols and the lanes
-//     that renormalise take consecutive words, in lane order (ballot + popc), from a window of the
+//     that renormalise take consecutive words, in lane order (ballot + popc), from a ring window of the
 //     stream staged in shared memory by 16-byte loads (Sec. 3.3, readings R9/R10).  Each delta nibble
 //     is folded into the P_delta op before it, so the warp writes exactly one op record per coded
 //     child, in stream order (byte: op | stop << 3 | delta << 4), plus the number of P_a records before
@@ -52,6 +52,13 @@ __device__ __forceinline__ uint32_t lt_of(uint32_t lane) { return (1u << lane) -
 // Decode one stream (whole warp) into records and P_a counts; returns the record count, | kRecBad if
 // malformed.  Decoding stops once `need` records are out (a coarse LOD uses only the stream's first
 // levels); the end of the stream is then not checked.
+//
+// The stream's words are staged in a ring of kWinWords words in shared memory (word a, counted from the
+// 16-byte boundary at or below the stream's start, sits at a % kWinWords), refilled half a ring at a time
+// with 16-byte loads that stay inside the stream's 16-byte chunks.  A malformed stream may read stale
+// ring words, never memory outside the ring; the final check (every word read, every state back at L)
+// rejects it.  The P_a count before every 8th record only changes at a P_a record, so the counts are
+// written in runs: the steps without P_delta / P_a write only their records.
 __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t n_sym, uint32_t K_max,
                                   uint32_t S_min, const uint32_t *lut, uint16_t *win, uint8_t *rec, uint16_t *t8,
                                   uint64_t cap, uint32_t need, uint32_t lane) {
@@ -61,58 +68,49 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     }
     const uint32_t K = lanes_for(n_sym, K_max, S_min);
     if (n_sym > cap || n_words < 2 * K) return kRecBad;
-    const uint32_t lt = lanemask_lt(), last = n_words - 1;
-    int32_t wb = 0;             // absolute word index held in win[0] (negative: alignment slack)
-    uint32_t stage_at = 0;      // restage once pos passes this (a step reads at most 32 words)
-    auto stage = [&](uint32_t pos) {
-        const uintptr_t g = reinterpret_cast<uintptr_t>(w + pos);
-        const uintptr_t g0 = g & ~(uintptr_t)15;
-        const uintptr_t gend = reinterpret_cast<uintptr_t>(w + n_words);
-        __syncwarp();
-        for (uint32_t c = lane; c < kWinWords / 8; c += 32) {
-            const uintptr_t a = g0 + 16 * (uintptr_t)c;
-            if (a < gend) reinterpret_cast<uint4 *>(win)[c] = __ldg(reinterpret_cast<const uint4 *>(a));
-        }
-        wb = (int32_t)pos - (int32_t)((g - g0) >> 1);
-        const uint32_t end = (uint32_t)(wb + (int32_t)kWinWords);
-        stage_at = end < n_words ? end - 32 : 0xFFFFFFFFu;
-        __syncwarp();
-    };
-    stage(0);
+    constexpr uint32_t kRingChunks = kWinWords / 8, kHalf = kRingChunks / 2;
+    const uint32_t lt = lanemask_lt();
+    const uintptr_t g0 = reinterpret_cast<uintptr_t>(w) & ~(uintptr_t)15;
+    const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(w) - g0) >> 1;  // words before the stream (0..7)
+    const uint32_t n_chunks = (sh + n_words + 7) / 8;  // 16-byte chunks holding the stream
+    const uint4 *src = reinterpret_cast<const uint4 *>(g0);
+    uint4 *ring = reinterpret_cast<uint4 *>(win);
+    __syncwarp();  // the previous stream's reads of the ring are done
+    if (lane < n_chunks) ring[lane] = __ldg(src + lane);
+    uint32_t filled = kRingChunks;  // chunks staged so far
+    uint32_t lim = filled < n_chunks ? 8 * filled - 32 : 0xFFFFFFFFu;  // refill once pos passes this
+    __syncwarp();
     uint32_t x = kL;
-    if (lane < K) x = (uint32_t)win[2 * lane - wb] | ((uint32_t)win[2 * lane + 1 - wb] << 16);
-    uint32_t pos = 2 * K, remaining = n_sym, otail = 0, pend = 0, held = 0, pa_run = 0;
-    bool bad = false;
+    if (lane < K) x = (uint32_t)win[sh + 2 * lane] | ((uint32_t)win[sh + 2 * lane + 1] << 16);
+    uint32_t pos = sh + 2 * K, remaining = n_sym, otail = 0, pend = 0, held = 0, pa_run = 0, t8n = 0;
     while (remaining > 0 && otail < need) {
-        if (pos > stage_at) {
-            if (pos > n_words) {  // the words ran out
-                bad = true;
-                break;
-            }
-            stage(pos);
+        if (pos > lim) {  // a step reads at most 32 words: stage the next half ring over the half already read
+            __syncwarp();
+            const uint32_t c = filled + lane;
+            if (lane < kHalf && c < n_chunks) ring[c % kRingChunks] = __ldg(src + c);
+            filled += kHalf;
+            lim = filled < n_chunks ? 8 * filled - 32 : 0xFFFFFFFFu;
+            __syncwarp();
         }
         const uint32_t n = min(K, remaining);
         const bool act = lane < n;
         const uint32_t e = lut[x & (kM - 1u)];
         const uint32_t sym = e & 15u;
         const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
-        const bool need = act && xn < kL;
-        const uint32_t m = __ballot_sync(kFull, need);
-        const uint32_t off = min(pos + __popc(m & lt), last);
-        const uint32_t wv = win[min((uint32_t)((int32_t)off - wb), kWinWords - 1)];  // in the window
-        x = act ? (need ? ((xn << 16) | wv) : xn) : x;
+        const bool nrm = act && xn < kL;
+        const uint32_t m = __ballot_sync(kFull, nrm);
+        const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
+        x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
         pos += __popc(m);
         remaining -= n;
         const uint32_t rare = __ballot_sync(kFull, act && (sym & 7u) >= OP_PD);  // P_delta, P_a (or 7)
         if ((rare | pend) == 0) {  // common case: every symbol is an op, none of them P_a
-            if (act) {
-                const uint32_t r = otail + lane;
-                rec[r] = (uint8_t)sym;
-                if ((r & 7u) == 0) t8[r >> 3] = (uint16_t)pa_run;
-            }
+            if (act) rec[otail + lane] = (uint8_t)sym;
             otail += n;
             continue;
         }
+        // the P_a counts of the records before this step are all pa_run
+        for (uint32_t j = t8n + lane; 8 * j < otail; j += 32) t8[j] = (uint16_t)pa_run;
         // which symbols are delta nibbles: the one after each P_delta op (bit n: in the next step)
         uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD);
         uint64_t dm = pend;
@@ -149,13 +147,15 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
         }
         pa_run = min(pa_run + __popc(pam), 0xFFFFu);  // saturated: a count past any palette is caught later
         otail = base + __popc(emit);
+        t8n = (otail + 7) / 8;
         pend = hold;
         held = symlast;
     }
-    if (lane == 0 && (otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
-    if (remaining > 0 && !bad) return otail;  // stopped early: a prefix of the stream
+    // the counts not yet written: every 8th record from t8n on, and the one just past the last record
+    for (uint32_t j = t8n + lane; 8 * j <= otail; j += 32) t8[j] = (uint16_t)pa_run;
+    if (remaining > 0) return pos <= sh + n_words ? otail : (otail | kRecBad);  // stopped early: a prefix
     const bool lane_ok = lane >= K || x == kL;
-    const bool ok = __all_sync(kFull, lane_ok) && !bad && remaining == 0 && !pend && pos == n_words;
+    const bool ok = __all_sync(kFull, lane_ok) && !pend && pos == sh + n_words;
     __syncwarp();
     return ok ? otail : (otail | kRecBad);
 }
