@@ -27,6 +27,8 @@
 //     of the brick, L0 included, are held as palette indices in shared memory (uint8 when every palette
 //     has <= 253 entries, else uint16); level t is then written as x-fastest labels with 16-byte
 //     streaming stores.
+#include <type_traits>
+
 #include "csgv_internal.cuh"
 
 namespace csgv {
@@ -83,7 +85,9 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     uint32_t x = kL;
     if (lane < K) x = (uint32_t)win[sh + 2 * lane] | ((uint32_t)win[sh + 2 * lane + 1] << 16);
     uint32_t pos = sh + 2 * K, remaining = n_sym, otail = 0, pend = 0, held = 0, pa_run = 0, t8n = 0;
-    while (remaining > 0 && otail < need) {
+    // One step: n symbols, one per lane below n.  Full steps (n = K) need no test of which lanes take part
+    // beyond lane < K, and no lane keeps its state unchanged.
+    auto step = [&](const uint32_t n, const bool act, auto full) {
         if (pos > lim) {  // a step reads at most 32 words: stage the next half ring over the half already read
             __syncwarp();
             const uint32_t c = filled + lane;
@@ -92,22 +96,20 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
             lim = filled < n_chunks ? 8 * filled - 32 : 0xFFFFFFFFu;
             __syncwarp();
         }
-        const uint32_t n = min(K, remaining);
-        const bool act = lane < n;
         const uint32_t e = lut[x & (kM - 1u)];
         const uint32_t sym = e & 15u;
         const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
         const bool nrm = act && xn < kL;
         const uint32_t m = __ballot_sync(kFull, nrm);
         const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
-        x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
+        if (decltype(full)::value) x = nrm ? ((xn << 16) | wv) : xn;  // lanes >= K: never read
+        else x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
         pos += __popc(m);
-        remaining -= n;
         const uint32_t rare = __ballot_sync(kFull, act && (sym & 7u) >= OP_PD);  // P_delta, P_a (or 7)
         if ((rare | pend) == 0) {  // common case: every symbol is an op, none of them P_a
             if (act) rec[otail + lane] = (uint8_t)sym;
             otail += n;
-            continue;
+            return;
         }
         // the P_a counts of the records before this step are all pa_run
         for (uint32_t j = t8n + lane; 8 * j < otail; j += 32) t8[j] = (uint16_t)pa_run;
@@ -150,6 +152,12 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
         t8n = (otail + 7) / 8;
         pend = hold;
         held = symlast;
+    };
+    const bool actK = lane < K;
+    for (; remaining >= K && otail < need; remaining -= K) step(K, actK, std::true_type{});
+    if (remaining > 0 && otail < need) {
+        step(remaining, lane < remaining, std::false_type{});
+        remaining = 0;
     }
     // the counts not yet written: every 8th record from t8n on, and the one just past the last record
     for (uint32_t j = t8n + lane; 8 * j <= otail; j += 32) t8[j] = (uint16_t)pa_run;
