@@ -3,7 +3,8 @@
 // A batch of requests (brick id, target LOD t) is decoded in slices of requests; a slice takes two
 // launches:
 //
-//   rans_records (one warp per rANS stream; persistent CTAs hold both decode tables in shared memory).
+//   rans_records (one warp per rANS stream; persistent CTAs hold both decode tables in shared memory;
+//     for bricks of 16^3 and smaller, rans_records_packed: several short streams per warp, see there).
 //     The K interleaved states of a stream live in lanes 0..K-1; a step decodes K symbols and the lanes
 //     that renormalise take consecutive words, in lane order (ballot + popc), from a ring window of the
 //     stream staged in shared memory by 16-byte loads (Sec. 3.3, readings R9/R10).  Each delta nibble
@@ -198,6 +199,214 @@ __global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records(VolDev V, RecJ
         const uint32_t r = decode_stream((s ? V.leaf_words : V.int_words) + w0, n_words, n_sym, V.K_max, V.S_min,
                                          lut_s + s * kM, win, rec, t8, cap, need, lane);
         if (lane == 0) J.info[2 * i + s] = r;
+    }
+}
+
+// Short streams (bricks of 16^3 and smaller have K = 1..4 states per stream at the default S_min) leave most
+// lanes of a one-stream warp idle, so for them the streams go to warps in groups: a warp takes streams from
+// the queue (all interior streams, then all leaf streams) while their K lanes fit in its 32, at most kPkSegs
+// of them, each with K <= 16 (a stream with more states is decoded alone), and decodes the group in one loop:
+// a step decodes min(K, symbols left) symbols of every stream of the group, each stream on its own run of
+// lanes (its segment).  Every per-stream quantity (word position, record tail, P_a count, ...) is held by
+// all lanes of the stream's segment; warp votes are masked to the segment; a step with a P_delta or P_a in
+// any stream takes the general path for all of them.  Since K = clamp(n / S_min, 1, K_max), the streams with
+// K >= 2 take between S_min and 1.5 S_min steps, so the streams of a group end close together.  Each stream
+// has its own ring of words (kPkRing words, or the warp's whole area when it is alone), staged as in
+// decode_stream.  Same records, counts and statuses as rans_records.
+constexpr uint32_t kPkSegs = 8;          // streams per warp at most
+constexpr uint32_t kPkRing = 64;         // ring words per stream of a group (uint16)
+constexpr uint32_t kPkMaxK = 16;         // most states of a stream that shares its warp
+constexpr uint32_t kPkWarpWords = 512;   // ring words per warp
+constexpr uint32_t kNoStream = 0xFFFFFFFFu;
+
+__global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records_packed(VolDev V, RecJob J) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *lut_s = (uint32_t *)smem;
+    for (uint32_t i = threadIdx.x; i < 2 * kM / 4; i += blockDim.x)
+        ((uint4 *)lut_s)[i] = __ldg((const uint4 *)V.lut + i);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = lanemask_lt();
+    uint16_t *rings = (uint16_t *)(smem + 2 * kM * 4) + warp * kPkWarpWords;
+    const uint32_t n_q = 2 * J.n;
+    uint32_t nxt = kNoStream;  // a stream taken from the queue and not yet placed
+    for (;;) {
+        // ---- form a group (warp-uniform); lane g keeps the queue index of the group's stream g
+        uint32_t my_q = 0, nseg = 0, used = 0, ends = 0;  // ends: bit e set for the last lane e of a segment
+        while (nseg < kPkSegs) {
+            if (nxt == kNoStream) {
+                uint32_t q = 0;
+                if (lane == 0) q = atomicAdd(J.counter, 1u);
+                nxt = __shfl_sync(kFull, q, 0);
+            }
+            if (nxt >= n_q) break;
+            const uint32_t s = nxt >= J.n ? 1u : 0u, i = nxt - s * J.n;
+            const uint32_t id = J.ids[i], t = J.lods[i];
+            // interior stream: needed below the root (t < N); leaf stream: needed for t == 0
+            if (id >= V.n_bricks || t > V.N || (s == 0 ? t >= V.N : t != 0)) {
+                nxt = kNoStream;
+                continue;
+            }
+            const uint64_t *offs = s ? V.leaf_off : V.int_off;
+            const uint32_t n_words = (uint32_t)(offs[id + 1] - offs[id]);
+            const uint32_t n_sym = s ? V.n_leaf_sym[id] : V.n_int_sym[id];
+            const uint32_t K = lanes_for(n_sym, V.K_max, V.S_min);
+            const uint64_t cap = s ? J.t8_at - J.leaf_at : J.leaf_at;  // the records' room: 8 * (t8 entries - 1)
+            if (n_sym == 0 || n_sym > cap || n_words < 2 * K || K > 32) {  // settled without decoding
+                if (lane == 0) {
+                    uint8_t *base = J.recs + (uint64_t)i * J.stride;
+                    if (n_sym == 0) *(uint16_t *)(base + (s ? J.t8_leaf_at : J.t8_at)) = 0;
+                    J.info[2 * i + s] = (n_sym == 0 && n_words == 0) ? 0u : kRecBad;
+                }
+                nxt = kNoStream;
+                continue;
+            }
+            if (nseg > 0 && (K > kPkMaxK || used + K > 32)) break;  // kept for the next group
+            if (lane == nseg) my_q = nxt;
+            used += K;
+            ends |= 1u << (used - 1);
+            nseg++;
+            nxt = kNoStream;
+            if (K > kPkMaxK) break;  // decoded alone
+        }
+        if (nseg == 0) break;  // the queue is empty
+
+        // ---- this lane's stream
+        const bool mine = lane < used;  // the lane belongs to a stream of the group
+        const uint32_t before = ends & lt;
+        const uint32_t seg = __popc(before), sb = before ? 32 - __clz(before) : 0u;  // its stream, first lane
+        const uint32_t q = __shfl_sync(kFull, my_q, mine ? seg : 0u);  // seg < nseg <= kPkSegs
+        const uint32_t s = q >= J.n ? 1u : 0u, i = q - s * J.n;
+        const uint32_t rwords = nseg == 1 ? kPkWarpWords : kPkRing, rchunks = rwords / 8, rhalf = rchunks / 2;
+        uint32_t K = 1, n_words = 0, sh = 0, n_chunks = 0, need = 0, remaining = 0;
+        const uint4 *src = nullptr;
+        uint8_t *rec = nullptr;
+        uint16_t *t8 = nullptr;
+        const uint32_t *lut = lut_s + s * kM;
+        uint16_t *win = rings + (mine ? seg : 0u) * kPkRing;
+        if (mine) {
+            const uint32_t id = J.ids[i], t = J.lods[i];
+            const uint64_t *offs = s ? V.leaf_off : V.int_off;
+            const uint64_t w0 = offs[id];
+            n_words = (uint32_t)(offs[id + 1] - w0);
+            remaining = s ? V.n_leaf_sym[id] : V.n_int_sym[id];
+            K = lanes_for(remaining, V.K_max, V.S_min);
+            const uint16_t *w = (s ? V.leaf_words : V.int_words) + w0;
+            const uintptr_t g0 = reinterpret_cast<uintptr_t>(w) & ~(uintptr_t)15;
+            sh = (uint32_t)(reinterpret_cast<uintptr_t>(w) - g0) >> 1;  // words before the stream (0..7)
+            n_chunks = (sh + n_words + 7) / 8;                          // 16-byte chunks holding the stream
+            src = reinterpret_cast<const uint4 *>(g0);
+            uint8_t *base = J.recs + (uint64_t)i * J.stride;
+            rec = base + (s ? J.leaf_at : 0);
+            t8 = (uint16_t *)(base + (s ? J.t8_leaf_at : J.t8_at));
+            // LOD t >= 2 uses the interior levels N-1 .. t only: at most 8 records per node of levels N .. t+1
+            need = (s == 0 && t >= 2) ? 8u * (((1u << (3 * (V.N - t))) - 1u) / 7u) : 0xFFFFFFFFu;
+        }
+        const uint32_t j = lane - sb;  // lane within the segment
+        const uint32_t smask = mine ? (K >= 32 ? kFull : ((1u << K) - 1u) << sb) : 0u;
+        uint4 *ring = reinterpret_cast<uint4 *>(win);
+        __syncwarp();  // the previous group's reads of the rings are done
+        if (mine)
+            for (uint32_t c = j; c < rchunks && c < n_chunks; c += K) ring[c] = __ldg(src + c);
+        // a step reads at most K words of a stream, K <= half a ring: refill once pos passes lim
+        uint32_t filled = rchunks;  // chunks staged so far
+        uint32_t lim = filled < n_chunks ? 8 * filled - K : 0xFFFFFFFFu;
+        __syncwarp();
+        uint32_t x = kL;
+        if (mine) x = (uint32_t)win[sh + 2 * j] | ((uint32_t)win[sh + 2 * j + 1] << 16);
+        uint32_t pos = sh + 2 * K, otail = 0, pend = 0, held = 0, pa_run = 0, t8n = 0;
+
+        // ---- decode the group
+        for (;;) {
+            const bool run = mine && remaining > 0 && otail < need;
+            if (!__any_sync(kFull, run)) break;
+            if (__any_sync(kFull, run && pos > lim)) {
+                __syncwarp();
+                if (run && pos > lim) {  // stage the next half ring over the half already read
+                    for (uint32_t c = j; c < rhalf; c += K)
+                        if (filled + c < n_chunks) ring[(filled + c) & (rchunks - 1u)] = __ldg(src + filled + c);
+                    filled += rhalf;
+                    lim = filled < n_chunks ? 8 * filled - K : 0xFFFFFFFFu;
+                }
+                __syncwarp();
+            }
+            const uint32_t n = run ? min(K, remaining) : 0u;
+            const bool act = j < n;
+            const uint32_t e = lut[x & (kM - 1u)];
+            const uint32_t sym = e & 15u;
+            const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
+            const bool nrm = act && xn < kL;
+            const uint32_t m = __ballot_sync(kFull, nrm) & smask;
+            const uint32_t wv = win[(pos + __popc(m & lt)) & (rwords - 1u)];
+            x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
+            pos += __popc(m);
+            remaining -= n;
+            const uint32_t rare = __ballot_sync(kFull, act && (sym & 7u) >= OP_PD);  // P_delta, P_a (or 7)
+            if (!__any_sync(kFull, run && ((rare & smask) | pend) != 0)) {  // common case: every symbol an op, no P_a
+                if (act) rec[otail + j] = (uint8_t)sym;
+                otail += n;
+                continue;
+            }
+            // every stream of the group takes the general step (exact for the common case too); the P_a
+            // counts of the records before this step are all pa_run
+            if (run)
+                for (uint32_t k = t8n + j; 8 * k < otail; k += K) t8[k] = (uint16_t)pa_run;
+            // which symbols are delta nibbles: the one after each P_delta op of the same stream; a P_delta
+            // on a stream's last symbol of the step is held back (its delta comes next step)
+            const uint32_t lastm = __ballot_sync(kFull, act && j == n - 1);
+            const uint32_t pendm = __ballot_sync(kFull, run && pend && j == 0);
+            uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD) & ~pendm;
+            uint32_t dm = pendm, holdm = 0;
+            while (cand) {
+                const uint32_t b = __ffs(cand) - 1;
+                cand &= cand - 1;
+                if (!((dm >> b) & 1u)) {
+                    if ((lastm >> b) & 1u) holdm |= 1u << b;
+                    else {
+                        dm |= 2u << b;
+                        cand &= ~(2u << b);
+                    }
+                }
+            }
+            const uint32_t nxt_sym = __shfl_down_sync(kFull, sym, 1);
+            const uint32_t sym_last = __shfl_sync(kFull, sym, (sb + n - 1) & 31u);
+            const bool hold = (holdm & smask) != 0;
+            uint32_t base = otail;
+            if (run && pend) {  // the P_delta held back from the previous step takes the first symbol as its delta
+                if (j == 0) {
+                    rec[otail] = (uint8_t)(held | (sym << 4));
+                    if ((otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
+                }
+                base++;
+            }
+            const bool em = act && !((dm >> lane) & 1u) && !((holdm >> lane) & 1u);
+            const uint32_t emit = __ballot_sync(kFull, em) & smask;
+            const uint32_t pam = __ballot_sync(kFull, em && (sym & 7u) == OP_PA) & smask;
+            if (em) {
+                const bool pd = (sym & 7u) == OP_PD;
+                const uint32_t r = base + __popc(emit & lt);
+                rec[r] = (uint8_t)(sym | (pd ? nxt_sym << 4 : 0u));
+                if ((r & 7u) == 0) t8[r >> 3] = (uint16_t)min(pa_run + __popc(pam & lt), 0xFFFFu);
+            }
+            if (run) {
+                pa_run = min(pa_run + __popc(pam), 0xFFFFu);  // saturated: a count past any palette is caught later
+                otail = base + __popc(emit);
+                t8n = (otail + 7) / 8;
+                pend = hold;
+                held = sym_last;
+            }
+        }
+
+        // ---- results: the counts not yet written (every 8th record from t8n on, and the one just past the
+        // last record), then the record count and the checks of the stream's end
+        if (mine)
+            for (uint32_t k = t8n + j; 8 * k <= otail; k += K) t8[k] = (uint16_t)pa_run;
+        const uint32_t badx = __ballot_sync(kFull, mine && j < K && x != kL) & smask;
+        if (mine && j == 0) {
+            uint32_t r;
+            if (remaining > 0) r = pos <= sh + n_words ? otail : (otail | kRecBad);  // stopped early: a prefix
+            else r = (badx == 0 && !pend && pos == sh + n_words) ? otail : (otail | kRecBad);
+            J.info[2 * i + s] = r;
+        }
     }
 }
 
@@ -862,6 +1071,7 @@ __global__ void __launch_bounds__(kGwThreads) rebuild_global(VolDev V, RecJob J,
 // ---------------------------------------------------------------- launchers (host)
 
 uint32_t rans_records_smem_bytes() { return 2 * kM * 4 + kRecWarps * kWinWords * 2; }
+uint32_t rans_records_packed_smem_bytes() { return 2 * kM * 4 + kRecWarps * kPkWarpWords * 2; }
 
 uint32_t rebuild_smem_bytes(uint32_t N, bool wide) {
     return wide ? rb_layout<uint16_t>(N).total : rb_layout<uint8_t>(N).total;
@@ -871,15 +1081,19 @@ uint32_t rebuild_smem_bytes(uint32_t N, bool wide) {
 cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uint32_t *out, const uint64_t *out_off,
                                 int32_t *status, uint32_t rec_blocks, cudaStream_t st) {
     if (J.n == 0) return cudaSuccess;
-    const uint32_t smem_a = rans_records_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(rans_records, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_a);
+    // bricks of 16^3 and smaller: streams of a few states, decoded several to a warp
+    const bool packed = V.N <= 4;
+    const uint32_t smem_a = packed ? rans_records_packed_smem_bytes() : rans_records_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(packed ? rans_records_packed : rans_records,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_a);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(J.counter, 0, 4, st);
     if (e != cudaSuccess) return e;
     const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
     {
         ProfScope ps("rans_records", st);
-        rans_records<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+        if (packed) rans_records_packed<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+        else rans_records<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -237,12 +237,16 @@ def test_wide_palette_path():
     assert_same_arrays(g2.export(), V)
 
 
-def test_range_and_corrupt_status():
+@pytest.mark.parametrize("N", [5, 4, 3])
+def test_range_and_corrupt_status(N):
+    """Statuses for bad ids and LODs, truncated streams, a cut palette and random word flips, with the
+    one-stream-per-warp rANS kernel (b = 32) and the packed one (b <= 16); the other bricks stay exact."""
     vol = structured_volume(4, (32, 32, 64), 50)
-    V = O.encode_volume(vol, 5, stride=1)
+    V = O.encode_volume(vol, N, stride=1)
     gv = import_oracle_volume(V)
+    nb = V.n_bricks
     # out-of-range brick id and LOD
-    out, off, st = gpu_decode(gv, 5, [0, 2, 1, 0, 1], [0, 0, 0, 6, 5])
+    out, off, st = gpu_decode(gv, N, [0, nb, 1, 0, 1], [0, 0, 0, N + 1, N])
     assert st.tolist() == [0, 7, 0, 7, 0]
     csgv = _csgv()
     ids = np.array([0, 1], np.uint32)
@@ -251,9 +255,9 @@ def test_range_and_corrupt_status():
     lo = V.leaf_off.copy()
     lw = np.delete(V.leaf_words, np.arange(int(lo[1]) - 5, int(lo[1])))
     lo[1:] -= 5
-    bad = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words, lo,
+    bad = csgv.csgv_volume_import(N, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words, lo,
                                   lw, V.n_int_sym, V.n_leaf_sym)
-    out, off, st = gpu_decode(bad, 5, ids, lods)
+    out, off, st = gpu_decode(bad, N, ids, lods)
     ref, _, _ = O.decode_bricks(V, ids, lods)
     assert st[0] == 4 and st[1] == 0
     assert np.array_equal(out[off[1]:], ref[off[1]:])
@@ -262,9 +266,9 @@ def test_range_and_corrupt_status():
     cut = int(po[1]) - 1
     pal = np.delete(V.pal, np.arange(1, 1 + cut))
     po[1:] -= cut
-    bad = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, po, pal, V.int_off, V.int_words, V.leaf_off,
+    bad = csgv.csgv_volume_import(N, V.dims, V.K_max, V.S_min, V.freq, po, pal, V.int_off, V.int_words, V.leaf_off,
                                   V.leaf_words, V.n_int_sym, V.n_leaf_sym)
-    out, off, st = gpu_decode(bad, 5, ids, lods)
+    out, off, st = gpu_decode(bad, N, ids, lods)
     assert st[0] == 4 and st[1] == 0
     # random word flips: never a fault; untouched bricks stay exact
     rng = np.random.default_rng(8)
@@ -275,9 +279,9 @@ def test_range_and_corrupt_status():
         iw[k] ^= rng.integers(1, 65535, size=3).astype(np.uint16)
         k = rng.integers(int(V.leaf_off[0]), int(V.leaf_off[1]), size=3)
         lw[k] ^= rng.integers(1, 65535, size=3).astype(np.uint16)
-        bad = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, iw,
+        bad = csgv.csgv_volume_import(N, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, iw,
                                       V.leaf_off, lw, V.n_int_sym, V.n_leaf_sym)
-        out, off, st = gpu_decode(bad, 5, ids, lods)
+        out, off, st = gpu_decode(bad, N, ids, lods)
         assert st[0] in (0, 4) and st[1] == 0
         assert np.array_equal(out[off[1]:], ref[off[1]:])
 
