@@ -745,6 +745,133 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     }
 }
 
+// rans_encode_kernel for bricks of 16^3 and smaller, whose streams have few states (K = 1..4 at the default
+// S_min): a warp takes kEpkSegs consecutive streams and codes as many of them at once as their K lanes fit
+// in 32, each on its own run of lanes (its segment) with its own window of kEpkWin staged nibbles; a step
+// codes one symbol per lane of every stream that has steps left (the streams' steps run from their ends, so
+// shorter streams start later only in the sense that they finish earlier).  Lanes 0..15 hold the interior
+// table, lanes 16..31 the leaf table.  Same words as rans_encode_kernel.
+constexpr uint32_t kEpkSegs = 8;
+constexpr uint32_t kEpkWin = kRansEncWin / kEpkSegs;  // 256 bytes
+
+__global__ void __launch_bounds__(kRansEncWarps * 32)
+    rans_encode_packed(EncGeom G, EncScratch SC, uint32_t n_in_batch, const uint32_t *freq) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = lanemask_lt();
+    const uint32_t q0 = (blockIdx.x * kRansEncWarps + warp) * kEpkSegs, n_q = 2 * n_in_batch;
+    if (q0 >= n_q) return;
+    const uint32_t tab = lane >> 4, tsym = lane & 15u;  // this lane's table entry
+    const uint32_t *F = freq + 16 * tab;
+    const uint32_t f_reg = F[tsym];
+    const float rcp_reg = 1.0f / (float)(f_reg ? f_reg : 1u);
+    uint32_t c_reg = 0;
+    for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < tsym) ? F[s2] : 0u;
+    uint8_t *wbase = smem_raw + warp * kRansEncWin;
+    const uint32_t g_end = min(kEpkSegs, n_q - q0);
+    uint32_t g = 0;
+    while (g < g_end) {
+        // ---- a group: the next streams of the warp's share while their lanes fit (warp-uniform)
+        uint32_t my_q = 0, nseg = 0, used = 0, ends = 0;  // ends: bit e set for the last lane e of a segment
+        while (g < g_end) {
+            const uint32_t q = q0 + g, slot = q >> 1, st = q & 1u;
+            const uint32_t n = SC.sizes[(size_t)slot * 8 + 1 + st];
+            if (n == 0) {  // nothing to code: no words
+                if (lane == 0) {
+                    const uint32_t cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
+                    SC.sizes[(size_t)slot * 8 + 3 + st] = 0;
+                    SC.sizes[(size_t)slot * 8 + 5 + st] = cap;
+                }
+                g++;
+                continue;
+            }
+            const uint32_t K = lanes_for(n, G.K_max, G.S_min);
+            if (used + K > 32) break;  // next group (a group's first stream always fits: K <= 32)
+            if (lane == nseg) my_q = q;
+            used += K;
+            ends |= 1u << (used - 1);
+            nseg++;
+            g++;
+        }
+        if (nseg == 0) break;
+        // ---- this lane's stream
+        const bool mine = lane < used;
+        const uint32_t before = ends & lt;
+        const uint32_t seg = __popc(before), sb = before ? 32 - __clz(before) : 0u;
+        const uint32_t q = __shfl_sync(kFull, my_q, mine ? seg : 0u);
+        const uint32_t slot = q >> 1, st = q & 1u, j = lane - sb;
+        uint32_t n = 0, K = 1, cap = 0;
+        uint16_t *words = nullptr;
+        const uint8_t *nib = nullptr;
+        if (mine) {
+            n = SC.sizes[(size_t)slot * 8 + 1 + st];
+            K = lanes_for(n, G.K_max, G.S_min);
+            cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
+            words = (st == 0 ? SC.w_int : SC.w_leaf) + (size_t)slot * cap;
+            nib = st == 0 ? SC.nib_int + (size_t)slot * G.int_cap : SC.nib_leaf + (size_t)slot * G.leaf_cap;
+        }
+        const uint32_t smask = mine ? (K >= 32 ? kFull : ((1u << K) - 1u) << sb) : 0u;
+        // the window of a lone stream is the warp's whole area
+        const uint32_t win_bytes = nseg == 1 ? kRansEncWin : kEpkWin;
+        uint8_t *wsm = wbase + (mine ? seg : 0u) * kEpkWin;
+        const uint32_t win_steps = (win_bytes - 16) / K;  // steps per staged window (16 bytes of alignment slack)
+        uint32_t x = kL, top = cap;
+        uint32_t s_hi = mine ? (n + K - 1) / K : 0u;  // steps left: the next step coded is s_hi - 1
+        uint32_t s_lo = s_hi, lo16 = 0;               // staged: steps [s_lo, s_hi of the window)
+        for (;;) {
+            const bool run = s_hi > 0;
+            if (!__any_sync(kFull, run)) break;
+            if (__any_sync(kFull, run && s_hi == s_lo)) {  // stage the window of steps below s_hi
+                __syncwarp();
+                if (run && s_hi == s_lo) {
+                    s_lo = s_hi > win_steps ? s_hi - win_steps : 0u;
+                    lo16 = (s_lo * K) & ~15u;
+                    const uint32_t sym_hi = min(n, s_hi * K);
+                    for (uint32_t c16 = j; lo16 + 16 * c16 < sym_hi; c16 += K)
+                        reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(nib + lo16) + c16);
+                }
+                __syncwarp();
+            }
+            const uint32_t s2 = s_hi - 1, i = s2 * K + j;
+            const bool act = run && j < K && i < n;
+            const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
+            const uint32_t e = sym + 16 * st;  // entry of this stream's table
+            const uint32_t f = __shfl_sync(kFull, f_reg, e), c = __shfl_sync(kFull, c_reg, e);
+            const float rf = __shfl_sync(kFull, rcp_reg, e);
+            // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
+            const bool emit = act && x >= (f << 20);
+            const uint32_t m = __ballot_sync(kFull, emit) & smask;
+            if (emit) {
+                words[top - __popc(m) + __popc(m & lt)] = (uint16_t)(x & 0xFFFFu);
+                x >>= 16;
+            }
+            top -= __popc(m);
+            if (act) {
+                // x / f through a float reciprocal: here x < f * 2^20, so the estimate is within one of the
+                // quotient; the integer remainder check makes it exact
+                uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
+                int32_t r = (int32_t)(x - qt * f);
+                if (r < 0) { qt -= 1; r += (int32_t)f; }
+                if (r < 0) { qt -= 1; r += (int32_t)f; }
+                if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+                if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+                x = qt * kM + (uint32_t)r + c;
+            }
+            if (run) s_hi--;
+        }
+        // final states ahead of the words, state 0 first, low half first
+        if (mine) {
+            words[top - 2 * K + 2 * j] = (uint16_t)(x & 0xFFFFu);
+            words[top - 2 * K + 2 * j + 1] = (uint16_t)(x >> 16);
+            top -= 2 * K;
+            if (j == 0) {
+                SC.sizes[(size_t)slot * 8 + 3 + st] = cap - top;  // words
+                SC.sizes[(size_t)slot * 8 + 5 + st] = top;        // start inside the scratch area
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Nibble counts (interior then leaf) of the bricks of a batch whose slot is a multiple of `stride`, from
 // the nibbles in scratch: the counts of the frequency prepass (Sec. 3.3), taken from an encode.  Grid
 // (sampled bricks, kHistSplit): each CTA counts a share of one brick's nibbles, 16 bytes per load.  Counts
@@ -1061,11 +1188,20 @@ cudaError_t launch_rans_encode(const EncGeom &G, const EncScratch &SC, uint32_t 
     if (n == 0) return cudaSuccess;
     cudaError_t e;
     const uint32_t smem_e = kRansEncWarps * kRansEncWin;
-    e = cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
+    // bricks of 16^3 and smaller: streams of a few states, coded several to a warp
+    const bool packed = G.N <= 4;
+    e = cudaFuncSetAttribute(packed ? rans_encode_packed : rans_encode_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
     if (e != cudaSuccess) return e;
     {
         ProfScope ps("rans_encode", st);
-        rans_encode_kernel<<<(2 * n + kRansEncWarps - 1) / kRansEncWarps, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
+        if (packed) {
+            const uint32_t per_cta = kRansEncWarps * kEpkSegs;
+            rans_encode_packed<<<(2 * n + per_cta - 1) / per_cta, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
+        } else {
+            rans_encode_kernel<<<(2 * n + kRansEncWarps - 1) / kRansEncWarps, kRansEncWarps * 32, smem_e, st>>>(
+                G, SC, n, freq);
+        }
     }
     return cudaGetLastError();
 }
