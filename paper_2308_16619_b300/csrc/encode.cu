@@ -224,12 +224,9 @@ __device__ __forceinline__ uint32_t palette_chunk(uint32_t lab, uint32_t kn, uin
     return res;
 }
 
-// Encode (or, when count != nullptr, only count the nibbles of) one brick: phases A-D.  kMinB: CTAs per SM
-// the registers must allow (1: no limit).
-template <int kMinB>
-__global__ void __launch_bounds__(kEncThreads, kMinB)
-    encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
-                  EncScratch SC, unsigned long long *count) {
+// Encode (or, when count != nullptr, only count the nibbles of) one brick: phases A-D.
+__device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride,
+                                             uint32_t n_in_batch, EncScratch SC, unsigned long long *count) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     EncSmem S(smem_raw, G, SC.lvl + (size_t)blockIdx.x * G.lvl_bytes);
     __shared__ uint32_t hist[32];
@@ -670,6 +667,21 @@ __global__ void __launch_bounds__(kEncThreads, kMinB)
         sz[2] = sym_tot[1];
         sz[7] = 0;
     }
+}
+
+__global__ void __launch_bounds__(kEncThreads)
+    encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
+                  EncScratch SC, unsigned long long *count) {
+    encode_brick(EV, G, brick0, brick_stride, n_in_batch, SC, count);
+}
+
+// The same for bricks of 16^3 and smaller, which need little shared memory (6.4 KB at 16^3): 8 CTAs per SM at
+// 32 registers a thread; the spills cost less than the exposed latency of 4 CTAs (0.594 against 0.710 ms for
+// the 32768 bricks of a 512^3 volume at 16^3).
+__global__ void __launch_bounds__(kEncThreads, 8)
+    encode_kernel_small(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
+                        EncScratch SC, unsigned long long *count) {
+    encode_brick(EV, G, brick0, brick_stride, n_in_batch, SC, count);
 }
 
 // ---- E. rANS, one warp per stream (brick slot q / 2, stream q % 2) over the nibbles in scratch; the
@@ -1173,18 +1185,16 @@ size_t scratch_bytes_per_brick(const EncGeom &G) {
 
 cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, uint64_t stride, uint32_t n,
                           const uint32_t *freq, const EncScratch &SC, unsigned long long *count, cudaStream_t st) {
-    // bricks of 16^3 and smaller need little shared memory (6.4 KB at 16^3): 8 CTAs per SM at 32 registers a
-    // thread; the spills cost less than the exposed latency of 4 CTAs (0.594 against 0.710 ms for the 32768
-    // bricks of a 512^3 volume at 16^3)
+    // bricks of 16^3 and smaller: more CTAs per SM (encode_kernel_small)
     const bool small = G.N <= 4;
-    cudaError_t e = cudaFuncSetAttribute(small ? encode_kernel<8> : encode_kernel<1>,
+    cudaError_t e = cudaFuncSetAttribute(small ? encode_kernel_small : encode_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps(count ? "encode_count" : "encode", st);
-        if (small) encode_kernel<8><<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
-        else encode_kernel<1><<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+        if (small) encode_kernel_small<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+        else encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || count || !freq) return e;  // no tables yet: the caller codes later
