@@ -14,7 +14,7 @@
 
 // kernels' launchers (decode.cu, encode.cu)
 namespace csgv {
-cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uint32_t *out, const uint64_t *out_off,
+cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob &J, uint32_t *out, const uint64_t *out_off,
                                 int32_t *status, uint32_t rec_blocks, cudaStream_t st);
 }  // namespace csgv
 
@@ -709,7 +709,6 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     cudaMemPool_t pool;
     int rc = dev_pool(&pool);
     if (rc) return rc;
-    const bool wide = v->max_palette > 253;
     // a request's workspace: interior records at 0, leaf records at leaf_at (one byte per op record, at
     // most one per symbol), then the P_a counts before every 8th record of each stream (uint16)
     auto a16 = [](uint64_t x) { return (x + 15) & ~15ull; };
@@ -756,7 +755,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
         J.n = (uint32_t)std::min<uint64_t>(S, n - r0);
         J.ids = ids + r0;
         J.lods = lods + r0;
-        e = csgv::launch_decode_slice(dev_view(v), wide, J, out, off + r0, status + r0,
+        e = csgv::launch_decode_slice(dev_view(v), v->max_palette, J, out, off + r0, status + r0,
                                       v->dec_rec_per_sm * (uint32_t)sms, st);
     }
     cudaError_t ef = cudaFreeAsync(ws, st);

@@ -424,6 +424,10 @@ struct RbTraits<uint16_t> {
     static constexpr uint32_t kSent = 0xFFFDu;
     static constexpr uint32_t kRep = 0x00010001u;
 };
+template <>
+struct RbTraits<uint32_t> {  // the b = 64 kernel only
+    static constexpr uint32_t kSent = 0xFFFFFFFDu;
+};
 
 constexpr uint32_t kSmallPar = 64;  // levels with at most this many parents are rebuilt one thread per child
 
@@ -894,16 +898,19 @@ __global__ void __launch_bounds__(kRbThreads, 8) rebuild_small_brick(VolDev V, R
 
 // ------------------------------------------------------------------ rebuild for b = 64 (global memory)
 //
-// The levels of a 64^3 brick (299 593 palette indices, uint32: a palette may pass 2^16 entries) do not fit in
-// shared memory: they live in the request's workspace (lev_at), with one constant flag per node (flag_at)
-// and the listed parents of the level being rebuilt (list_at).  One CTA of kGwThreads threads per request,
-// level by level: the non-constant parents are listed by a block scan; every record of the level is decoded
-// by the thread owning its run of records, with i_p from a block scan of the P_a counts (so no sampled P_a
-// counts are needed); children of constant parents copy their parent; -axis sentinels are then followed (at
-// most 3 hops, as in the shared-memory kernel).  Same results and status codes as rebuild.
+// The levels of a 64^3 brick (299 593 palette indices) do not fit in shared memory: they live in the
+// request's workspace (lev_at), with one constant flag per node (flag_at) and the listed parents of the level
+// being rebuilt (list_at).  The indices are uint8 when every palette has at most 253 entries, uint16 up to
+// 65 533, else uint32 (a 64^3 palette may pass 2^16 entries), so that the levels of the bricks in flight
+// mostly stay in L2.  One CTA of kGwThreads threads per request, level by level: the non-constant parents are
+// listed by a block scan; every record of the level is decoded by the thread owning its run of records, with
+// i_p from a block scan of the P_a counts (so no sampled P_a counts are needed); children of constant parents
+// copy their parent; -axis sentinels are then followed (at most 3 hops, as in the shared-memory kernel), 16
+// bytes of a level tested at a time.  Level t is stored as in store_level: 16 Morton-consecutive nodes per
+// thread step, four 16-byte rows out.  Same results and status codes as rebuild.
 
 constexpr uint32_t kGwThreads = 1024;
-constexpr uint32_t kGwSent = 0xFFFFFFFDu;  // 0xFFFFFFFD..F: unresolved R_x-, R_y-, R_z-
+constexpr uint32_t kGwPalSmem = 1024;  // palettes up to this many entries are staged in shared memory
 
 __host__ __device__ __forceinline__ uint32_t spread6(uint32_t v) {
     return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8) | ((v & 32u) << 10);
@@ -938,13 +945,38 @@ __device__ __forceinline__ uint32_t gw_scan(uint32_t v, uint32_t *red, uint32_t 
     return r;
 }
 
+// any -axis sentinel among the indices packed in 16 bytes
+__device__ __forceinline__ bool gw_any_sent(uint4 q, uint8_t) {
+    return ((q.x & ((q.x & 0x7F7F7F7Fu) + 0x03030303u)) | (q.y & ((q.y & 0x7F7F7F7Fu) + 0x03030303u)) |
+            (q.z & ((q.z & 0x7F7F7F7Fu) + 0x03030303u)) | (q.w & ((q.w & 0x7F7F7F7Fu) + 0x03030303u))) &
+           0x80808080u;
+}
+__device__ __forceinline__ bool gw_any_sent(uint4 q, uint16_t) {
+    return ((q.x & ((q.x & 0x7FFF7FFFu) + 0x00030003u)) | (q.y & ((q.y & 0x7FFF7FFFu) + 0x00030003u)) |
+            (q.z & ((q.z & 0x7FFF7FFFu) + 0x00030003u)) | (q.w & ((q.w & 0x7FFF7FFFu) + 0x00030003u))) &
+           0x80008000u;
+}
+__device__ __forceinline__ bool gw_any_sent(uint4 q, uint32_t) {
+    return q.x >= 0xFFFFFFFDu || q.y >= 0xFFFFFFFDu || q.z >= 0xFFFFFFFDu || q.w >= 0xFFFFFFFDu;
+}
+
+// node e of a 16-byte group of indices
+template <typename IdxT>
+__device__ __forceinline__ uint32_t gw_elem(const uint32_t (&w)[4], uint32_t e) {
+    if (sizeof(IdxT) == 1) return (w[e >> 2] >> (8 * (e & 3u))) & 0xFFu;
+    if (sizeof(IdxT) == 2) return (w[e >> 1] >> (16 * (e & 1u))) & 0xFFFFu;
+    return w[e];
+}
+
+template <typename IdxT>
 __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint32_t i, uint32_t *out,
-                                          uint32_t *red, uint32_t &sh_bad) {
+                                          uint32_t *red, uint32_t &sh_bad, uint32_t *pal_s) {
+    const uint32_t sent = RbTraits<IdxT>::kSent;
     const uint32_t N = V.N, nt = blockDim.x, tid = threadIdx.x;
     const uint32_t id = J.ids[i], t = J.lods[i];
     if (id >= V.n_bricks || t > N) return kStRange;
     const uint64_t p0 = V.pal_off[id], np64 = V.pal_off[id + 1] - p0;
-    if (np64 == 0 || np64 >= kGwSent) return kStCorrupt;
+    if (np64 == 0 || np64 > sent) return kStCorrupt;
     const uint32_t np = (uint32_t)np64;
     const uint32_t *pal = V.pal + p0;
     const uint32_t n_int = V.n_int_sym[id], n_leaf = V.n_leaf_sym[id];
@@ -962,9 +994,12 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
     const uint32_t info_int = J.info[2 * i], info_leaf = t == 0 ? J.info[2 * i + 1] : 0u;
     if ((info_int | info_leaf) & kRecBad) return kStCorrupt;
     uint8_t *base = J.recs + (uint64_t)i * J.stride;
-    uint32_t *lev = (uint32_t *)(base + J.lev_at);
+    IdxT *lev = (IdxT *)(base + J.lev_at);
     uint8_t *flg = base + J.flag_at;
     uint32_t *lst = (uint32_t *)(base + J.list_at);
+    const bool pal_in_smem = np <= kGwPalSmem;
+    if (pal_in_smem)
+        for (uint32_t k = tid; k < np; k += nt) pal_s[k] = __ldg(pal + k);
     if (tid == 0) {
         lev[lev_off(N, N)] = 0;  // the root: palette index 0, not constant (the brick has symbols)
         flg[lev_off(N, N)] = 0;
@@ -974,8 +1009,8 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
     for (int li = (int)N - 1; li >= (int)t; li--) {
         const uint32_t l = (uint32_t)li;
         const uint32_t npar = 1u << (3 * (N - l - 1)), nch = 8 * npar, pbits = npar - 1, cbits = nch - 1;
-        const uint32_t *P = lev + lev_off(N, l + 1);
-        uint32_t *C = lev + lev_off(N, l);
+        const IdxT *P = lev + lev_off(N, l + 1);
+        IdxT *C = lev + lev_off(N, l);
         const uint8_t *fP = flg + lev_off(N, l + 1);
         uint8_t *fC = flg + lev_off(N, l);
         const uint8_t *R = base + used;
@@ -1019,41 +1054,59 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
                         else v = P[minc(k, ma) & pbits];
                     } else {  // -axis: the node before it on this level, resolved below
                         if ((q & ma & cbits) == 0) bad = true;
-                        v = kGwSent + a;
+                        v = sent + a;
                     }
                 } else if (op >= OP_P0) {
                     if (op == 7u || (op == OP_PD && ipc < 1 + delta) || (op == OP_PA && ipc + 1 >= np)) bad = true;
                     v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);
                 }
                 if (l == 0 && stop) bad = true;  // leaf records carry no stop bit
-                C[q] = v;
+                C[q] = (IdxT)v;
                 if (l >= 1) fC[q] = (uint8_t)stop;
                 ipc += op == OP_PA ? 1u : 0u;
             }
         }
-        // children of constant parents repeat their parent
+        // children of constant parents repeat their parent (8 children: one 8 / 16 / 32-byte store)
         for (uint32_t k = tid; k < npar; k += nt)
             if (fP[k]) {
                 const uint32_t v = P[k];
-                for (uint32_t c8 = 0; c8 < 8; c8++) {
-                    C[8 * k + c8] = v;
-                    if (l >= 1) fC[8 * k + c8] = 1;
+                if (sizeof(IdxT) == 1) {
+                    const uint32_t r4 = 0x01010101u * v;
+                    *(uint2 *)(C + 8 * k) = make_uint2(r4, r4);
+                } else if (sizeof(IdxT) == 2) {
+                    const uint32_t r2 = 0x00010001u * v;
+                    *(uint4 *)(C + 8 * k) = make_uint4(r2, r2, r2, r2);
+                } else {
+                    *(uint4 *)(C + 8 * k) = make_uint4(v, v, v, v);
+                    *(uint4 *)(C + 8 * k + 4) = make_uint4(v, v, v, v);
                 }
+                if (l >= 1) *(uint2 *)(fC + 8 * k) = make_uint2(0x01010101u, 0x01010101u);
             }
         if (bad) sh_bad = 1;
         __syncthreads();
-        volatile uint32_t *Cv = C;
-        for (uint32_t q = tid; q < nch; q += nt) {
+        // follow the -axis sentinels, 16 bytes of the level at a time (the 8-node level: one node at a time)
+        volatile IdxT *Cv = C;
+        auto resolve = [&](uint32_t q) {
             uint32_t w = Cv[q];
-            if (w >= kGwSent) {
+            if (w >= sent) {
                 uint32_t qq = q;
-                for (int hop = 0; hop < 4 && w >= kGwSent; hop++) {
-                    qq = mdec(qq, kMX << (w - kGwSent)) & cbits;
+                for (int hop = 0; hop < 4 && w >= sent; hop++) {
+                    qq = mdec(qq, kMX << (w - sent)) & cbits;
                     w = Cv[qq];
                 }
-                if (w >= kGwSent) sh_bad = 1;
-                else Cv[q] = w;
+                if (w >= sent) sh_bad = 1;
+                else Cv[q] = (IdxT)w;
             }
+        };
+        constexpr uint32_t per16 = 16 / sizeof(IdxT);
+        if (nch >= per16) {
+            for (uint32_t g = tid; g < nch / per16; g += nt) {
+                const uint4 q4 = __ldcg((const uint4 *)(C + per16 * g));  // L2: other threads resolve nodes meanwhile
+                if (gw_any_sent(q4, (IdxT)0))
+                    for (uint32_t e = 0; e < per16; e++) resolve(per16 * g + e);
+            }
+        } else {
+            for (uint32_t q = tid; q < nch; q += nt) resolve(q);
         }
         __syncthreads();
         if (sh_bad) return kStCorrupt;
@@ -1061,22 +1114,51 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
         used += nrec;
     }
     if ((t == 1 && used != info_int) || (t == 0 && used != info_leaf)) return kStCorrupt;
-    const uint32_t *Ct = lev + lev_off(N, t);
-    for (uint32_t q = tid; q < nvox; q += nt) {
-        const uint32_t x = q & (side - 1), y = (q >> s) & (side - 1), z = q >> (2 * s);
-        const uint32_t v = Ct[spread6(x) | (spread6(y) << 1) | (spread6(z) << 2)];
-        out[q] = __ldg(pal + min(v, np - 1));
+    const IdxT *Ct = lev + lev_off(N, t);
+    auto lab = [&](uint32_t v) { return pal_in_smem ? pal_s[min(v, np - 1)] : __ldg(pal + min(v, np - 1)); };
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    if (vec && side >= 4) {
+        // a unit is 16 Morton-consecutive nodes, a 4 x 2 x 2 block (Morton bits x0 y0 z0 x1); row (dy, dz)
+        // holds Morton offsets o, o+1, o+8, o+9 with o = 2 dy + 4 dz
+        const uint32_t units = nvox / 16, xb = s - 2, yb = s - 1;
+        for (uint32_t u = tid; u < units; u += nt) {
+            const uint32_t x0 = 4 * (u & ((1u << xb) - 1u)), y0 = 2 * ((u >> xb) & ((1u << yb) - 1u)),
+                           z0 = 2 * (u >> (xb + yb));
+            const uint32_t m = spread6(x0) | (spread6(y0) << 1) | (spread6(z0) << 2);
+            uint32_t n16[16];
+#pragma unroll
+            for (uint32_t h = 0; h < sizeof(IdxT); h++) {
+                const uint4 q4 = *(const uint4 *)(Ct + m + h * (16 / sizeof(IdxT)));
+                const uint32_t w[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                for (uint32_t e = 0; e < 16 / sizeof(IdxT); e++) n16[h * (16 / sizeof(IdxT)) + e] = gw_elem<IdxT>(w, e);
+            }
+            uint32_t *o = out + ((size_t)z0 * side + y0) * side + x0;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) {  // k = dy + 2 dz
+                const uint32_t b0 = 2 * k;
+                __stcs((uint4 *)(o + (size_t)(k >> 1) * side * side + (k & 1u) * side),
+                       make_uint4(lab(n16[b0]), lab(n16[b0 + 1]), lab(n16[b0 + 8]), lab(n16[b0 + 9])));
+            }
+        }
+    } else {
+        for (uint32_t q = tid; q < nvox; q += nt) {
+            const uint32_t x = q & (side - 1), y = (q >> s) & (side - 1), z = q >> (2 * s);
+            out[q] = lab(Ct[spread6(x) | (spread6(y) << 1) | (spread6(z) << 2)]);
+        }
     }
     return kStOk;
 }
 
+template <typename IdxT>
 __global__ void __launch_bounds__(kGwThreads) rebuild_global(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                              const uint64_t *__restrict__ out_off,
                                                              int32_t *__restrict__ status) {
     __shared__ uint32_t red[33];
     __shared__ uint32_t sh_bad;
+    __shared__ uint32_t pal_s[kGwPalSmem];
     const uint32_t i = blockIdx.x;
-    const int32_t st = rebuild_global_request(V, J, i, out + out_off[i], red, sh_bad);
+    const int32_t st = rebuild_global_request<IdxT>(V, J, i, out + out_off[i], red, sh_bad, pal_s);
     if (threadIdx.x == 0) status[i] = st;
 }
 
@@ -1092,7 +1174,7 @@ uint32_t rebuild_smem_bytes(uint32_t N, bool wide) {
 }
 
 // Decode requests [0, J.n) of a slice: records, then the rebuild (statuses and outputs already offset).
-cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uint32_t *out, const uint64_t *out_off,
+cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob &J, uint32_t *out, const uint64_t *out_off,
                                 int32_t *status, uint32_t rec_blocks, cudaStream_t st) {
     if (J.n == 0) return cudaSuccess;
     // bricks of 16^3 and smaller: streams of a few states, decoded several to a warp
@@ -1113,9 +1195,13 @@ cudaError_t launch_decode_slice(const VolDev &V, bool wide, const RecJob &J, uin
     if (e != cudaSuccess) return e;
     if (V.N >= 6) {  // b = 64: levels in the workspace
         ProfScope ps("rebuild", st);
-        rebuild_global<<<J.n, kGwThreads, 0, st>>>(V, J, out, out_off, status);
+        if (max_pal <= RbTraits<uint8_t>::kSent) rebuild_global<uint8_t><<<J.n, kGwThreads, 0, st>>>(V, J, out, out_off, status);
+        else if (max_pal <= RbTraits<uint16_t>::kSent)
+            rebuild_global<uint16_t><<<J.n, kGwThreads, 0, st>>>(V, J, out, out_off, status);
+        else rebuild_global<uint32_t><<<J.n, kGwThreads, 0, st>>>(V, J, out, out_off, status);
         return cudaGetLastError();
     }
+    const bool wide = max_pal > RbTraits<uint8_t>::kSent;  // uint16 palette indices
     const uint32_t smem_b = rebuild_smem_bytes(V.N, wide);
     if (wide) {
         e = cudaFuncSetAttribute(rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);

@@ -403,20 +403,25 @@ def test_palette_churn_byte_identical(block, n_labels):
     assert_same_arrays(gv.export(), V)
 
 
-@pytest.mark.parametrize("kind", ["voronoi", "small_alphabet", "noise_and_constant"])
+@pytest.mark.parametrize("kind", ["voronoi", "small_alphabet", "noise_and_constant", "thousand_labels"])
 def test_b64_encode_byte_identical_and_decode_all_lods(kind):
     """b = 64 (the level arrays in global memory on both sides): GPU streams byte-identical to the oracle's,
-    and every brick at every LOD 0..6 decodes to the oracle's labels.  The noise brick's palette (about
-    200 000 labels) is past 2^16 entries."""
+    and every brick at every LOD 0..6 decodes to the oracle's labels.  The decoder keeps the levels as uint8,
+    uint16 or uint32 palette indices by the largest palette: the noise brick's palette (about 200 000 labels)
+    is past 2^16 entries, the thousand-label brick's past 253."""
     csgv = _csgv()
     if kind == "voronoi":
         vol = synth.voronoi((64, 128, 192), 90, seed=61, warp_amp=3, bg_permille=250)
     elif kind == "small_alphabet":
         vol = structured_volume(62, (128, 64, 64), 150, 6)
-    else:
+    elif kind == "noise_and_constant":
         rng = np.random.default_rng(63)
         vol = np.full((64, 64, 128), 41, np.uint32)
         vol[:, :, :64] = rng.integers(0, 1 << 30, size=(64, 64, 64)).astype(np.uint32)
+    else:
+        vol = synth.voronoi((64, 64, 128), 90, seed=66, warp_amp=2, bg_permille=100)
+        rng = np.random.default_rng(67)
+        vol[20:44, 20:44, 20:44] = rng.integers(0, 1000, size=(24, 24, 24)).astype(np.uint32) + 7
     V = O.encode_volume(vol, 6, stride=1)
     d = to_dev(vol)
     t = csgv.csgv_build_freq_table(d, 64, 1)
@@ -425,6 +430,8 @@ def test_b64_encode_byte_identical_and_decode_all_lods(kind):
     assert_same_arrays(gv.export(), V)
     if kind == "noise_and_constant":
         assert gv.info().max_palette > 65536
+    if kind == "thousand_labels":
+        assert 253 < gv.info().max_palette <= 65533
     n = V.n_bricks
     ids = np.repeat(np.arange(n, dtype=np.uint32), 7)
     lods = np.tile(np.arange(7, dtype=np.uint8), n)
