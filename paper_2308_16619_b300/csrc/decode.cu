@@ -1034,17 +1034,31 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
         if (8 * n_act > n_left) return kStCorrupt;
         if (tid == 0) sh_bad = 0;
         __syncthreads();
-        // every record of the level: i_p before it = ip + the P_a records before it in this level
+        // every record of the level: i_p before it = ip + the P_a records before it in this level.  Warp w takes
+        // a contiguous range of records, 32 consecutive ones per step (one per lane), so that the record loads
+        // and the children's stores of a step are contiguous; i_p from a block scan of the warps' P_a counts
+        // and a ballot per step.
         const uint32_t nrec = 8 * n_act;
         bool bad = false;
         uint32_t n_pa;
         {
-            const uint32_t per = (nrec + nt - 1) / nt, r0 = min(tid * per, nrec), r1 = min(r0 + per, nrec);
+            const uint32_t lane = tid & 31, warp = tid >> 5, nw = nt >> 5, lt = lanemask_lt();
+            const uint32_t chunk = ((nrec + nw - 1) / nw + 31) & ~31u;
+            const uint32_t r0 = min(warp * chunk, nrec), r1 = min(r0 + chunk, nrec);
             uint32_t c = 0;
-            for (uint32_t r = r0; r < r1; r++) c += (R[r] & 7u) == OP_PA ? 1u : 0u;
-            uint32_t ipc = ip + gw_scan(c, red, n_pa);
-            for (uint32_t r = r0; r < r1; r++) {
-                const uint32_t o = R[r], op = o & 7u, stop = (o >> 3) & 1u, delta = o >> 4;
+            for (uint32_t r = r0 + lane; r < r1; r += 32) c += (R[r] & 7u) == OP_PA ? 1u : 0u;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+            const uint32_t before = gw_scan(lane == 0 ? c : 0u, red, n_pa);  // lane 0: P_a of the warps before
+            uint32_t ipc = ip + __shfl_sync(kFull, before, 0);
+            for (uint32_t rr = r0; rr < r1; rr += 32) {
+                const uint32_t r = rr + lane;
+                const bool in = r < r1;
+                const uint32_t o = in ? (uint32_t)R[r] : 0u, op = o & 7u, stop = (o >> 3) & 1u, delta = o >> 4;
+                const uint32_t pam = __ballot_sync(kFull, in && op == OP_PA);
+                const uint32_t ipr = ipc + __popc(pam & lt);
+                ipc += __popc(pam);
+                if (!in) continue;
                 const uint32_t k = lst[r >> 3], c8 = r & 7u, q = 8 * k + c8;
                 uint32_t v = P[k];  // R_p
                 if (op >= OP_RX && op <= OP_RZ) {
@@ -1057,13 +1071,12 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
                         v = sent + a;
                     }
                 } else if (op >= OP_P0) {
-                    if (op == 7u || (op == OP_PD && ipc < 1 + delta) || (op == OP_PA && ipc + 1 >= np)) bad = true;
-                    v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);
+                    if (op == 7u || (op == OP_PD && ipr < 1 + delta) || (op == OP_PA && ipr + 1 >= np)) bad = true;
+                    v = ipr + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);
                 }
                 if (l == 0 && stop) bad = true;  // leaf records carry no stop bit
                 C[q] = (IdxT)v;
                 if (l >= 1) fC[q] = (uint8_t)stop;
-                ipc += op == OP_PA ? 1u : 0u;
             }
         }
         // children of constant parents repeat their parent (8 children: one 8 / 16 / 32-byte store)
