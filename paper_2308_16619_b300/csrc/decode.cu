@@ -1026,10 +1026,27 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
         {
             const uint32_t per = (npar + nt - 1) / nt, k0 = min(tid * per, npar), k1 = min(k0 + per, npar);
             uint32_t c = 0;
-            for (uint32_t k = k0; k < k1; k++) c += fP[k] == 0 ? 1u : 0u;
+            if (per % 16 == 0) {  // 16 flags (0 or 1 each) per load; the range starts on a 16-byte boundary
+                for (uint32_t k = k0; k < k1; k += 16) {
+                    const uint4 f = *(const uint4 *)(fP + k);
+                    c += 16 - __popc(f.x) - __popc(f.y) - __popc(f.z) - __popc(f.w);
+                }
+            } else {
+                for (uint32_t k = k0; k < k1; k++) c += fP[k] == 0 ? 1u : 0u;
+            }
             uint32_t j = gw_scan(c, red, n_act);
-            for (uint32_t k = k0; k < k1; k++)
-                if (fP[k] == 0) lst[j++] = k;
+            if (per % 16 == 0) {
+                for (uint32_t k = k0; k < k1; k += 16) {
+                    const uint4 f = *(const uint4 *)(fP + k);
+                    const uint32_t w[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+                    for (uint32_t e = 0; e < 16; e++)
+                        if (((w[e >> 2] >> (8 * (e & 3u))) & 0xFFu) == 0) lst[j++] = k + e;
+                }
+            } else {
+                for (uint32_t k = k0; k < k1; k++)
+                    if (fP[k] == 0) lst[j++] = k;
+            }
         }
         if (8 * n_act > n_left) return kStCorrupt;
         if (tid == 0) sh_bad = 0;
