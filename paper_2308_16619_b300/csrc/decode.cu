@@ -502,14 +502,15 @@ __device__ __forceinline__ uint32_t lev_off(uint32_t N, uint32_t l) {
     return u;
 }
 
-// every voxel of a side^3 block gets one label
+// every voxel of a side^3 block gets one label (kT threads)
+template <uint32_t kT>
 __device__ __forceinline__ void store_const(uint32_t label, uint32_t side, uint32_t *out, bool vec) {
     const uint32_t n = side * side * side;
     if (vec && side >= 4) {
         const uint4 o = make_uint4(label, label, label, label);
-        for (uint32_t i = threadIdx.x; i < n / 4; i += kRbThreads) __stcs((uint4 *)out + i, o);
+        for (uint32_t i = threadIdx.x; i < n / 4; i += kT) __stcs((uint4 *)out + i, o);
     } else {
-        for (uint32_t i = threadIdx.x; i < n; i += kRbThreads) out[i] = label;
+        for (uint32_t i = threadIdx.x; i < n; i += kT) out[i] = label;
     }
 }
 
@@ -525,14 +526,14 @@ __device__ __forceinline__ uint32_t lab(uint32_t v, uint32_t pal_reg, const uint
 // 4 x 2 x 2 block (Morton bits x0 y0 z0 x1): one 16-byte shared-memory load per thread (two for uint16
 // indices) and four 16-byte rows out.  Units go to threads x-fastest, so that the threads of a warp
 // complete whole 128-byte rows; their loads are at most 2-way bank conflicts.
-template <typename IdxT, int kPal>
+template <typename IdxT, int kPal, uint32_t kT>
 __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t *out, bool vec, uint32_t pal_reg,
                                             const uint32_t *pal_s, const uint32_t *pal, uint32_t np) {
     const uint32_t side = 1u << s;
     if (vec && side >= 4) {
         const uint32_t units = 1u << (3 * s - 4);
         const uint32_t xb = s - 2, yb = s - 1;  // bits of the unit's x and y index
-        for (uint32_t u0 = 0; u0 < units; u0 += kRbThreads) {
+        for (uint32_t u0 = 0; u0 < units; u0 += kT) {
             const uint32_t u = u0 + threadIdx.x;
             const bool in = u < units;
             const uint32_t uu = in ? u : 0u;
@@ -573,7 +574,7 @@ __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t 
         }
     } else {
         const uint32_t n = side * side * side;
-        for (uint32_t i0 = 0; i0 < n; i0 += kRbThreads) {
+        for (uint32_t i0 = 0; i0 < n; i0 += kT) {
             const uint32_t i = i0 + threadIdx.x;
             const uint32_t ii = i < n ? i : 0u;
             const uint32_t x = ii & (side - 1), y = (ii >> s) & (side - 1), z = ii >> (2 * s);
@@ -587,7 +588,7 @@ __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t 
 // Levels with at most kSmallPar parents (the top of the tree): one thread per child in Morton order,
 // the whole CTA.  The j-th non-constant parent's records sit at 8j; j, i_p and the stop bits come from
 // the active-parent mask and warp ballots over a parent's 8 lanes.  Arguments as for rebuild_level.
-template <typename IdxT, bool kSmemRec>
+template <typename IdxT, bool kSmemRec, uint32_t kT>
 __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
                                                     const uint8_t *R, const uint16_t *T8, uint32_t n_left,
                                                     uint32_t ip0, uint32_t np, uint32_t &n_act) {
@@ -609,7 +610,7 @@ __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayou
     const uint32_t nch = 8 * npar, steps = (nch + 31) / 32;
     const uint32_t grp = 0xFFu << (lane & 24u), lt = lanemask_lt();
     bool bad = false;
-    for (uint32_t s = warp; s < steps; s += kRbWarps) {
+    for (uint32_t s = warp; s < steps; s += (kT / 32)) {
         const uint32_t q = 32 * s + lane;
         const bool in = q < nch;
         const uint32_t k = (q >> 3) & pbits, c = q & 7u;
@@ -643,7 +644,7 @@ __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayou
     __syncthreads();
     if (bad) ms->bad = 1;
     volatile IdxT *Cv = C;
-    for (uint32_t s = warp; s < steps; s += kRbWarps) {
+    for (uint32_t s = warp; s < steps; s += (kT / 32)) {
         if ((ms->msk[s] >> lane) & 1u) {
             const uint32_t q = 32 * s + lane;
             Cv[q] = (IdxT)chase<IdxT>(Cv, q, Cv[q], cbits);
@@ -782,7 +783,7 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     return ms->bad == 0;
 }
 
-template <typename IdxT>
+template <typename IdxT, uint32_t kT>  // kT: threads per CTA (kRbThreads, or fewer when no level has over 64 parents)
 __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *smem, uint32_t i, uint32_t *out) {
     const uint32_t N = V.N;
     const uint32_t id = J.ids[i], t = J.lods[i];
@@ -800,7 +801,7 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     // homogeneous brick: no symbols, every LOD is palette[0] (reading R2)
     if (n_int == 0 && n_leaf == 0) {
         if (V.int_off[id + 1] != V.int_off[id] || V.leaf_off[id + 1] != V.leaf_off[id]) return kStCorrupt;
-        store_const(__ldg(pal), side, out, vec);
+        store_const<kT>(__ldg(pal), side, out, vec);
         return kStOk;
     }
     if (t == N) {  // the root: palette index 0 (Alg. 1 initialisation)
@@ -822,12 +823,12 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     const uint16_t *st8 = (const uint16_t *)(srec + ri16);
     if (info_int > 0) {
         const uint32_t t8b = ((info_int / 8 + 1) * 2 + 15u) & ~15u;
-        for (uint32_t q = threadIdx.x; q < ri16 / 16; q += kRbThreads) ((uint4 *)srec)[q] = __ldg((const uint4 *)base + q);
-        for (uint32_t q = threadIdx.x; q < t8b / 16; q += kRbThreads)
+        for (uint32_t q = threadIdx.x; q < ri16 / 16; q += kT) ((uint4 *)srec)[q] = __ldg((const uint4 *)base + q);
+        for (uint32_t q = threadIdx.x; q < t8b / 16; q += kT)
             ((uint4 *)(srec + ri16))[q] = __ldg((const uint4 *)(base + J.t8_at) + q);
     }
     if (sizeof(IdxT) == 1)
-        for (uint32_t k = threadIdx.x; k < np; k += kRbThreads) pal_s[k] = __ldg(pal + k);
+        for (uint32_t k = threadIdx.x; k < np; k += kT) pal_s[k] = __ldg(pal + k);
     const uint32_t pal_reg = lane < np ? __ldg(pal + lane) : 0u;
     if (threadIdx.x == 0) lev[lev_off(N, N)] = 0;
     __syncthreads();
@@ -840,24 +841,31 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
         if (l == 0) {  // the leaf stream follows the complete interior stream
             if (used != info_int) return kStCorrupt;
             const uint32_t ip0 = __ldg(t8i + info_int / 8);
-            good = small ? rebuild_small_level<IdxT, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0,
-                                                            np, n_act)
-                         : rebuild_level<IdxT, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0, np,
-                                                      n_act);
+            if (small)
+                good = rebuild_small_level<IdxT, false, kT>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0,
+                                                            np, n_act);
+            else if constexpr (kT == kRbThreads)
+                good = rebuild_level<IdxT, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0, np, n_act);
+            else
+                good = false;
             used = 8 * n_act;
         } else {
             if (l == 1 && t == 0) {  // warm L1 with the leaf stream's records and P_a counts
                 const uint8_t *lr = base + J.leaf_at;
-                for (uint32_t q = 128 * threadIdx.x; q < info_leaf; q += 128 * kRbThreads)
+                for (uint32_t q = 128 * threadIdx.x; q < info_leaf; q += 128 * kT)
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(lr + q));
                 const uint8_t *lt8 = (const uint8_t *)t8l;
-                for (uint32_t q = 128 * threadIdx.x; q < 2 * (info_leaf / 8 + 1); q += 128 * kRbThreads)
+                for (uint32_t q = 128 * threadIdx.x; q < 2 * (info_leaf / 8 + 1); q += 128 * kT)
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(lt8 + q));
             }
-            good = small ? rebuild_small_level<IdxT, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
-                                                           info_int - used, 0u, np, n_act)
-                         : rebuild_level<IdxT, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
-                                                     info_int - used, 0u, np, n_act);
+            if (small)
+                good = rebuild_small_level<IdxT, true, kT>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
+                                                           info_int - used, 0u, np, n_act);
+            else if constexpr (kT == kRbThreads)
+                good = rebuild_level<IdxT, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
+                                                 info_int - used, 0u, np, n_act);
+            else
+                good = false;
             used += 8 * n_act;
         }
         if (!good) return kStCorrupt;
@@ -866,9 +874,9 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
 
     const IdxT *C = lev + lev_off(N, t);
     const uint32_t s = N - t;
-    if (np <= 32) store_level<IdxT, 0>(C, s, out, vec, pal_reg, pal_s, pal, np);
-    else if (sizeof(IdxT) == 1) store_level<IdxT, 1>(C, s, out, vec, pal_reg, pal_s, pal, np);
-    else store_level<IdxT, 2>(C, s, out, vec, pal_reg, pal_s, pal, np);
+    if (np <= 32) store_level<IdxT, 0, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
+    else if (sizeof(IdxT) == 1) store_level<IdxT, 1, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
+    else store_level<IdxT, 2, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
     return kStOk;
 }
 
@@ -878,7 +886,7 @@ __global__ void __launch_bounds__(kRbThreads) rebuild(VolDev V, RecJob J, uint32
                                                       int32_t *__restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t i = blockIdx.x;
-    const int32_t st = rebuild_request<IdxT>(V, J, smem, i, out + out_off[i]);
+    const int32_t st = rebuild_request<IdxT, kRbThreads>(V, J, smem, i, out + out_off[i]);
     if (threadIdx.x == 0) status[i] = st;
 }
 
@@ -892,7 +900,21 @@ __global__ void __launch_bounds__(kRbThreads, 8) rebuild_small_brick(VolDev V, R
                                                                    int32_t *__restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t i = blockIdx.x;
-    const int32_t st = rebuild_request<IdxT>(V, J, smem, i, out + out_off[i]);
+    const int32_t st = rebuild_request<IdxT, kRbThreads>(V, J, smem, i, out + out_off[i]);
+    if (threadIdx.x == 0) status[i] = st;
+}
+
+// Bricks of 8^3 and smaller (no level with over 64 parents): a CTA of kRbTinyThreads threads per request, 32
+// CTAs per SM, since a 512-voxel brick keeps few threads busy.
+constexpr uint32_t kRbTinyThreads = 64;
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                                   const uint64_t *__restrict__ out_off,
+                                                                   int32_t *__restrict__ status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t i = blockIdx.x;
+    const int32_t st = rebuild_request<IdxT, kRbTinyThreads>(V, J, smem, i, out + out_off[i]);
     if (threadIdx.x == 0) status[i] = st;
 }
 
@@ -1239,6 +1261,13 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         ProfScope ps("rebuild", st);
         rebuild<uint16_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     } else {
+        if (V.N <= 3) {
+            e = cudaFuncSetAttribute(rebuild_tiny_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            if (e != cudaSuccess) return e;
+            ProfScope ps("rebuild", st);
+            rebuild_tiny_brick<uint8_t><<<J.n, kRbTinyThreads, smem_b, st>>>(V, J, out, out_off, status);
+            return cudaGetLastError();
+        }
         if (V.N <= 4) {
             e = cudaFuncSetAttribute(rebuild_small_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;
