@@ -465,6 +465,8 @@ __device__ __forceinline__ uint32_t chase(const volatile IdxT *L, uint32_t q, ui
 // shared-memory layout of a rebuild CTA for a brick of side 2^N (byte offsets)
 struct RbLayout {
     uint32_t lev, cm, act, mls, misc, pal, total;
+    uint32_t lev_shift;          // entries of the levels below the first one held (levels start at lev - shift)
+    uint32_t stage, stage_bytes;  // where the interior records and their P_a counts are staged
 };
 // const bytes of level l (1..N-1): one byte per parent (bit c = child c constant), 16-byte aligned levels
 __host__ __device__ __forceinline__ uint32_t cm_off(uint32_t N, uint32_t l) {
@@ -488,6 +490,31 @@ __host__ __device__ constexpr RbLayout rb_layout(uint32_t N) {
     L.act = L.cm + cm_off(N, 0);
     L.mls = L.act + ((maxpar * 2u + 15u) & ~15u);
     L.misc = L.mls + ((maxpar + 15u) & ~15u);
+    L.pal = L.misc + (((uint32_t)sizeof(RbMisc) + 15u) & ~15u);
+    L.total = L.pal + (sizeof(IdxT) == 1 ? 256u * 4u : 0u);
+    L.lev_shift = 0;
+    L.stage = L.lev;  // the L0 area, free until the leaf level
+    L.stage_bytes = (1u << (3 * N)) * (uint32_t)sizeof(IdxT);
+    return L;
+}
+
+// Layout for a request at LOD t >= 2 (coarse): levels 2..N only, the staged interior records (at most the
+// records of levels N-1..2 plus one step of the rANS kernel, which stops once they are out) in a region of
+// their own, no parent lists (every level has at most 64 parents).
+constexpr uint32_t kCoarseStage = 1024;
+template <typename IdxT>
+__host__ __device__ constexpr RbLayout rb_layout_coarse(uint32_t N) {
+    uint32_t nodes = 0;
+    for (uint32_t l = 2; l <= N; l++) nodes += 1u << (3 * (N - l));
+    RbLayout L{};
+    L.lev = 0;
+    L.lev_shift = (1u << (3 * N)) + (1u << (3 * (N - 1)));  // L0 and L1
+    L.stage = (nodes * (uint32_t)sizeof(IdxT) + 15u) & ~15u;
+    L.stage_bytes = kCoarseStage;
+    L.cm = L.stage + kCoarseStage;
+    L.act = L.cm + cm_off(N, 0);
+    L.mls = L.act;
+    L.misc = L.mls;
     L.pal = L.misc + (((uint32_t)sizeof(RbMisc) + 15u) & ~15u);
     L.total = L.pal + (sizeof(IdxT) == 1 ? 256u * 4u : 0u);
     return L;
@@ -594,7 +621,7 @@ __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayou
                                                     uint32_t ip0, uint32_t np, uint32_t &n_act) {
     typedef RbTraits<IdxT> T;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    IdxT *lev = (IdxT *)(smem + Ly.lev);
+    IdxT *lev = (IdxT *)(smem + Ly.lev) - Ly.lev_shift;
     uint8_t *cm = smem + Ly.cm;
     RbMisc *ms = (RbMisc *)(smem + Ly.misc);
     const uint32_t npar = 1u << (3 * (N - l - 1));  // 1, 8 or 64
@@ -666,7 +693,7 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     typedef RbTraits<IdxT> T;
     constexpr uint32_t nw = kRbWarps;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    IdxT *lev = (IdxT *)(smem + Ly.lev);
+    IdxT *lev = (IdxT *)(smem + Ly.lev) - Ly.lev_shift;
     uint8_t *cm = smem + Ly.cm;
     uint16_t *act = (uint16_t *)(smem + Ly.act);
     RbMisc *ms = (RbMisc *)(smem + Ly.misc);
@@ -783,12 +810,14 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     return ms->bad == 0;
 }
 
-template <typename IdxT, uint32_t kT>  // kT: threads per CTA (kRbThreads, or fewer when no level has over 64 parents)
+// kT: threads per CTA (kRbThreads, or fewer when no level has over 64 parents); kCoarse: requests at LOD >= 2 only
+template <typename IdxT, uint32_t kT, bool kCoarse = false>
 __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *smem, uint32_t i, uint32_t *out) {
     const uint32_t N = V.N;
     const uint32_t id = J.ids[i], t = J.lods[i];
     if (id >= V.n_bricks || t > N) return kStRange;
-    const RbLayout Ly = rb_layout<IdxT>(N);
+    if (kCoarse && t < 2) return kStCorrupt;  // not a coarse request: the caller's lists are wrong
+    const RbLayout Ly = kCoarse ? rb_layout_coarse<IdxT>(N) : rb_layout<IdxT>(N);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t p0 = V.pal_off[id];
     const uint32_t np = (uint32_t)(V.pal_off[id + 1] - p0);
@@ -813,16 +842,17 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     const uint8_t *base = J.recs + (uint64_t)i * J.stride;
     const uint16_t *t8i = (const uint16_t *)(base + J.t8_at), *t8l = (const uint16_t *)(base + J.t8_leaf_at);
 
-    IdxT *lev = (IdxT *)(smem + Ly.lev);
+    IdxT *lev = (IdxT *)(smem + Ly.lev) - Ly.lev_shift;
     uint32_t *pal_s = (uint32_t *)(smem + Ly.pal);
     // The interior stream (at most 8 records per parent of an interior level) and its P_a counts are
-    // staged in the L0 area, which is free until the leaf level.
+    // staged in the L0 area, which is free until the leaf level (coarse requests: a region of their own).
     if (info_int > 8 * (((1u << (3 * (N - 1))) - 1u) / 7u)) return kStCorrupt;
-    uint8_t *srec = smem + Ly.lev;
+    uint8_t *srec = smem + Ly.stage;
     const uint32_t ri16 = (info_int + 15u) & ~15u;
+    const uint32_t t8b = ((info_int / 8 + 1) * 2 + 15u) & ~15u;
+    if (info_int > 0 && ri16 + t8b > Ly.stage_bytes) return kStCorrupt;
     const uint16_t *st8 = (const uint16_t *)(srec + ri16);
     if (info_int > 0) {
-        const uint32_t t8b = ((info_int / 8 + 1) * 2 + 15u) & ~15u;
         for (uint32_t q = threadIdx.x; q < ri16 / 16; q += kT) ((uint4 *)srec)[q] = __ldg((const uint4 *)base + q);
         for (uint32_t q = threadIdx.x; q < t8b / 16; q += kT)
             ((uint4 *)(srec + ri16))[q] = __ldg((const uint4 *)(base + J.t8_at) + q);
@@ -915,6 +945,48 @@ __global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev 
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t i = blockIdx.x;
     const int32_t st = rebuild_request<IdxT, kRbTinyThreads>(V, J, smem, i, out + out_off[i]);
+    if (threadIdx.x == 0) status[i] = st;
+}
+
+// Large mixed-LOD batches of 32^3 bricks: split_lods lists the requests at LOD 0..1 (fine) and at LOD >= 2
+// (coarse); rebuild_listed runs the fine ones as rebuild does, rebuild_coarse the coarse ones with 64-thread
+// CTAs and the compact layout, 32 per SM: a coarse request has at most 64 parents per level and a few KB
+// of state, where a 256-thread CTA with the full 51 KB layout kept 4 per SM.  Both grids have one CTA per
+// request of the slice; CTAs past their list's count return at once.
+constexpr uint32_t kRbCoarseThreads = 64;
+constexpr uint32_t kSplitMin = 8192;  // requests per slice from which the split pays for its extra launches
+
+__global__ void split_lods(RecJob J, uint32_t N, uint32_t *lists, uint32_t *counts) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= J.n) return;
+    const uint32_t t = J.lods[i];
+    const uint32_t c = (t >= 2 && t <= N) ? 1u : 0u;
+    lists[c * J.n + atomicAdd(&counts[c], 1u)] = i;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kRbThreads) rebuild_listed(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                             const uint64_t *__restrict__ out_off,
+                                                             int32_t *__restrict__ status,
+                                                             const uint32_t *__restrict__ list,
+                                                             const uint32_t *__restrict__ count) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    if (blockIdx.x >= *count) return;
+    const uint32_t i = list[blockIdx.x];
+    const int32_t st = rebuild_request<IdxT, kRbThreads>(V, J, smem, i, out + out_off[i]);
+    if (threadIdx.x == 0) status[i] = st;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kRbCoarseThreads, 32) rebuild_coarse(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                                  const uint64_t *__restrict__ out_off,
+                                                                  int32_t *__restrict__ status,
+                                                                  const uint32_t *__restrict__ list,
+                                                                  const uint32_t *__restrict__ count) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    if (blockIdx.x >= *count) return;
+    const uint32_t i = list[blockIdx.x];
+    const int32_t st = rebuild_request<IdxT, kRbCoarseThreads, true>(V, J, smem, i, out + out_off[i]);
     if (threadIdx.x == 0) status[i] = st;
 }
 
@@ -1261,6 +1333,20 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         ProfScope ps("rebuild", st);
         rebuild<uint16_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     } else {
+        if (V.N == 5 && J.lists && J.n >= kSplitMin) {  // large batch: fine and coarse requests apart
+            uint32_t *counts = J.counter + 16, *lists = J.lists;
+            const uint32_t smem_c = rb_layout_coarse<uint8_t>(V.N).total;
+            e = cudaMemsetAsync(counts, 0, 8, st);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_coarse<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
+            if (e != cudaSuccess) return e;
+            split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, lists, counts);
+            ProfScope ps("rebuild", st);
+            rebuild_listed<uint8_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists, counts);
+            rebuild_coarse<uint8_t><<<J.n, kRbCoarseThreads, smem_c, st>>>(V, J, out, out_off, status, lists + J.n,
+                                                                       counts + 1);
+            return cudaGetLastError();
+        }
         if (V.N <= 3) {
             e = cudaFuncSetAttribute(rebuild_tiny_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;

@@ -78,3 +78,39 @@ def test_cells1024_mixed_lod_batch():
         assert int(s1.item()) == 0
         assert np.array_equal(o1.cpu().numpy().view(np.uint32), out_h[offs[r]:offs[r] + B3])
     v.close()
+
+
+def test_large_mixed_batch_split_by_lod_equals_oracle_and_small_batches():
+    """A batch of 32^3 requests large enough that the rebuild runs the LOD 0..1 requests and the LOD >= 2
+    requests in separate kernels (one CTA size each) gives the oracle's labels and the same bytes as the
+    same requests decoded in batches too small for that split."""
+    import torch
+    import paper_2308_16619_b300 as csgv
+    vol = synth.voronoi((128, 128, 128), 150, seed=21, warp_amp=3, bg_permille=300)
+    V = O.encode_volume(vol, 5, stride=1)
+    gv = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words,
+                                 V.leaf_off, V.leaf_words, V.n_int_sym, V.n_leaf_sym)
+    rng = np.random.default_rng(22)
+    n = 9000
+    ids = rng.integers(0, V.n_bricks, size=n).astype(np.uint32)
+    lods = rng.integers(0, 6, size=n).astype(np.uint8)
+    offs, total = csgv.request_layout(32, lods)
+    ids_d = torch.from_numpy(ids.view(np.int32)).cuda()
+    lods_d = torch.from_numpy(lods).cuda()
+    offs_d = torch.from_numpy(np.asarray(offs, np.int64)).cuda()
+    out = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    status = torch.full((n,), -99, dtype=torch.int32, device="cuda")
+    csgv.csgv_decode_bricks(gv, ids_d, lods_d, out, offs_d, status)
+    ref, roff, rst = O.decode_bricks(V, ids, lods)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all() and (rst == 0).all()
+    got = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, ref)
+    out2 = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    status2 = torch.full((n,), -99, dtype=torch.int32, device="cuda")
+    for r0 in range(0, n, 2000):
+        r1 = min(n, r0 + 2000)
+        csgv.csgv_decode_bricks(gv, ids_d[r0:r1], lods_d[r0:r1], out2, offs_d[r0:r1], status2[r0:r1])
+    torch.cuda.synchronize()
+    assert (status2.cpu().numpy() == 0).all()
+    assert np.array_equal(out2.cpu().numpy().view(np.uint32), got)
