@@ -686,12 +686,12 @@ __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayou
 // shared memory if kSmemRec); T8: P_a counts before every 8th record of the stream from R's first
 // record on; n_left: records of the stream from R on; ip0: i_p at the stream's start.  Sets n_act
 // (listed parents: 8 * n_act records were used).
-template <typename IdxT, bool kSmemRec>
+template <typename IdxT, bool kSmemRec, uint32_t kT>
 __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
                                               const uint8_t *R, const uint16_t *T8, uint32_t n_left, uint32_t ip0,
                                               uint32_t np, uint32_t &n_act) {
     typedef RbTraits<IdxT> T;
-    constexpr uint32_t nw = kRbWarps;
+    constexpr uint32_t nw = kT / 32;  // needs nb = npar / 32 >= nw: npar >= 512 here, 64 <= kT <= 256
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     IdxT *lev = (IdxT *)(smem + Ly.lev) - Ly.lev_shift;
     uint8_t *cm = smem + Ly.cm;
@@ -874,8 +874,8 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
             if (small)
                 good = rebuild_small_level<IdxT, false, kT>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0,
                                                             np, n_act);
-            else if constexpr (kT == kRbThreads)
-                good = rebuild_level<IdxT, false>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0, np, n_act);
+            else if constexpr (kT >= 64)
+                good = rebuild_level<IdxT, false, kT>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0, np, n_act);
             else
                 good = false;
             used = 8 * n_act;
@@ -891,9 +891,9 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
             if (small)
                 good = rebuild_small_level<IdxT, true, kT>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
                                                            info_int - used, 0u, np, n_act);
-            else if constexpr (kT == kRbThreads)
-                good = rebuild_level<IdxT, true>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
-                                                 info_int - used, 0u, np, n_act);
+            else if constexpr (kT >= 64)
+                good = rebuild_level<IdxT, true, kT>(smem, Ly, N, (uint32_t)l, srec + used, st8 + used / 8,
+                                                     info_int - used, 0u, np, n_act);
             else
                 good = false;
             used += 8 * n_act;
@@ -920,17 +920,17 @@ __global__ void __launch_bounds__(kRbThreads) rebuild(VolDev V, RecJob J, uint32
     if (threadIdx.x == 0) status[i] = st;
 }
 
-// The same for bricks of 16^3 and smaller: their CTAs need little shared memory (7.5 KB at 16^3), so 8 of them
-// fit on an SM once each thread keeps to 32 registers.  The spills that costs are cheaper than the latency
-// that fewer CTAs leave exposed: 0.45 ms against 0.59 ms (4 CTAs per SM) for the 32768 bricks of a 512^3
-// volume at 16^3.
+// The same for bricks of 16^3: 64-thread CTAs (the leaf level's 512 parents in 2 warps), 24 per SM at 40
+// registers a thread (7.5 KB of shared memory each).  For the 32768 bricks of a 512^3 volume: 0.27 ms, against
+// 0.30 (128 threads, 16 per SM), 0.45 (256 threads, 8 per SM) and 0.59 ms (256 threads, 4 per SM).
+constexpr uint32_t kRbSmallThreads = 64;
 template <typename IdxT>
-__global__ void __launch_bounds__(kRbThreads, 8) rebuild_small_brick(VolDev V, RecJob J, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kRbSmallThreads, 24) rebuild_small_brick(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                                    const uint64_t *__restrict__ out_off,
                                                                    int32_t *__restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t i = blockIdx.x;
-    const int32_t st = rebuild_request<IdxT, kRbThreads>(V, J, smem, i, out + out_off[i]);
+    const int32_t st = rebuild_request<IdxT, kRbSmallThreads>(V, J, smem, i, out + out_off[i]);
     if (threadIdx.x == 0) status[i] = st;
 }
 
@@ -1358,7 +1358,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             e = cudaFuncSetAttribute(rebuild_small_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;
             ProfScope ps("rebuild", st);
-            rebuild_small_brick<uint8_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
+            rebuild_small_brick<uint8_t><<<J.n, kRbSmallThreads, smem_b, st>>>(V, J, out, out_off, status);
             return cudaGetLastError();
         }
         e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
