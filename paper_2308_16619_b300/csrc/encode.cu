@@ -132,12 +132,13 @@ __host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes, bool level
 }
 
 // exclusive block scan of one value per warp (warp totals in `red`), returns warp's offset and the total
+template <uint32_t kW>
 __device__ __forceinline__ uint32_t block_excl_warp(uint32_t *red, uint32_t warp_total, uint32_t &total) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = warp_total;
     __syncthreads();
     uint32_t off = 0, tot = 0;
-    for (uint32_t w = 0; w < kEncWarps; w++) {
+    for (uint32_t w = 0; w < kW; w++) {
         const uint32_t v = red[w];
         if (w < warp) off += v;
         tot += v;
@@ -225,6 +226,7 @@ __device__ __forceinline__ uint32_t palette_chunk(uint32_t lab, uint32_t kn, uin
 }
 
 // Encode (or, when count != nullptr, only count the nibbles of) one brick: phases A-D.
+template <uint32_t kT>  // threads per CTA: 64..256
 __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride,
                                              uint32_t n_in_batch, EncScratch SC, unsigned long long *count) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -266,7 +268,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             // words): four 16-byte rows (y, z) of 4 voxels
             const uint32_t npairs = 1u << (3 * h - 1);
 #pragma unroll 2
-            for (uint32_t i = tid; i < npairs; i += kEncThreads) {
+            for (uint32_t i = tid; i < npairs; i += kT) {
                 const uint32_t m2 = 2 * i;
                 const uint32_t x = compact6(m2), y = compact6(m2 >> 1), z = compact6(m2 >> 2);  // x even
                 const uint32_t *r = B.base + B.sz * (2 * z) + B.sy * (2 * y) + 2 * x;
@@ -281,7 +283,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             }
         } else {
             const uint32_t n1 = 1u << (3 * h);
-            for (uint32_t i = tid; i < n1; i += kEncThreads) {
+            for (uint32_t i = tid; i < n1; i += kT) {
                 const uint32_t x = i & ((1u << h) - 1u), y = (i >> h) & ((1u << h) - 1u), z = i >> (2 * h);
                 bool eq;
                 const uint32_t m = loff(G.N, 1) + morton3(x, y, z);
@@ -298,7 +300,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             const uint32_t nl = 1u << (3 * (N - l));
             const bool big = nl > 64;
             if (!big && warp != 0) break;
-            for (uint32_t i = big ? tid : lane; i < nl; i += big ? kEncThreads : 32u) {
+            for (uint32_t i = big ? tid : lane; i < nl; i += big ? kT : 32u) {
                 const uint4 wa = *(const uint4 *)(S.lab + loff(G.N, l - 1) + 8 * i),
                             wb = *(const uint4 *)(S.lab + loff(G.N, l - 1) + 8 * i + 4);
                 const uint2 cs = *(const uint2 *)(S.cst + loff(G.N, l - 1) + 8 * i);  // 8 flags, 0 or 1 each
@@ -320,7 +322,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     // so every level is coded in one pass.  The flags are counted in their storage order (level 1 first),
     // 16 per 16-byte load, by contiguous runs of chunks per thread.
     {
-        const uint32_t ne = G.up_nodes, nq = (ne + 15) >> 4, cpt = (nq + kEncThreads - 1) / kEncThreads;
+        const uint32_t ne = G.up_nodes, nq = (ne + 15) >> 4, cpt = (nq + kT - 1) / kT;
         const uint32_t q0 = min(tid * cpt, nq), q1 = min(q0 + cpt, nq);
         // active (flag 0) bytes of chunk q as a 16-bit mask, bytes at or past ne excluded
         auto act_mask = [&](uint32_t q) {
@@ -341,7 +343,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             if (lane >= (uint32_t)d) incl += u;
         }
         uint32_t n_act_all;
-        const uint32_t wb = block_excl_warp(S.red, __shfl_sync(kFull, incl, 31), n_act_all);
+        const uint32_t wb = block_excl_warp<kT / 32>(S.red, __shfl_sync(kFull, incl, 31), n_act_all);
         const uint32_t base = wb + incl - cnt;  // active flags before this thread's first chunk
         // level starts in storage order (levels 2..N); lvl_sp[l]: active flags before level l's first node
         uint32_t bnd[kMaxN + 1];
@@ -387,7 +389,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         n_act_total = n_act_all;
     }
     const uint32_t n_ops = 8 * n_act_total, n_int_ops = 8 * lvl_rank[1];
-    for (uint32_t r = tid; r < n_act_total; r += kEncThreads) {
+    for (uint32_t r = tid; r < n_act_total; r += kT) {
         uint32_t l = N;
         for (uint32_t L = 1; L < N; L++)
             if (r >= lvl_rank[L]) {
@@ -472,7 +474,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     __syncthreads();
 
     // each warp takes a contiguous range of the op array in phases C and D
-    const uint32_t per = ((n_ops + kEncWarps - 1) / kEncWarps + 127) & ~127u;  // phase D: 128 ops per warp step
+    const uint32_t per = ((n_ops + (kT / 32) - 1) / (kT / 32) + 127) & ~127u;  // phase D: 128 ops per warp step
     const uint32_t j0 = min(warp * per, n_ops), j1 = min(j0 + per, n_ops);
 
     // ---- C. palette pass in stream order: warp 0 walks the children no reuse fits, with the last 17 palette
@@ -480,7 +482,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     // labels; they are put in stream order by rank and the walk also counts the P_delta ops per warp range
     // of phase D.  Bricks with more go through the gathering below, 256 at a time.
     const uint32_t n_need = sh_npc;
-    const bool fast = n_need <= 256;
+    const bool fast = n_need <= 256 && n_need <= kT;  // one thread per gathered child ranks it
     if (fast) {
         uint2 mine = make_uint2(0u, 0u);
         uint32_t rank = 0;
@@ -488,7 +490,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             mine = S.plist[tid];
             for (uint32_t k = 0; k < n_need; k++) rank += S.plist[k].x < mine.x ? 1u : 0u;
         }
-        if (tid < 2 * kEncWarps) sh_pd[tid] = 0;
+        if (tid < 2 * (kT / 32)) sh_pd[tid] = 0;
         __syncthreads();
         if (tid < n_need) S.plist[rank] = mine;
         __syncthreads();
@@ -505,7 +507,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
                 if (lane < kn) {
                     ops[mine2.x] = (uint8_t)((ops[mine2.x] & 8u) | res);
                     if ((res & 7u) == OP_PD)
-                        atomicAdd(&sh_pd[(mine2.x >= n_int_ops ? kEncWarps : 0u) + mine2.x / per], 1u);
+                        atomicAdd(&sh_pd[(mine2.x >= n_int_ops ? (kT / 32) : 0u) + mine2.x / per], 1u);
                 }
             }
             if (lane == 0) sh_np = np;
@@ -518,7 +520,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             cnt += __popc(__ballot_sync(kFull, j < j1 && (ops[j] & 7u) == kNeedPal));
         }
         uint32_t total;
-        const uint32_t wbase = block_excl_warp(S.red, cnt, total);
+        const uint32_t wbase = block_excl_warp<kT / 32>(S.red, cnt, total);
         const uint32_t root = S.lab[loff(G.N, N)];
         uint32_t win = root;
         uint32_t ip = 0, np = 1;  // i_p and palette size (kept by warp 0)
@@ -584,13 +586,13 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             }
             if (lane == 0) {
                 sh_pd[warp] = pdi;
-                sh_pd[kEncWarps + warp] = pdl;
+                sh_pd[(kT / 32) + warp] = pdl;
             }
             __syncthreads();
         }
         uint32_t bi = 0, bl = 0, toti = 0, totl = 0;
-        for (uint32_t w2 = 0; w2 < kEncWarps; w2++) {
-            const uint32_t vi = pdc[w2], vl = pdc[kEncWarps + w2];
+        for (uint32_t w2 = 0; w2 < (kT / 32); w2++) {
+            const uint32_t vi = pdc[w2], vl = pdc[(kT / 32) + w2];
             bi += w2 < warp ? vi : 0u;
             bl += w2 < warp ? vl : 0u;
             toti += vi;
@@ -604,7 +606,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         uint8_t *nib_l = count ? nullptr : SC.nib_leaf + (size_t)slot * G.leaf_cap;
         // this warp's ops are staged in shared memory (the pyramid and lists are dead now), stage bytes at a
         // time with 16-byte loads: one round trip to L2 instead of one per 32 ops
-        const uint32_t stage = (G.smem / kEncWarps) & ~(kStageMin - 1u);
+        const uint32_t stage = (G.smem / (kT / 32)) & ~(kStageMin - 1u);
         uint8_t *stg = smem_raw + warp * stage;
         for (uint32_t js = j0; js < j1; js += stage) {
             const uint32_t len = min(stage, j1 - js), nv = (len + 15u) >> 4;  // j0, js: multiples of 16
@@ -672,16 +674,17 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
 __global__ void __launch_bounds__(kEncThreads)
     encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
                   EncScratch SC, unsigned long long *count) {
-    encode_brick(EV, G, brick0, brick_stride, n_in_batch, SC, count);
+    encode_brick<kEncThreads>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
 }
 
-// The same for bricks of 16^3 and smaller, which need little shared memory (6.4 KB at 16^3): 8 CTAs per SM at
-// 32 registers a thread; the spills cost less than the exposed latency of 4 CTAs (0.594 against 0.710 ms for
-// the 32768 bricks of a 512^3 volume at 16^3).
-__global__ void __launch_bounds__(kEncThreads, 8)
+// The same for bricks of 16^3 and smaller, which need little shared memory (6.4 KB at 16^3): 128-thread CTAs,
+// 16 per SM at 32 registers a thread.  For the 32768 bricks of a 512^3 volume at 16^3: 0.51 ms, against 0.53
+// (64 threads, 24 per SM), 0.60 (256 threads, 8 per SM) and 0.71 ms (256 threads, 4 per SM).
+constexpr uint32_t kEncSmallThreads = 128;
+__global__ void __launch_bounds__(kEncSmallThreads, 16)
     encode_kernel_small(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
                         EncScratch SC, unsigned long long *count) {
-    encode_brick(EV, G, brick0, brick_stride, n_in_batch, SC, count);
+    encode_brick<kEncSmallThreads>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
 }
 
 // ---- E. rANS, one warp per stream (brick slot q / 2, stream q % 2) over the nibbles in scratch; the
@@ -1193,7 +1196,7 @@ cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, u
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps(count ? "encode_count" : "encode", st);
-        if (small) encode_kernel_small<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+        if (small) encode_kernel_small<<<n, kEncSmallThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
         else encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
     }
     e = cudaGetLastError();
