@@ -731,7 +731,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     const uint64_t budget = v->N >= 6 ? std::max<uint64_t>(v->dec_ws_bytes, 2ull << 30) : v->dec_ws_bytes;
     uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, budget / stride));
     const size_t info_bytes = ((size_t)S * 8 + 255) & ~(size_t)255;
-    const size_t bytes = 256 + info_bytes + (size_t)S * stride + (size_t)S * 8;  // + the rebuild split's lists
+    const size_t bytes = 256 + info_bytes + (size_t)S * stride + (size_t)S * 12;  // + the rebuild split's lists
     // the volume may come from another stream; a captured graph cannot depend on uncaptured work, so a
     // decode being captured does not wait (the graph is launched once the volume is complete)
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

@@ -37,8 +37,8 @@ struct RecJob {
     uint64_t stride, leaf_at, t8_at, t8_leaf_at;
     uint64_t lev_at, flag_at, list_at;  // b = 64 only
     uint32_t *info;
-    uint32_t *counter;  // work counter of the rANS kernel; counter[16..17]: list counts of the rebuild split
-    uint32_t *lists;    // 2 x n request indices (the rebuild split), or nullptr
+    uint32_t *counter;  // work counter of the rANS kernel; counter[16..21]: list counts and work counters of the rebuild split
+    uint32_t *lists;    // 3 x n request indices (the rebuild split), or nullptr
 };
 
 // Device view of a compressed volume (passed to kernels by value).

@@ -498,23 +498,28 @@ __host__ __device__ constexpr RbLayout rb_layout(uint32_t N) {
     return L;
 }
 
-// Layout for a request at LOD t >= 2 (coarse): levels 2..N only, the staged interior records (at most the
-// records of levels N-1..2 plus one step of the rANS kernel, which stops once they are out) in a region of
-// their own, no parent lists (every level has at most 64 parents).
-constexpr uint32_t kCoarseStage = 1024;
+// Layout for a request at LOD t >= lmin (1 or 2): levels lmin..N only, the staged interior records (at most
+// the records of levels N-1..lmin, plus one step of the rANS kernel for lmin = 2, which stops once they are
+// out) in a region of their own, and parent lists only for level 1's 8^(N-2) parents (lmin = 1: level 1 is
+// the one level with over 64 parents).
+constexpr uint32_t kStageCoarse = 1024, kStageMedium = 6144;
 template <typename IdxT>
-__host__ __device__ constexpr RbLayout rb_layout_coarse(uint32_t N) {
-    uint32_t nodes = 0;
-    for (uint32_t l = 2; l <= N; l++) nodes += 1u << (3 * (N - l));
+__host__ __device__ constexpr RbLayout rb_layout_part(uint32_t N, uint32_t lmin) {
+    uint32_t nodes = 0, below = 0;
+    for (uint32_t l = 0; l <= N; l++) {
+        if (l >= lmin) nodes += 1u << (3 * (N - l));
+        else below += 1u << (3 * (N - l));
+    }
+    const uint32_t maxpar = lmin >= 2 ? 0u : 1u << (3 * (N - 2));
     RbLayout L{};
     L.lev = 0;
-    L.lev_shift = (1u << (3 * N)) + (1u << (3 * (N - 1)));  // L0 and L1
+    L.lev_shift = below;
     L.stage = (nodes * (uint32_t)sizeof(IdxT) + 15u) & ~15u;
-    L.stage_bytes = kCoarseStage;
-    L.cm = L.stage + kCoarseStage;
+    L.stage_bytes = lmin >= 2 ? kStageCoarse : kStageMedium;
+    L.cm = L.stage + L.stage_bytes;
     L.act = L.cm + cm_off(N, 0);
-    L.mls = L.act;
-    L.misc = L.mls;
+    L.mls = L.act + ((maxpar * 2u + 15u) & ~15u);
+    L.misc = L.mls + ((maxpar + 15u) & ~15u);
     L.pal = L.misc + (((uint32_t)sizeof(RbMisc) + 15u) & ~15u);
     L.total = L.pal + (sizeof(IdxT) == 1 ? 256u * 4u : 0u);
     return L;
@@ -810,14 +815,15 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     return ms->bad == 0;
 }
 
-// kT: threads per CTA (kRbThreads, or fewer when no level has over 64 parents); kCoarse: requests at LOD >= 2 only
-template <typename IdxT, uint32_t kT, bool kCoarse = false>
+// kT: threads per CTA (64..256; the leaf-level pass needs 64 or more); kLmin: 0, or 1 / 2 for requests at LOD
+// >= kLmin only, in the compact layout rb_layout_part
+template <typename IdxT, uint32_t kT, uint32_t kLmin = 0>
 __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *smem, uint32_t i, uint32_t *out) {
     const uint32_t N = V.N;
     const uint32_t id = J.ids[i], t = J.lods[i];
     if (id >= V.n_bricks || t > N) return kStRange;
-    if (kCoarse && t < 2) return kStCorrupt;  // not a coarse request: the caller's lists are wrong
-    const RbLayout Ly = kCoarse ? rb_layout_coarse<IdxT>(N) : rb_layout<IdxT>(N);
+    if (kLmin && t < kLmin) return kStCorrupt;  // the caller's lists are wrong
+    const RbLayout Ly = kLmin ? rb_layout_part<IdxT>(N, kLmin) : rb_layout<IdxT>(N);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t p0 = V.pal_off[id];
     const uint32_t np = (uint32_t)(V.pal_off[id + 1] - p0);
@@ -954,40 +960,63 @@ __global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev 
 // of state, where a 256-thread CTA with the full 51 KB layout kept 4 per SM.  Both grids have one CTA per
 // request of the slice; CTAs past their list's count return at once.
 constexpr uint32_t kRbCoarseThreads = 64;
+constexpr uint32_t kRbMediumThreads = 128;
 constexpr uint32_t kSplitMin = 8192;  // requests per slice from which the split pays for its extra launches
 
 __global__ void split_lods(RecJob J, uint32_t N, uint32_t *lists, uint32_t *counts) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= J.n) return;
     const uint32_t t = J.lods[i];
-    const uint32_t c = (t >= 2 && t <= N) ? 1u : 0u;
+    const uint32_t c = (t >= 2 && t <= N) ? 2u : t == 1 ? 1u : 0u;
     lists[c * J.n + atomicAdd(&counts[c], 1u)] = i;
+}
+
+// One list of the split: persistent CTAs take the list's requests one at a time (a counter per list), so a
+// grid is sized to the CTAs that fit on the GPU, not to the batch.
+template <typename IdxT, uint32_t kT, uint32_t kLmin>
+__device__ __forceinline__ void rebuild_list(const VolDev &V, const RecJob &J, uint32_t *out, const uint64_t *out_off,
+                                             int32_t *status, const uint32_t *list, const uint32_t *count,
+                                             uint32_t *next, uint8_t *smem) {
+    __shared__ uint32_t sh_j;
+    const uint32_t n = *count;
+    for (;;) {
+        if (threadIdx.x == 0) sh_j = atomicAdd(next, 1u);
+        __syncthreads();
+        const uint32_t j = sh_j;
+        __syncthreads();
+        if (j >= n) return;
+        const uint32_t i = list[j];
+        const int32_t st = rebuild_request<IdxT, kT, kLmin>(V, J, smem, i, out + out_off[i]);
+        if (threadIdx.x == 0) status[i] = st;
+        __syncthreads();  // the next request reuses the shared memory
+    }
 }
 
 template <typename IdxT>
 __global__ void __launch_bounds__(kRbThreads) rebuild_listed(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                              const uint64_t *__restrict__ out_off,
-                                                             int32_t *__restrict__ status,
-                                                             const uint32_t *__restrict__ list,
-                                                             const uint32_t *__restrict__ count) {
+                                                             int32_t *__restrict__ status, const uint32_t *list,
+                                                             const uint32_t *count, uint32_t *next) {
     extern __shared__ __align__(16) uint8_t smem[];
-    if (blockIdx.x >= *count) return;
-    const uint32_t i = list[blockIdx.x];
-    const int32_t st = rebuild_request<IdxT, kRbThreads>(V, J, smem, i, out + out_off[i]);
-    if (threadIdx.x == 0) status[i] = st;
+    rebuild_list<IdxT, kRbThreads, 0>(V, J, out, out_off, status, list, count, next, smem);
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kRbMediumThreads, 14) rebuild_medium(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                                  const uint64_t *__restrict__ out_off,
+                                                                  int32_t *__restrict__ status, const uint32_t *list,
+                                                                  const uint32_t *count, uint32_t *next) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    rebuild_list<IdxT, kRbMediumThreads, 1>(V, J, out, out_off, status, list, count, next, smem);
 }
 
 template <typename IdxT>
 __global__ void __launch_bounds__(kRbCoarseThreads, 32) rebuild_coarse(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                                   const uint64_t *__restrict__ out_off,
-                                                                  int32_t *__restrict__ status,
-                                                                  const uint32_t *__restrict__ list,
-                                                                  const uint32_t *__restrict__ count) {
+                                                                  int32_t *__restrict__ status, const uint32_t *list,
+                                                                  const uint32_t *count, uint32_t *next) {
     extern __shared__ __align__(16) uint8_t smem[];
-    if (blockIdx.x >= *count) return;
-    const uint32_t i = list[blockIdx.x];
-    const int32_t st = rebuild_request<IdxT, kRbCoarseThreads, true>(V, J, smem, i, out + out_off[i]);
-    if (threadIdx.x == 0) status[i] = st;
+    rebuild_list<IdxT, kRbCoarseThreads, 2>(V, J, out, out_off, status, list, count, next, smem);
 }
 
 // ------------------------------------------------------------------ rebuild for b = 64 (global memory)
@@ -1335,16 +1364,24 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     } else {
         if (V.N == 5 && J.lists && J.n >= kSplitMin) {  // large batch: fine and coarse requests apart
             uint32_t *counts = J.counter + 16, *lists = J.lists;
-            const uint32_t smem_c = rb_layout_coarse<uint8_t>(V.N).total;
-            e = cudaMemsetAsync(counts, 0, 8, st);
+            const uint32_t smem_m = rb_layout_part<uint8_t>(V.N, 1).total, smem_c = rb_layout_part<uint8_t>(V.N, 2).total;
+            e = cudaMemsetAsync(counts, 0, 24, st);  // list counts, then the lists' work counters
             if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_medium<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_m);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_coarse<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
             if (e != cudaSuccess) return e;
             split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, lists, counts);
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const uint32_t g = (uint32_t)sms;
             ProfScope ps("rebuild", st);
-            rebuild_listed<uint8_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists, counts);
-            rebuild_coarse<uint8_t><<<J.n, kRbCoarseThreads, smem_c, st>>>(V, J, out, out_off, status, lists + J.n,
-                                                                       counts + 1);
+            rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists,
+                                                                             counts, counts + 3);
+            rebuild_medium<uint8_t><<<min(J.n, 14 * g), kRbMediumThreads, smem_m, st>>>(
+                V, J, out, out_off, status, lists + J.n, counts + 1, counts + 4);
+            rebuild_coarse<uint8_t><<<min(J.n, 32 * g), kRbCoarseThreads, smem_c, st>>>(
+                V, J, out, out_off, status, lists + 2 * J.n, counts + 2, counts + 5);
             return cudaGetLastError();
         }
         if (V.N <= 3) {
