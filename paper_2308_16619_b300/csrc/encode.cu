@@ -763,14 +763,12 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
 }
 
 // rans_encode_kernel for bricks of 16^3 and smaller, whose streams have few states (K = 1..4 at the default
-// S_min): a warp takes kEpkSegs consecutive streams and codes as many of them at once as their K lanes fit
-// in 32, each on its own run of lanes (its segment) with its own window of kEpkWin staged nibbles; a step
-// codes one symbol per lane of every stream that has steps left (the streams' steps run from their ends, so
-// shorter streams start later only in the sense that they finish earlier).  Lanes 0..15 hold the interior
-// table, lanes 16..31 the leaf table.  Same words as rans_encode_kernel.
-constexpr uint32_t kEpkSegs = 8;
-constexpr uint32_t kEpkWin = kRansEncWin / kEpkSegs;  // 256 bytes
-
+// S_min): a warp takes kEpkSegs consecutive streams (16 at 16^3, 32 at 8^3 and smaller) and codes as many of
+// them at once as their K lanes fit in 32, each on its own run of lanes (its segment) with its own window of
+// staged nibbles; a step codes one symbol per lane of every stream that has steps left (the streams' steps
+// run from their ends, so shorter streams finish earlier).  Lanes 0..15 hold the interior table, lanes
+// 16..31 the leaf table.  Same words as rans_encode_kernel.
+template <uint32_t kEpkSegs>  // streams per warp; each stream of a group stages kRansEncWin / kEpkSegs bytes
 __global__ void __launch_bounds__(kRansEncWarps * 32)
     rans_encode_packed(EncGeom G, EncScratch SC, uint32_t n_in_batch, const uint32_t *freq) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -828,8 +826,8 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
         }
         const uint32_t smask = mine ? (K >= 32 ? kFull : ((1u << K) - 1u) << sb) : 0u;
         // the window of a lone stream is the warp's whole area
-        const uint32_t win_bytes = nseg == 1 ? kRansEncWin : kEpkWin;
-        uint8_t *wsm = wbase + (mine ? seg : 0u) * kEpkWin;
+        const uint32_t win_bytes = nseg == 1 ? kRansEncWin : (kRansEncWin / kEpkSegs);
+        uint8_t *wsm = wbase + (mine ? seg : 0u) * (kRansEncWin / kEpkSegs);
         const uint32_t win_steps = (win_bytes - 16) / K;  // steps per staged window (16 bytes of alignment slack)
         uint32_t x = kL, top = cap;
         uint32_t s_hi = mine ? (n + K - 1) / K : 0u;  // steps left: the next step coded is s_hi - 1
@@ -1211,14 +1209,17 @@ cudaError_t launch_rans_encode(const EncGeom &G, const EncScratch &SC, uint32_t 
     const uint32_t smem_e = kRansEncWarps * kRansEncWin;
     // bricks of 16^3 and smaller: streams of a few states, coded several to a warp
     const bool packed = G.N <= 4;
-    e = cudaFuncSetAttribute(packed ? rans_encode_packed : rans_encode_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
+    // streams per warp: 16 at 16^3 (0.27 ms for 32768 bricks, against 0.31 with 8 and 0.39 with 32), 32 below
+    // (8^3: 0.09 ms, against 0.19 with 8)
+    const uint32_t segs = G.N <= 3 ? 32u : 16u;
+    auto kp = segs == 32 ? rans_encode_packed<32> : rans_encode_packed<16>;
+    e = cudaFuncSetAttribute(packed ? kp : rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_e);
     if (e != cudaSuccess) return e;
     {
         ProfScope ps("rans_encode", st);
         if (packed) {
-            const uint32_t per_cta = kRansEncWarps * kEpkSegs;
-            rans_encode_packed<<<(2 * n + per_cta - 1) / per_cta, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
+            const uint32_t per_cta = kRansEncWarps * segs;
+            kp<<<(2 * n + per_cta - 1) / per_cta, kRansEncWarps * 32, smem_e, st>>>(G, SC, n, freq);
         } else {
             rans_encode_kernel<<<(2 * n + kRansEncWarps - 1) / kRansEncWarps, kRansEncWarps * 32, smem_e, st>>>(
                 G, SC, n, freq);
