@@ -114,3 +114,34 @@ def test_large_mixed_batch_split_by_lod_equals_oracle_and_small_batches():
     torch.cuda.synchronize()
     assert (status2.cpu().numpy() == 0).all()
     assert np.array_equal(out2.cpu().numpy().view(np.uint32), got)
+
+
+@pytest.mark.parametrize("mix", ["all_lod1", "coarse_and_few_fine", "all_lod0"])
+def test_large_batch_split_with_empty_classes(mix):
+    """Large batches whose LOD classes are lopsided or empty (the per-class rebuild kernels find nothing to
+    do, or all of it) give the oracle's labels and statuses."""
+    import torch
+    import paper_2308_16619_b300 as csgv
+    vol = synth.voronoi((128, 128, 128), 120, seed=23, warp_amp=2, bg_permille=200)
+    V = O.encode_volume(vol, 5, stride=1)
+    gv = csgv.csgv_volume_import(5, V.dims, V.K_max, V.S_min, V.freq, V.pal_off, V.pal, V.int_off, V.int_words,
+                                 V.leaf_off, V.leaf_words, V.n_int_sym, V.n_leaf_sym)
+    rng = np.random.default_rng(24)
+    n = 8500
+    ids = rng.integers(0, V.n_bricks, size=n).astype(np.uint32)
+    if mix == "all_lod1":
+        lods = np.ones(n, np.uint8)
+    elif mix == "all_lod0":
+        lods = np.zeros(n, np.uint8)
+    else:
+        lods = rng.integers(2, 6, size=n).astype(np.uint8)
+        lods[rng.choice(n, size=5, replace=False)] = 0
+    offs, total = csgv.request_layout(32, lods)
+    out = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    status = torch.full((n,), -99, dtype=torch.int32, device="cuda")
+    csgv.csgv_decode_bricks(gv, torch.from_numpy(ids.view(np.int32)).cuda(), torch.from_numpy(lods).cuda(), out,
+                            torch.from_numpy(np.asarray(offs, np.int64)).cuda(), status)
+    ref, _, rst = O.decode_bricks(V, ids, lods)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all() and (rst == 0).all()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
