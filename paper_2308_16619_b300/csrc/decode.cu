@@ -954,11 +954,12 @@ __global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev 
     if (threadIdx.x == 0) status[i] = st;
 }
 
-// Large mixed-LOD batches of 32^3 bricks: split_lods lists the requests at LOD 0..1 (fine) and at LOD >= 2
-// (coarse); rebuild_listed runs the fine ones as rebuild does, rebuild_coarse the coarse ones with 64-thread
-// CTAs and the compact layout, 32 per SM: a coarse request has at most 64 parents per level and a few KB
-// of state, where a 256-thread CTA with the full 51 KB layout kept 4 per SM.  Both grids have one CTA per
-// request of the slice; CTAs past their list's count return at once.
+// Large mixed-LOD batches of 32^3 bricks: split_lods lists the requests by class (LOD 0, LOD 1, LOD >= 2),
+// and one kernel per class rebuilds its list: rebuild_listed as rebuild does; rebuild_medium (LOD 1) with
+// 128-thread CTAs in a layout without L0 (14 KB), 14 per SM; rebuild_coarse (LOD >= 2) with 64-thread CTAs
+// in a layout of levels 2..N (3.4 KB), 32 per SM, since such a request has at most 64 parents per level,
+// where a 256-thread CTA with the full 51 KB layout ran 4 per SM.  The three kernels are persistent (see
+// rebuild_list).
 constexpr uint32_t kRbCoarseThreads = 64;
 constexpr uint32_t kRbMediumThreads = 128;
 constexpr uint32_t kSplitMin = 8192;  // requests per slice from which the split pays for its extra launches
