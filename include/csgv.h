@@ -83,8 +83,8 @@ typedef struct {
 CSGV_API const char *csgv_last_error(void);
 
 /*
- * Frequency prepass (Sec. 3.3 and 3.4: "a quick prepass over a subset of
- * bricks ... to determine the two frequency tables").  Runs the brick
+ * Frequency prepass (Sec. 3.3 and 3.4: the two frequency tables come from
+ * the nibbles of a sample of the bricks, encoded beforehand).  Runs the brick
  * encoder in count-only mode over every brick whose id is a multiple of
  * sample_stride, counts interior and leaf nibbles, and normalises each
  * table to 4096 (f = 1 + floor(c * 4080 / total), remainder to the largest
@@ -133,12 +133,14 @@ CSGV_API int csgv_encode_bricks_sampled(const uint32_t *vol_dev, const uint64_t 
                                         csgv_volume **out, void *stream);
 
 /*
- * Batched decoding (Alg. 1, Sec. 4.1: "the decompression is executed in
- * parallel for all required bricks").  Request r decodes brick
- * brick_ids_dev[r] to level of detail lods_dev[r] (0 = full resolution,
- * N = the single root label) into out_dev + out_offsets_dev[r]:
- * (b >> lod)^3 labels, x fastest.  One persistent launch; warps take
- * requests from a work counter.  status_dev[r] receives CSGV_OK,
+ * Batched decoding (Alg. 1, Sec. 4.1: all the bricks a frame needs, each at
+ * its own level of detail, decoded on the GPU at once).  Request r decodes
+ * brick brick_ids_dev[r] to level of detail lods_dev[r] (0 = full
+ * resolution, N = the single root label) into out_dev + out_offsets_dev[r]:
+ * (b >> lod)^3 labels, x fastest.  Per slice of requests (sized by the
+ * workspace): a persistent rANS kernel whose warps take streams from a work
+ * counter, then the reconstruction, one CTA per request (large mixed-LOD
+ * slices: one persistent kernel per LOD class).  status_dev[r] receives CSGV_OK,
  * CSGV_ERR_CORRUPT or CSGV_ERR_RANGE.  All request arrays are device arrays
  * of n entries owned by the caller.  Asynchronous; the return value covers
  * argument and launch errors only.

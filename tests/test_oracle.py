@@ -164,7 +164,7 @@ def test_noise_bricks_palette_duplicates_and_deltas():
 
 
 def test_homogeneous_brick_is_single_palette_entry():
-    # "completely homogeneous bricks represented as a single P_a entry" (Sec. 5 CR histogram): one label, no ops
+    # Sec. 5 (CR histogram): a brick of one label costs one palette entry and no ops
     for b in (2, 4, 8, 16, 32):
         brick = np.full((b, b, b), 0xDEADBEEF, np.uint32)
         pal, ni, nl = O.encode_brick(brick)
@@ -382,7 +382,7 @@ def test_volume_mixed_requests_and_duplicates():
 
 
 def test_subsampled_prepass_barely_changes_cr():
-    # "CRs only varied very subtly when increasing or decreasing the subsampling" (Sec. 5)
+    # Sec. 5: the compression ratio hardly changes with the prepass sampling stride
     import synth
     vol = synth.voronoi((128, 128, 128), 400, seed=21, warp_amp=4, bg_permille=300)
     full = O.encode_volume(vol, 4, stride=1)
