@@ -964,12 +964,22 @@ constexpr uint32_t kRbCoarseThreads = 64;
 constexpr uint32_t kRbMediumThreads = 128;
 constexpr uint32_t kSplitMin = 8192;  // requests per slice from which the split pays for its extra launches
 
+// one atomic per warp and class (a warp's requests of a class take consecutive list entries)
 __global__ void split_lods(RecJob J, uint32_t N, uint32_t *lists, uint32_t *counts) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= J.n) return;
-    const uint32_t t = J.lods[i];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31, lt = lanemask_lt();
+    const bool in = i < J.n;
+    const uint32_t t = in ? (uint32_t)J.lods[i] : 0u;
     const uint32_t c = (t >= 2 && t <= N) ? 2u : t == 1 ? 1u : 0u;
-    lists[c * J.n + atomicAdd(&counts[c], 1u)] = i;
+#pragma unroll
+    for (uint32_t k = 0; k < 3; k++) {
+        const uint32_t m = __ballot_sync(kFull, in && c == k);
+        if (m == 0) continue;
+        const uint32_t leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&counts[k], (uint32_t)__popc(m));
+        base = __shfl_sync(kFull, base, leader);
+        if (in && c == k) lists[k * J.n + base + __popc(m & lt)] = i;
+    }
 }
 
 // One list of the split: persistent CTAs take the list's requests one at a time (a counter per list), so a
