@@ -23,7 +23,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        # CSGV_ORACLE_LIB points the tests at another build of csgv_oracle.c (the planted-mistake
+        # copies of tests/test_oracle_mutants.py); by default the library built from this directory
+        _lib = C.CDLL(os.environ.get("CSGV_ORACLE_LIB") or _build.build())
         u64p = C.POINTER(C.c_uint64)
         _lib.csgvo_pyramid_nodes.restype = C.c_uint64
         _lib.csgvo_pyramid_nodes.argtypes = [C.c_int]

@@ -373,7 +373,11 @@ int csgvo_decode_brick(const uint32_t *palette, uint32_t n_palette,
 /* Sec. 3.3: static frequency tables                                   */
 /* ------------------------------------------------------------------ */
 
-/* Normalise 16 nibble counts to frequencies summing to M = 4096, each >= 1 (R11). */
+/*
+ * Normalise 16 nibble counts to frequencies summing to M = 4096, each >= 1 (R11).
+ * Exact for any counts whose sum fits in 64 bits: the product count * 4080 is
+ * formed in 128 bits before the division.
+ */
 void csgvo_normalize(const uint64_t counts[16], uint32_t freq[16]) {
     uint64_t total = 0;
     for (int s = 0; s < 16; s++) total += counts[s];
@@ -383,8 +387,8 @@ void csgvo_normalize(const uint64_t counts[16], uint32_t freq[16]) {
     }
     uint32_t sum = 0;
     for (int s = 0; s < 16; s++) {
-        /* 128-bit safe: counts * 4080 fits in 64 bits for counts < 4.5e15 */
-        freq[s] = 1u + (uint32_t)((counts[s] * (uint64_t)(RANS_M - 16)) / total);
+        unsigned __int128 scaled = (unsigned __int128)counts[s] * (RANS_M - 16);
+        freq[s] = 1u + (uint32_t)(scaled / total);
         sum += freq[s];
     }
     uint32_t r = RANS_M - sum; /* 0 <= r < 16 */

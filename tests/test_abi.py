@@ -55,7 +55,10 @@ def test_table_from_counts_matches_oracle_normalisation():
         if trial == 0:
             counts[:] = 0
         if trial == 1:
-            counts[:] = np.uint64(2 ** 50)  # within the oracle's stated domain (counts * 4080 < 2^64)
+            counts[:] = np.uint64(2 ** 59)  # count * 4080 needs more than 64 bits on both sides
+        if trial == 2:
+            counts[:16] = 0
+            counts[0], counts[5], counts[15] = 2 ** 63, 2 ** 62, 2 ** 62 - 1  # interior total 2^64 - 1
         t = csgv.csgv_freq_table_from_counts(counts)
         want = np.concatenate([O.normalize(counts[:16]), O.normalize(counts[16:])])
         assert list(t.freq) == want.tolist()

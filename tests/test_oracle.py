@@ -239,6 +239,63 @@ def test_normalize_sums_and_floors():
     assert f[8] == 4096 - 15 and f.sum() == 4096
 
 
+TABLES = os.path.join(os.path.dirname(__file__), "golden", "tables")
+
+
+def _read_golden(path):
+    out = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = line.split(":", 1)
+            out[k.strip()] = [int(x, 0) for x in v.split()]
+    return out
+
+
+@pytest.mark.parametrize("name", ["normalize_tie_at_minimum", "normalize_tied_maxima", "normalize_large_counts"])
+def test_normalize_hand_derived(name):
+    # R11, worked by hand in tests/golden/tables: which symbols take the leftover units, ties to the lower symbol
+    g = _read_golden(os.path.join(TABLES, name + ".txt"))
+    counts = np.array(g["counts"], np.uint64)
+    assert int(counts.sum()) == g["total"][0]
+    floors = [1 + (c * 4080) // g["total"][0] for c in g["counts"]]  # exact Python integers
+    assert 4096 - sum(floors) == g["leftover"][0]
+    assert O.normalize(counts).tolist() == g["freq"]
+
+
+def test_normalize_is_exact_near_the_top_of_the_domain():
+    # counts whose product with 4080 passes 2^64; expected values from the closed form with exact integers
+    c = np.zeros(16, np.uint64)
+    c[0], c[5], c[15] = 2 ** 63, 2 ** 62, 2 ** 62 - 1  # total 2^64 - 1
+    total = 2 ** 63 + 2 ** 62 + 2 ** 62 - 1
+    f = O.normalize(c)
+    assert f.sum() == 4096
+    assert f[0] >= 1 + (2 ** 63 * 4080) // total and f[5] >= 1 + (2 ** 62 * 4080) // total
+    assert f[0] <= 2 + (2 ** 63 * 4080) // total and f[5] <= 2 + (2 ** 62 * 4080) // total
+    assert all(f[s] == 1 for s in range(16) if s not in (0, 5, 15))
+
+
+def test_prepass_counts_the_nibbles_of_bricks_whose_id_is_a_multiple_of_stride():
+    # R12 ("every s-th brick", Sec. 3.4): the prepass histogram equals the sum of the per-brick nibble
+    # histograms of exactly the bricks with id % stride == 0, counted here brick by brick
+    vol = _small_volume(seed=7, shape=(40, 36, 50), n_sites=60)  # 7 x 5 x 5 bricks of 8^3, padded
+    b, N = 8, 3
+    n = 7 * 5 * 5
+    per = []
+    for bid in range(n):
+        _, ni, nl = O.encode_brick(_brick_of(vol, b, bid))
+        per.append((np.bincount(ni, minlength=16), np.bincount(nl, minlength=16)))
+    for stride in (1, 3, 7, 512):
+        ids = [i for i in range(n) if i % stride == 0]
+        want_i = sum(per[i][0] for i in ids)
+        want_l = sum(per[i][1] for i in ids)
+        ci, cl = O.count_nibbles(vol, N, stride=stride, n_threads=3)
+        assert ci.tolist() == want_i.tolist() and cl.tolist() == want_l.tolist(), stride
+    # the histograms of neighbouring offsets differ on this volume, so an offset slip cannot pass
+    other = sum(per[i][1] for i in range(n) if i % 3 == 1)
+    assert other.tolist() != sum(per[i][1] for i in range(n) if i % 3 == 0).tolist()
+
+
 # ---------------------------------------------------------------- rANS (Sec. 3.3, R9, R10)
 
 def _rand_freq(rng):
@@ -294,6 +351,18 @@ def test_rans_code_length_against_entropy():
         CE = -(cnt * np.log2(q)).sum()
         assert bits + 32 * K >= n * H * (1 - 1e-3)
         assert bits <= CE + 0.005 * n + 48 * K
+
+
+def test_rans_hand_derived_stream():
+    # R9/R10 worked by hand (tests/golden/tables/rans_uniform_k2.txt): lane i mod K, final states low half
+    # first and state 0 first, renormalisation words in decode order
+    g = _read_golden(os.path.join(TABLES, "rans_uniform_k2.txt"))
+    sym = np.array(g["symbols"], np.uint8)
+    f = np.array(g["freq"], np.uint32)
+    w = O.rans_encode(sym, g["K"][0], f)
+    assert w.tolist() == g["words"]
+    dec, rc = O.rans_decode(np.array(g["words"], np.uint16), len(sym), g["K"][0], f)
+    assert rc == 0 and dec.tolist() == g["symbols"]
 
 
 def test_rans_detects_wrong_final_state():
