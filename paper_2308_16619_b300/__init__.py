@@ -268,6 +268,19 @@ def csgv_encode_bricks_noalloc(vol, b, table, pal_off, pal, int_off, int_words, 
     labels, interior words and leaf words.
     """
     assert vol.is_cuda and vol.element_size() == 4 and vol.is_contiguous()
+    # the library cannot see the lengths of the offset and count arrays: check them here, so that a short
+    # array is an error and not a device write past its end
+    n = 1
+    for d in _dims3(vol):
+        n *= (d + b - 1) // b
+    for name, t, elem, need in (("pal_off", pal_off, 8, n + 1), ("int_off", int_off, 8, n + 1),
+                                ("leaf_off", leaf_off, 8, n + 1), ("n_int_sym", n_int_sym, 4, n),
+                                ("n_leaf_sym", n_leaf_sym, 4, n), ("pal", pal, 4, 1), ("int_words", int_words, 2, 1),
+                                ("leaf_words", leaf_words, 2, 1)):
+        if not (t.is_cuda and t.is_contiguous() and t.element_size() == elem):
+            raise ValueError(f"{name}: a contiguous CUDA tensor of {elem}-byte elements is needed")
+        if t.numel() < need:
+            raise ValueError(f"{name}: {t.numel()} elements, {need} needed for {n} bricks")
     cfg = Config(K_max, S_min)
     totals = (C.c_uint64 * 3)()
     rc = lib().csgv_encode_bricks_noalloc(_ptr(vol), _dims3(vol), b, C.byref(table), C.byref(cfg), _ptr(pal_off),

@@ -123,15 +123,23 @@ int csgv_encode_bricks_noalloc(const uint32_t *vol_dev, const uint64_t dims[3], 
     if (K_max < 1 || K_max > 32 || S_min < 1) return err(CSGV_ERR_INVALID_ARG, "K_max must be 1..32, S_min >= 1");
     csgv::EncVol EV;
     EV.vol = vol_dev;
+    const csgv::EncGeom G = csgv::make_geom(N, K_max, S_min);
+    const size_t cmax = max_bricks(G);
     uint64_t n = 1;
+    bool wrapped = false;
     for (int a = 0; a < 3; a++) {
         if (dims[a] == 0 || dims[a] > (1ull << 31)) return err(CSGV_ERR_INVALID_ARG, "bad dimension");
         EV.dims[a] = dims[a];
         EV.nb[a] = (dims[a] + b - 1) / b;
-        n *= EV.nb[a];
+        wrapped |= __builtin_mul_overflow(n, EV.nb[a], &n);  // up to 2^90 bricks: must not wrap to a small n
     }
-    const csgv::EncGeom G = csgv::make_geom(N, K_max, S_min);
-    const size_t cmax = max_bricks(G);
+    if (wrapped) {
+        snprintf(msg, sizeof msg,
+                 "volume has %llu x %llu x %llu bricks of %u^3; the allocation-free encoder's %zu MiB scratch holds "
+                 "at most %zu", (unsigned long long)EV.nb[0], (unsigned long long)EV.nb[1],
+                 (unsigned long long)EV.nb[2], b, kNoAllocScratchBytes >> 20, cmax);
+        return err(CSGV_ERR_INVALID_ARG, msg);
+    }
     if (n > cmax) {
         snprintf(msg, sizeof msg,
                  "volume has %llu bricks of %u^3; the allocation-free encoder's %zu MiB scratch holds at most %zu",

@@ -63,3 +63,20 @@ def test_table_from_counts_matches_oracle_normalisation():
         want = np.concatenate([O.normalize(counts[:16]), O.normalize(counts[16:])])
         assert list(t.freq) == want.tolist()
         assert list(t.counts) == counts.tolist()
+
+
+def test_noalloc_encoder_rejects_a_brick_count_that_would_wrap_without_gpu():
+    # 2^30 x 2^30 x 16 bricks of 2^3 is 2^64: a 64-bit product wraps to 0; the call must refuse it on the
+    # host, before any CUDA call (the pointers are never dereferenced)
+    L = csgv.lib()
+    t = csgv.FreqTable()
+    for i in range(32):
+        t.freq[i] = 256
+    dims = (ctypes.c_uint64 * 3)(2 ** 31, 2 ** 31, 32)
+    totals = (ctypes.c_uint64 * 3)()
+    p = ctypes.c_void_p(256)
+    rc = L.csgv_encode_bricks_noalloc(p, dims, 2, ctypes.byref(t), None, p, p, 1, p, p, 1, p, p, 1, p, p, totals,
+                                      None)
+    assert rc == csgv.CSGV_ERR_INVALID_ARG
+    msg = L.csgv_last_error()
+    assert b"bricks of 2^3" in msg and b"at most" in msg, msg

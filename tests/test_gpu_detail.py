@@ -1,9 +1,11 @@
 """Detail separation (Sec. 4.2): the leaf streams live in mapped host memory and decoding reads them in
-place.  Every LOD must decode to the same bytes as with all data on the device (integer data, tolerance
-zero), coarse LODs must not need the leaf data, and moving the leaves back must restore the volume."""
+place.  Every LOD must decode to the oracle's labels and to the same bytes as with all data on the device
+(integer data, tolerance zero), coarse LODs must not need the leaf data, and moving the leaves back must
+restore the volume."""
 import numpy as np
 import pytest
 
+import oracle as O
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -33,9 +35,14 @@ def test_leaves_in_host_memory_decode_every_lod_exactly():
     lods = torch.from_numpy(lods_h).cuda()
     offs = torch.from_numpy(offs_h).cuda()
     ref = decode_all(csgv, torch, v, ids, lods, offs, total)
+    want, want_off, st = O.decode_bricks(O.encode_volume(vol, 5, stride=1), ids_h, lods_h)
+    assert (st == 0).all() and np.array_equal(want_off.astype(np.int64), offs_h)
+    assert np.array_equal(ref.view(np.uint32), want[:total])
     before = v.export()
     v.leaves_to_host()
-    assert np.array_equal(decode_all(csgv, torch, v, ids, lods, offs, total), ref)
+    host = decode_all(csgv, torch, v, ids, lods, offs, total)
+    assert np.array_equal(host.view(np.uint32), want[:total])  # leaves read over the host link: the oracle's labels
+    assert np.array_equal(host, ref)
     assert np.array_equal(v.export()["leaf_words"], before["leaf_words"])
     v.leaves_to_device()
     assert np.array_equal(decode_all(csgv, torch, v, ids, lods, offs, total), ref)

@@ -1,12 +1,13 @@
 """The decode server (csgv_serve_*): continuous batching over a device cache of decoded bricks.
 
-Every served result must equal the same request decoded alone by csgv_decode_bricks (bit-exact),
-whatever else was in flight; the cache must hit on repeats, evict least recently used entries when
+Every served result must equal the oracle's decode of the same request and the same request decoded
+alone by csgv_decode_bricks (bit-exact), whatever else was in flight; the cache must hit on repeats, evict least recently used entries when
 full, and hold back requests (admission by free memory) until releases free space.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -20,6 +21,7 @@ def served_volume():
     d = torch.from_numpy(vol.view(np.int32)).cuda()
     t = csgv.csgv_build_freq_table(d, 32, 1)
     v = csgv.csgv_encode_bricks(d, 32, t)
+    v.oracle = O.encode_volume(vol, 5, stride=1)  # the CPU oracle's encoding of the same volume
     yield v
     v.close()
 
@@ -39,10 +41,15 @@ def decode_alone(v, brick, lod):
 
 
 def check_results(srv, v, bricks, lods, res):
-    import torch
-    for br, lod, r in zip(bricks, lods, res):
+    bricks = np.asarray(bricks, np.uint32)
+    lods = np.asarray(lods, np.uint8)
+    want, off, st = O.decode_bricks(v.oracle, bricks, lods)
+    assert (st == 0).all()
+    for k, (br, lod, r) in enumerate(zip(bricks, lods, res)):
         assert r.status == 0 and r.brick == br and r.lod == lod
-        got = srv.labels(r, 32).cpu().numpy()
+        got = srv.labels(r, 32).cpu().numpy().view(np.uint32)
+        B3 = (32 >> int(lod)) ** 3
+        assert np.array_equal(got, want[int(off[k]):int(off[k]) + B3])
         assert np.array_equal(got, decode_alone(v, int(br), int(lod)))
 
 

@@ -18,15 +18,18 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_encoder_matches_allocating_encoder_on_two_calls():
+@pytest.mark.parametrize("b", [32, 64, 16, 8])
+def test_noalloc_encoder_matches_allocating_encoder_on_two_calls(b):
+    # 128^3: 64 bricks of 32^3, 8 of 64^3 (the level arrays carved from the scratch too), 512 of 16^3 and
+    # 4096 of 8^3, each within the scratch's limit for its brick size
     import torch
     import synth
     import paper_2308_16619_b300 as csgv
 
-    vol = synth.make("voronoi128")  # 128^3, 64 bricks of 32^3
+    vol = synth.make("voronoi128")
     d = torch.from_numpy(vol.view(np.int32)).cuda()
-    table = csgv.csgv_build_freq_table(d, 32, 1)
-    ref_vol = csgv.csgv_encode_bricks(d, 32, table)
+    table = csgv.csgv_build_freq_table(d, b, 1)
+    ref_vol = csgv.csgv_encode_bricks(d, b, table)
     ref = ref_vol.export()
     n = len(ref["n_int_sym"])
 
@@ -42,7 +45,7 @@ def test_noalloc_encoder_matches_allocating_encoder_on_two_calls():
         for t in dev.values():
             t.fill_(-1)  # stale contents must not leak into the result
         torch.cuda.synchronize()
-        rc, totals = csgv.csgv_encode_bricks_noalloc(d, 32, table, dev["pal_off"], dev["pal"], dev["int_off"],
+        rc, totals = csgv.csgv_encode_bricks_noalloc(d, b, table, dev["pal_off"], dev["pal"], dev["int_off"],
                                                      dev["int_words"], dev["leaf_off"], dev["leaf_words"],
                                                      dev["n_int_sym"], dev["n_leaf_sym"])
         torch.cuda.synchronize()
@@ -68,10 +71,10 @@ def test_noalloc_encoder_rejects_volumes_beyond_its_scratch():
     table = csgv.FreqTable()
     for i in range(32):
         table.freq[i] = 256
-    small = torch.empty(16, dtype=torch.int64, device="cuda")
-    rc, _ = csgv.csgv_encode_bricks_noalloc(big, 32, table, small, small.view(torch.int32), small,
-                                            small.view(torch.int16), small, small.view(torch.int16),
-                                            small.view(torch.int32), small.view(torch.int32))
+    off = torch.empty(97, dtype=torch.int64, device="cuda")
+    small = torch.empty(96, dtype=torch.int32, device="cuda")
+    rc, _ = csgv.csgv_encode_bricks_noalloc(big, 32, table, off, small, off.clone(), small.view(torch.int16),
+                                            off.clone(), small.view(torch.int16), small.clone(), small.clone())
     assert rc == csgv.CSGV_ERR_INVALID_ARG
     msg = csgv.lib().csgv_last_error().decode()
     assert "96 bricks" in msg and "at most 81" in msg
