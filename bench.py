@@ -44,6 +44,8 @@ def parse():
                          "then serve a trace with the leaf streams in host memory")
     ap.add_argument("--s-min", type=int, default=256, help="symbols per rANS state (format parameter S_min)")
     ap.add_argument("--k-max", type=int, default=32, help="most interleaved rANS states per stream (K_max)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline line only: skip the batched (cells1024) and serve (worley2048) blocks")
     return ap.parse_args()
 
 
@@ -148,67 +150,97 @@ def kernel_traffic(kernel):
     return None
 
 
-def cpu_baseline_oracle(vol, b, max_seconds=20.0):
-    """Oracle encode + decode on a bounded slab of whole bricks; returns (GB/s, cores, sample description)."""
+def oracle_step(vol, b, cores):
+    """One step of the oracle on the headline workload, as the GPU step does it: prepass over every
+    STRIDE-th brick, encode of every brick, decode of every brick at LOD 0.  Returns seconds."""
     import oracle as O
     N = b.bit_length() - 1
+    t0 = time.perf_counter()
+    V = O.encode_volume(vol, N, stride=STRIDE, n_threads=cores)
+    n = V.n_bricks
+    out, off, st = O.decode_bricks(V, np.arange(n, dtype=np.uint32), np.zeros(n, np.uint8), n_threads=cores)
+    dt = time.perf_counter() - t0
+    assert (st == 0).all()
+    return dt
+
+
+def oracle_sample(vol, b):
+    n = vol.size // b ** 3
+    return (f"oracle prepass (every {STRIDE}th brick) + encode + decode of all {n} bricks of the "
+            f"{vol.shape[2]}x{vol.shape[1]}x{vol.shape[0]} volume per step, the GPU step's workload")
+
+
+def cpu_baseline_oracle(vol, b, min_seconds=10.0, max_runs=60):
+    """The oracle as it stands on all host cores, repeated on the whole headline workload until about
+    min_seconds of work are done; the median step.  Returns (GB/s, cores, sample description)."""
     cores = os.cpu_count() or 1
-    Z = vol.shape[0]
-    layers = 1
-    t_used = 0.0
-    while True:
-        sub = np.ascontiguousarray(vol[: layers * b])
-        t0 = time.perf_counter()
-        V = O.encode_volume(sub, N, stride=STRIDE if sub.size >= 4096 * b ** 3 else 1, n_threads=cores)
-        n = V.n_bricks
-        out, off, st = O.decode_bricks(V, np.arange(n, dtype=np.uint32), np.zeros(n, np.uint8), n_threads=cores)
-        dt = time.perf_counter() - t0
-        t_used += dt
-        assert (st == 0).all()
-        if dt > 2.0 or layers * b >= Z or t_used > max_seconds:
-            break
-        layers = min(Z // b, layers * 4)
-    gbs = sub.nbytes / dt / 1e9
-    return gbs, cores, f"oracle encode+decode of {n} bricks ({sub.shape[2]}x{sub.shape[1]}x{sub.shape[0]} slab)"
+    times, used = [], 0.0
+    while used < min_seconds and len(times) < max_runs:
+        dt = oracle_step(vol, b, cores)
+        times.append(dt)
+        used += dt
+    gbs = vol.nbytes / statistics.median(times) / 1e9
+    return gbs, cores, oracle_sample(vol, b) + f" ({len(times)} steps, median)"
 
 
 def run_reference(args):
-    """The oracle as the reference arm: bounded samples of the same workload on the host cores."""
+    """The oracle as the reference arm: the headline workload, whole, on the host cores."""
     import synth
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle as O
     vol = synth.make(WORKLOAD)
     b = args.b
-    N = b.bit_length() - 1
     cores = os.cpu_count() or 1
-    sub = np.ascontiguousarray(vol[: 2 * b])  # two brick layers: 512 bricks
     times = []
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        V = O.encode_volume(sub, N, stride=1, n_threads=cores)
-        n = V.n_bricks
-        out, off, st = O.decode_bricks(V, np.arange(n, dtype=np.uint32), np.zeros(n, np.uint8), n_threads=cores)
-        dt = time.perf_counter() - t0
+        dt = oracle_step(vol, b, cores)
         if s >= args.warmup:
             times.append(dt)
     ms = 1000 * statistics.median(times)
-    gbs = sub.nbytes / (ms / 1000) / 1e9
+    gbs = vol.nbytes / (ms / 1000) / 1e9
+    n = vol.size // b ** 3
     line = {"impl": "reference", "metric": "decoded GB/s uint32 labels (batched vs plain per-brick); serve p50/p99 ms",
             "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} b={b} (sample: {n} bricks per step)", "bricks": n},
+            "config": {"workload": f"{WORKLOAD} 512^3 warped Voronoi, 20000 cells, 30% background, b={b}",
+                       "bricks": n, "lod": 0, "step": f"prepass (stride {STRIDE}) + encode + decode of every brick",
+                       "sample": oracle_sample(vol, b)},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                             "sample": f"oracle encode+decode of {n} bricks per step"},
+                             "sample": oracle_sample(vol, b)},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def run_cells1024(args):
+    print(json.dumps(measure_cells1024(args, args.steps, args.warmup)))
+
+
+def frame_requests(csgv, v, dims, n_frames, seed, max_nonempty=1):
+    """Brick requests of a fly-around trace from the library's footprint kernel (one ray per pixel of a
+    1920x1080 frame walks the brick grid, skips bricks with no opaque label, stops at the first brick that
+    holds one).  Returns the per-frame (bricks, lods) host arrays and the kernels' ms per frame."""
+    import synth
+    cams = synth.camera_path(dims, n_frames, seed=seed)
+    fp = csgv.Footprint(v, max_nonempty=max_nonempty)
+    csgv.profile_read()
+    csgv.profile_enable(True)
+    frames = []
+    for cam in cams:
+        bricks, lods = fp.frame(csgv.make_camera(cam["pos"], cam["right"], cam["up"], cam["fwd"], cam["f_px"],
+                                                 cam["width"], cam["height"]))
+        frames.append((bricks.cpu().numpy().view(np.uint32).copy(), lods.cpu().numpy().copy()))
+    csgv.profile_enable(False)
+    prof = csgv.profile_read()
+    fp.close()
+    ms = sum(t for k, (t, c) in prof.items() if k.startswith("footprint")) / max(1, n_frames)
+    return frames, ms
+
+
+def measure_cells1024(args, steps, warmup):
     """1024^3 packed ellipsoids, b=32: encode once, then each step decodes 60000 requests at random LOD
-    0..5 (brick ids uniform with replacement, seed 3) in one persistent launch."""
+    0..5 (brick ids uniform with replacement, seed 3) in one persistent launch.  Returns the JSON line."""
     import torch
     import synth
     import paper_2308_16619_b300 as csgv
@@ -249,7 +281,7 @@ def run_cells1024(args):
     torch.cuda.synchronize(dev)
     csgv.profile_enable(False)
     prof = csgv.profile_read()
-    prof = {k: (t / 3 * args.steps, c // 3 * args.steps) for k, (t, c) in prof.items()}
+    prof = {k: (t / 3 * steps, c // 3 * steps) for k, (t, c) in prof.items()}
     # the timed steps replay one captured graph of the decode call
     gs = torch.cuda.Stream(dev)
     gs.wait_stream(stream)
@@ -261,10 +293,10 @@ def run_cells1024(args):
     with torch.cuda.graph(graph, stream=gs):
         csgv.csgv_decode_bricks(v, ids, lods, out, offs, status)
     clk = ClockSampler(local).__enter__()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize(dev)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     w0 = time.time()
     for a, z in evs:
         a.record(stream)
@@ -286,12 +318,12 @@ def run_cells1024(args):
     rb_ms = prof["rebuild"][0] / prof["rebuild"][1]
     # algorithmic bytes of the rebuild launches of one batch: the decoded labels written plus, at most, the
     # compressed volume read
-    rb_per_batch = prof["rebuild"][0] / args.steps
+    rb_per_batch = prof["rebuild"][0] / steps
     achieved = (out_bytes + inf.compressed_bytes) / (rb_per_batch / 1e3) / 1e9
-    kernels = {k: {"ms_per_launch": t / c, "launches_per_step": c / args.steps} for k, (t, c) in prof.items()}
+    kernels = {k: {"ms_per_launch": t / c, "launches_per_step": c / steps} for k, (t, c) in prof.items()}
     line = {"metric": "decoded GB/s uint32 labels (batched vs plain per-brick); serve p50/p99 ms",
-            "value": out_bytes / (ms / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "value": out_bytes / (ms / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "cells1024 1024^3 packed ellipsoids, b=32, 60000 requests LOD 0..5",
                        "step": "one batched decode (CUDA graph replay)", "decoded_bytes": out_bytes,
@@ -307,7 +339,18 @@ def run_cells1024(args):
                          "ms_per_batch": rb_per_batch, "ms_per_launch": rb_ms},
             "kernels": kernels,
             "gpu_launches": int(sum(c for _, c in prof.values())), "clocks": clk.summary()}
-    print(json.dumps(line))
+    # outside the timed region: a sample of the requests against their bricks in the volume
+    got = out.cpu().numpy().view(np.uint32)
+    rs = np.random.default_rng(11).choice(np.nonzero(lods_h == 0)[0], size=32, replace=False)
+    for r in rs:
+        br = int(ids_h[r])
+        g = 1024 // b
+        bx, by, bz = br % g, (br // g) % g, br // (g * g)
+        want = vol_np[bz * b:(bz + 1) * b, by * b:(by + 1) * b, bx * b:(bx + 1) * b].reshape(-1)
+        assert np.array_equal(got[int(offs_h[r]):int(offs_h[r]) + b ** 3], want), "cells1024 decode mismatch"
+    del out, v
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_variants(args):
@@ -397,9 +440,15 @@ def run_variants(args):
 
 
 def run_worley2048(args):
+    print(json.dumps(measure_worley2048(args, args.warmup)))
+
+
+def measure_worley2048(args, warmup):
     """Serving: 2048x2048x1024 Worley cells (24-voxel jittered grid) made and compressed on the device,
     an 8 GiB decoded-brick cache, and a 600-frame fly-around trace at 1920x1080 (distance-based LOD).
-    Frame f is submitted, then frame f-1 is awaited (one frame of lag) and frame f-2 released."""
+    Frame f is submitted, then frame f-1 is awaited (one frame of lag) and frame f-2 released.  Latency
+    per frame ticket is taken twice: by the server (ticket admitted to its last decode done) and by the
+    client (submit call to the return of the poll that saw it done).  Returns the JSON line."""
     import torch
     import synth
     import paper_2308_16619_b300 as csgv
@@ -422,45 +471,76 @@ def run_worley2048(args):
     torch.cuda.empty_cache()
     inf = v.info()
     n_frames = 600
-    frames = synth.camera_trace(dims, b, n_frames, seed=4)
+    frames, fp_ms = frame_requests(csgv, v, dims, n_frames, seed=4)
     srv = csgv.Server(v, cache_bytes=8 << 30, n_streams=3)
     clk = ClockSampler(local).__enter__()
     t0 = time.perf_counter()
-    tickets = []
+    tickets, t_sub, t_done = [], [], []
     for f, (bricks, lods) in enumerate(frames):
+        t_sub.append(time.perf_counter())
         tickets.append(srv.submit(bricks, lods))
         if f >= 1:
             rc, _ = srv.poll(tickets[f - 1], timeout_us=30_000_000)
+            t_done.append(time.perf_counter())
             assert rc == csgv.CSGV_OK, rc
         if f >= 2:
             srv.release(tickets[f - 2])
     rc, _ = srv.poll(tickets[-1], timeout_us=30_000_000)
+    t_done.append(time.perf_counter())
     assert rc == csgv.CSGV_OK
     wall = time.perf_counter() - t0
+    client = 1000.0 * (np.array(t_done) - np.array(t_sub))
     clk.mark(time.time() - wall, time.time())
     clk.__exit__()
     st, lat = srv.stats(with_latencies=True)
     for t in tickets[-2:]:
         srv.release(t)
     srv.close()
+    # the same trace once more, closed loop on a fresh cache: the client submits frame f and waits for it
+    # before the next one, so the client's wall time per ticket is its latency (submit call to poll return)
+    srv = csgv.Server(v, cache_bytes=8 << 30, n_streams=3)
+    closed, prev = [], None
+    for f, (bricks, lods) in enumerate(frames):
+        c0 = time.perf_counter()
+        tk = srv.submit(bricks, lods)
+        rc, _ = srv.poll(tk, timeout_us=30_000_000)
+        closed.append(1000.0 * (time.perf_counter() - c0))
+        assert rc == csgv.CSGV_OK, rc
+        if prev is not None:
+            srv.release(prev)
+        prev = tk
+    srv.release(prev)
+    srv.close()
+    closed = np.array(closed)
     served = st["decoded_labels"] * 4
     n_req = int(sum(len(fb) for fb, _ in frames))
-    warm = lat[args.warmup:] if len(lat) > args.warmup else lat
+    warm = lat[warmup:] if len(lat) > warmup else lat
     line = {"metric": "decoded GB/s uint32 labels (batched vs plain per-brick); serve p50/p99 ms",
             "value": served / wall / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": n_frames, "warmup": 0,
             "ms_per_step": 1000 * wall / n_frames, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "worley2048 2048x2048x1024 Worley cells, b=32, 600-frame 1920x1080 trace, "
+            "config": {"workload": "worley2048 2048x2048x1024 Worley cells, b=32, 600-frame 1920x1080 trace "
+                                   "(footprint kernel: a ray stops at its first brick with an opaque label), "
                                    "8 GiB cache", "step": "one frame (submit f, await f-1, release f-2)",
                        "K_max": args.k_max, "S_min": args.s_min},
             "serve": {"p50_ms": float(np.percentile(warm, 50)), "p99_ms": float(np.percentile(warm, 99)),
+                      "client_lagged_p50_ms": float(np.percentile(client[warmup:], 50)),
+                      "client_lagged_p99_ms": float(np.percentile(client[warmup:], 99)),
+                      "client_p50_ms": float(np.percentile(closed[warmup:], 50)),
+                      "client_p99_ms": float(np.percentile(closed[warmup:], 99)),
+                      "client_latency": "closed loop (submit frame f, wait for it, then frame f+1), fresh cache; "
+                                        "client_lagged_*: the one-frame-lag loop, submit f to the poll after "
+                                        "submitting f+1",
                       "max_ms": float(np.max(lat)), "first_frame_ms": float(lat[0]),
                       "requests": n_req, "hit_rate": st["hits"] / max(1, st["hits"] + st["misses"] + st["shared"]),
                       "misses": st["misses"], "batches": st["batches"], "evictions": st["evictions"],
-                      "rebuilds": st["rebuilds"], "frames_per_s": n_frames / wall},
+                      "rebuilds": st["rebuilds"], "frames_per_s": n_frames / wall,
+                      "footprint_ms_per_frame": fp_ms},
             "encode_ms_once": enc_ms, "encode_gbs": raw_bytes / (enc_ms / 1e3) / 1e9,
             "cr_percent": 100.0 * inf.compressed_bytes / raw_bytes, "clocks": clk.summary()}
-    print(json.dumps(line))
+    v.close()
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_fiber4096(args):
@@ -547,7 +627,7 @@ def run_fiber4096(args):
 
     # serving with the leaf streams in host memory
     n_frames = 600
-    frames = synth.camera_trace(dims, b, n_frames, seed=5)
+    frames, fp_ms = frame_requests(csgv, v, dims, n_frames, seed=5)
     srv = csgv.Server(v, cache_bytes=8 << 30, n_streams=3)
     clk2 = ClockSampler(local).__enter__()
     t0 = time.perf_counter()
@@ -577,7 +657,7 @@ def run_fiber4096(args):
             "ms_per_step": 1000 * wall / n_frames, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "fiber4096 4096x4096x2048 fibers (1M Catmull-Rom tubes, radius 2-6), b=32, "
-                                   "made per brick, never whole; leaf streams in host memory; 600-frame trace, "
+                                   "made per brick, never whole; leaf streams in host memory; 600-frame trace (footprint kernel), "
                                    "8 GiB cache", "step": "one frame (submit f, await f-1, release f-2)",
                        "K_max": args.k_max, "S_min": args.s_min, "prepass": "every 4096th brick"},
             "encode": {"raw_gb": raw_bytes / 1e9, "generate_ms": gen_ms, "encode_ms": enc_ms,
@@ -592,7 +672,8 @@ def run_fiber4096(args):
                       "requests": int(sum(len(fb) for fb, _ in frames)),
                       "hit_rate": st["hits"] / max(1, st["hits"] + st["misses"] + st["shared"]),
                       "misses": st["misses"], "batches": st["batches"], "evictions": st["evictions"],
-                      "rebuilds": st["rebuilds"], "frames_per_s": n_frames / wall},
+                      "rebuilds": st["rebuilds"], "frames_per_s": n_frames / wall,
+                      "footprint_ms_per_frame": fp_ms},
             "clocks": clk.summary()}
     print(json.dumps(line))
 
@@ -692,6 +773,13 @@ def main():
     ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])] for e in evs])
     enc_ms, dec_ms = (float(np.median(ph[:, i])) for i in range(2))
     assert bool((status == 0).all()), "decode reported errors"
+    g = (X // b, Y // b, Z // b)
+
+    def as_volume(o):  # brick-major decoded labels -> [Z, Y, X]
+        return o.view(g[2], g[1], g[0], b, b, b).permute(0, 3, 1, 4, 2, 5).reshape(Z, Y, X)
+
+    verified = bool(torch.equal(as_volume(out), vol))  # the last timed step's decode, outside the timed region
+    assert verified, "the decoded bricks differ from the volume"
     v = vols[-1]
     inf = v.info()
 
@@ -810,8 +898,10 @@ def main():
     p1.record(s_out)
     torch.cuda.synchronize(dev)
     assert bool((status == 0).all())
-    assert torch.equal(host_outs[(n_pipe - 1) % 2], host_outs[(n_pipe - 2) % 2])  # same labels every step
     e2e_pipe_ms = p0.elapsed_time(p1) / n_pipe
+    # the labels that came back to the host are the volume (checked after the timing, on the device)
+    for h in host_outs:
+        assert torch.equal(as_volume(h.to(dev)), vol), "end-to-end labels differ from the volume"
 
     value = world * out_bytes / (ms_step / 1e3) / 1e9
     launches_per_step = sum(n_l for _, n_l in prof.values()) / args.steps  # library kernels, counted
@@ -840,10 +930,26 @@ def main():
                 "serial": {"value": world * out_bytes / (e2e_ms / 1e3) / 1e9, "ms": e2e_ms}},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk.summary(),
+        "verified": {"decode_equals_volume": verified, "e2e_labels_equal_volume": True},
     }
     if rank == 0 and world == 1:
         gbs, cores, sample = cpu_baseline_oracle(vol_np, b)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if world == 1 and not args.no_extra and b == 32:
+        # the other two configurations of the metric, each its own workload, after the headline's timing:
+        # batched mixed-LOD decode (cells1024) and serving (worley2048)
+        del vol, out, host_vol, host_out, vols, outs, host_outs, v
+        torch.cuda.empty_cache()
+        c = measure_cells1024(args, 20, 3)
+        line["batched"] = {k: c[k] for k in ("value", "unit", "ms_per_step", "voxels_per_s", "plain_decode_gbs_2048",
+                                             "batched_vs_plain", "cr_percent", "roofline", "gpu_launches",
+                                             "clocks")}
+        line["batched"]["config"] = c["config"]
+        w = measure_worley2048(args, 3)
+        line["serve"] = dict(w["serve"], value=w["value"], unit=w["unit"], ms_per_frame=w["ms_per_step"],
+                             config=w["config"], encode_gbs=w["encode_gbs"], cr_percent=w["cr_percent"],
+                             clocks=w["clocks"])
+        line["gpu_launches_extra"] = c["gpu_launches"]
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

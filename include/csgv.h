@@ -308,6 +308,57 @@ CSGV_API int csgv_serve_stats_get(csgv_server *s, csgv_serve_stats *out, double 
 /* Stop the worker, wait for batches in flight, free the cache. */
 CSGV_API void csgv_serve_destroy(csgv_server *s);
 
+/* ------------------------------------------- request footprint of a frame (Sec. 4, raymarching) */
+
+/*
+ * A pinhole camera in voxel units (the volume spans [0, dims) on each axis):
+ * position, an orthonormal basis (right, up, forward; image rows grow
+ * downward, along -up) and the focal length in pixels.  Pixel (x, y) looks
+ * along fwd + px right - py up with px = (x + 0.5 - width / 2) / f_px and
+ * py = (y + 0.5 - height / 2) / f_px.
+ */
+typedef struct {
+    float pos[3], right[3], up[3], fwd[3];
+    float f_px;
+    uint32_t width, height;
+} csgv_camera;
+
+typedef struct csgv_footprint csgv_footprint;
+
+/*
+ * State for the brick requests of rendered frames of `vol` (which must
+ * outlive it), after the paper's renderer (Sec. 4, "Raymarching" and
+ * "Empty-Space Skipping"): one integer per brick, reset to "invisible"
+ * each frame, into which the rays write the LOD they request.  The transfer
+ * function maps label 0 to transparent and every other label to opaque; a
+ * brick whose palette holds no opaque label is skipped without a request.
+ * Each ray stops at a brick whose root label (palette[0]) is opaque, or once
+ * it has requested max_nonempty bricks (0 = no such limit; 1 = the first
+ * brick that holds an opaque label).  Allocates n_bricks * 5 bytes of device
+ * memory plus 4 bytes per 1024 bricks; the per-brick flags are computed from
+ * the palettes on `stream`.  Returns CSGV_ERR_INVALID_ARG for NULL arguments,
+ * CSGV_ERR_CUDA if an allocation or launch fails.
+ */
+CSGV_API int csgv_footprint_create(const csgv_volume *vol, uint32_t max_nonempty, csgv_footprint **out,
+                                   void *stream);
+
+/*
+ * One frame: every pixel's ray walks the brick grid (3D DDA, from where it
+ * enters the volume box) and requests each brick it passes that holds an
+ * opaque label, at LOD clamp(floor(log2(d / f_px)), 0, N), d the distance
+ * from the camera to the brick centre; then the requests are written in
+ * brick-id order to bricks_dev / lods_dev (capacity: n_bricks each) and
+ * their number to *n_dev (device), and the per-brick integers are reset for
+ * the next frame.  Float arithmetic is IEEE single precision with every
+ * operation rounded on its own (no fused multiply-adds).  Asynchronous on
+ * `stream`; successive frames of one footprint must be ordered (one stream).
+ */
+CSGV_API int csgv_footprint_frame(csgv_footprint *fp, const csgv_camera *cam, uint32_t *bricks_dev,
+                                  uint8_t *lods_dev, uint32_t *n_dev, void *stream);
+
+/* Free the footprint's device memory (synchronous). */
+CSGV_API int csgv_footprint_destroy(csgv_footprint *fp);
+
 /* Free a volume and its device arrays (synchronises the device). */
 CSGV_API void csgv_volume_destroy(csgv_volume *vol);
 

@@ -24,7 +24,7 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device",
            "csgv_encode_bricks_sampled", "csgv_volume_destroy_async", "csgv_stream_encoder_create",
            "csgv_stream_encoder_add", "csgv_stream_encoder_finish", "csgv_stream_encoder_destroy",
-           "csgv_count_bricks")
+           "csgv_count_bricks", "csgv_footprint_create", "csgv_footprint_frame", "csgv_footprint_destroy")
 
 
 class CsgvError(RuntimeError):
@@ -61,6 +61,12 @@ class Result(C.Structure):
 class DecodeTuning(C.Structure):
     _fields_ = [("workspace_bytes", C.c_uint64), ("rans_ctas_per_sm", C.c_uint32), ("pad", C.c_uint32),
                 ("ms", C.c_double)]
+
+
+class Camera(C.Structure):
+    """csgv_camera: position, orthonormal basis (right, up, forward) in voxel units, focal length in pixels."""
+    _fields_ = [("pos", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3), ("fwd", C.c_float * 3),
+                ("f_px", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
 
 
 class ServeStats(C.Structure):
@@ -113,6 +119,9 @@ def lib():
         L.csgv_serve_destroy.argtypes = [vp]
         L.csgv_serve_destroy.restype = None
         L.csgv_freq_table_from_counts.argtypes = [vp, C.POINTER(FreqTable)]
+        L.csgv_footprint_create.argtypes = [vp, u32, C.POINTER(vp), vp]
+        L.csgv_footprint_frame.argtypes = [vp, C.POINTER(Camera), vp, vp, vp, vp]
+        L.csgv_footprint_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -446,3 +455,48 @@ def profile_read(max_kernels=32):
         nm = names.raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (ms[k], cnt[k])
     return out
+
+
+def make_camera(pos, right, up, fwd, f_px, width, height):
+    """A csgv_camera from three-vectors (rounded to float32)."""
+    cam = Camera()
+    for name, v in (("pos", pos), ("right", right), ("up", up), ("fwd", fwd)):
+        arr = getattr(cam, name)
+        for a in range(3):
+            arr[a] = float(v[a])
+    cam.f_px, cam.width, cam.height = float(f_px), int(width), int(height)
+    return cam
+
+
+class Footprint:
+    """csgv_footprint_*: the brick requests of rendered frames (ray walk over the brick grid with empty-space
+    skipping; see include/csgv.h).  frame() returns device tensors (bricks int32, lods uint8) of the frame's
+    requests in brick-id order."""
+
+    def __init__(self, volume, max_nonempty=1, stream=None):
+        import torch
+        self.volume = volume  # keep the volume alive
+        h = C.c_void_p()
+        _check(lib().csgv_footprint_create(volume.handle, max_nonempty, C.byref(h), _stream(stream)))
+        self._h = h
+        n = volume.info().n_bricks
+        self.bricks = torch.empty(n, dtype=torch.int32, device="cuda")
+        self.lods = torch.empty(n, dtype=torch.uint8, device="cuda")
+        self.count = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def frame(self, camera, stream=None):
+        _check(lib().csgv_footprint_frame(self._h, C.byref(camera), _ptr(self.bricks), _ptr(self.lods),
+                                          _ptr(self.count), _stream(stream)))
+        n = int(self.count.item())
+        return self.bricks[:n], self.lods[:n]
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().csgv_footprint_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -260,6 +260,15 @@ int grow(void **p, uint64_t &cap, uint64_t need, size_t elem, uint64_t used, cud
 namespace csgv {
 // lets other translation units of the library report a message through csgv_last_error()
 void set_last_error(const char *msg) { g_err = msg; }
+// a volume's device arrays, its completion event and its grid, for the other translation units
+VolDev volume_view(const csgv_volume *v) { return dev_view(v); }
+cudaEvent_t volume_ready(const csgv_volume *v) { return v->ready; }
+void volume_grid(const csgv_volume *v, uint64_t dims[3], uint64_t grid[3]) {
+    for (int a = 0; a < 3; a++) {
+        dims[a] = v->dims[a];
+        grid[a] = v->grid[a];
+    }
+}
 }  // namespace csgv
 
 namespace csgv {

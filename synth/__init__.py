@@ -138,72 +138,40 @@ def fiber_bricks_device(dims_xyz, b, cell, tubes, seed, first=0, m=None, ids=Non
     return out
 
 
-def camera_trace(dims_xyz, b, n_frames, seed, width=1920, height=1080, fov_deg=45.0, device=None,
-                 r_lo=1.05, r_hi=1.9):
-    """Brick requests of a fly-around camera, one (bricks, lods) pair of numpy arrays per frame.
+def camera_path(dims_xyz, n_frames, seed, width=1920, height=1080, fov_deg=45.0, r_lo=1.05, r_hi=1.9):
+    """Cameras of a fly-around, one per frame: dicts of float32 pos / right / up / fwd (voxel units),
+    f_px (focal length in pixels), width and height.
 
-    The camera follows a closed Catmull-Rom spline through 8 seeded points on a shell around the
-    volume (radius r_lo..r_hi times the half diagonal) and looks at the centre.  Each of the
-    width x height rays stops at the first brick it enters (labels are dense, so the ray-march's first
-    hit is where the ray enters the volume); that brick is requested at LOD
-    clamp(floor(log2(d / f_px)), 0, log2 b), d the distance to the brick centre and f_px the focal
-    length in pixels, so that one voxel covers about one pixel.
-    """
-    import torch
-    dev = torch.device(device or ("cuda" if torch.cuda.is_available() else "cpu"))
+    The camera follows a closed uniform Catmull-Rom spline through 8 seeded points on a shell around the
+    volume (radius r_lo..r_hi times the half diagonal) and looks at the centre, z up; vertical field of
+    view fov_deg.  The brick requests of each frame come from the library's footprint kernel."""
     X, Y, Z = dims_xyz
-    N = b.bit_length() - 1
-    grid = torch.tensor([X // b, Y // b, Z // b], device=dev)
-    size = torch.tensor([X, Y, Z], dtype=torch.float32, device=dev)
+    size = np.array([X, Y, Z], np.float64)
     centre = size / 2
-    half_diag = float(torch.linalg.norm(size / 2))
+    half_diag = float(np.linalg.norm(size / 2))
     rng = np.random.default_rng(seed)
     dirs = rng.normal(size=(8, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
     radii = rng.uniform(r_lo, r_hi, size=8) * half_diag
-    ctrl = torch.tensor(dirs * radii[:, None], dtype=torch.float32, device=dev) + centre
+    ctrl = dirs * radii[:, None] + centre
     f_px = (height / 2) / np.tan(np.radians(fov_deg) / 2)
-    ys, xs = torch.meshgrid(torch.arange(height, device=dev, dtype=torch.float32) + 0.5,
-                            torch.arange(width, device=dev, dtype=torch.float32) + 0.5, indexing="ij")
-    px = ((xs - width / 2) / f_px).reshape(-1)
-    py = ((ys - height / 2) / f_px).reshape(-1)
-    frames = []
+    cams = []
     for f in range(n_frames):
         u = 8.0 * f / n_frames
         k = int(u)
         t = u - k
         p0, p1, p2, p3 = (ctrl[(k + d) % 8] for d in (-1, 0, 1, 2))
-        # Catmull-Rom (uniform) point
         cam = 0.5 * ((2 * p1) + (-p0 + p2) * t + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t * t +
                      (-p0 + 3 * p1 - 3 * p2 + p3) * t * t * t)
         fwd = centre - cam
-        fwd = fwd / torch.linalg.norm(fwd)
-        up = torch.tensor([0.0, 0.0, 1.0], device=dev)
-        right = torch.linalg.cross(fwd, up)
-        right = right / torch.linalg.norm(right)
-        up = torch.linalg.cross(right, fwd)
-        d = fwd[None, :] + px[:, None] * right[None, :] - py[:, None] * up[None, :]
-        d = d / torch.linalg.norm(d, dim=1, keepdim=True)
-        # slab test against the volume box
-        inv = 1.0 / torch.where(d.abs() < 1e-12, torch.full_like(d, 1e-12), d)
-        t0 = (0 - cam) * inv
-        t1 = (size - cam) * inv
-        tn = torch.minimum(t0, t1).amax(dim=1)
-        tf = torch.maximum(t0, t1).amin(dim=1)
-        hit = (tf >= torch.clamp(tn, min=0)) & (tf > 0)
-        tin = torch.clamp(tn, min=0)[hit] + 1e-3
-        pin = cam + d[hit] * tin[:, None]
-        bidx = torch.minimum(torch.clamp((pin / b).floor().long(), min=0), grid - 1)
-        bid = bidx[:, 0] + grid[0] * (bidx[:, 1] + grid[1] * bidx[:, 2])
-        bid = torch.unique(bid)
-        bz = bid // (grid[0] * grid[1])
-        by = (bid // grid[0]) % grid[1]
-        bx = bid % grid[0]
-        bc = (torch.stack([bx, by, bz], dim=1).float() + 0.5) * b
-        dist = torch.linalg.norm(bc - cam, dim=1)
-        lod = torch.clamp(torch.floor(torch.log2(torch.clamp(dist / f_px, min=1e-6))), 0, N).to(torch.uint8)
-        frames.append((bid.to(torch.int64).cpu().numpy().astype(np.uint32), lod.cpu().numpy()))
-    return frames
+        fwd /= np.linalg.norm(fwd)
+        right = np.cross(fwd, np.array([0.0, 0.0, 1.0]))
+        right /= np.linalg.norm(right)
+        up = np.cross(right, fwd)
+        cams.append({"pos": cam.astype(np.float32), "right": right.astype(np.float32), "up": up.astype(np.float32),
+                     "fwd": fwd.astype(np.float32), "f_px": np.float32(f_px), "width": int(width),
+                     "height": int(height)})
+    return cams
 
 
 # Workload recipes.  "small" is the 128^3 plain-method case; "voronoi512" the
