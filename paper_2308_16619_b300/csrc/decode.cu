@@ -467,6 +467,9 @@ struct RbLayout {
     uint32_t lev, cm, act, mls, misc, pal, total;
     uint32_t lev_shift;          // entries of the levels below the first one held (levels start at lev - shift)
     uint32_t stage, stage_bytes;  // where the interior records and their P_a counts are staged
+    // compact leaf level (rb_layout_leafc): the children of the listed L1 nodes, their list, their -axis
+    // masks, and the rank of every 32 L1 nodes
+    uint32_t e0, act0, mls0, rk;
 };
 // const bytes of level l (1..N-1): one byte per parent (bit c = child c constant), 16-byte aligned levels
 __host__ __device__ __forceinline__ uint32_t cm_off(uint32_t N, uint32_t l) {
@@ -522,6 +525,40 @@ __host__ __device__ constexpr RbLayout rb_layout_part(uint32_t N, uint32_t lmin)
     L.misc = L.mls + ((maxpar + 15u) & ~15u);
     L.pal = L.misc + (((uint32_t)sizeof(RbMisc) + 15u) & ~15u);
     L.total = L.pal + (sizeof(IdxT) == 1 ? 256u * 4u : 0u);
+    return L;
+}
+
+// Layout of the compact leaf level (LOD 0 of a brick, uint8 indices): levels 1..N as in rb_layout_part(N, 1);
+// L0 is not held whole.  Its nodes under a constant L1 node are that node's index (read from L1 when needed);
+// only the 8 children of each non-constant ("listed") L1 node are held, in listed (Morton) order, at most
+// kLeafCap nodes.  They share one region with the staged interior records and the level-1 parent lists, which
+// are dead once level 1 is rebuilt.  A request with more listed L1 nodes (more than 8 kLeafCap leaf records)
+// goes to the full-layout kernel.
+constexpr uint32_t kLeafCap = 1792;
+template <typename IdxT>
+__host__ __device__ constexpr RbLayout rb_layout_leafc(uint32_t N) {
+    uint32_t nodes = 0;
+    for (uint32_t l = 1; l <= N; l++) nodes += 1u << (3 * (N - l));
+    RbLayout L{};
+    L.lev = 0;
+    L.lev_shift = 1u << (3 * N);
+    L.cm = (nodes + 15u) & ~15u;
+    L.misc = L.cm + cm_off(N, 0);
+    L.pal = L.misc + (((uint32_t)sizeof(RbMisc) + 15u) & ~15u);
+    const uint32_t x = L.pal + 256u * 4u;
+    // region x: interior stage, level-1 lists (up to level 1) | L0 children, list, masks, ranks (level 0)
+    L.stage = x;
+    L.stage_bytes = kStageMedium;
+    const uint32_t maxpar1 = 1u << (3 * (N - 2));  // parents of level 1
+    L.act = x + kStageMedium;
+    L.mls = L.act + ((maxpar1 * 2u + 15u) & ~15u);
+    const uint32_t upper_end = L.mls + ((maxpar1 + 15u) & ~15u);
+    L.e0 = x;
+    L.act0 = L.e0 + 8u * kLeafCap;
+    L.mls0 = L.act0 + 2u * kLeafCap;
+    L.rk = L.mls0 + ((kLeafCap + 15u) & ~15u);
+    const uint32_t leaf_end = L.rk + (((1u << (3 * (N - 1))) / 32u) * 2u + 15u & ~15u);
+    L.total = upper_end > leaf_end ? upper_end : leaf_end;
     return L;
 }
 
@@ -815,15 +852,218 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     return ms->bad == 0;
 }
 
+// The leaf level in the compact layout (rb_layout_leafc), the whole CTA; returns false if the records are
+// malformed.  Same decisions as rebuild_level for l = 0, but the children of constant L1 nodes are never
+// written: pass A ranks the non-constant L1 nodes (their constant bits are level 1's cm bytes read as 32-bit
+// words, bit i = node 32w + i) and lists them; pass B gives one thread per listed node j, which decodes its 8
+// records into the 8 children at E[8j] (one 8-byte store); pass C resolves the -axis sentinels, a neighbour
+// under a constant L1 node being that node's index and any other E[8 rank + child].  Arguments as for
+// rebuild_level; sets n_act.
+template <uint32_t kT>
+__device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayout &Ly, uint32_t N, const uint8_t *R,
+                                                     const uint16_t *T8, uint32_t n_left, uint32_t ip0, uint32_t np,
+                                                     uint32_t &n_act) {
+    typedef uint8_t IdxT;
+    typedef RbTraits<IdxT> T;
+    constexpr uint32_t nw = kT / 32;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const IdxT *P = (const IdxT *)(smem + Ly.lev) - Ly.lev_shift + lev_off(N, 1);  // L1
+    const uint32_t *cw = (const uint32_t *)(smem + Ly.cm + cm_off(N, 1));          // constant bits of L1 nodes
+    uint16_t *act = (uint16_t *)(smem + Ly.act0);
+    uint8_t *mm = smem + Ly.mls0;
+    uint16_t *rk = (uint16_t *)(smem + Ly.rk);
+    IdxT *E = (IdxT *)(smem + Ly.e0);
+    RbMisc *ms = (RbMisc *)(smem + Ly.misc);
+    const uint32_t npar = 1u << (3 * (N - 1)), pbits = npar - 1, cbits = 8 * npar - 1;
+    const uint32_t nwords = npar / 32, wpt = (nwords + kT - 1) / kT;  // a contiguous run of words per thread
+    const uint32_t w0 = min(threadIdx.x * wpt, nwords), w1 = min(w0 + wpt, nwords);
+    const uint32_t sent = T::kSent;
+
+    // pass A: rank and list the non-constant L1 nodes
+    uint32_t c = 0;
+    for (uint32_t w = w0; w < w1; w++) c += __popc(~cw[w]);
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += u;
+    }
+    if (lane == 31) ms->wcnt[warp] = incl;
+    __syncthreads();
+    uint32_t wb = 0;
+    n_act = 0;
+#pragma unroll
+    for (uint32_t v = 0; v < nw; v++) {
+        const uint32_t x = ms->wcnt[v];
+        wb += v < warp ? x : 0u;
+        n_act += x;
+    }
+    if (8 * n_act > n_left || n_act > kLeafCap) return false;  // uniform
+    uint32_t run = wb + incl - c;
+    for (uint32_t w = w0; w < w1; w++) {
+        uint32_t nc = ~cw[w];
+        rk[w] = (uint16_t)run;
+        while (nc) {
+            act[run++] = (uint16_t)(32 * w + __ffs(nc) - 1);
+            nc &= nc - 1;
+        }
+    }
+    if (threadIdx.x == 0) ms->bad = 0;
+    __syncthreads();
+
+    // pass B: one thread per listed node decodes its 8 records (children of R_p keep the node's index)
+    bool bad = false;
+    for (uint32_t j = threadIdx.x; j < n_act; j += kT) {
+        const uint32_t k = act[j];
+        const uint64_t r8 = __ldg((const unsigned long long *)(R + 8 * j));
+        const uint32_t ipl = ip0 + __ldg(T8 + j);
+        uint32_t nr, pm, st;
+        rec_masks(r8, nr, pm, st);
+        const uint32_t lo = (uint32_t)r8, hi = (uint32_t)(r8 >> 32);
+        bad |= (((lo & 0x07070707u) + 0x01010101u) & 0x08080808u) != 0 ||
+               (((hi & 0x07070707u) + 0x01010101u) & 0x08080808u) != 0 || st != 0 ||
+               (pm != 0 && ipl + __popc(pm) >= np);
+        const uint32_t lo3 = ((k & kMX & pbits) == 0 ? 1u : 0u) | ((k & kMY & pbits) == 0 ? 2u : 0u) |
+                             ((k & kMZ & pbits) == 0 ? 4u : 0u);
+        const uint32_t hi3 = ((k & kMX & pbits) == (kMX & pbits) ? 1u : 0u) |
+                             ((k & kMY & pbits) == (kMY & pbits) ? 2u : 0u) |
+                             ((k & kMZ & pbits) == (kMZ & pbits) ? 4u : 0u);
+        uint64_t e8 = 0x0101010101010101ull * (uint64_t)P[k];
+        uint32_t minus_m = 0;
+        while (nr) {
+            const uint32_t ch = __ffs(nr) - 1;
+            nr &= nr - 1;
+            const uint32_t o = ((ch & 4u ? hi : lo) >> (8 * (ch & 3u))) & 0xFFu;
+            const uint32_t op = o & 7u, delta = o >> 4;
+            const uint32_t ipc = ipl + __popc(pm & ((1u << ch) - 1u));
+            const bool rx = op <= OP_RZ;  // R_x, R_y, R_z (op != R_p here)
+            const uint32_t a = (op - OP_RX) & 3u;
+            const bool plus = rx && ((ch >> a) & 1u);
+            const bool minus = rx && !plus;
+            const uint32_t pv = P[minc(k, kMX << a) & pbits];  // +axis: the neighbour's parent (R4)
+            uint32_t v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);  // R1, R3
+            v = plus ? pv : minus ? sent + a : v;
+            bad |= (plus && ((hi3 >> a) & 1u)) || (minus && ((lo3 >> a) & 1u)) || (op == OP_PD && ipc < 1 + delta);
+            e8 = (e8 & ~(0xFFull << (8 * ch))) | ((uint64_t)(v & 0xFFu) << (8 * ch));
+            minus_m |= (minus ? 1u : 0u) << ch;
+        }
+        *(uint64_t *)(E + 8 * j) = e8;
+        mm[j] = (uint8_t)minus_m;
+    }
+    __syncthreads();
+    if (bad) ms->bad = 1;
+
+    // pass C: resolve the -axis children (chains of at most 3 hops, as in rebuild_level)
+    volatile IdxT *Ev = E;
+    for (uint32_t j = threadIdx.x; j < n_act; j += kT) {
+        uint32_t m = mm[j];
+        if (!m) continue;
+        const uint32_t k = act[j];
+        while (m) {
+            const uint32_t ch = __ffs(m) - 1;
+            m &= m - 1;
+            uint32_t q = 8 * k + ch, w = Ev[8 * j + ch];
+            for (int hop = 0; hop < 4 && w >= sent; hop++) {
+                q = mdec(q, kMX << (w - sent)) & cbits;
+                const uint32_t k2 = q >> 3, word = cw[k2 >> 5], bit = k2 & 31u;
+                if ((word >> bit) & 1u) w = P[k2];
+                else w = Ev[8 * (rk[k2 >> 5] + __popc(~word & ((1u << bit) - 1u))) + (q & 7u)];
+            }
+            Ev[8 * j + ch] = (IdxT)(w < sent ? w : 0u);
+        }
+    }
+    __syncthreads();
+    return ms->bad == 0;
+}
+
+// Store the leaf level of the compact layout as x-fastest labels: store_level's 16-node units (4 x 2 x 2
+// voxels: two x-neighbouring L1 nodes, four 16-byte rows), units x-fastest over the threads so that a warp's
+// stores fill whole 128-byte lines.  A thread's units share their x and y (unit index = thread + kT i), so
+// only the z part of the Morton base moves.  The children of a node come from E (non-constant node, at its
+// rank) or repeat its L1 index; both are loaded and one is selected (the rank of a constant node points
+// inside the E area, or at its end), so that the lanes of a warp take one path.
+template <int kPal, uint32_t kT>
+__device__ __forceinline__ void store_leaf_compact(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t *out, bool vec,
+                                                   uint32_t pal_reg, const uint32_t *pal_s, const uint32_t *pal,
+                                                   uint32_t np) {
+    typedef uint8_t IdxT;
+    static_assert(kT == 128, "one z-layer pair of 32^3 units per pass of the CTA");
+    const IdxT *P = (const IdxT *)(smem + Ly.lev) - Ly.lev_shift + lev_off(N, 1);
+    const uint32_t *cw = (const uint32_t *)(smem + Ly.cm + cm_off(N, 1));
+    const uint16_t *rk = (const uint16_t *)(smem + Ly.rk);
+    const IdxT *E = (const IdxT *)(smem + Ly.e0);
+    const uint32_t s = N, side = 1u << s;
+    // the 8 children of the x-neighbouring L1 nodes k0 (even) and k0 + 1, four words (Morton offsets 0..15)
+    auto kids2 = [&](uint32_t k0, uint32_t (&w)[4]) {
+        const uint32_t word = cw[k0 >> 5], bit = k0 & 31u;
+        const uint32_t r0 = rk[k0 >> 5] + __popc(~word & ((1u << bit) - 1u));
+        const bool c0 = (word >> bit) & 1u, c1 = (word >> (bit + 1)) & 1u;
+        const uint32_t r1 = r0 + (c0 ? 0u : 1u);
+        const uint32_t p2 = *(const uint16_t *)(P + k0);  // L1 indices of k0, k0 + 1
+        const uint2 e0 = *(const uint2 *)(E + 8 * r0), e1 = *(const uint2 *)(E + 8 * r1);
+        const uint32_t rep0 = 0x01010101u * (p2 & 0xFFu), rep1 = 0x01010101u * (p2 >> 8);
+        w[0] = c0 ? rep0 : e0.x;
+        w[1] = c0 ? rep0 : e0.y;
+        w[2] = c1 ? rep1 : e1.x;
+        w[3] = c1 ? rep1 : e1.y;
+    };
+    if (!vec) {
+        const uint32_t n = side * side * side;
+        for (uint32_t i0 = 0; i0 < n; i0 += kT) {
+            const uint32_t i = i0 + threadIdx.x;
+            const uint32_t ii = i < n ? i : 0u;
+            const uint32_t x = ii & (side - 1), y = (ii >> s) & (side - 1), z = ii >> (2 * s);
+            const uint32_t mq = spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
+            uint32_t w[4];
+            kids2((mq >> 3) & ~1u, w);
+            const uint32_t v = (w[(mq >> 2) & 3u] >> (8 * (mq & 3u))) & 0xFFu;
+            const uint32_t l = lab<IdxT, kPal>(v, pal_reg, pal_s, pal, np);
+            if (i < n) out[i] = l;
+        }
+        return;
+    }
+    const uint32_t units = 1u << (3 * s - 4);
+    const uint32_t xb = s - 2, yb = s - 1;
+    // kT is a multiple of the units of one z-layer pair (2^(xb + yb) = 128 for N = 5): x0 and y0 per thread
+    const uint32_t u = threadIdx.x;
+    const uint32_t x0 = 4 * (u & ((1u << xb) - 1u)), y0 = 2 * ((u >> xb) & ((1u << yb) - 1u));
+    const uint32_t mxy = spread5(x0) | (spread5(y0) << 1);
+    const uint32_t zstep = kT >> (xb + yb);  // z0 advances by 2 zstep per iteration
+    uint32_t z0 = 2 * (u >> (xb + yb));
+    for (uint32_t u0 = 0; u0 < units; u0 += kT, z0 += 2 * zstep) {
+        const uint32_t m = mxy | (spread5(z0) << 2);
+        uint32_t w[4];
+        kids2(m >> 3, w);
+        uint32_t r[4][4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) {  // k = dy + 2 dz: word k/2, byte pair (k % 2) * 2
+            const uint32_t aa = w[k >> 1] >> (16 * (k & 1u)), cc = w[2 + (k >> 1)] >> (16 * (k & 1u));
+            r[k][0] = lab<IdxT, kPal>(aa, pal_reg, pal_s, pal, np);
+            r[k][1] = lab<IdxT, kPal>(aa >> 8, pal_reg, pal_s, pal, np);
+            r[k][2] = lab<IdxT, kPal>(cc, pal_reg, pal_s, pal, np);
+            r[k][3] = lab<IdxT, kPal>(cc >> 8, pal_reg, pal_s, pal, np);
+        }
+        uint32_t *o = out + ((size_t)z0 * side + y0) * side + x0;
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++)
+            __stcs((uint4 *)(o + (size_t)(k >> 1) * side * side + (k & 1u) * side),
+                   make_uint4(r[k][0], r[k][1], r[k][2], r[k][3]));
+    }
+}
+
+constexpr int32_t kStToFull = -2;  // internal: the request needs the full-layout kernel
+
 // kT: threads per CTA (64..256; the leaf-level pass needs 64 or more); kLmin: 0, or 1 / 2 for requests at LOD
 // >= kLmin only, in the compact layout rb_layout_part
-template <typename IdxT, uint32_t kT, uint32_t kLmin = 0>
+// kLeafC: the compact leaf level (rb_layout_leafc, uint8 indices); a LOD 0 request with more than kLeafCap
+// non-constant L1 nodes returns kStToFull untouched (nothing written).
+template <typename IdxT, uint32_t kT, uint32_t kLmin = 0, bool kLeafC = false>
 __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *smem, uint32_t i, uint32_t *out) {
     const uint32_t N = V.N;
     const uint32_t id = J.ids[i], t = J.lods[i];
     if (id >= V.n_bricks || t > N) return kStRange;
     if (kLmin && t < kLmin) return kStCorrupt;  // the caller's lists are wrong
-    const RbLayout Ly = kLmin ? rb_layout_part<IdxT>(N, kLmin) : rb_layout<IdxT>(N);
+    const RbLayout Ly = kLeafC ? rb_layout_leafc<IdxT>(N) : kLmin ? rb_layout_part<IdxT>(N, kLmin) : rb_layout<IdxT>(N);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t p0 = V.pal_off[id];
     const uint32_t np = (uint32_t)(V.pal_off[id + 1] - p0);
@@ -845,6 +1085,7 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     }
     const uint32_t info_int = J.info[2 * i], info_leaf = t == 0 ? J.info[2 * i + 1] : 0u;
     if ((info_int | info_leaf) & kRecBad) return kStCorrupt;
+    if (kLeafC && t == 0 && info_leaf > 8 * kLeafCap) return kStToFull;
     const uint8_t *base = J.recs + (uint64_t)i * J.stride;
     const uint16_t *t8i = (const uint16_t *)(base + J.t8_at), *t8l = (const uint16_t *)(base + J.t8_leaf_at);
 
@@ -877,7 +1118,9 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
         if (l == 0) {  // the leaf stream follows the complete interior stream
             if (used != info_int) return kStCorrupt;
             const uint32_t ip0 = __ldg(t8i + info_int / 8);
-            if (small)
+            if constexpr (kLeafC)
+                good = rebuild_leaf_compact<kT>(smem, Ly, N, base + J.leaf_at, t8l, info_leaf, ip0, np, n_act);
+            else if (small)
                 good = rebuild_small_level<IdxT, false, kT>(smem, Ly, N, 0u, base + J.leaf_at, t8l, info_leaf, ip0,
                                                             np, n_act);
             else if constexpr (kT >= 64)
@@ -908,6 +1151,13 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     }
     if ((t == 1 && used != info_int) || (t == 0 && used != info_leaf)) return kStCorrupt;
 
+    if constexpr (kLeafC) {
+        if (t == 0) {
+            if (np <= 32) store_leaf_compact<0, kT>(smem, Ly, N, out, vec, pal_reg, pal_s, pal, np);
+            else store_leaf_compact<1, kT>(smem, Ly, N, out, vec, pal_reg, pal_s, pal, np);
+            return kStOk;
+        }
+    }
     const IdxT *C = lev + lev_off(N, t);
     const uint32_t s = N - t;
     if (np <= 32) store_level<IdxT, 0, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
@@ -1028,6 +1278,23 @@ __global__ void __launch_bounds__(kRbCoarseThreads, 32) rebuild_coarse(VolDev V,
                                                                   const uint32_t *count, uint32_t *next) {
     extern __shared__ __align__(16) uint8_t smem[];
     rebuild_list<IdxT, kRbCoarseThreads, 2>(V, J, out, out_off, status, list, count, next, smem);
+}
+
+// Requests of 32^3 bricks with uint8 indices at any LOD, in the compact leaf layout (rb_layout_leafc, 25.8 KB):
+// 128-thread CTAs, 8 per SM, twice the bricks in flight of rebuild's 51 KB layout.  A LOD 0 request with more
+// than kLeafCap non-constant L1 nodes is appended to `full` (count in *n_full) for rebuild_listed.
+constexpr uint32_t kRbLeafCThreads = 128;
+__global__ void __launch_bounds__(kRbLeafCThreads, 8) rebuild_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                                   const uint64_t *__restrict__ out_off,
+                                                                   int32_t *__restrict__ status, uint32_t *full,
+                                                                   uint32_t *n_full) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t i = blockIdx.x;
+    const int32_t st = rebuild_request<uint8_t, kRbLeafCThreads, 0, true>(V, J, smem, i, out + out_off[i]);
+    if (threadIdx.x == 0) {
+        if (st == kStToFull) full[atomicAdd(n_full, 1u)] = i;
+        else status[i] = st;
+    }
 }
 
 // ------------------------------------------------------------------ rebuild for b = 64 (global memory)
@@ -1407,6 +1674,25 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             if (e != cudaSuccess) return e;
             ProfScope ps("rebuild", st);
             rebuild_small_brick<uint8_t><<<J.n, kRbSmallThreads, smem_b, st>>>(V, J, out, out_off, status);
+            return cudaGetLastError();
+        }
+        if (V.N == 5) {  // 32^3 bricks: the compact leaf layout, the few requests it cannot hold in rebuild_listed
+            const uint32_t smem_l = rb_layout_leafc<uint8_t>(V.N).total;
+            uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
+            e = cudaMemsetAsync(n_full, 0, 8, st);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_leafc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            if (e == cudaSuccess)  // the largest shared-memory carve-out: 8 CTAs per SM
+                e = cudaFuncSetAttribute(rebuild_leafc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            ProfScope ps("rebuild", st);
+            rebuild_leafc<<<J.n, kRbLeafCThreads, smem_l, st>>>(V, J, out, out_off, status, J.lists, n_full);
+            rebuild_listed<uint8_t><<<min(J.n, (uint32_t)(sms > 0 ? sms : 1)), kRbThreads, smem_b, st>>>(
+                V, J, out, out_off, status, J.lists, n_full, n_full + 1);
             return cudaGetLastError();
         }
         e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);

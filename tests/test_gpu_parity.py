@@ -222,6 +222,39 @@ def test_unaligned_output_offsets_use_scalar_stores():
         assert np.array_equal(out[offsets[i]:offsets[i] + 4096], ref[roff[i]:roff[i] + 4096])
 
 
+def test_b32_bricks_with_many_non_constant_l1_nodes_take_the_full_layout():
+    """32^3 bricks with uint8 palette indices decode in a compact leaf layout that holds at most 1792
+    non-constant L1 nodes; bricks with more go to the full-layout kernel in the same decode call.  Here half
+    the bricks are 8-label noise (every L1 node non-constant, small palettes), half are Voronoi cells, and
+    some are mixed; every LOD of every brick, requests in shuffled order, against the oracle."""
+    rng = np.random.default_rng(31)
+    shape = (64, 64, 128)  # 2 x 2 x 4 bricks
+    vol = structured_volume(3, shape, 40)
+    noise = rng.integers(1, 9, size=shape).astype(np.uint32)
+    vol[:, :, 64:] = noise[:, :, 64:]  # two brick columns of noise
+    vol[:32, :32, 40:56] = noise[:32, :32, 40:56]  # part of one Voronoi brick
+    V = O.encode_volume(vol, 5, stride=1)
+    gv = import_oracle_volume(V)
+    assert gv.info().max_palette <= 253
+    # non-constant L1 nodes per brick, from the volume: some bricks above the compact layout's 1792
+    n_nc = []
+    for bid in range(V.n_bricks):
+        bx, by, bz = bid % 4, (bid // 4) % 2, bid // 8
+        br = vol[bz * 32:bz * 32 + 32, by * 32:by * 32 + 32, bx * 32:bx * 32 + 32]
+        blocks = br.reshape(16, 2, 16, 2, 16, 2).transpose(0, 2, 4, 1, 3, 5).reshape(4096, 8)
+        n_nc.append(int((blocks != blocks[:, :1]).any(axis=1).sum()))
+    assert max(n_nc) > 1792 and min(n_nc) <= 1792
+    n = V.n_bricks
+    ids = np.repeat(np.arange(n, dtype=np.uint32), 6)
+    lods = np.tile(np.arange(6, dtype=np.uint8), n)
+    perm = rng.permutation(len(ids))
+    ids, lods = ids[perm], lods[perm]
+    out, off, st = gpu_decode(gv, 5, ids, lods)
+    ref, roff, rst = O.decode_bricks(V, ids, lods)
+    assert (rst == 0).all() and (st == 0).all(), np.unique(st, return_counts=True)
+    assert np.array_equal(out[:len(ref)], ref)
+
+
 def test_wide_palette_path():
     """Bricks with more than 253 palette entries use 16-bit indices in shared memory."""
     rng = np.random.default_rng(2)
