@@ -263,9 +263,38 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     {
         const uint32_t h = N - 1;  // log2 of the L1 side
         const bool vec = B.interior && N >= 2 && (B.X & 3u) == 0 && (reinterpret_cast<uintptr_t>(B.vol) & 15u) == 0;
-        if (vec) {
-            // two x-neighbouring L1 nodes per thread, Morton 2i and 2i+1 (consecutive threads store consecutive
-            // words): four 16-byte rows (y, z) of 4 voxels
+        if (vec && kT >= 256) {
+            // two x-neighbouring L1 nodes per thread: four 16-byte rows (y, z) of 4 voxels.  Pairs go to threads
+            // x-fastest (px = x / 4 of the brick's 32-voxel rows, then y / 2, then z / 2), so that each load of a
+            // warp reads whole 128-byte rows, and the rows of a thread's next pair are loaded before the modes of
+            // this pair are computed (the loads of one pair are in flight while the previous pair is reduced).
+            const uint32_t npairs = 1u << (3 * h - 1);
+            const uint32_t xb = h - 1;  // bits of px (pairs per L1 row)
+            auto rows = [&](uint32_t i, uint4 (&q)[4]) {
+                const uint32_t px = i & ((1u << xb) - 1u), y = (i >> xb) & ((1u << h) - 1u), z = i >> (xb + h);
+                const uint32_t *r = B.base + B.sz * (2 * z) + B.sy * (2 * y) + 4 * px;
+                q[0] = __ldg((const uint4 *)r);
+                q[1] = __ldg((const uint4 *)(r + B.sy));
+                q[2] = __ldg((const uint4 *)(r + B.sz));
+                q[3] = __ldg((const uint4 *)(r + B.sz + B.sy));
+            };
+            uint4 cur[4], nxt[4];
+            if (tid < npairs) rows(tid, cur);
+            for (uint32_t i = tid; i < npairs; i += kT) {
+                if (i + kT < npairs) rows(i + kT, nxt);
+                const uint32_t px = i & ((1u << xb) - 1u), y = (i >> xb) & ((1u << h) - 1u), z = i >> (xb + h);
+                bool e0, e1;
+                const uint32_t m = loff(G.N, 1) + morton3(2 * px, y, z);
+                S.lab[m] = mode8(cur[0].x, cur[0].y, cur[1].x, cur[1].y, cur[2].x, cur[2].y, cur[3].x, cur[3].y, e0);
+                S.cst[m] = e0;
+                S.lab[m + 1] = mode8(cur[0].z, cur[0].w, cur[1].z, cur[1].w, cur[2].z, cur[2].w, cur[3].z, cur[3].w, e1);
+                S.cst[m + 1] = e1;
+#pragma unroll
+                for (int k = 0; k < 4; k++) cur[k] = nxt[k];
+            }
+        } else if (vec) {
+            // small CTAs (bricks of 16^3 and smaller, registers bounded): Morton pairs 2i, 2i+1 per thread,
+            // without the prefetch
             const uint32_t npairs = 1u << (3 * h - 1);
 #pragma unroll 2
             for (uint32_t i = tid; i < npairs; i += kT) {
