@@ -40,10 +40,15 @@
  *       nibble in the same stream (decode order).
  *   R9  rANS: 32-bit state, scale M = 4096, lower bound L = 2^16, 16-bit
  *       words, at most one word per symbol.
- *   R10 K interleaved states per stream, K = clamp(n / S_min, 1, K_max);
- *       symbol i uses state i mod K.  Stream = K final states (low half
- *       first, state 0 first) followed by the renormalisation words in the
- *       order the decoder reads them.
+ *   R10 K interleaved states per stream, K = clamp(n / S_min, 1, K_max)
+ *       with n the stream's nibble count.  The j-th op nibble of the stream
+ *       uses state j mod K, and the delta nibble of a P_delta op uses the
+ *       same state as its op.  Coding order, step by step: step t holds the
+ *       ops tK .. tK+K-1 in state order, then the delta nibbles of those of
+ *       them that are P_delta, again in state order.  Stream = K final
+ *       states (low half first, state 0 first) followed by the
+ *       renormalisation words in coding order.  With K = 1 the coding order
+ *       is the nibble order itself.
  *   R11 table: f_s = 1 + floor(count_s * (M - 16) / total), the remaining
  *       r < 16 units go +1 to the r largest counts (ties: lower symbol);
  *       total = 0 gives f_s = 256.
@@ -425,23 +430,20 @@ static uint32_t cum_of(const uint32_t freq[16], uint32_t s) {
 }
 
 /*
- * Encode n nibbles with K interleaved rANS states.  words receives 2K state
- * words followed by the renormalisation words in decode order; *n_words is
- * the total.  Empty input gives an empty stream.
+ * The coder itself (Sec. 3.3, R9): n symbols in coding order, symbol i coded
+ * with state lane[i].  Encoding runs from the last symbol to the first, so
+ * that the decoder reads forward; words receives the K final states, then
+ * the renormalisation words in the order the decoder takes them.
  */
-int csgvo_rans_encode(const uint8_t *sym, uint32_t n, uint32_t K, const uint32_t freq[16],
-                      uint16_t *words, uint32_t cap, uint32_t *n_words) {
-    *n_words = 0;
-    if (n == 0) return ORC_OK;
-    if (K == 0 || K > n) return ORC_ERR_ARG;
+static int rans_encode_order(const uint8_t *sym, const uint32_t *lane, uint32_t n, uint32_t K,
+                             const uint32_t freq[16], uint16_t *words, uint32_t cap, uint32_t *n_words) {
     uint32_t *x = (uint32_t *)malloc(sizeof(uint32_t) * K);
     uint16_t *emit = (uint16_t *)malloc(sizeof(uint16_t) * (n + 1));
     if (!x || !emit) { free(x); free(emit); return ORC_ERR_NOMEM; }
     for (uint32_t k = 0; k < K; k++) x[k] = RANS_L;
     uint32_t ne = 0;
-    /* encode in reverse: the decoder then reads forward */
     for (uint32_t i = n; i-- > 0;) {
-        uint32_t k = i % K, s = sym[i];
+        uint32_t k = lane[i], s = sym[i];
         uint32_t f = freq[s], c = cum_of(freq, s);
         /* renormalise: keep x below f * 2^20 = ((L >> scale) << 16) * f */
         uint64_t bound = ((uint64_t)(RANS_L >> RANS_SCALE_BITS) << 16) * f;
@@ -464,10 +466,66 @@ int csgvo_rans_encode(const uint8_t *sym, uint32_t n, uint32_t K, const uint32_t
     return ORC_OK;
 }
 
+/* decode one symbol with state *x, reading a renormalisation word when needed */
+static int rans_decode_one(uint32_t *x, const uint32_t freq[16], const uint16_t *words, uint32_t n_words,
+                           uint32_t *pos, uint8_t *out) {
+    uint32_t slot = *x & (RANS_M - 1);
+    uint32_t s = 0;
+    while (s + 1 < 16 && cum_of(freq, s + 1) <= slot) s++;
+    *out = (uint8_t)s;
+    *x = freq[s] * (*x >> RANS_SCALE_BITS) + slot - cum_of(freq, s);
+    if (*x < RANS_L) {
+        if (*pos >= n_words) return ORC_ERR_CORRUPT;
+        *x = (*x << 16) | words[(*pos)++];
+    }
+    return ORC_OK;
+}
+
 /*
- * Decode the first m of the n symbols of a K-state stream.  When m == n the
- * end of the stream is checked: every state must be back at L and every word
- * used; otherwise ORC_ERR_CORRUPT.
+ * Encode a nibble stream of n symbols (stream order: each P_delta op nibble
+ * followed by its delta nibble, R6) with K interleaved states under the
+ * coding order of R10.  Empty input gives an empty stream.
+ */
+int csgvo_rans_encode(const uint8_t *sym, uint32_t n, uint32_t K, const uint32_t freq[16],
+                      uint16_t *words, uint32_t cap, uint32_t *n_words) {
+    *n_words = 0;
+    if (n == 0) return ORC_OK;
+    if (K == 0 || K > n) return ORC_ERR_ARG;
+    /* the ops: stream position of each op nibble */
+    uint32_t *op_at = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    uint8_t *cs = (uint8_t *)malloc(n);
+    uint32_t *cl = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    if (!op_at || !cs || !cl) { free(op_at); free(cs); free(cl); return ORC_ERR_NOMEM; }
+    uint32_t m = 0;
+    int rc = ORC_OK;
+    for (uint32_t i = 0; i < n; i++) {
+        op_at[m++] = i;
+        if ((sym[i] & 7u) == OP_PD) {
+            if (i + 1 >= n) { rc = ORC_ERR_ARG; break; } /* a P_delta needs its delta nibble */
+            i++;
+        }
+    }
+    /* coding order: per step of K ops, the ops in state order, then their deltas */
+    uint32_t c = 0;
+    for (uint32_t t0 = 0; rc == ORC_OK && t0 < m; t0 += K) {
+        uint32_t t1 = t0 + K < m ? t0 + K : m;
+        for (uint32_t j = t0; j < t1; j++) { cs[c] = sym[op_at[j]]; cl[c++] = j - t0; }
+        for (uint32_t j = t0; j < t1; j++)
+            if ((sym[op_at[j]] & 7u) == OP_PD) { cs[c] = sym[op_at[j] + 1]; cl[c++] = j - t0; }
+    }
+    if (rc == ORC_OK) rc = rans_encode_order(cs, cl, n, K, freq, words, cap, n_words);
+    free(op_at); free(cs); free(cl);
+    return rc;
+}
+
+/*
+ * Decode the first m of the n symbols (stream order) of a K-state stream.
+ * Steps follow the coding order of R10: in state order, a state decodes an
+ * op nibble while more symbols remain than the delta nibbles owed to the
+ * step's P_delta ops so far; then each P_delta op's state decodes its delta
+ * nibble.  Whole steps are decoded until the first m stream symbols are out.
+ * When m == n the end of the stream is checked: every state must be back at
+ * L and every word used; otherwise ORC_ERR_CORRUPT.
  */
 int csgvo_rans_decode(const uint16_t *words, uint32_t n_words, uint32_t n, uint32_t m, uint32_t K,
                       const uint32_t freq[16], uint8_t *sym) {
@@ -475,28 +533,42 @@ int csgvo_rans_decode(const uint16_t *words, uint32_t n_words, uint32_t n, uint3
     if (n == 0) return n_words == 0 ? ORC_OK : ORC_ERR_CORRUPT;
     if (K == 0 || K > n || n_words < 2 * K) return ORC_ERR_CORRUPT;
     uint32_t *x = (uint32_t *)malloc(sizeof(uint32_t) * K);
-    if (!x) return ORC_ERR_NOMEM;
+    uint8_t *op = (uint8_t *)malloc(K), *dl = (uint8_t *)malloc(K);
+    uint8_t *st = (uint8_t *)malloc(n + 1);
+    if (!x || !op || !dl || !st) { free(x); free(op); free(dl); free(st); return ORC_ERR_NOMEM; }
     for (uint32_t k = 0; k < K; k++) x[k] = (uint32_t)words[2 * k] | ((uint32_t)words[2 * k + 1] << 16);
-    uint32_t pos = 2 * K;
+    uint32_t pos = 2 * K, used = 0, out = 0;
     int rc = ORC_OK;
-    for (uint32_t i = 0; i < m; i++) {
-        uint32_t k = i % K;
-        uint32_t slot = x[k] & (RANS_M - 1);
-        uint32_t s = 0;
-        while (s + 1 < 16 && cum_of(freq, s + 1) <= slot) s++;
-        sym[i] = (uint8_t)s;
-        x[k] = freq[s] * (x[k] >> RANS_SCALE_BITS) + slot - cum_of(freq, s);
-        if (x[k] < RANS_L) {
-            if (pos >= n_words) { rc = ORC_ERR_CORRUPT; break; }
-            x[k] = (x[k] << 16) | words[pos++];
+    while (rc == ORC_OK && out < m) {
+        uint32_t nops = 0, owed = 0;
+        for (uint32_t k = 0; k < K && rc == ORC_OK; k++) {
+            if (used + owed >= n) break;
+            rc = rans_decode_one(&x[k], freq, words, n_words, &pos, &op[k]);
+            used++;
+            nops++;
+            if ((op[k] & 7u) == OP_PD) owed++;
+        }
+        if (rc == ORC_OK && nops == 0) rc = ORC_ERR_CORRUPT;
+        for (uint32_t k = 0; k < nops && rc == ORC_OK; k++)
+            if ((op[k] & 7u) == OP_PD) {
+                if (used >= n) { rc = ORC_ERR_CORRUPT; break; } /* a delta past the stream's symbols */
+                rc = rans_decode_one(&x[k], freq, words, n_words, &pos, &dl[k]);
+                used++;
+            }
+        for (uint32_t k = 0; k < nops && rc == ORC_OK; k++) {
+            st[out++] = op[k];
+            if ((op[k] & 7u) == OP_PD) st[out++] = dl[k];
         }
     }
-    if (rc == ORC_OK && m == n) {
-        for (uint32_t k = 0; k < K; k++)
-            if (x[k] != RANS_L) rc = ORC_ERR_CORRUPT;
-        if (pos != n_words) rc = ORC_ERR_CORRUPT;
+    if (rc == ORC_OK) {
+        memcpy(sym, st, m);
+        if (m == n) {
+            for (uint32_t k = 0; k < K; k++)
+                if (x[k] != RANS_L) rc = ORC_ERR_CORRUPT;
+            if (pos != n_words) rc = ORC_ERR_CORRUPT;
+        }
     }
-    free(x);
+    free(x); free(op); free(dl); free(st);
     return rc;
 }
 

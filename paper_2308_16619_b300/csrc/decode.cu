@@ -56,6 +56,13 @@ __device__ __forceinline__ uint32_t lt_of(uint32_t lane) { return (1u << lane) -
 // malformed.  Decoding stops once `need` records are out (a coarse LOD uses only the stream's first
 // levels); the end of the stream is then not checked.
 //
+// Coding order (reading R10): op j of the stream is on state j mod K, a P_delta's delta nibble on its op's
+// state; a step decodes the ops of its K states in state order, then the deltas of its P_delta ops in state
+// order.  Lane k holds state k, so a step is one warp-wide op decode plus, when a P_delta came out, one
+// more decode by those lanes; each lane then writes its own record (op | stop << 3 | delta << 4).  The op
+// count is not stored: in the stream's last steps (fewer than 2K symbols left) a lane decodes an op only if
+// its op and the deltas owed by the lanes before it still fit in the symbols left.
+//
 // The stream's words are staged in a ring of kWinWords words in shared memory (word a, counted from the
 // 16-byte boundary at or below the stream's start, sits at a % kWinWords), refilled half a ring at a time
 // with 16-byte loads that stay inside the stream's 16-byte chunks.  A malformed stream may read stale
@@ -80,91 +87,99 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     uint4 *ring = reinterpret_cast<uint4 *>(win);
     __syncwarp();  // the previous stream's reads of the ring are done
     if (lane < n_chunks) ring[lane] = __ldg(src + lane);
+    // a step reads at most 2K <= 64 words: refill once pos passes lim
     uint32_t filled = kRingChunks;  // chunks staged so far
-    uint32_t lim = filled < n_chunks ? 8 * filled - 32 : 0xFFFFFFFFu;  // refill once pos passes this
+    uint32_t lim = filled < n_chunks ? 8 * filled - 64 : 0xFFFFFFFFu;
     __syncwarp();
     uint32_t x = kL;
     if (lane < K) x = (uint32_t)win[sh + 2 * lane] | ((uint32_t)win[sh + 2 * lane + 1] << 16);
-    uint32_t pos = sh + 2 * K, remaining = n_sym, otail = 0, pend = 0, held = 0, pa_run = 0, t8n = 0;
-    // One step: n symbols, one per lane below n.  Full steps (n = K) need no test of which lanes take part
-    // beyond lane < K, and no lane keeps its state unchanged.
-    auto step = [&](const uint32_t n, const bool act, auto full) {
-        if (pos > lim) {  // a step reads at most 32 words: stage the next half ring over the half already read
-            __syncwarp();
-            const uint32_t c = filled + lane;
-            if (lane < kHalf && c < n_chunks) ring[c % kRingChunks] = __ldg(src + c);
-            filled += kHalf;
-            lim = filled < n_chunks ? 8 * filled - 32 : 0xFFFFFFFFu;
-            __syncwarp();
-        }
-        const uint32_t e = lut[x & (kM - 1u)];
-        const uint32_t sym = e & 15u;
-        const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
-        const bool nrm = act && xn < kL;
-        const uint32_t m = __ballot_sync(kFull, nrm);
-        const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
-        if (decltype(full)::value) x = nrm ? ((xn << 16) | wv) : xn;  // lanes >= K: never read
-        else x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
-        pos += __popc(m);
-        const uint32_t rare = __ballot_sync(kFull, act && (sym & 7u) >= OP_PD);  // P_delta, P_a (or 7)
-        if ((rare | pend) == 0) {  // common case: every symbol is an op, none of them P_a
-            if (act) rec[otail + lane] = (uint8_t)sym;
-            otail += n;
-            return;
+    uint32_t pos = sh + 2 * K, left = n_sym, otail = 0, pa_run = 0, t8n = 0;
+    bool stuck = false;
+    const bool actK = lane < K;
+    auto refill = [&]() {  // stage the next half ring over the half already read
+        __syncwarp();
+        const uint32_t c = filled + lane;
+        if (lane < kHalf && c < n_chunks) ring[c % kRingChunks] = __ldg(src + c);
+        filled += kHalf;
+        lim = filled < n_chunks ? 8 * filled - 64 : 0xFFFFFFFFu;
+        __syncwarp();
+    };
+    // The step after the ops' decode when a P_delta or P_a came out: the deltas of the P_delta lanes, in lane
+    // order, then the records and the P_a counts.
+    auto general = [&](uint32_t sym, bool act, uint32_t n) {
+        const bool pd = act && (sym & 7u) == OP_PD;
+        const uint32_t pdm = __ballot_sync(kFull, pd);
+        uint32_t dl = 0;
+        if (pdm) {
+            const uint32_t e2 = lut[x & (kM - 1u)];
+            dl = e2 & 15u;
+            const uint32_t xn2 = ((e2 >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e2 >> 17);
+            const bool nrm2 = pd && xn2 < kL;
+            const uint32_t m2 = __ballot_sync(kFull, nrm2);
+            const uint32_t wv2 = win[(pos + __popc(m2 & lt)) % kWinWords];
+            x = pd ? (nrm2 ? ((xn2 << 16) | wv2) : xn2) : x;
+            pos += __popc(m2);
         }
         // the P_a counts of the records before this step are all pa_run
         for (uint32_t j = t8n + lane; 8 * j < otail; j += 32) t8[j] = (uint16_t)pa_run;
-        // which symbols are delta nibbles: the one after each P_delta op (bit n: in the next step)
-        uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD);
-        uint64_t dm = pend;
-        cand &= ~(uint32_t)dm;
-        while (cand) {
-            const uint32_t i = __ffs(cand) - 1;
-            cand &= cand - 1;
-            if (!((dm >> i) & 1ull)) {
-                dm |= 2ull << i;
-                cand &= ~(uint32_t)(2ull << i);
-            }
-        }
-        const uint32_t nxt = __shfl_down_sync(kFull, sym, 1);
-        const uint32_t sym0 = __shfl_sync(kFull, sym, 0);
-        const uint32_t symlast = __shfl_sync(kFull, sym, (n - 1) & 31u);
-        uint32_t base = otail;
-        if (pend) {  // the P_delta held back from the previous step takes symbol 0 as its delta
-            if (lane == 0) {
-                rec[otail] = (uint8_t)(held | (sym0 << 4));
-                if ((otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
-            }
-            base++;
-        }
-        const uint32_t actm = n >= 32 ? kFull : ((1u << n) - 1u);
-        const bool hold = (dm >> n) & 1ull;  // the last symbol is a P_delta whose delta comes next step
-        const uint32_t emit = actm & ~(uint32_t)dm & ~(hold ? (1u << (n - 1)) : 0u);
-        const bool em = (emit >> lane) & 1u;
-        const uint32_t pam = __ballot_sync(kFull, em && (sym & 7u) == OP_PA);
-        if (em) {
-            const bool pd = (sym & 7u) == OP_PD;
-            const uint32_t r = base + __popc(emit & lt);
-            rec[r] = (uint8_t)(sym | (pd ? nxt << 4 : 0u));
+        const uint32_t pam = __ballot_sync(kFull, act && (sym & 7u) == OP_PA);
+        if (act) {
+            const uint32_t r = otail + lane;
+            rec[r] = (uint8_t)(sym | (pd ? dl << 4 : 0u));
             if ((r & 7u) == 0) t8[r >> 3] = (uint16_t)min(pa_run + __popc(pam & lt), 0xFFFFu);
         }
         pa_run = min(pa_run + __popc(pam), 0xFFFFu);  // saturated: a count past any palette is caught later
-        otail = base + __popc(emit);
+        otail += n;
+        left -= n + __popc(pdm);
         t8n = (otail + 7) / 8;
-        pend = hold;
-        held = symlast;
     };
-    const bool actK = lane < K;
-    for (; remaining >= K && otail < need; remaining -= K) step(K, actK, std::true_type{});
-    if (remaining > 0 && otail < need) {
-        step(remaining, lane < remaining, std::false_type{});
-        remaining = 0;
+    // full steps: at least 2K symbols left, so every lane below K decodes an op
+    while (left >= 2 * K && otail < need) {
+        if (pos > lim) refill();
+        const uint32_t e = lut[x & (kM - 1u)];
+        const uint32_t sym = e & 15u;
+        const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
+        const bool nrm = actK && xn < kL;
+        const uint32_t m = __ballot_sync(kFull, nrm);
+        const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
+        x = nrm ? ((xn << 16) | wv) : xn;  // lanes >= K: never read
+        pos += __popc(m);
+        if (__ballot_sync(kFull, actK && (sym & 7u) >= OP_PD)) {  // a P_delta or P_a (or 7)
+            general(sym, actK, K);
+        } else {
+            if (actK) rec[otail + lane] = (uint8_t)sym;
+            otail += K;
+            left -= K;
+        }
+    }
+    // the last steps: a lane decodes an op only if it and the deltas owed by the lanes before it fit
+    while (left > 0 && otail < need) {
+        if (pos > lim) refill();
+        const bool cand = actK && lane < left;
+        const uint32_t e = lut[x & (kM - 1u)];
+        const uint32_t sym = e & 15u;
+        const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
+        const uint32_t pdc = __ballot_sync(kFull, cand && (sym & 7u) == OP_PD);
+        const uint32_t need_k = lane + 1 + __popc(pdc & ((2u << lane) - 1u));
+        const uint32_t n = __popc(__ballot_sync(kFull, cand && need_k <= left));
+        if (n == 0) {  // a P_delta whose delta is not in the stream: malformed
+            stuck = true;
+            break;
+        }
+        const bool act = lane < n;
+        const bool nrm = act && xn < kL;
+        const uint32_t m = __ballot_sync(kFull, nrm);
+        const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
+        x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
+        pos += __popc(m);
+        general(sym, act, n);
     }
     // the counts not yet written: every 8th record from t8n on, and the one just past the last record
     for (uint32_t j = t8n + lane; 8 * j <= otail; j += 32) t8[j] = (uint16_t)pa_run;
-    if (remaining > 0) return pos <= sh + n_words ? otail : (otail | kRecBad);  // stopped early: a prefix
+    if (stuck) return otail | kRecBad;
+    if (left > 0) return pos <= sh + n_words ? otail : (otail | kRecBad);  // stopped early: a prefix
     const bool lane_ok = lane >= K || x == kL;
-    const bool ok = __all_sync(kFull, lane_ok) && !pend && pos == sh + n_words;
+    const bool ok = __all_sync(kFull, lane_ok) && pos == sh + n_words;
     __syncwarp();
     return ok ? otail : (otail | kRecBad);
 }
@@ -307,17 +322,18 @@ __global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records_packed(VolDev 
         __syncwarp();  // the previous group's reads of the rings are done
         if (mine)
             for (uint32_t c = j; c < rchunks && c < n_chunks; c += K) ring[c] = __ldg(src + c);
-        // a step reads at most K words of a stream, K <= half a ring: refill once pos passes lim
+        // a step reads at most 2K words of a stream, 2K <= half a ring: refill once pos passes lim
         uint32_t filled = rchunks;  // chunks staged so far
-        uint32_t lim = filled < n_chunks ? 8 * filled - K : 0xFFFFFFFFu;
+        uint32_t lim = filled < n_chunks ? 8 * filled - 2 * K : 0xFFFFFFFFu;
         __syncwarp();
         uint32_t x = kL;
         if (mine) x = (uint32_t)win[sh + 2 * j] | ((uint32_t)win[sh + 2 * j + 1] << 16);
-        uint32_t pos = sh + 2 * K, otail = 0, pend = 0, held = 0, pa_run = 0, t8n = 0;
+        uint32_t pos = sh + 2 * K, otail = 0, pa_run = 0, t8n = 0;
+        bool stuck = false;
 
-        // ---- decode the group
+        // ---- decode the group: per step, each stream's ops on its lanes, then its deltas (reading R10)
         for (;;) {
-            const bool run = mine && remaining > 0 && otail < need;
+            const bool run = mine && remaining > 0 && otail < need && !stuck;
             if (!__any_sync(kFull, run)) break;
             if (__any_sync(kFull, run && pos > lim)) {
                 __syncwarp();
@@ -325,74 +341,66 @@ __global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records_packed(VolDev 
                     for (uint32_t c = j; c < rhalf; c += K)
                         if (filled + c < n_chunks) ring[(filled + c) & (rchunks - 1u)] = __ldg(src + filled + c);
                     filled += rhalf;
-                    lim = filled < n_chunks ? 8 * filled - K : 0xFFFFFFFFu;
+                    lim = filled < n_chunks ? 8 * filled - 2 * K : 0xFFFFFFFFu;
                 }
                 __syncwarp();
             }
-            const uint32_t n = run ? min(K, remaining) : 0u;
-            const bool act = j < n;
+            bool act = run && j < K && j < remaining;
             const uint32_t e = lut[x & (kM - 1u)];
             const uint32_t sym = e & 15u;
             const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
+            uint32_t n = run ? K : 0u;
+            if (__any_sync(kFull, run && remaining < 2 * K)) {
+                // a stream's last steps: the lanes whose op and the deltas owed before it fit in what is left
+                const uint32_t pdm = __ballot_sync(kFull, act && (sym & 7u) == OP_PD) & smask;
+                const uint32_t need_k = j + 1 + __popc(pdm & ((2u << lane) - 1u));
+                const uint32_t fit = __ballot_sync(kFull, act && need_k <= remaining) & smask;
+                if (run && remaining < 2 * K) {
+                    n = __popc(fit);
+                    stuck = n == 0;  // a P_delta whose delta is not in the stream: malformed
+                }
+            }
+            act = act && j < n;
             const bool nrm = act && xn < kL;
             const uint32_t m = __ballot_sync(kFull, nrm) & smask;
             const uint32_t wv = win[(pos + __popc(m & lt)) & (rwords - 1u)];
             x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
             pos += __popc(m);
-            remaining -= n;
             const uint32_t rare = __ballot_sync(kFull, act && (sym & 7u) >= OP_PD);  // P_delta, P_a (or 7)
-            if (!__any_sync(kFull, run && ((rare & smask) | pend) != 0)) {  // common case: every symbol an op, no P_a
+            if (rare == 0) {  // common case, every stream of the group: no delta to decode, no P_a
                 if (act) rec[otail + j] = (uint8_t)sym;
                 otail += n;
+                remaining -= n;
                 continue;
             }
-            // every stream of the group takes the general step (exact for the common case too); the P_a
-            // counts of the records before this step are all pa_run
+            // every stream of the group takes the general step (exact for the common case too)
+            const bool pd = act && (sym & 7u) == OP_PD;
+            const uint32_t pdm = __ballot_sync(kFull, pd) & smask;
+            uint32_t dl = 0;
+            if (__any_sync(kFull, pd)) {  // the deltas of the P_delta ops, in lane order per stream
+                const uint32_t e2 = lut[x & (kM - 1u)];
+                dl = e2 & 15u;
+                const uint32_t xn2 = ((e2 >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e2 >> 17);
+                const bool nrm2 = pd && xn2 < kL;
+                const uint32_t m2 = __ballot_sync(kFull, nrm2) & smask;
+                const uint32_t wv2 = win[(pos + __popc(m2 & lt)) & (rwords - 1u)];
+                x = pd ? (nrm2 ? ((xn2 << 16) | wv2) : xn2) : x;
+                pos += __popc(m2);
+            }
+            // the P_a counts of the records before this step are all pa_run
             if (run)
                 for (uint32_t k = t8n + j; 8 * k < otail; k += K) t8[k] = (uint16_t)pa_run;
-            // which symbols are delta nibbles: the one after each P_delta op of the same stream; a P_delta
-            // on a stream's last symbol of the step is held back (its delta comes next step)
-            const uint32_t lastm = __ballot_sync(kFull, act && j == n - 1);
-            const uint32_t pendm = __ballot_sync(kFull, run && pend && j == 0);
-            uint32_t cand = __ballot_sync(kFull, act && (sym & 7u) == OP_PD) & ~pendm;
-            uint32_t dm = pendm, holdm = 0;
-            while (cand) {
-                const uint32_t b = __ffs(cand) - 1;
-                cand &= cand - 1;
-                if (!((dm >> b) & 1u)) {
-                    if ((lastm >> b) & 1u) holdm |= 1u << b;
-                    else {
-                        dm |= 2u << b;
-                        cand &= ~(2u << b);
-                    }
-                }
-            }
-            const uint32_t nxt_sym = __shfl_down_sync(kFull, sym, 1);
-            const uint32_t sym_last = __shfl_sync(kFull, sym, (sb + n - 1) & 31u);
-            const bool hold = (holdm & smask) != 0;
-            uint32_t base = otail;
-            if (run && pend) {  // the P_delta held back from the previous step takes the first symbol as its delta
-                if (j == 0) {
-                    rec[otail] = (uint8_t)(held | (sym << 4));
-                    if ((otail & 7u) == 0) t8[otail >> 3] = (uint16_t)pa_run;
-                }
-                base++;
-            }
-            const bool em = act && !((dm >> lane) & 1u) && !((holdm >> lane) & 1u);
-            const uint32_t emit = __ballot_sync(kFull, em) & smask;
-            const uint32_t pam = __ballot_sync(kFull, em && (sym & 7u) == OP_PA) & smask;
-            if (em) {
-                const bool pd = (sym & 7u) == OP_PD;
-                const uint32_t r = base + __popc(emit & lt);
-                rec[r] = (uint8_t)(sym | (pd ? nxt_sym << 4 : 0u));
+            const uint32_t pam = __ballot_sync(kFull, act && (sym & 7u) == OP_PA) & smask;
+            if (act) {
+                const uint32_t r = otail + j;
+                rec[r] = (uint8_t)(sym | (pd ? dl << 4 : 0u));
                 if ((r & 7u) == 0) t8[r >> 3] = (uint16_t)min(pa_run + __popc(pam & lt), 0xFFFFu);
             }
             if (run) {
                 pa_run = min(pa_run + __popc(pam), 0xFFFFu);  // saturated: a count past any palette is caught later
-                otail = base + __popc(emit);
+                otail += n;
+                remaining -= n + __popc(pdm);
                 t8n = (otail + 7) / 8;
-                pend = hold;
-                held = sym_last;
             }
         }
 
@@ -403,8 +411,9 @@ __global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records_packed(VolDev 
         const uint32_t badx = __ballot_sync(kFull, mine && j < K && x != kL) & smask;
         if (mine && j == 0) {
             uint32_t r;
-            if (remaining > 0) r = pos <= sh + n_words ? otail : (otail | kRecBad);  // stopped early: a prefix
-            else r = (badx == 0 && !pend && pos == sh + n_words) ? otail : (otail | kRecBad);
+            if (stuck) r = otail | kRecBad;
+            else if (remaining > 0) r = pos <= sh + n_words ? otail : (otail | kRecBad);  // stopped early: a prefix
+            else r = (badx == 0 && pos == sh + n_words) ? otail : (otail | kRecBad);
             J.info[2 * i + s] = r;
         }
     }

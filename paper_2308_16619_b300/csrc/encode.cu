@@ -634,10 +634,12 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         uint8_t *nib_i = count ? nullptr : SC.nib_int + (size_t)slot * G.int_cap;
         uint8_t *nib_l = count ? nullptr : SC.nib_leaf + (size_t)slot * G.leaf_cap;
         // this warp's ops are staged in shared memory (the pyramid and lists are dead now), stage bytes at a
-        // time with 16-byte loads: one round trip to L2 instead of one per 32 ops
+        // time with 16-byte loads: one round trip to L2 instead of one per 32 ops.  Bricks of 32^3 and larger
+        // skip the scatter: rans_encode_kernel expands their op bytes itself.
         const uint32_t stage = (G.smem / (kT / 32)) & ~(kStageMin - 1u);
         uint8_t *stg = smem_raw + warp * stage;
-        for (uint32_t js = j0; js < j1; js += stage) {
+        const uint32_t jend = (count || G.nib) ? j1 : j0;
+        for (uint32_t js = j0; js < jend; js += stage) {
             const uint32_t len = min(stage, j1 - js), nv = (len + 15u) >> 4;  // j0, js: multiples of 16
             for (uint32_t q = lane; q < nv; q += 32) *(uint4 *)(stg + 16 * q) = *(const uint4 *)(ops + js + 16 * q);
             __syncwarp();
@@ -696,7 +698,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         sz[0] = sh_np;
         sz[1] = sym_tot[0];
         sz[2] = sym_tot[1];
-        sz[7] = 0;
+        sz[7] = (n_int_ops >> 3) | (((n_ops - n_int_ops) >> 3) << 16);  // active parents per stream (< 2^16)
     }
 }
 
@@ -716,8 +718,41 @@ __global__ void __launch_bounds__(kEncSmallThreads, 16)
     encode_brick<kEncSmallThreads>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
 }
 
-// ---- E. rANS, one warp per stream (brick slot q / 2, stream q % 2) over the nibbles in scratch; the
-// symbols are staged in shared memory window by window from the end
+// ---- E. rANS, one warp per stream (brick slot q / 2, stream q % 2), from the op bytes of the encode kernel
+// (op | stop << 3 | delta << 4, in stream order).  Coding order (reading R10): op j on state j mod K, a
+// P_delta's delta nibble on its op's state; a step holds K ops in state order, then the deltas of its P_delta
+// ops in state order.  Lane k holds state k and codes the steps from the last one down: in a step, first the
+// deltas (lanes of P_delta ops), then the ops, each of the two a warp-wide substep whose renormalisation words
+// are pushed downward from the top of the scratch area so that the decoder reads them forward in lane order.
+// The ops are staged in shared memory window by window from the end.
+
+// One coding substep: lanes with `act` code `sym` into their state x (Sec. 3.3, R9); renormalisation words go
+// below `top`, in lane order.
+__device__ __forceinline__ void rans_code_substep(uint32_t &x, uint32_t &top, uint16_t *words, uint32_t sym, bool act,
+                                                  uint32_t f_reg, uint32_t c_reg, float rcp_reg, uint32_t smask,
+                                                  uint32_t lt) {
+    const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
+    const float rf = __shfl_sync(kFull, rcp_reg, sym);
+    // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
+    const bool emit = act && x >= (f << 20);
+    const uint32_t m = __ballot_sync(kFull, emit) & smask;
+    if (emit) {
+        words[top - __popc(m) + __popc(m & lt)] = (uint16_t)(x & 0xFFFFu);
+        x >>= 16;
+    }
+    top -= __popc(m);
+    if (act) {
+        // x / f through a float reciprocal: here x < f * 2^20, so the rounded estimate is within one of the
+        // quotient (three roundings of relative error 2^-24 each on a quotient below 2^20); the integer
+        // remainder check makes it exact
+        uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
+        int32_t r = (int32_t)(x - qt * f);
+        if (r < 0) { qt -= 1; r += (int32_t)f; }
+        if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
+        x = qt * kM + (uint32_t)r + c;
+    }
+}
+
 __global__ void __launch_bounds__(kRansEncWarps * 32)
     rans_encode_kernel(EncGeom G, EncScratch SC, uint32_t n_in_batch, const uint32_t *freq) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -727,9 +762,12 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     const uint32_t slot = q >> 1, st = q & 1u;
     uint32_t *sz = SC.sizes + (size_t)slot * 8;
     const uint32_t n = sz[1 + st];
+    const uint32_t apc = sz[7];  // active parents per stream: 8 ops each
+    const uint32_t first = st == 0 ? 0u : 8u * (apc & 0xFFFFu);             // the stream's first op in the brick
+    const uint32_t n_ops = st == 0 ? 8u * (apc & 0xFFFFu) : 8u * (apc >> 16);
+    const uint8_t *ops = SC.ops + (size_t)slot * G.ops_cap;  // 16-byte aligned, ops_cap a multiple of 16
     const uint32_t cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
     uint16_t *words = (st == 0 ? SC.w_int : SC.w_leaf) + (size_t)slot * cap;
-    const uint8_t *nib = st == 0 ? SC.nib_int + (size_t)slot * G.int_cap : SC.nib_leaf + (size_t)slot * G.leaf_cap;
     uint8_t *wsm = smem_raw + warp * kRansEncWin;
     const uint32_t *F = freq + 16 * st;
     const uint32_t f_reg = lane < 16 ? F[lane] : 1u;
@@ -737,44 +775,27 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     uint32_t c_reg = 0;
     for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < lane) ? F[s2] : 0u;
     const uint32_t K = lanes_for(n, G.K_max, G.S_min);
+    const uint32_t lt = lanemask_lt();
     uint32_t top = cap;
     if (n > 0) {
         uint32_t x = kL;
-        const uint32_t steps = (n + K - 1) / K;
+        const uint32_t steps = (n_ops + K - 1) / K;
         const uint32_t win_steps = (kRansEncWin - 16) / K;  // steps per staged window (16 bytes of alignment slack)
-        // windows of steps from the end: [s_lo, s_hi) covers symbols [s_lo*K, min(n, s_hi*K))
+        // windows of steps from the end: [s_lo, s_hi) covers ops [s_lo*K, min(n_ops, s_hi*K)) of the stream
         for (uint32_t s_hi = steps; s_hi > 0;) {
             const uint32_t s_lo = s_hi > win_steps ? s_hi - win_steps : 0u;
-            const uint32_t lo16 = (s_lo * K) & ~15u, sym_hi = min(n, s_hi * K);
+            const uint32_t lo16 = (first + s_lo * K) & ~15u, op_hi = first + min(n_ops, s_hi * K);
             __syncwarp();
-            for (uint32_t c16 = lane; lo16 + 16 * c16 < sym_hi; c16 += 32)
-                reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(nib + lo16) + c16);
+            for (uint32_t c16 = lane; lo16 + 16 * c16 < op_hi; c16 += 32)
+                reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(ops + lo16) + c16);
             __syncwarp();
             for (uint32_t s2 = s_hi; s2-- > s_lo;) {
                 const uint32_t i = s2 * K + lane;
-                const bool act = lane < K && i < n;
-                const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
-                const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
-                const float rf = __shfl_sync(kFull, rcp_reg, sym);
-                // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
-                const bool emit = act && x >= (f << 20);
-                const uint32_t m = __ballot_sync(kFull, emit);
-                if (emit) {
-                    words[top - __popc(m) + __popc(m & lanemask_lt())] = (uint16_t)(x & 0xFFFFu);
-                    x >>= 16;
-                }
-                top -= __popc(m);
-                if (act) {
-                    // x / f through a float reciprocal: here x < f * 2^20, so the estimate is within one of
-                    // the quotient; the integer remainder check makes it exact
-                    uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
-                    int32_t r = (int32_t)(x - qt * f);
-                    if (r < 0) { qt -= 1; r += (int32_t)f; }
-                    if (r < 0) { qt -= 1; r += (int32_t)f; }
-                    if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-                    if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-                    x = qt * kM + (uint32_t)r + c;
-                }
+                const bool act = lane < K && i < n_ops;
+                const uint32_t o = act ? (uint32_t)wsm[first + i - lo16] : 0u;
+                const bool pd = act && (o & 7u) == OP_PD;
+                if (__any_sync(kFull, pd)) rans_code_substep(x, top, words, o >> 4, pd, f_reg, c_reg, rcp_reg, kFull, lt);
+                rans_code_substep(x, top, words, o & 15u, act, f_reg, c_reg, rcp_reg, kFull, lt);
             }
             s_hi = s_lo;
         }
@@ -794,9 +815,9 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
 // rans_encode_kernel for bricks of 16^3 and smaller, whose streams have few states (K = 1..4 at the default
 // S_min): a warp takes kEpkSegs consecutive streams (16 at 16^3, 32 at 8^3 and smaller) and codes as many of
 // them at once as their K lanes fit in 32, each on its own run of lanes (its segment) with its own window of
-// staged nibbles; a step codes one symbol per lane of every stream that has steps left (the streams' steps
-// run from their ends, so shorter streams finish earlier).  Lanes 0..15 hold the interior table, lanes
-// 16..31 the leaf table.  Same words as rans_encode_kernel.
+// staged op bytes; a step codes, on every stream that has steps left, the deltas of its P_delta ops and then
+// its ops (the streams' steps run from their ends, so shorter streams finish earlier).  Lanes 0..15 hold the
+// interior table, lanes 16..31 the leaf table.  Same words as rans_encode_kernel.
 template <uint32_t kEpkSegs>  // streams per warp; each stream of a group stages kRansEncWin / kEpkSegs bytes
 __global__ void __launch_bounds__(kRansEncWarps * 32)
     rans_encode_packed(EncGeom G, EncScratch SC, uint32_t n_in_batch, const uint32_t *freq) {
@@ -843,15 +864,18 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
         const uint32_t seg = __popc(before), sb = before ? 32 - __clz(before) : 0u;
         const uint32_t q = __shfl_sync(kFull, my_q, mine ? seg : 0u);
         const uint32_t slot = q >> 1, st = q & 1u, j = lane - sb;
-        uint32_t n = 0, K = 1, cap = 0;
+        uint32_t n = 0, K = 1, cap = 0, first = 0, n_ops = 0;
         uint16_t *words = nullptr;
-        const uint8_t *nib = nullptr;
+        const uint8_t *ops = nullptr;
         if (mine) {
             n = SC.sizes[(size_t)slot * 8 + 1 + st];
             K = lanes_for(n, G.K_max, G.S_min);
             cap = (st == 0 ? G.int_cap : G.leaf_cap) + 64;
             words = (st == 0 ? SC.w_int : SC.w_leaf) + (size_t)slot * cap;
-            nib = st == 0 ? SC.nib_int + (size_t)slot * G.int_cap : SC.nib_leaf + (size_t)slot * G.leaf_cap;
+            const uint32_t apc = SC.sizes[(size_t)slot * 8 + 7];  // active parents per stream: 8 ops each
+            first = st == 0 ? 0u : 8u * (apc & 0xFFFFu);
+            n_ops = st == 0 ? 8u * (apc & 0xFFFFu) : 8u * (apc >> 16);
+            ops = SC.ops + (size_t)slot * G.ops_cap;  // 16-byte aligned
         }
         const uint32_t smask = mine ? (K >= 32 ? kFull : ((1u << K) - 1u) << sb) : 0u;
         // the window of a lone stream is the warp's whole area
@@ -859,8 +883,8 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
         uint8_t *wsm = wbase + (mine ? seg : 0u) * (kRansEncWin / kEpkSegs);
         const uint32_t win_steps = (win_bytes - 16) / K;  // steps per staged window (16 bytes of alignment slack)
         uint32_t x = kL, top = cap;
-        uint32_t s_hi = mine ? (n + K - 1) / K : 0u;  // steps left: the next step coded is s_hi - 1
-        uint32_t s_lo = s_hi, lo16 = 0;               // staged: steps [s_lo, s_hi of the window)
+        uint32_t s_hi = mine ? (n_ops + K - 1) / K : 0u;  // steps left: the next step coded is s_hi - 1
+        uint32_t s_lo = s_hi, lo16 = 0;                   // staged: steps [s_lo, s_hi of the window)
         for (;;) {
             const bool run = s_hi > 0;
             if (!__any_sync(kFull, run)) break;
@@ -868,38 +892,21 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
                 __syncwarp();
                 if (run && s_hi == s_lo) {
                     s_lo = s_hi > win_steps ? s_hi - win_steps : 0u;
-                    lo16 = (s_lo * K) & ~15u;
-                    const uint32_t sym_hi = min(n, s_hi * K);
-                    for (uint32_t c16 = j; lo16 + 16 * c16 < sym_hi; c16 += K)
-                        reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(nib + lo16) + c16);
+                    lo16 = (first + s_lo * K) & ~15u;
+                    const uint32_t op_hi = first + min(n_ops, s_hi * K);
+                    for (uint32_t c16 = j; lo16 + 16 * c16 < op_hi; c16 += K)
+                        reinterpret_cast<uint4 *>(wsm)[c16] = __ldcg(reinterpret_cast<const uint4 *>(ops + lo16) + c16);
                 }
                 __syncwarp();
             }
-            const uint32_t s2 = s_hi - 1, i = s2 * K + j;
-            const bool act = run && j < K && i < n;
-            const uint32_t sym = act ? (uint32_t)wsm[i - lo16] : 0u;
-            const uint32_t e = sym + 16 * st;  // entry of this stream's table
-            const uint32_t f = __shfl_sync(kFull, f_reg, e), c = __shfl_sync(kFull, c_reg, e);
-            const float rf = __shfl_sync(kFull, rcp_reg, e);
-            // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
-            const bool emit = act && x >= (f << 20);
-            const uint32_t m = __ballot_sync(kFull, emit) & smask;
-            if (emit) {
-                words[top - __popc(m) + __popc(m & lt)] = (uint16_t)(x & 0xFFFFu);
-                x >>= 16;
-            }
-            top -= __popc(m);
-            if (act) {
-                // x / f through a float reciprocal: here x < f * 2^20, so the estimate is within one of the
-                // quotient; the integer remainder check makes it exact
-                uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
-                int32_t r = (int32_t)(x - qt * f);
-                if (r < 0) { qt -= 1; r += (int32_t)f; }
-                if (r < 0) { qt -= 1; r += (int32_t)f; }
-                if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-                if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-                x = qt * kM + (uint32_t)r + c;
-            }
+            const uint32_t i = (s_hi - 1) * K + j;
+            const bool act = run && j < K && i < n_ops;
+            const uint32_t o = act ? (uint32_t)wsm[first + i - lo16] : 0u;
+            const bool pd = act && (o & 7u) == OP_PD;
+            // the deltas first, then the ops: the reverse of the decoder's order (entry 16 st + s of the tables)
+            if (__any_sync(kFull, pd))
+                rans_code_substep(x, top, words, (o >> 4) + 16 * st, pd, f_reg, c_reg, rcp_reg, smask, lt);
+            rans_code_substep(x, top, words, (o & 15u) + 16 * st, act, f_reg, c_reg, rcp_reg, smask, lt);
             if (run) s_hi--;
         }
         // final states ahead of the words, state 0 first, low half first
@@ -960,6 +967,42 @@ __global__ void __launch_bounds__(256) nibble_hist_kernel(EncGeom G, EncScratch 
     }
     __syncthreads();
     if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(counts + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
+// The same counts for bricks of 32^3 and larger, whose streams exist only as op bytes at this point: every op
+// byte counts its nibble (op | stop << 3), a P_delta also its delta nibble; ops before the interior op count
+// belong to the interior stream.  Per-warp histograms in shared memory.
+__global__ void __launch_bounds__(256) op_hist_kernel(EncGeom G, EncScratch SC, uint32_t stride,
+                                                      unsigned long long *counts) {
+    __shared__ uint32_t h[8][32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    h[warp][lane] = 0;
+    __syncthreads();
+    const uint32_t slot = blockIdx.x * stride;
+    const uint32_t apc = SC.sizes[(size_t)slot * 8 + 7];
+    const uint32_t n_int_ops = 8u * (apc & 0xFFFFu), n_ops = n_int_ops + 8u * (apc >> 16);
+    const uint4 *src = (const uint4 *)(SC.ops + (size_t)slot * G.ops_cap);
+    const uint32_t t0 = blockIdx.y * blockDim.x + threadIdx.x, step = kHistSplit * blockDim.x;
+    for (uint32_t i = t0; 16 * i < n_ops; i += step) {
+        const uint4 v = src[i];
+        const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (uint32_t k = 0; k < 16; k++) {
+            const uint32_t j = 16 * i + k;
+            if (j < n_ops) {
+                const uint32_t o = (wd[k >> 2] >> (8 * (k & 3u))) & 255u, part = j < n_int_ops ? 0u : 16u;
+                atomicAdd(&h[warp][part + (o & 15u)], 1u);
+                if ((o & 7u) == OP_PD) atomicAdd(&h[warp][part + (o >> 4)], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t c = 0;
+#pragma unroll
+        for (uint32_t w2 = 0; w2 < 8; w2++) c += h[w2][lane];
+        if (c) atomicAdd(counts + lane, (unsigned long long)c);
+    }
 }
 
 // Exclusive scan of per-brick sizes (palette labels, interior words, leaf words) of one batch into the
@@ -1205,6 +1248,7 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
     G.smem = enc_smem_bytes(G.up_nodes, G.lvl_bytes != 0);
     G.K_max = K_max;
     G.S_min = S_min;
+    G.nib = 0;
     return G;
 }
 
@@ -1263,7 +1307,8 @@ cudaError_t launch_nibble_hist(const EncGeom &G, const EncScratch &SC, uint32_t 
     if (sampled == 0) return cudaSuccess;
     {
         ProfScope ps("nibble_hist", st);
-        nibble_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
+        if (G.nib) nibble_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
+        else op_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
     }
     return cudaGetLastError();
 }

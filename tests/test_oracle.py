@@ -303,13 +303,39 @@ def _rand_freq(rng):
     return O.normalize(counts)
 
 
+def _stream(rng, n, p):
+    """n nibbles drawn from p, read as a stream (a P_delta op, op bits 5, is followed by its delta nibble);
+    a P_delta op drawn as the very last nibble would lack its delta, so it becomes a P_0 op."""
+    sym = rng.choice(16, size=n, p=p).astype(np.uint8)
+    i = 0
+    while i < n:
+        if (sym[i] & 7) == 5:
+            if i + 1 == n:
+                sym[i] ^= 1
+            i += 2
+        else:
+            i += 1
+    return sym
+
+
+def _state_counts(sym, K):
+    """symbols per state under R10: op j and the delta of a P_delta op j on state j mod K"""
+    n_k, i, j = [0] * K, 0, 0
+    while i < len(sym):
+        pd = (sym[i] & 7) == 5
+        n_k[j % K] += 2 if pd else 1
+        i += 2 if pd else 1
+        j += 1
+    return n_k
+
+
 def test_rans_roundtrip_random():
     rng = np.random.default_rng(5)
     for _ in range(150):
         f = _rand_freq(rng)
         n = int(rng.integers(1, 3000))
         p = f / f.sum()
-        sym = rng.choice(16, size=n, p=p).astype(np.uint8)
+        sym = _stream(rng, n, p)
         K = int(rng.integers(1, min(32, n) + 1))
         w = O.rans_encode(sym, K, f)
         dec, rc = O.rans_decode(w, n, K, f)
@@ -321,16 +347,17 @@ def test_rans_roundtrip_random():
 
 def test_rans_uniform_table_is_four_bits_per_symbol():
     # f_s = 256 for all s: every symbol costs exactly 4 bits, so each state emits one 16-bit word per 4 of its
-    # symbols and ends with a 32-bit flush: 2K + sum_k floor(n_k / 4) words (closed form)
+    # symbols and ends with a 32-bit flush: 2K + sum_k floor(n_k / 4) words (closed form), n_k the symbols
+    # of state k
     f = np.full(16, 256, np.uint32)
     rng = np.random.default_rng(9)
     for n in (1, 3, 4, 5, 17, 100, 1001):
         for K in (1, 2, 5, min(32, n)):
             if K > n:
                 continue
-            sym = rng.integers(0, 16, size=n).astype(np.uint8)
+            sym = _stream(rng, n, np.full(16, 1 / 16))
             w = O.rans_encode(sym, K, f)
-            n_k = [len(range(k, n, K)) for k in range(K)]
+            n_k = _state_counts(sym, K)
             assert len(w) == 2 * K + sum(x // 4 for x in n_k), (n, K)
 
 
@@ -340,7 +367,7 @@ def test_rans_code_length_against_entropy():
     for _ in range(30):
         f = _rand_freq(rng)
         n = int(rng.integers(2000, 20000))
-        sym = rng.choice(16, size=n, p=f / f.sum()).astype(np.uint8)
+        sym = _stream(rng, n, f / f.sum())
         K = int(rng.integers(1, 33))
         w = O.rans_encode(sym, K, f)
         bits = 16 * (len(w) - 2 * K)  # renormalisation words only
@@ -353,10 +380,13 @@ def test_rans_code_length_against_entropy():
         assert bits <= CE + 0.005 * n + 48 * K
 
 
-def test_rans_hand_derived_stream():
-    # R9/R10 worked by hand (tests/golden/tables/rans_uniform_k2.txt): lane i mod K, final states low half
-    # first and state 0 first, renormalisation words in decode order
-    g = _read_golden(os.path.join(TABLES, "rans_uniform_k2.txt"))
+@pytest.mark.parametrize("name", ["rans_uniform_k2", "rans_uniform_k2_delta_last", "rans_uniform_k2_delta_word"])
+def test_rans_hand_derived_stream(name):
+    # R9/R10 worked by hand (tests/golden/tables/): op j on state j mod K, a delta on its op's state, per
+    # step the ops then the deltas, final states low half first and state 0 first, renormalisation words in
+    # coding order; the second file ends on a step whose one op is a P_delta, the third places a delta's
+    # renormalisation word after that of the other state's op of its step
+    g = _read_golden(os.path.join(TABLES, name + ".txt"))
     sym = np.array(g["symbols"], np.uint8)
     f = np.array(g["freq"], np.uint32)
     w = O.rans_encode(sym, g["K"][0], f)
@@ -368,7 +398,7 @@ def test_rans_hand_derived_stream():
 def test_rans_detects_wrong_final_state():
     rng = np.random.default_rng(17)
     f = _rand_freq(rng)
-    sym = rng.choice(16, size=500, p=f / f.sum()).astype(np.uint8)
+    sym = _stream(rng, 500, f / f.sum())
     w = O.rans_encode(sym, 4, f)
     bad = w.copy(); bad[0] ^= 0x10  # perturb a final state
     dec, rc = O.rans_decode(bad, 500, 4, f)

@@ -40,9 +40,23 @@ MUTANTS = [
                                 "(uint32_t)words[2 * k + 1] | ((uint32_t)words[2 * k] << 16)")]),
     # R10: renormalisation words in the order they were emitted (the decoder reading them the same way)
     ("words_in_emit_order", [("words[2 * K + j] = emit[ne - 1 - j];", "words[2 * K + j] = emit[j];")]),
-    # R10: symbol i on state K-1 - i mod K, in encoder and decoder alike
-    ("lane_mapping_reversed", [("uint32_t k = i % K, s = sym[i];", "uint32_t k = K - 1 - i % K, s = sym[i];"),
-                               ("uint32_t k = i % K;", "uint32_t k = K - 1 - i % K;")]),
+    # R10: op j on state K-1 - j mod K, in encoder and decoder alike
+    ("op_state_reversed", [("cl[c++] = j - t0;", "cl[c++] = K - 1 - (j - t0);"),
+                           ("rans_decode_one(&x[k], freq, words, n_words, &pos, &op[k]);",
+                            "rans_decode_one(&x[K - 1 - k], freq, words, n_words, &pos, &op[k]);"),
+                           ("rans_decode_one(&x[k], freq, words, n_words, &pos, &dl[k]);",
+                            "rans_decode_one(&x[K - 1 - k], freq, words, n_words, &pos, &dl[k]);")]),
+    # R10: a delta coded right after its op instead of after the step's ops, in encoder and decoder alike
+    ("delta_right_after_its_op", [
+        ("for (uint32_t j = t0; j < t1; j++) { cs[c] = sym[op_at[j]]; cl[c++] = j - t0; }",
+         "for (uint32_t j = t0; j < t1; j++) { cs[c] = sym[op_at[j]]; cl[c++] = j - t0;"
+         " if ((sym[op_at[j]] & 7u) == OP_PD) { cs[c] = sym[op_at[j] + 1]; cl[c++] = j - t0; } }"),
+        ("            if ((sym[op_at[j]] & 7u) == OP_PD) { cs[c]", "            if (0) { cs[c]"),
+        ("if ((op[k] & 7u) == OP_PD) owed++;",
+         "if ((op[k] & 7u) == OP_PD && rc == ORC_OK) { rc = rans_decode_one(&x[k], freq, words, n_words, &pos,"
+         " &dl[k]); used++; }"),
+        ("            if ((op[k] & 7u) == OP_PD) {\n                if (used >= n)",
+         "            if (0) {\n                if (used >= n)")]),
 ]
 
 
