@@ -229,8 +229,8 @@ CSGV_API int csgv_count_bricks(const uint32_t *bricks_dev, uint32_t m, uint32_t 
  * offsets with n_bricks + 1 entries (u64), palettes (u32), interior and leaf
  * words (u16), symbol counts (u32, n_bricks).  *_capacity give the sizes of
  * pal_dev, int_words_dev and leaf_words_dev in elements.
- * Limits: at most 81 bricks of 32^3 (9 of 64^3, 647 of 16^3, 4954 of 8^3,
- * 25496 of 4^3, 49634 of 2^3) per call; larger volumes are rejected with
+ * Limits: at most 99 bricks of 32^3 (11 of 64^3, 790 of 16^3, 6004 of 8^3,
+ * 29025 of 4^3, 52101 of 2^3) per call; larger volumes are rejected with
  * CSGV_ERR_INVALID_ARG and a message.  totals[3] (host) receives the number of
  * palette labels, interior words and leaf words; if an output array is too
  * small the call returns CSGV_ERR_INVALID_ARG with totals filled and writes

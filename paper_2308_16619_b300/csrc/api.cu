@@ -442,7 +442,7 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
         off = (off + bytes + 255) & ~(size_t)255;
         return o;
     };
-    const size_t o_pal = take(C * G.pal_cap * 4), o_ni = take(C * G.int_cap), o_nl = take(C * G.leaf_cap);
+    const size_t o_pal = take(C * G.pal_cap * 4);
     const size_t o_wi = take(C * (G.int_cap + 64) * 2), o_wl = take(C * (G.leaf_cap + 64) * 2);
     const size_t o_sz = take(C * 8 * 4), o_rb = take(sizeof(Readback)), o_ops = take(C * G.ops_cap);
     const size_t o_lvl = take(C * G.lvl_bytes);
@@ -451,8 +451,6 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
     unsigned char *A = (unsigned char *)arena;
     csgv::EncScratch SC{};
     SC.pal = (uint32_t *)(A + o_pal);
-    SC.nib_int = A + o_ni;
-    SC.nib_leaf = A + o_nl;
     SC.w_int = (uint16_t *)(A + o_wi);
     SC.w_leaf = (uint16_t *)(A + o_wl);
     SC.sizes = (uint32_t *)(A + o_sz);

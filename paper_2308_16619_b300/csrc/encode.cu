@@ -124,11 +124,8 @@ __host__ __device__ inline uint32_t enc_level_bytes(uint32_t up_nodes) {
     return EncSmem::r16(up_nodes * 4) + EncSmem::r16(up_nodes) + EncSmem::r16(up_nodes * 2);
 }
 
-// phase D reuses the whole dynamic area as per-warp op staging, at least 512 bytes per warp
-constexpr uint32_t kStageMin = 512;
 __host__ __device__ inline uint32_t enc_smem_bytes(uint32_t up_nodes, bool levels_in_global) {
-    const uint32_t a = (levels_in_global ? 0u : enc_level_bytes(up_nodes)) + 64 * 4 + 256 * 8;
-    return a > kEncWarps * kStageMin ? a : kEncWarps * kStageMin;
+    return (levels_in_global ? 0u : enc_level_bytes(up_nodes)) + 64 * 4 + 256 * 8;
 }
 
 // exclusive block scan of one value per warp (warp totals in `red`), returns warp's offset and the total
@@ -503,7 +500,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     __syncthreads();
 
     // each warp takes a contiguous range of the op array in phases C and D
-    const uint32_t per = ((n_ops + (kT / 32) - 1) / (kT / 32) + 127) & ~127u;  // phase D: 128 ops per warp step
+    const uint32_t per = ((n_ops + (kT / 32) - 1) / (kT / 32) + 127) & ~127u;  // a multiple of 128 ops
     const uint32_t j0 = min(warp * per, n_ops), j1 = min(j0 + per, n_ops);
 
     // ---- C. palette pass in stream order: warp 0 walks the children no reuse fits, with the last 17 palette
@@ -601,7 +598,8 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     }
     __syncthreads();
 
-    // ---- D. nibble positions: an op's index in its stream plus the P_delta ops before it in that stream
+    // ---- D. symbol counts: a stream's ops plus its P_delta ops (each adds a delta nibble); in count mode (the
+    // frequency prepass) the nibbles themselves are counted.  The rANS kernels code the op bytes directly.
     uint32_t sym_tot[2];
     {
         const uint32_t *pdc = sh_pd;  // P_delta per warp range: counted by the walk, or here
@@ -619,74 +617,19 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             }
             __syncthreads();
         }
-        uint32_t bi = 0, bl = 0, toti = 0, totl = 0;
+        uint32_t toti = 0, totl = 0;
         for (uint32_t w2 = 0; w2 < (kT / 32); w2++) {
-            const uint32_t vi = pdc[w2], vl = pdc[(kT / 32) + w2];
-            bi += w2 < warp ? vi : 0u;
-            bl += w2 < warp ? vl : 0u;
-            toti += vi;
-            totl += vl;
+            toti += pdc[w2];
+            totl += pdc[(kT / 32) + w2];
         }
         sym_tot[0] = n_int_ops + toti;
         sym_tot[1] = n_ops - n_int_ops + totl;
-        // next nibble position of this warp's range in each stream: index in the stream plus the P_delta before
-        uint32_t oi = j0 + bi, ol = (j0 > n_int_ops ? j0 - n_int_ops : 0u) + bl;
-        uint8_t *nib_i = count ? nullptr : SC.nib_int + (size_t)slot * G.int_cap;
-        uint8_t *nib_l = count ? nullptr : SC.nib_leaf + (size_t)slot * G.leaf_cap;
-        // this warp's ops are staged in shared memory (the pyramid and lists are dead now), stage bytes at a
-        // time with 16-byte loads: one round trip to L2 instead of one per 32 ops.  Bricks of 32^3 and larger
-        // skip the scatter: rans_encode_kernel expands their op bytes itself.
-        const uint32_t stage = (G.smem / (kT / 32)) & ~(kStageMin - 1u);
-        uint8_t *stg = smem_raw + warp * stage;
-        const uint32_t jend = (count || G.nib) ? j1 : j0;
-        for (uint32_t js = j0; js < jend; js += stage) {
-            const uint32_t len = min(stage, j1 - js), nv = (len + 15u) >> 4;  // j0, js: multiples of 16
-            for (uint32_t q = lane; q < nv; q += 32) *(uint4 *)(stg + 16 * q) = *(const uint4 *)(ops + js + 16 * q);
-            __syncwarp();
-            // 4 consecutive ops per lane (groups never straddle the interior / leaf boundary, a multiple of 8);
-            // a lane emits one nibble per op plus the delta nibble of a P_delta, at consecutive positions found
-            // by a warp scan of the nibble counts (interior in the low half, leaf in the high half)
-            for (uint32_t g = js; g < js + len; g += 128) {
-                const uint32_t j = g + 4 * lane;
-                const uint32_t nin = j < js + len ? min(4u, js + len - j) : 0u;
-                const uint32_t w = nin ? *(const uint32_t *)(stg + (j - js)) : 0u;
-                const bool leaf = j >= n_int_ops;
-                uint32_t pdm = 0;
-#pragma unroll
-                for (uint32_t k = 0; k < 4; k++)
-                    pdm |= (k < nin && ((w >> (8 * k)) & 7u) == OP_PD) ? 1u << k : 0u;
-                const uint32_t outn = nin + __popc(pdm);
-                const uint32_t v = leaf ? outn << 16 : outn;
-                uint32_t incl = v;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t u = __shfl_up_sync(kFull, incl, d);
-                    if (lane >= (uint32_t)d) incl += u;
-                }
-                const uint32_t excl = incl - v, tot = __shfl_sync(kFull, incl, 31);
-                if (count) {
-#pragma unroll
-                    for (uint32_t k = 0; k < 4; k++)
-                        if (k < nin) {
-                            const uint32_t o = (w >> (8 * k)) & 255u;
-                            atomicAdd(&hist[16 * leaf + (o & 15u)], 1u);
-                            if ((pdm >> k) & 1u) atomicAdd(&hist[16 * leaf + (o >> 4)], 1u);
-                        }
-                } else if (nin) {
-                    uint8_t *nb = leaf ? nib_l + ol + (excl >> 16) : nib_i + oi + (excl & 0xFFFFu);
-#pragma unroll
-                    for (uint32_t k = 0; k < 4; k++)
-                        if (k < nin) {
-                            const uint32_t o = (w >> (8 * k)) & 255u;
-                            *nb++ = (uint8_t)(o & 15u);
-                            if ((pdm >> k) & 1u) *nb++ = (uint8_t)(o >> 4);
-                        }
-                }
-                oi += tot & 0xFFFFu;
-                ol += tot >> 16;
+        if (count)
+            for (uint32_t j = j0 + lane; j < j1; j += 32) {
+                const uint32_t o = ops[j], leaf = j >= n_int_ops ? 16u : 0u;
+                atomicAdd(&hist[leaf + (o & 15u)], 1u);
+                if ((o & 7u) == OP_PD) atomicAdd(&hist[leaf + (o >> 4)], 1u);
             }
-            __syncwarp();
-        }
     }
     if (count) {
         __syncthreads();
@@ -702,7 +645,9 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
     }
 }
 
-__global__ void __launch_bounds__(kEncThreads)
+// 4 CTAs per SM (64 registers): the compiler's own choice for this body, kept as a bound so that edits
+// elsewhere in it do not drop the kernel to 3 CTAs per SM
+__global__ void __launch_bounds__(kEncThreads, 4)
     encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
                   EncScratch SC, unsigned long long *count) {
     encode_brick<kEncThreads>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
@@ -923,55 +868,12 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     }
 }
 
-// Nibble counts (interior then leaf) of the bricks of a batch whose slot is a multiple of `stride`, from
-// the nibbles in scratch: the counts of the frequency prepass (Sec. 3.3), taken from an encode.  Grid
-// (sampled bricks, kHistSplit): each CTA counts a share of one brick's nibbles, 16 bytes per load.  Counts
-// are packed 8 bits per bin in four 64-bit words per thread (bins 0-7, 8-15 interior; 16-23, 24-31 leaf):
-// a thread sees at most 2 x 16 bytes of each stream for b <= 32, far below 255.
+// Nibble counts (interior then leaf) of the bricks of a batch whose slot is a multiple of `stride`: the counts
+// of the frequency prepass (Sec. 3.3), taken from an encode's op bytes.  Every op byte counts its nibble
+// (op | stop << 3), a P_delta also its delta nibble; the ops before the interior op count belong to the
+// interior stream.  Grid (sampled bricks, kHistSplit), 16 bytes per load, per-warp histograms in shared memory.
 constexpr uint32_t kHistSplit = 8;
 
-__device__ __forceinline__ void hist16(uint4 v, uint32_t nb, unsigned long long &lo, unsigned long long &hi) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (uint32_t k = 0; k < 16; k++) {
-        const uint32_t nib = (w[k >> 2] >> (8 * (k & 3))) & 15u;
-        const unsigned long long inc = k < nb ? 1ull << (8 * (nib & 7u)) : 0ull;
-        if (nib & 8u) hi += inc;
-        else lo += inc;
-    }
-}
-
-__global__ void __launch_bounds__(256) nibble_hist_kernel(EncGeom G, EncScratch SC, uint32_t stride,
-                                                          unsigned long long *counts) {
-    __shared__ uint32_t h[32];
-    if (threadIdx.x < 32) h[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t slot = blockIdx.x * stride;
-    const uint32_t *sz = SC.sizes + (size_t)slot * 8;
-    const uint32_t n_of[2] = {sz[1], sz[2]};
-    const uint4 *src[2] = {(const uint4 *)(SC.nib_int + (size_t)slot * G.int_cap),
-                           (const uint4 *)(SC.nib_leaf + (size_t)slot * G.leaf_cap)};
-    unsigned long long w[4] = {0, 0, 0, 0};
-    const uint32_t t0 = blockIdx.y * blockDim.x + threadIdx.x, step = kHistSplit * blockDim.x;
-#pragma unroll
-    for (int part = 0; part < 2; part++) {
-        const uint32_t n = n_of[part];
-        for (uint32_t i = t0; 16 * i < n; i += step)
-            hist16(src[part][i], min(16u, n - 16 * i), w[2 * part], w[2 * part + 1]);
-    }
-    const uint32_t lane = threadIdx.x & 31;
-#pragma unroll
-    for (uint32_t bin = 0; bin < 32; bin++) {
-        const uint32_t c = __reduce_add_sync(kFull, (uint32_t)(w[bin >> 3] >> (8 * (bin & 7))) & 255u);
-        if (lane == 0 && c) atomicAdd(&h[bin], c);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(counts + threadIdx.x, (unsigned long long)h[threadIdx.x]);
-}
-
-// The same counts for bricks of 32^3 and larger, whose streams exist only as op bytes at this point: every op
-// byte counts its nibble (op | stop << 3), a P_delta also its delta nibble; ops before the interior op count
-// belong to the interior stream.  Per-warp histograms in shared memory.
 __global__ void __launch_bounds__(256) op_hist_kernel(EncGeom G, EncScratch SC, uint32_t stride,
                                                       unsigned long long *counts) {
     __shared__ uint32_t h[8][32];
@@ -1242,19 +1144,18 @@ EncGeom make_geom(uint32_t N, uint32_t K_max, uint32_t S_min) {
     // array starts on a 16-byte boundary (phase D stages it with 16-byte loads)
     G.ops_cap = ((u + b3 - 1 > 256u ? u + b3 - 1 : 256u) + 15u) & ~15u;
     G.pal_cap = u + b3;             // palette: root + one per P_a
-    G.int_cap = (2 * (u - 1) + 2 + 15) & ~15u;  // interior nibbles (op + delta each), 16-byte pitch
+    G.int_cap = (2 * (u - 1) + 2 + 15) & ~15u;  // interior nibbles at most (op + delta each), 16-byte pitch
     G.leaf_cap = (2 * b3 + 15) & ~15u;
     G.lvl_bytes = N >= 6 ? enc_level_bytes(G.up_nodes) : 0u;  // b = 64: level arrays in global scratch
     G.smem = enc_smem_bytes(G.up_nodes, G.lvl_bytes != 0);
     G.K_max = K_max;
     G.S_min = S_min;
-    G.nib = 0;
     return G;
 }
 
 size_t scratch_bytes_per_brick(const EncGeom &G) {
-    return (size_t)G.pal_cap * 4 + G.int_cap + G.leaf_cap + (size_t)(G.int_cap + 64) * 2 +
-           (size_t)(G.leaf_cap + 64) * 2 + 8 * 4 + 64 + G.ops_cap + G.lvl_bytes;
+    return (size_t)G.pal_cap * 4 + (size_t)(G.int_cap + 64) * 2 + (size_t)(G.leaf_cap + 64) * 2 + 8 * 4 + 64 +
+           G.ops_cap + G.lvl_bytes;
 }
 
 cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, uint64_t stride, uint32_t n,
@@ -1307,8 +1208,7 @@ cudaError_t launch_nibble_hist(const EncGeom &G, const EncScratch &SC, uint32_t 
     if (sampled == 0) return cudaSuccess;
     {
         ProfScope ps("nibble_hist", st);
-        if (G.nib) nibble_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
-        else op_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
+        op_hist_kernel<<<dim3(sampled, kHistSplit), 256, 0, st>>>(G, SC, stride, counts);
     }
     return cudaGetLastError();
 }

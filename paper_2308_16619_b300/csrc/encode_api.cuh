@@ -10,24 +10,20 @@ struct EncGeom {
     uint32_t off[kMaxN + 2];  // offset of level l (1..N) in the level arrays (Morton order within a level)
     uint32_t up_nodes;        // sum over l >= 1 of (b>>l)^3
     uint32_t ops_cap;         // coded children at most: nodes - 1
-    uint32_t pal_cap, int_cap, leaf_cap;  // scratch capacities per brick (labels, nibbles, nibbles)
+    uint32_t pal_cap, int_cap, leaf_cap;  // per brick: palette labels, interior and leaf nibbles at most
     uint32_t smem;            // dynamic shared memory bytes
     uint32_t lvl_bytes;       // level arrays in global scratch per brick (b = 64), else 0
     uint32_t K_max, S_min;    // interleaving rule (R10)
-    uint32_t nib;             // 1: phase D scatters nibbles for rans_encode_packed (b <= 16); 0: rans_encode_kernel
-                              // expands the op bytes itself (b >= 32)
 };
 
 // per-brick scratch of one encode batch of C bricks
 struct EncScratch {
     uint32_t *pal;      // C x pal_cap
-    uint8_t *nib_int;   // C x int_cap (nibbles, b <= 16 only)
-    uint8_t *nib_leaf;  // C x leaf_cap (nibbles, b <= 16 only)
     uint16_t *w_int;    // C x (int_cap + 64)
     uint16_t *w_leaf;   // C x (leaf_cap + 64)
     uint32_t *sizes;    // C x 8: n_pal, n_int_sym, n_leaf_sym, n_int_words, n_leaf_words, int_start, leaf_start,
                         // interior op count / 8 | leaf op count / 8 << 16
-    uint8_t *ops;       // C x ops_cap: op bytes of the brick in stream order (encode kernel only)
+    uint8_t *ops;       // C x ops_cap: op bytes (op | stop << 3 | delta << 4) of the brick in stream order
     uint8_t *lvl;       // C x lvl_bytes: level arrays (b = 64 only)
 };
 

@@ -13,8 +13,8 @@
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes
 // (32 MiB), present on every GPU that loads the library until the process
 // exits.  It holds the per-brick buffers of the encoder, so a call accepts at
-// most a fixed number of bricks (b = 64: 9, b = 32: 81, b = 16: 647, b = 8: 4954,
-// b = 4: 25496, b = 2: 49634) and rejects larger volumes with
+// most a fixed number of bricks (b = 64: 11, b = 32: 99, b = 16: 790, b = 8: 6004,
+// b = 4: 29025, b = 2: 52101) and rejects larger volumes with
 // CSGV_ERR_INVALID_ARG.  Every call shares the array and it keeps the last
 // call's contents: the counters that must start at zero are cleared at the
 // start of each call, and two calls whose work overlaps on the GPU (different
@@ -59,7 +59,6 @@ size_t carve(const csgv::EncGeom &G, size_t C, unsigned char *base, csgv::EncScr
     };
     unsigned char *f = take(32 * 4), *t = take(3 * 8), *m = take(3 * 4);
     unsigned char *sz = take(C * 8 * 4), *pal = take(C * G.pal_cap * 4);
-    unsigned char *ni = take(C * G.int_cap), *nl = take(C * G.leaf_cap);
     unsigned char *wi = take(C * (G.int_cap + 64) * 2), *wl = take(C * (G.leaf_cap + 64) * 2);
     unsigned char *op = take(C * G.ops_cap), *lv = take(C * G.lvl_bytes);
     if (base) {
@@ -68,8 +67,6 @@ size_t carve(const csgv::EncGeom &G, size_t C, unsigned char *base, csgv::EncScr
         *maxpal = (uint32_t *)m;
         SC->sizes = (uint32_t *)sz;
         SC->pal = (uint32_t *)pal;
-        SC->nib_int = ni;
-        SC->nib_leaf = nl;
         SC->w_int = (uint16_t *)wi;
         SC->w_leaf = (uint16_t *)wl;
         SC->ops = op;

@@ -67,17 +67,17 @@ def test_noalloc_encoder_rejects_volumes_beyond_its_scratch():
     import torch
     import paper_2308_16619_b300 as csgv
 
-    big = torch.zeros((128, 128, 192), dtype=torch.int32, device="cuda")  # 96 bricks of 32^3 > 81
+    big = torch.zeros((224, 128, 128), dtype=torch.int32, device="cuda")  # 112 bricks of 32^3 > 99
     table = csgv.FreqTable()
     for i in range(32):
         table.freq[i] = 256
-    off = torch.empty(97, dtype=torch.int64, device="cuda")
-    small = torch.empty(96, dtype=torch.int32, device="cuda")
+    off = torch.empty(113, dtype=torch.int64, device="cuda")
+    small = torch.empty(112, dtype=torch.int32, device="cuda")
     rc, _ = csgv.csgv_encode_bricks_noalloc(big, 32, table, off, small, off.clone(), small.view(torch.int16),
                                             off.clone(), small.view(torch.int16), small.clone(), small.clone())
     assert rc == csgv.CSGV_ERR_INVALID_ARG
     msg = csgv.lib().csgv_last_error().decode()
-    assert "96 bricks" in msg and "at most 81" in msg
+    assert "112 bricks" in msg and "at most 99" in msg
     # output arrays that are too small are refused once the sizes are known, with the sizes reported
     vol = torch.zeros((64, 64, 64), dtype=torch.int32, device="cuda")
     vol[:, :, 17:] = 5
