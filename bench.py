@@ -271,7 +271,8 @@ def measure_cells1024(args, steps, warmup):
     out = torch.empty(total, dtype=torch.int32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
     out_bytes = total * 4
-    # the autotuner picks the workspace size and rANS kernel occupancy for this batch
+    # the autotuner picks the launch shape for this batch (rANS ring depth and CTAs per SM, threads per LOD 0 and
+    # LOD 1 request, workspace per slice)
     tune = csgv.csgv_decode_autotune(v, ids, lods, out, offs, status)
     # per-kernel times from CUDA events around each launch (direct calls)
     csgv.profile_read()
@@ -327,9 +328,7 @@ def measure_cells1024(args, steps, warmup):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "cells1024 1024^3 packed ellipsoids, b=32, 60000 requests LOD 0..5",
                        "step": "one batched decode (CUDA graph replay)", "decoded_bytes": out_bytes,
-                       "K_max": args.k_max, "autotuned": {"workspace_bytes": tune.workspace_bytes,
-                                                          "rans_ctas_per_sm": tune.rans_ctas_per_sm,
-                                                          "ms": tune.ms},
+                       "K_max": args.k_max, "autotuned": tune.as_dict(),
                        "S_min": args.s_min, "l2": "outputs (1.5 GB) larger than L2"},
             "voxels_per_s": out_bytes / 4 / (ms / 1e3), "encode_ms_once": enc_ms,
             "plain_decode_gbs_2048": plain_gbs, "batched_vs_plain": (out_bytes / (ms / 1e3) / 1e9) / plain_gbs,

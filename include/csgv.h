@@ -385,25 +385,44 @@ CSGV_API int csgv_volume_destroy_async(csgv_volume *vol, void *stream);
 CSGV_API int csgv_volume_leaves_to_host(csgv_volume *vol);
 CSGV_API int csgv_volume_leaves_to_device(csgv_volume *vol);
 
-/* A decode configuration of a volume (csgv_decode_autotune). */
+/*
+ * The launch shape of a volume's decodes (csgv_decode_autotune picks it; it
+ * changes speed only, never the decoded labels).  Defaults: 192 MiB, 4, 512,
+ * 128, 128 (the fastest point for 4096 LOD 0 requests of 32^3 bricks).
+ */
 typedef struct csgv_decode_tuning {
     uint64_t workspace_bytes;  /* op-record workspace per slice of requests (more: fewer, larger slices) */
-    uint32_t rans_ctas_per_sm; /* CTAs (8 warps each) per SM of the rANS record kernel (4 or 5) */
-    uint32_t pad;
-    double ms;                 /* measured time of the batch with this configuration */
+    uint32_t rans_ctas_per_sm; /* CTAs (8 warps each) per SM of the rANS record kernel: 4, 5 or 6 */
+    uint32_t ring_words;       /* stream words each rANS warp stages in shared memory: 128, 256 or 512
+                                  (512 allows at most 5 CTAs per SM) */
+    uint32_t rebuild_threads;  /* threads (warps x 32) per LOD 0 request of a 32^3 brick: 128 or 256 */
+    uint32_t medium_threads;   /* threads per LOD 1 request of a 32^3 brick in batches of 8192 or more
+                                  requests: 64, 128 or 256 */
+    double ms;                 /* measured time of the batch with this configuration (autotune only) */
 } csgv_decode_tuning;
 
 /*
- * Autotuner (batching at scale): time candidate decode configurations on this
- * batch (workspace 64 MiB .. 1 GiB per slice x rANS kernel 4 or 5 CTAs per SM;
- * one warm-up and two timed runs each, CUDA events on the stream), keep the
- * fastest in the volume for later csgv_decode_bricks calls, and return it in
- * *best.  The batch's outputs are written (by every run).  Synchronises the
- * stream.  The paper has no counterpart.
+ * Autotuner (batching at scale): time decode configurations on this batch and
+ * keep the fastest in the volume for later csgv_decode_bricks calls; *best
+ * receives it.  One knob at a time, each from the best point so far: rANS ring
+ * depth x CTAs per SM, threads per LOD 0 request, threads per LOD 1 request,
+ * workspace per slice (64 MiB .. 1 GiB); each point is timed as the median of
+ * five runs after a warm-up run (CUDA events on the stream).  The batch's
+ * outputs are written by every run.  Synchronises the stream.  The paper has
+ * no counterpart (it names work queues and batching as future work, Sec. 4.3).
  */
 CSGV_API int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
                                   uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream,
                                   csgv_decode_tuning *best);
+
+/*
+ * Read or set a volume's decode configuration (for instance one found by an
+ * earlier autotune).  csgv_decode_set_tuning checks every field against the
+ * values listed above (CSGV_ERR_INVALID_ARG otherwise; t->ms is ignored) and
+ * applies to decodes issued after it returns.  No counterpart in the paper.
+ */
+CSGV_API int csgv_decode_get_tuning(const csgv_volume *vol, csgv_decode_tuning *t);
+CSGV_API int csgv_decode_set_tuning(csgv_volume *vol, const csgv_decode_tuning *t);
 
 /*
  * Kernel timing (measurement aid; the paper has no counterpart).  While

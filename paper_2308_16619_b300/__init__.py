@@ -21,6 +21,7 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
            "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune",
+           "csgv_decode_get_tuning", "csgv_decode_set_tuning",
            "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device",
            "csgv_encode_bricks_sampled", "csgv_volume_destroy_async", "csgv_stream_encoder_create",
            "csgv_stream_encoder_add", "csgv_stream_encoder_finish", "csgv_stream_encoder_destroy",
@@ -59,8 +60,11 @@ class Result(C.Structure):
 
 
 class DecodeTuning(C.Structure):
-    _fields_ = [("workspace_bytes", C.c_uint64), ("rans_ctas_per_sm", C.c_uint32), ("pad", C.c_uint32),
-                ("ms", C.c_double)]
+    _fields_ = [("workspace_bytes", C.c_uint64), ("rans_ctas_per_sm", C.c_uint32), ("ring_words", C.c_uint32),
+                ("rebuild_threads", C.c_uint32), ("medium_threads", C.c_uint32), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Camera(C.Structure):
@@ -86,6 +90,8 @@ def lib():
         L = C.CDLL(LIB_PATH)
         vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
         L.csgv_decode_autotune.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, C.POINTER(DecodeTuning)]
+        L.csgv_decode_get_tuning.argtypes = [vp, C.POINTER(DecodeTuning)]
+        L.csgv_decode_set_tuning.argtypes = [vp, C.POINTER(DecodeTuning)]
         L.csgv_volume_leaves_to_host.argtypes = [vp]
         L.csgv_encode_bricks_sampled.argtypes = [vp, vp, u32, u32, C.POINTER(Config), C.POINTER(FreqTable),
                                                  C.POINTER(vp), vp]
@@ -262,6 +268,17 @@ def csgv_decode_autotune(volume, brick_ids, lods, out, out_offsets, status, stre
     _check(lib().csgv_decode_autotune(volume.handle, _ptr(brick_ids), _ptr(lods), n, _ptr(out), _ptr(out_offsets),
                                       _ptr(status), _stream(stream), C.byref(best)))
     return best
+
+
+def csgv_decode_get_tuning(volume):
+    t = DecodeTuning()
+    _check(lib().csgv_decode_get_tuning(volume.handle, C.byref(t)))
+    return t
+
+
+def csgv_decode_set_tuning(volume, tuning):
+    """Set the volume's decode launch shape (a DecodeTuning); raises on values out of range."""
+    _check(lib().csgv_decode_set_tuning(volume.handle, C.byref(tuning)))
 
 
 def csgv_decode_bricks_plain(volume, brick_ids, lods, out, out_offsets, status, stream=None):

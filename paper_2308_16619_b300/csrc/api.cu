@@ -15,7 +15,7 @@
 // kernels' launchers (decode.cu, encode.cu)
 namespace csgv {
 cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob &J, uint32_t *out, const uint64_t *out_off,
-                                int32_t *status, uint32_t rec_blocks, cudaStream_t st);
+                                int32_t *status, const DecodeShape &S, cudaStream_t st);
 }  // namespace csgv
 
 #include "encode_api.cuh"
@@ -34,7 +34,7 @@ struct csgv_volume {
     uint32_t max_int_sym, max_leaf_sym;  // largest per-brick symbol counts: size the decode workspace
     uint16_t *leaf_host = nullptr;        // leaf words in mapped host memory (csgv_volume_leaves_to_host)
     uint64_t dec_ws_bytes = 192ull << 20;  // decode configuration (csgv_decode_autotune)
-    uint32_t dec_rec_per_sm = 5;
+    csgv::DecodeShape dec_shape;
     cudaEvent_t ready = nullptr;  // recorded when the arrays are complete on the stream that made them
 };
 
@@ -763,8 +763,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
         J.n = (uint32_t)std::min<uint64_t>(S, n - r0);
         J.ids = ids + r0;
         J.lods = lods + r0;
-        e = csgv::launch_decode_slice(dev_view(v), v->max_palette, J, out, off + r0, status + r0,
-                                      v->dec_rec_per_sm * (uint32_t)sms, st);
+        e = csgv::launch_decode_slice(dev_view(v), v->max_palette, J, out, off + r0, status + r0, v->dec_shape, st);
     }
     cudaError_t ef = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
@@ -828,6 +827,49 @@ int csgv_volume_leaves_to_device(csgv_volume *v) {
     return CSGV_OK;
 }
 
+namespace {
+csgv_decode_tuning tuning_of(const csgv_volume *v) {
+    csgv_decode_tuning t{};
+    t.workspace_bytes = v->dec_ws_bytes;
+    t.rans_ctas_per_sm = v->dec_shape.rec_per_sm;
+    t.ring_words = v->dec_shape.ring_words;
+    t.rebuild_threads = v->dec_shape.leafc_threads;
+    t.medium_threads = v->dec_shape.medium_threads;
+    t.ms = 0.0;
+    return t;
+}
+bool tuning_valid(const csgv_decode_tuning &t) {
+    return t.workspace_bytes >= (1ull << 20) && t.rans_ctas_per_sm >= 4 && t.rans_ctas_per_sm <= 6 &&
+           (t.ring_words == 128 || t.ring_words == 256 || t.ring_words == 512) &&
+           (t.rebuild_threads == 128 || t.rebuild_threads == 256) &&
+           (t.medium_threads == 64 || t.medium_threads == 128 || t.medium_threads == 256) &&
+           !(t.ring_words == 512 && t.rans_ctas_per_sm == 6);  // 6 x 40 KB of shared memory do not fit an SM
+}
+void apply_tuning(csgv_volume *v, const csgv_decode_tuning &t) {
+    v->dec_ws_bytes = t.workspace_bytes;
+    v->dec_shape.rec_per_sm = t.rans_ctas_per_sm;
+    v->dec_shape.ring_words = t.ring_words;
+    v->dec_shape.leafc_threads = t.rebuild_threads;
+    v->dec_shape.medium_threads = t.medium_threads;
+}
+}  // namespace
+
+int csgv_decode_get_tuning(const csgv_volume *vol, csgv_decode_tuning *t) {
+    if (!vol || !t) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    *t = tuning_of(vol);
+    return CSGV_OK;
+}
+
+int csgv_decode_set_tuning(csgv_volume *vol, const csgv_decode_tuning *t) {
+    if (!vol || !t) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
+    if (!tuning_valid(*t))
+        return fail(CSGV_ERR_INVALID_ARG, "decode tuning out of range (workspace %llu B, %u rANS CTAs per SM, ring %u "
+                    "words, rebuild %u threads, LOD 1 kernel %u threads)", (unsigned long long)t->workspace_bytes,
+                    t->rans_ctas_per_sm, t->ring_words, t->rebuild_threads, t->medium_threads);
+    apply_tuning(vol, *t);
+    return CSGV_OK;
+}
+
 int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const uint8_t *lods_dev, uint32_t n,
                          uint32_t *out_dev, const uint64_t *out_offsets_dev, int32_t *status_dev, void *stream,
                          csgv_decode_tuning *best) {
@@ -835,10 +877,7 @@ int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const 
     if (rc) return rc;
     if (!best) return fail(CSGV_ERR_INVALID_ARG, "NULL output");
     cudaStream_t st = (cudaStream_t)stream;
-    csgv_decode_tuning b{};
-    b.ms = 1e30;
-    b.workspace_bytes = vol->dec_ws_bytes;
-    b.rans_ctas_per_sm = vol->dec_rec_per_sm;
+    csgv_decode_tuning b = tuning_of(vol);
     if (n == 0) {
         *best = b;
         return CSGV_OK;
@@ -846,33 +885,44 @@ int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const uint64_t ws[] = {64ull << 20, 192ull << 20, 512ull << 20, 1024ull << 20};
-    const uint32_t rec[] = {4, 5};
-    for (uint64_t w : ws)
-        for (uint32_t r : rec) {
-            vol->dec_ws_bytes = w;
-            vol->dec_rec_per_sm = r;
-            float t_min = 1e30f;
-            for (int k = 0; k < 3 && rc == CSGV_OK; k++) {
-                cudaEventRecord(e0, st);
-                rc = decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, false, st);
-                cudaEventRecord(e1, st);
-                float t = 0.f;
-                if (rc == CSGV_OK && cudaEventSynchronize(e1) == cudaSuccess &&
-                    cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && k > 0)
-                    t_min = std::min(t_min, t);
-            }
-            if (rc != CSGV_OK) break;
-            if (t_min < b.ms) {
-                b.ms = t_min;
-                b.workspace_bytes = w;
-                b.rans_ctas_per_sm = r;
-            }
+    // median of kRuns timed runs after one warm-up run of the candidate
+    constexpr int kRuns = 5;
+    auto time_of = [&](const csgv_decode_tuning &t, double &ms) {
+        apply_tuning(vol, t);
+        float v[kRuns];
+        for (int k = 0; k <= kRuns && rc == CSGV_OK; k++) {
+            cudaEventRecord(e0, st);
+            rc = decode_range(vol, brick_ids_dev, lods_dev, n, out_dev, out_offsets_dev, status_dev, false, st);
+            cudaEventRecord(e1, st);
+            float x = 0.f;
+            if (rc == CSGV_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
+                rc = fail(CSGV_ERR_CUDA, "autotune timing failed");
+            if (k > 0) v[k - 1] = x;
         }
+        std::sort(v, v + kRuns);
+        ms = v[kRuns / 2];
+    };
+    // one knob at a time, each search starting from the best point so far: the rANS kernel's ring depth and
+    // CTAs per SM, the rebuild's threads per request (warps per brick) for LOD 0 and for LOD 1 requests,
+    // then the workspace per slice (the number of slices)
+    time_of(b, b.ms);
+    auto search = [&](auto set, std::initializer_list<uint32_t> vals) {
+        for (uint32_t x : vals) {
+            csgv_decode_tuning c = b;
+            set(c, x);
+            if (!tuning_valid(c) || rc != CSGV_OK) continue;
+            time_of(c, c.ms);
+            if (rc == CSGV_OK && c.ms < b.ms) b = c;
+        }
+    };
+    for (uint32_t ring : {128u, 256u, 512u})
+        search([&](csgv_decode_tuning &c, uint32_t x) { c.ring_words = ring; c.rans_ctas_per_sm = x; }, {4u, 5u, 6u});
+    search([](csgv_decode_tuning &c, uint32_t x) { c.rebuild_threads = x; }, {128u, 256u});
+    search([](csgv_decode_tuning &c, uint32_t x) { c.medium_threads = x; }, {64u, 128u, 256u});
+    search([](csgv_decode_tuning &c, uint32_t x) { c.workspace_bytes = (uint64_t)x << 20; }, {64u, 192u, 512u, 1024u});
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    vol->dec_ws_bytes = b.workspace_bytes;
-    vol->dec_rec_per_sm = b.rans_ctas_per_sm;
+    apply_tuning(vol, b);
     if (rc) return rc;
     *best = b;
     return CSGV_OK;

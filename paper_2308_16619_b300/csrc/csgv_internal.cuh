@@ -93,6 +93,14 @@ __host__ __device__ inline uint32_t lanes_for(uint32_t n, uint32_t K_max, uint32
     return k;
 }
 
+// Launch shape of a decode (csgv_decode_autotune searches it; kept per volume)
+struct DecodeShape {
+    uint32_t rec_per_sm = 4;        // rANS record kernel: CTAs of 8 warps per SM (4..6)
+    uint32_t ring_words = 512;      // rANS record kernel: stream words staged per warp (128, 256, 512)
+    uint32_t leafc_threads = 128;   // 32^3 bricks, compact leaf layout: threads per request (128, 256)
+    uint32_t medium_threads = 128;  // 32^3 bricks, LOD 1 requests of large mixed batches (64, 128, 256)
+};
+
 // Kernel timing (csgv_profile_*): while enabled, a ProfScope around a launch records CUDA events on the
 // launching stream before and after it (api.cu keeps the records).
 // Events come from a per-device free list that csgv_profile_read refills, so that timing a launch costs

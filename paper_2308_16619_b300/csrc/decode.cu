@@ -38,8 +38,7 @@ namespace csgv {
 namespace {
 
 constexpr uint32_t kRecBad = 0x80000000u;
-constexpr uint32_t kWinWords = 256;   // staged stream words per warp (uint16)
-constexpr uint32_t kRecWarps = 8;     // rans_records: warps per CTA (8-warp CTAs, 5 per SM: no register cap below 51)
+constexpr uint32_t kRecWarps = 8;     // rans_records: warps per CTA (8-warp CTAs, 4 to 6 per SM)
 constexpr uint32_t kRbThreads = 256;  // rebuild: threads per CTA
 constexpr uint32_t kRbWarps = kRbThreads / 32;
 
@@ -63,12 +62,13 @@ __device__ __forceinline__ uint32_t lt_of(uint32_t lane) { return (1u << lane) -
 // count is not stored: in the stream's last steps (fewer than 2K symbols left) a lane decodes an op only if
 // its op and the deltas owed by the lanes before it still fit in the symbols left.
 //
-// The stream's words are staged in a ring of kWinWords words in shared memory (word a, counted from the
-// 16-byte boundary at or below the stream's start, sits at a % kWinWords), refilled half a ring at a time
+// The stream's words are staged in a ring of kWin words in shared memory (word a, counted from the
+// 16-byte boundary at or below the stream's start, sits at a % kWin), refilled half a ring at a time
 // with 16-byte loads that stay inside the stream's 16-byte chunks.  A malformed stream may read stale
 // ring words, never memory outside the ring; the final check (every word read, every state back at L)
 // rejects it.  The P_a count before every 8th record only changes at a P_a record, so the counts are
 // written in runs: the steps without P_delta / P_a write only their records.
+template <uint32_t kWin>  // ring words per warp: 128, 256 or 512 (a step reads at most 64)
 __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t n_sym, uint32_t K_max,
                                   uint32_t S_min, const uint32_t *lut, uint16_t *win, uint8_t *rec, uint16_t *t8,
                                   uint64_t cap, uint32_t need, uint32_t lane) {
@@ -78,7 +78,8 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     }
     const uint32_t K = lanes_for(n_sym, K_max, S_min);
     if (n_sym > cap || n_words < 2 * K) return kRecBad;
-    constexpr uint32_t kRingChunks = kWinWords / 8, kHalf = kRingChunks / 2;
+    static_assert(kWin >= 128 && (kWin & (kWin - 1)) == 0, "half a ring must hold a step's 64 words");
+    constexpr uint32_t kRingChunks = kWin / 8, kHalf = kRingChunks / 2;
     const uint32_t lt = lanemask_lt();
     const uintptr_t g0 = reinterpret_cast<uintptr_t>(w) & ~(uintptr_t)15;
     const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(w) - g0) >> 1;  // words before the stream (0..7)
@@ -86,7 +87,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     const uint4 *src = reinterpret_cast<const uint4 *>(g0);
     uint4 *ring = reinterpret_cast<uint4 *>(win);
     __syncwarp();  // the previous stream's reads of the ring are done
-    if (lane < n_chunks) ring[lane] = __ldg(src + lane);
+    for (uint32_t c = lane; c < kRingChunks && c < n_chunks; c += 32) ring[c] = __ldg(src + c);
     // a step reads at most 2K <= 64 words: refill once pos passes lim
     uint32_t filled = kRingChunks;  // chunks staged so far
     uint32_t lim = filled < n_chunks ? 8 * filled - 64 : 0xFFFFFFFFu;
@@ -116,7 +117,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
             const uint32_t xn2 = ((e2 >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e2 >> 17);
             const bool nrm2 = pd && xn2 < kL;
             const uint32_t m2 = __ballot_sync(kFull, nrm2);
-            const uint32_t wv2 = win[(pos + __popc(m2 & lt)) % kWinWords];
+            const uint32_t wv2 = win[(pos + __popc(m2 & lt)) % kWin];
             x = pd ? (nrm2 ? ((xn2 << 16) | wv2) : xn2) : x;
             pos += __popc(m2);
         }
@@ -141,7 +142,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
         const uint32_t xn = ((e >> 4) & 0x1FFFu) * (x >> kScaleBits) + (e >> 17);
         const bool nrm = actK && xn < kL;
         const uint32_t m = __ballot_sync(kFull, nrm);
-        const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
+        const uint32_t wv = win[(pos + __popc(m & lt)) % kWin];
         x = nrm ? ((xn << 16) | wv) : xn;  // lanes >= K: never read
         pos += __popc(m);
         if (__ballot_sync(kFull, actK && (sym & 7u) >= OP_PD)) {  // a P_delta or P_a (or 7)
@@ -169,7 +170,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
         const bool act = lane < n;
         const bool nrm = act && xn < kL;
         const uint32_t m = __ballot_sync(kFull, nrm);
-        const uint32_t wv = win[(pos + __popc(m & lt)) % kWinWords];
+        const uint32_t wv = win[(pos + __popc(m & lt)) % kWin];
         x = act ? (nrm ? ((xn << 16) | wv) : xn) : x;
         pos += __popc(m);
         general(sym, act, n);
@@ -184,14 +185,15 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     return ok ? otail : (otail | kRecBad);
 }
 
-__global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records(VolDev V, RecJob J) {
+template <uint32_t kWin>
+__global__ void __launch_bounds__(kRecWarps * 32, 6) rans_records(VolDev V, RecJob J) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *lut_s = (uint32_t *)smem;
     for (uint32_t i = threadIdx.x; i < 2 * kM / 4; i += blockDim.x)
         ((uint4 *)lut_s)[i] = __ldg((const uint4 *)V.lut + i);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint16_t *win = (uint16_t *)(smem + 2 * kM * 4) + warp * kWinWords;
+    uint16_t *win = (uint16_t *)(smem + 2 * kM * 4) + warp * kWin;
     for (;;) {
         uint32_t q = 0;
         if (lane == 0) q = atomicAdd(J.counter, 1u);
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kRecWarps * 32, 5) rans_records(VolDev V, RecJ
         const uint64_t cap = s ? J.t8_at - J.leaf_at : J.leaf_at;  // the records' room: 8 * (t8 entries - 1)
         // LOD t >= 2 uses the interior levels N-1 .. t only: at most 8 records per node of levels N .. t+1
         const uint32_t need = (s == 0 && t >= 2) ? 8u * (((1u << (3 * (V.N - t))) - 1u) / 7u) : 0xFFFFFFFFu;
-        const uint32_t r = decode_stream((s ? V.leaf_words : V.int_words) + w0, n_words, n_sym, V.K_max, V.S_min,
+        const uint32_t r = decode_stream<kWin>((s ? V.leaf_words : V.int_words) + w0, n_words, n_sym, V.K_max, V.S_min,
                                          lut_s + s * kM, win, rec, t8, cap, need, lane);
         if (lane == 0) J.info[2 * i + s] = r;
     }
@@ -996,7 +998,7 @@ __device__ __forceinline__ void store_leaf_compact(uint8_t *smem, const RbLayout
                                                    uint32_t pal_reg, const uint32_t *pal_s, const uint32_t *pal,
                                                    uint32_t np) {
     typedef uint8_t IdxT;
-    static_assert(kT == 128, "one z-layer pair of 32^3 units per pass of the CTA");
+    static_assert(kT % 128 == 0, "whole z-layer pairs of 32^3 units per pass of the CTA");
     const IdxT *P = (const IdxT *)(smem + Ly.lev) - Ly.lev_shift + lev_off(N, 1);
     const uint32_t *cw = (const uint32_t *)(smem + Ly.cm + cm_off(N, 1));
     const uint16_t *rk = (const uint16_t *)(smem + Ly.rk);
@@ -1220,7 +1222,6 @@ __global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev 
 // where a 256-thread CTA with the full 51 KB layout ran 4 per SM.  The three kernels are persistent (see
 // rebuild_list).
 constexpr uint32_t kRbCoarseThreads = 64;
-constexpr uint32_t kRbMediumThreads = 128;
 constexpr uint32_t kSplitMin = 8192;  // requests per slice from which the split pays for its extra launches
 
 // one atomic per warp and class (a warp's requests of a class take consecutive list entries)
@@ -1271,13 +1272,13 @@ __global__ void __launch_bounds__(kRbThreads) rebuild_listed(VolDev V, RecJob J,
     rebuild_list<IdxT, kRbThreads, 0>(V, J, out, out_off, status, list, count, next, smem);
 }
 
-template <typename IdxT>
-__global__ void __launch_bounds__(kRbMediumThreads, 14) rebuild_medium(VolDev V, RecJob J, uint32_t *__restrict__ out,
+template <typename IdxT, uint32_t kT>  // kT: 64, 128 (default) or 256 threads, the autotuner's choice
+__global__ void __launch_bounds__(kT, kT == 64 ? 16 : 1792 / kT) rebuild_medium(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                                   const uint64_t *__restrict__ out_off,
                                                                   int32_t *__restrict__ status, const uint32_t *list,
                                                                   const uint32_t *count, uint32_t *next) {
     extern __shared__ __align__(16) uint8_t smem[];
-    rebuild_list<IdxT, kRbMediumThreads, 1>(V, J, out, out_off, status, list, count, next, smem);
+    rebuild_list<IdxT, kT, 1>(V, J, out, out_off, status, list, count, next, smem);
 }
 
 template <typename IdxT>
@@ -1290,16 +1291,17 @@ __global__ void __launch_bounds__(kRbCoarseThreads, 32) rebuild_coarse(VolDev V,
 }
 
 // Requests of 32^3 bricks with uint8 indices at any LOD, in the compact leaf layout (rb_layout_leafc, 25.8 KB):
-// 128-thread CTAs, 8 per SM, twice the bricks in flight of rebuild's 51 KB layout.  A LOD 0 request with more
-// than kLeafCap non-constant L1 nodes is appended to `full` (count in *n_full) for rebuild_listed.
-constexpr uint32_t kRbLeafCThreads = 128;
-__global__ void __launch_bounds__(kRbLeafCThreads, 8) rebuild_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
-                                                                   const uint64_t *__restrict__ out_off,
-                                                                   int32_t *__restrict__ status, uint32_t *full,
-                                                                   uint32_t *n_full) {
+// 128-thread CTAs, 8 per SM, twice the bricks in flight of rebuild's 51 KB layout (or 256-thread CTAs, 4 per
+// SM: the autotuner's choice of warps per brick).  A LOD 0 request with more than kLeafCap non-constant L1
+// nodes is appended to `full` (count in *n_full) for rebuild_listed.
+template <uint32_t kT>
+__global__ void __launch_bounds__(kT, 1024 / kT) rebuild_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                             const uint64_t *__restrict__ out_off,
+                                                             int32_t *__restrict__ status, uint32_t *full,
+                                                             uint32_t *n_full) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t i = blockIdx.x;
-    const int32_t st = rebuild_request<uint8_t, kRbLeafCThreads, 0, true>(V, J, smem, i, out + out_off[i]);
+    const int32_t st = rebuild_request<uint8_t, kT, 0, true>(V, J, smem, i, out + out_off[i]);
     if (threadIdx.x == 0) {
         if (st == kStToFull) full[atomicAdd(n_full, 1u)] = i;
         else status[i] = st;
@@ -1606,30 +1608,40 @@ __global__ void __launch_bounds__(kGwThreads) rebuild_global(VolDev V, RecJob J,
 
 // ---------------------------------------------------------------- launchers (host)
 
-uint32_t rans_records_smem_bytes() { return 2 * kM * 4 + kRecWarps * kWinWords * 2; }
+uint32_t rans_records_smem_bytes(uint32_t ring_words) { return 2 * kM * 4 + kRecWarps * ring_words * 2; }
 uint32_t rans_records_packed_smem_bytes() { return 2 * kM * 4 + kRecWarps * kPkWarpWords * 2; }
 
 uint32_t rebuild_smem_bytes(uint32_t N, bool wide) {
     return wide ? rb_layout<uint16_t>(N).total : rb_layout<uint8_t>(N).total;
 }
 
-// Decode requests [0, J.n) of a slice: records, then the rebuild (statuses and outputs already offset).
+// Decode requests [0, J.n) of a slice: records, then the rebuild (statuses and outputs already offset), in the
+// launch shape S (rANS grid and ring depth, threads per request of the 32^3 kernels).
 cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob &J, uint32_t *out, const uint64_t *out_off,
-                                int32_t *status, uint32_t rec_blocks, cudaStream_t st) {
+                                int32_t *status, const DecodeShape &S, cudaStream_t st) {
     if (J.n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t g = sms > 0 ? (uint32_t)sms : 1u;
     // bricks of 16^3 and smaller: streams of a few states, decoded several to a warp
     const bool packed = V.N <= 4;
-    const uint32_t smem_a = packed ? rans_records_packed_smem_bytes() : rans_records_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(packed ? rans_records_packed : rans_records,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_a);
+    const uint32_t ring = S.ring_words == 128 || S.ring_words == 512 ? S.ring_words : 256u;
+    auto rk = ring == 128 ? rans_records<128> : ring == 512 ? rans_records<512> : rans_records<256>;
+    const uint32_t smem_a = packed ? rans_records_packed_smem_bytes() : rans_records_smem_bytes(ring);
+    cudaError_t e = cudaFuncSetAttribute(packed ? rans_records_packed : rk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_a);
+    if (e == cudaSuccess && !packed)  // the largest shared-memory carve-out: up to 6 CTAs per SM
+        e = cudaFuncSetAttribute(rk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(J.counter, 0, 4, st);
     if (e != cudaSuccess) return e;
     const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
+    const uint32_t rec_blocks = max(1u, min(S.rec_per_sm, 6u)) * g;
     {
         ProfScope ps("rans_records", st);
         if (packed) rans_records_packed<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
-        else rans_records<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+        else rk<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1654,19 +1666,22 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             const uint32_t smem_m = rb_layout_part<uint8_t>(V.N, 1).total, smem_c = rb_layout_part<uint8_t>(V.N, 2).total;
             e = cudaMemsetAsync(counts, 0, 24, st);  // list counts, then the lists' work counters
             if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_medium<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_m);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_coarse<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
             if (e != cudaSuccess) return e;
+            const uint32_t mt = S.medium_threads == 64 || S.medium_threads == 256 ? S.medium_threads : 128u;
+            auto mk = mt == 64 ? rebuild_medium<uint8_t, 64> : mt == 256 ? rebuild_medium<uint8_t, 256>
+                                                                         : rebuild_medium<uint8_t, 128>;
+            e = cudaFuncSetAttribute(mk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_m);
+            if (e != cudaSuccess) return e;
+            int per_m = 0;  // persistent grid: the CTAs that fit
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_m, mk, (int)mt, smem_m) != cudaSuccess || per_m < 1)
+                per_m = 1;
             split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, lists, counts);
-            int dev = 0, sms = 148;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const uint32_t g = (uint32_t)sms;
             ProfScope ps("rebuild", st);
             rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists,
                                                                              counts, counts + 3);
-            rebuild_medium<uint8_t><<<min(J.n, 14 * g), kRbMediumThreads, smem_m, st>>>(
-                V, J, out, out_off, status, lists + J.n, counts + 1, counts + 4);
+            mk<<<min(J.n, (uint32_t)per_m * g), mt, smem_m, st>>>(V, J, out, out_off, status, lists + J.n, counts + 1,
+                                                                  counts + 4);
             rebuild_coarse<uint8_t><<<min(J.n, 32 * g), kRbCoarseThreads, smem_c, st>>>(
                 V, J, out, out_off, status, lists + 2 * J.n, counts + 2, counts + 5);
             return cudaGetLastError();
@@ -1687,21 +1702,20 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         }
         if (V.N == 5) {  // 32^3 bricks: the compact leaf layout, the few requests it cannot hold in rebuild_listed
             const uint32_t smem_l = rb_layout_leafc<uint8_t>(V.N).total;
+            const uint32_t lt = S.leafc_threads == 256 ? 256u : 128u;
+            auto lk = lt == 256 ? rebuild_leafc<256> : rebuild_leafc<128>;
             uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
             e = cudaMemsetAsync(n_full, 0, 8, st);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_leafc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
-            if (e == cudaSuccess)  // the largest shared-memory carve-out: 8 CTAs per SM
-                e = cudaFuncSetAttribute(rebuild_leafc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            if (e == cudaSuccess)  // the largest shared-memory carve-out: 8 CTAs per SM at 128 threads
+                e = cudaFuncSetAttribute(lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             ProfScope ps("rebuild", st);
-            rebuild_leafc<<<J.n, kRbLeafCThreads, smem_l, st>>>(V, J, out, out_off, status, J.lists, n_full);
-            rebuild_listed<uint8_t><<<min(J.n, (uint32_t)(sms > 0 ? sms : 1)), kRbThreads, smem_b, st>>>(
-                V, J, out, out_off, status, J.lists, n_full, n_full + 1);
+            lk<<<J.n, lt, smem_l, st>>>(V, J, out, out_off, status, J.lists, n_full);
+            rebuild_listed<uint8_t><<<min(J.n, g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, J.lists,
+                                                                         n_full, n_full + 1);
             return cudaGetLastError();
         }
         e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);

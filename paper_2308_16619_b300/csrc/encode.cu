@@ -42,6 +42,13 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+// Drop the 128-byte L2 lines that lie wholly inside [lo, hi) without writing them back: scratch nobody reads
+// again (the lanes of a warp take every 32nd line)
+__device__ __forceinline__ void discard_l2(uintptr_t lo, uintptr_t hi, uint32_t lane) {
+    const uintptr_t a0 = (lo + 127) & ~(uintptr_t)127, a1 = hi & ~(uintptr_t)127;
+    for (uintptr_t a = a0 + 128 * (uintptr_t)lane; a < a1; a += 128 * 32)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+}
 // 6-bit coordinate <-> every third bit of a Morton code
 __device__ __forceinline__ uint32_t spread6(uint32_t v) {
     return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4) | ((v & 8u) << 6) | ((v & 16u) << 8) | ((v & 32u) << 10);
@@ -742,6 +749,9 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
                 if (__any_sync(kFull, pd)) rans_code_substep(x, top, words, o >> 4, pd, f_reg, c_reg, rcp_reg, kFull, lt);
                 rans_code_substep(x, top, words, o & 15u, act, f_reg, c_reg, rcp_reg, kFull, lt);
             }
+            // this window's op bytes are read for the last time (the op array is dead after this kernel); the
+            // lines shared with the next window down or with the brick's other stream are kept
+            discard_l2(reinterpret_cast<uintptr_t>(ops + first + s_lo * K), reinterpret_cast<uintptr_t>(ops + op_hi), lane);
             s_hi = s_lo;
         }
         // final states ahead of the words, state 0 first, low half first
