@@ -61,10 +61,11 @@ class Result(C.Structure):
 
 class DecodeTuning(C.Structure):
     _fields_ = [("workspace_bytes", C.c_uint64), ("rans_ctas_per_sm", C.c_uint32), ("ring_words", C.c_uint32),
-                ("rebuild_threads", C.c_uint32), ("medium_threads", C.c_uint32), ("ms", C.c_double)]
+                ("rebuild_threads", C.c_uint32), ("medium_threads", C.c_uint32), ("compact_nodes", C.c_uint32),
+                ("pad", C.c_uint32), ("ms", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class Camera(C.Structure):

@@ -738,7 +738,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     const uint64_t budget = v->N >= 6 ? std::max<uint64_t>(v->dec_ws_bytes, 2ull << 30) : v->dec_ws_bytes;
     uint64_t S = one_per_launch ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(n, budget / stride));
     const size_t info_bytes = ((size_t)S * 8 + 255) & ~(size_t)255;
-    const size_t bytes = 256 + info_bytes + (size_t)S * stride + (size_t)S * 12;  // + the rebuild split's lists
+    const size_t bytes = 256 + info_bytes + (size_t)S * stride + (size_t)S * 16;  // + the rebuild split's lists
     // the volume may come from another stream; a captured graph cannot depend on uncaptured work, so a
     // decode being captured does not wait (the graph is launched once the volume is complete)
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -758,6 +758,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     J.lev_at = lev_at;
     J.flag_at = flag_at;
     J.list_at = list_at;
+    J.compact_nodes = v->dec_shape.compact_nodes;
     cudaError_t e = cudaSuccess;
     for (uint64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += S) {
         J.n = (uint32_t)std::min<uint64_t>(S, n - r0);
@@ -835,6 +836,7 @@ csgv_decode_tuning tuning_of(const csgv_volume *v) {
     t.ring_words = v->dec_shape.ring_words;
     t.rebuild_threads = v->dec_shape.leafc_threads;
     t.medium_threads = v->dec_shape.medium_threads;
+    t.compact_nodes = v->dec_shape.compact_nodes;
     t.ms = 0.0;
     return t;
 }
@@ -842,7 +844,7 @@ bool tuning_valid(const csgv_decode_tuning &t) {
     return t.workspace_bytes >= (1ull << 20) && t.rans_ctas_per_sm >= 4 && t.rans_ctas_per_sm <= 6 &&
            (t.ring_words == 128 || t.ring_words == 256 || t.ring_words == 512) &&
            (t.rebuild_threads == 128 || t.rebuild_threads == 256) &&
-           (t.medium_threads == 64 || t.medium_threads == 128 || t.medium_threads == 256) &&
+           (t.medium_threads == 64 || t.medium_threads == 128 || t.medium_threads == 256) && t.compact_nodes <= 1792 &&
            !(t.ring_words == 512 && t.rans_ctas_per_sm == 6);  // 6 x 40 KB of shared memory do not fit an SM
 }
 void apply_tuning(csgv_volume *v, const csgv_decode_tuning &t) {
@@ -851,6 +853,7 @@ void apply_tuning(csgv_volume *v, const csgv_decode_tuning &t) {
     v->dec_shape.ring_words = t.ring_words;
     v->dec_shape.leafc_threads = t.rebuild_threads;
     v->dec_shape.medium_threads = t.medium_threads;
+    v->dec_shape.compact_nodes = t.compact_nodes;
 }
 }  // namespace
 
@@ -864,8 +867,9 @@ int csgv_decode_set_tuning(csgv_volume *vol, const csgv_decode_tuning *t) {
     if (!vol || !t) return fail(CSGV_ERR_INVALID_ARG, "NULL argument");
     if (!tuning_valid(*t))
         return fail(CSGV_ERR_INVALID_ARG, "decode tuning out of range (workspace %llu B, %u rANS CTAs per SM, ring %u "
-                    "words, rebuild %u threads, LOD 1 kernel %u threads)", (unsigned long long)t->workspace_bytes,
-                    t->rans_ctas_per_sm, t->ring_words, t->rebuild_threads, t->medium_threads);
+                    "words, rebuild %u threads, LOD 1 kernel %u threads, compact layout up to %u nodes)",
+                    (unsigned long long)t->workspace_bytes, t->rans_ctas_per_sm, t->ring_words, t->rebuild_threads,
+                    t->medium_threads, t->compact_nodes);
     apply_tuning(vol, *t);
     return CSGV_OK;
 }
@@ -903,8 +907,9 @@ int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const 
         ms = v[kRuns / 2];
     };
     // one knob at a time, each search starting from the best point so far: the rANS kernel's ring depth and
-    // CTAs per SM, the rebuild's threads per request (warps per brick) for LOD 0 and for LOD 1 requests,
-    // then the workspace per slice (the number of slices)
+    // CTAs per SM, the rebuild's threads per request (warps per brick) for LOD 0 requests, the LOD 0 requests
+    // that take the compact layout (4 or 8 warps) rather than the full one (8 warps), the threads per LOD 1
+    // request, then the workspace per slice (the number of slices)
     time_of(b, b.ms);
     auto search = [&](auto set, std::initializer_list<uint32_t> vals) {
         for (uint32_t x : vals) {
@@ -918,6 +923,7 @@ int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const 
     for (uint32_t ring : {128u, 256u, 512u})
         search([&](csgv_decode_tuning &c, uint32_t x) { c.ring_words = ring; c.rans_ctas_per_sm = x; }, {4u, 5u, 6u});
     search([](csgv_decode_tuning &c, uint32_t x) { c.rebuild_threads = x; }, {128u, 256u});
+    search([](csgv_decode_tuning &c, uint32_t x) { c.compact_nodes = x; }, {0u, 256u, 512u, 1024u, 1792u});
     search([](csgv_decode_tuning &c, uint32_t x) { c.medium_threads = x; }, {64u, 128u, 256u});
     search([](csgv_decode_tuning &c, uint32_t x) { c.workspace_bytes = (uint64_t)x << 20; }, {64u, 192u, 512u, 1024u});
     cudaEventDestroy(e0);

@@ -38,7 +38,8 @@ struct RecJob {
     uint64_t lev_at, flag_at, list_at;  // b = 64 only
     uint32_t *info;
     uint32_t *counter;  // work counter of the rANS kernel; counter[16..21]: list counts and work counters of the rebuild split
-    uint32_t *lists;    // 3 x n request indices (the rebuild split), or nullptr
+    uint32_t *lists;    // 4 x n request indices (the rebuild split's three lists, then oversized LOD 0 requests)
+    uint32_t compact_nodes;  // 32^3 bricks: LOD 0 requests with more non-constant L1 nodes take the full layout
 };
 
 // Device view of a compressed volume (passed to kernels by value).
@@ -98,6 +99,8 @@ struct DecodeShape {
     uint32_t rec_per_sm = 4;        // rANS record kernel: CTAs of 8 warps per SM (4..6)
     uint32_t ring_words = 512;      // rANS record kernel: stream words staged per warp (128, 256, 512)
     uint32_t leafc_threads = 128;   // 32^3 bricks, compact leaf layout: threads per request (128, 256)
+    uint32_t compact_nodes = 1792;  // 32^3 bricks: LOD 0 requests with at most this many non-constant L1 nodes take
+                                    // the compact layout, the others the full one (256 threads, 8 warps)
     uint32_t medium_threads = 128;  // 32^3 bricks, LOD 1 requests of large mixed batches (64, 128, 256)
 };
 

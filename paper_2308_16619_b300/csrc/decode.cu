@@ -1066,8 +1066,9 @@ constexpr int32_t kStToFull = -2;  // internal: the request needs the full-layou
 
 // kT: threads per CTA (64..256; the leaf-level pass needs 64 or more); kLmin: 0, or 1 / 2 for requests at LOD
 // >= kLmin only, in the compact layout rb_layout_part
-// kLeafC: the compact leaf level (rb_layout_leafc, uint8 indices); a LOD 0 request with more than kLeafCap
-// non-constant L1 nodes returns kStToFull untouched (nothing written).
+// kLeafC: the compact leaf level (rb_layout_leafc, uint8 indices); a LOD 0 request with more non-constant L1
+// nodes than kLeafCap (the layout's room) or J.compact_nodes (the launch shape's choice) returns kStToFull
+// untouched (nothing written).
 template <typename IdxT, uint32_t kT, uint32_t kLmin = 0, bool kLeafC = false>
 __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *smem, uint32_t i, uint32_t *out) {
     const uint32_t N = V.N;
@@ -1096,7 +1097,7 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     }
     const uint32_t info_int = J.info[2 * i], info_leaf = t == 0 ? J.info[2 * i + 1] : 0u;
     if ((info_int | info_leaf) & kRecBad) return kStCorrupt;
-    if (kLeafC && t == 0 && info_leaf > 8 * kLeafCap) return kStToFull;
+    if (kLeafC && t == 0 && info_leaf > 8 * min(kLeafCap, J.compact_nodes)) return kStToFull;
     const uint8_t *base = J.recs + (uint64_t)i * J.stride;
     const uint16_t *t8i = (const uint16_t *)(base + J.t8_at), *t8l = (const uint16_t *)(base + J.t8_leaf_at);
 
@@ -1216,7 +1217,8 @@ __global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev 
 }
 
 // Large mixed-LOD batches of 32^3 bricks: split_lods lists the requests by class (LOD 0, LOD 1, LOD >= 2),
-// and one kernel per class rebuilds its list: rebuild_listed as rebuild does; rebuild_medium (LOD 1) with
+// and one kernel per class rebuilds its list: rebuild_listed_leafc in the compact leaf layout (its few
+// oversized requests then by rebuild_listed, as rebuild does); rebuild_medium (LOD 1) with
 // 128-thread CTAs in a layout without L0 (14 KB), 14 per SM; rebuild_coarse (LOD >= 2) with 64-thread CTAs
 // in a layout of levels 2..N (3.4 KB), 32 per SM, since such a request has at most 64 parents per level,
 // where a 256-thread CTA with the full 51 KB layout ran 4 per SM.  The three kernels are persistent (see
@@ -1243,11 +1245,13 @@ __global__ void split_lods(RecJob J, uint32_t N, uint32_t *lists, uint32_t *coun
 }
 
 // One list of the split: persistent CTAs take the list's requests one at a time (a counter per list), so a
-// grid is sized to the CTAs that fit on the GPU, not to the batch.
-template <typename IdxT, uint32_t kT, uint32_t kLmin>
+// grid is sized to the CTAs that fit on the GPU, not to the batch.  kLeafC: the compact leaf layout, whose
+// oversized requests are appended to `full` (count in *n_full) for rebuild_listed.
+template <typename IdxT, uint32_t kT, uint32_t kLmin, bool kLeafC = false>
 __device__ __forceinline__ void rebuild_list(const VolDev &V, const RecJob &J, uint32_t *out, const uint64_t *out_off,
                                              int32_t *status, const uint32_t *list, const uint32_t *count,
-                                             uint32_t *next, uint8_t *smem) {
+                                             uint32_t *next, uint8_t *smem, uint32_t *full = nullptr,
+                                             uint32_t *n_full = nullptr) {
     __shared__ uint32_t sh_j;
     const uint32_t n = *count;
     for (;;) {
@@ -1257,10 +1261,24 @@ __device__ __forceinline__ void rebuild_list(const VolDev &V, const RecJob &J, u
         __syncthreads();
         if (j >= n) return;
         const uint32_t i = list[j];
-        const int32_t st = rebuild_request<IdxT, kT, kLmin>(V, J, smem, i, out + out_off[i]);
-        if (threadIdx.x == 0) status[i] = st;
+        const int32_t st = rebuild_request<IdxT, kT, kLmin, kLeafC>(V, J, smem, i, out + out_off[i]);
+        if (threadIdx.x == 0) {
+            if (kLeafC && st == kStToFull) full[atomicAdd(n_full, 1u)] = i;
+            else status[i] = st;
+        }
         __syncthreads();  // the next request reuses the shared memory
     }
+}
+
+// The LOD 0 list of a large mixed batch of 32^3 bricks in the compact leaf layout (as rebuild_leafc, persistent)
+template <uint32_t kT>
+__global__ void __launch_bounds__(kT, 1024 / kT) rebuild_listed_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
+                                                                    const uint64_t *__restrict__ out_off,
+                                                                    int32_t *__restrict__ status, const uint32_t *list,
+                                                                    const uint32_t *count, uint32_t *next,
+                                                                    uint32_t *full, uint32_t *n_full) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    rebuild_list<uint8_t, kT, 0, true>(V, J, out, out_off, status, list, count, next, smem, full, n_full);
 }
 
 template <typename IdxT>
@@ -1676,10 +1694,24 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             int per_m = 0;  // persistent grid: the CTAs that fit
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_m, mk, (int)mt, smem_m) != cudaSuccess || per_m < 1)
                 per_m = 1;
+            // LOD 0: the compact leaf layout (persistent), its oversized requests then by rebuild_listed
+            const uint32_t smem_l = rb_layout_leafc<uint8_t>(V.N).total;
+            const uint32_t lt = S.leafc_threads == 256 ? 256u : 128u;
+            auto lk = lt == 256 ? rebuild_listed_leafc<256> : rebuild_listed_leafc<128>;
+            uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
+            e = cudaMemsetAsync(n_full, 0, 8, st);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e != cudaSuccess) return e;
+            int per_l = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, lk, (int)lt, smem_l) != cudaSuccess || per_l < 1)
+                per_l = 1;
             split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, lists, counts);
             ProfScope ps("rebuild", st);
-            rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists,
-                                                                             counts, counts + 3);
+            lk<<<min(J.n, (uint32_t)per_l * g), lt, smem_l, st>>>(V, J, out, out_off, status, lists, counts, counts + 3,
+                                                                   lists + 3 * J.n, n_full);
+            rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status,
+                                                                             lists + 3 * J.n, n_full, n_full + 1);
             mk<<<min(J.n, (uint32_t)per_m * g), mt, smem_m, st>>>(V, J, out, out_off, status, lists + J.n, counts + 1,
                                                                   counts + 4);
             rebuild_coarse<uint8_t><<<min(J.n, 32 * g), kRbCoarseThreads, smem_c, st>>>(
@@ -1714,8 +1746,8 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             if (e != cudaSuccess) return e;
             ProfScope ps("rebuild", st);
             lk<<<J.n, lt, smem_l, st>>>(V, J, out, out_off, status, J.lists, n_full);
-            rebuild_listed<uint8_t><<<min(J.n, g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, J.lists,
-                                                                         n_full, n_full + 1);
+            rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, J.lists,
+                                                                             n_full, n_full + 1);
             return cudaGetLastError();
         }
         e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);

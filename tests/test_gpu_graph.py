@@ -69,6 +69,7 @@ def test_autotune_keeps_decoding_exact(batch):
     assert best.workspace_bytes in (64 << 20, 192 << 20, 512 << 20, 1024 << 20)
     assert best.rans_ctas_per_sm in (4, 5, 6) and best.ring_words in (128, 256, 512)
     assert best.rebuild_threads in (128, 256) and best.medium_threads in (64, 128, 256) and 0 < best.ms < 1e3
+    assert best.compact_nodes in (0, 256, 512, 1024, 1792)
     assert csgv.csgv_decode_get_tuning(v).as_dict() == dict(best.as_dict(), ms=0.0)  # kept in the volume
     out.fill_(-1)
     csgv.csgv_decode_bricks(v, t["ids"], t["lods"], out, t["offs"], st)
@@ -78,7 +79,8 @@ def test_autotune_keeps_decoding_exact(batch):
 
 def test_every_decode_tuning_point_decodes_exactly():
     # Every launch shape the autotuner can pick (rANS ring depth x CTAs per SM, threads per LOD 0 and per LOD 1
-    # request, workspace per slice) on a 9000-request mixed-LOD batch, which is above the size from which LOD 1
+    # request, workspace per slice; the compact/full split of LOD 0 requests cycled through its five values) on a
+    # 9000-request mixed-LOD batch, which is above the size from which LOD 1
     # requests go to their own kernel; each result equals the oracle's pyramid level of every request's brick.
     import itertools
     import torch
@@ -112,8 +114,9 @@ def test_every_decode_tuning_point_decodes_exactly():
     points = 0
     for ring, ctas, lt, mt, ws in itertools.product((128, 256, 512), (4, 5, 6), (128, 256), (64, 128, 256),
                                                     (64, 1024)):
+        cn = (0, 256, 512, 1024, 1792)[points % 5]  # the compact/full split, cycled over the points
         tu = csgv.DecodeTuning(workspace_bytes=ws << 20, rans_ctas_per_sm=ctas, ring_words=ring, rebuild_threads=lt,
-                               medium_threads=mt)
+                               medium_threads=mt, compact_nodes=cn)
         if ring == 512 and ctas == 6:  # 6 x 40 KB of shared memory: refused
             with pytest.raises(csgv.CsgvError):
                 csgv.csgv_decode_set_tuning(v, tu)
