@@ -462,6 +462,14 @@ __device__ __forceinline__ void rec_masks(uint64_t r8, uint32_t &nr, uint32_t &p
     st = gather4(lo << 4) | gather4(hi << 4) << 4;
 }
 
+// The -axis children of a level are resolved in three rounds.  A child c whose a-bit is 0 and whose op is R_a
+// reads the node before it along a, which is child c | (1 << a) of the neighbouring parent: a child index with
+// one more bit set.  Children with all three bits set are never -axis children, so resolving the -axis children
+// with two bits set, then one, then none, each round reads only values that are final (R4).
+__device__ __forceinline__ uint32_t sent_round(uint32_t r) {  // child indices {3, 5, 6}, {1, 2, 4}, {0}
+    return (0x011668u >> (8 * r)) & 0xFFu;
+}
+
 // Final index of node q of a level whose value w is a -axis sentinel: follow the chain (at most 3 hops).
 template <typename IdxT>
 __device__ __forceinline__ uint32_t chase(const volatile IdxT *L, uint32_t q, uint32_t w, uint32_t lbits) {
@@ -843,23 +851,25 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     __syncthreads();
     if (bad) ms->bad = 1;
 
-    // pass 3: resolve the -axis children of this warp's listed parents (chains of at most 3 hops;
-    // a target is final or a sentinel itself)
+    // pass 3: resolve the -axis children of this warp's listed parents in rounds (see sent_round)
     const uint32_t cbits = 8 * npar - 1;
-    volatile IdxT *Cv = C;
-    for (uint32_t b = warp; b < nlb; b += nw) {
-        const uint32_t j = 32 * b + lane;
-        uint32_t m = j < n_act ? mm[j] : 0u;
-        if (!m) continue;
-        const uint32_t k = parent_of(j);
-        while (m) {
-            const uint32_t c = __ffs(m) - 1;
-            m &= m - 1;
-            const uint32_t q = 8 * k + c;
-            Cv[q] = (IdxT)chase<IdxT>(Cv, q, Cv[q], cbits);
+#pragma unroll 1
+    for (uint32_t r = 0; r < 3; r++) {
+        for (uint32_t b = warp; b < nlb; b += nw) {
+            const uint32_t j = 32 * b + lane;
+            uint32_t m = j < n_act ? mm[j] & sent_round(r) : 0u;
+            if (!m) continue;
+            const uint32_t k = parent_of(j);
+            while (m) {
+                const uint32_t c = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t q = 8 * k + c;
+                const uint32_t w = C[mdec(q, kMX << ((uint32_t)C[q] - sent)) & cbits];
+                C[q] = (IdxT)(w < sent ? w : 0u);
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     return ms->bad == 0;
 }
 
@@ -964,26 +974,26 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
     __syncthreads();
     if (bad) ms->bad = 1;
 
-    // pass C: resolve the -axis children (chains of at most 3 hops, as in rebuild_level)
-    volatile IdxT *Ev = E;
-    for (uint32_t j = threadIdx.x; j < n_act; j += kT) {
-        uint32_t m = mm[j];
-        if (!m) continue;
-        const uint32_t k = act[j];
-        while (m) {
-            const uint32_t ch = __ffs(m) - 1;
-            m &= m - 1;
-            uint32_t q = 8 * k + ch, w = Ev[8 * j + ch];
-            for (int hop = 0; hop < 4 && w >= sent; hop++) {
-                q = mdec(q, kMX << (w - sent)) & cbits;
+    // pass C: resolve the -axis children in rounds (see sent_round); a neighbour under a constant L1 node is that
+    // node's index, any other E[8 rank + child]
+#pragma unroll 1
+    for (uint32_t r = 0; r < 3; r++) {
+        for (uint32_t j = threadIdx.x; j < n_act; j += kT) {
+            uint32_t m = mm[j] & sent_round(r);
+            if (!m) continue;
+            const uint32_t k = act[j];
+            while (m) {
+                const uint32_t ch = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t q = mdec(8 * k + ch, kMX << (E[8 * j + ch] - sent)) & cbits;
                 const uint32_t k2 = q >> 3, word = cw[k2 >> 5], bit = k2 & 31u;
-                if ((word >> bit) & 1u) w = P[k2];
-                else w = Ev[8 * (rk[k2 >> 5] + __popc(~word & ((1u << bit) - 1u))) + (q & 7u)];
+                const uint32_t w = ((word >> bit) & 1u) ? (uint32_t)P[k2]
+                                                        : (uint32_t)E[8 * (rk[k2 >> 5] + __popc(~word & ((1u << bit) - 1u))) + (q & 7u)];
+                E[8 * j + ch] = (IdxT)(w < sent ? w : 0u);
             }
-            Ev[8 * j + ch] = (IdxT)(w < sent ? w : 0u);
         }
+        __syncthreads();
     }
-    __syncthreads();
     return ms->bad == 0;
 }
 
