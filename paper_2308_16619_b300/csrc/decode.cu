@@ -929,12 +929,22 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
             nc &= nc - 1;
         }
     }
-    if (threadIdx.x == 0) ms->bad = 0;
+    if (threadIdx.x == 0) {
+        ms->bad = 0;
+        ms->pad[0] = 0;  // pass B's list of -axis children
+    }
     __syncthreads();
 
-    // pass B: one thread per listed node decodes its 8 records (children of R_p keep the node's index)
+    // pass B: one thread per listed node decodes its 8 records (children of R_p keep the node's index).  Its
+    // -axis children are also appended to a list (node << 3 | child) in the part of the E area past the listed
+    // nodes, for pass C; the list's length is counted even when it does not fit.
     bool bad = false;
-    for (uint32_t j = threadIdx.x; j < n_act; j += kT) {
+    uint16_t *lst = (uint16_t *)(E + 8 * n_act);
+    const uint32_t lst_cap = 4 * (kLeafCap - n_act);
+    for (uint32_t j0 = 0; j0 < n_act; j0 += kT) {
+      const uint32_t j = j0 + threadIdx.x;
+      uint32_t minus_m = 0;
+      if (j < n_act) {
         const uint32_t k = act[j];
         const uint64_t r8 = __ldg((const unsigned long long *)(R + 8 * j));
         const uint32_t ipl = ip0 + __ldg(T8 + j);
@@ -950,7 +960,6 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
                              ((k & kMY & pbits) == (kMY & pbits) ? 2u : 0u) |
                              ((k & kMZ & pbits) == (kMZ & pbits) ? 4u : 0u);
         uint64_t e8 = 0x0101010101010101ull * (uint64_t)P[k];
-        uint32_t minus_m = 0;
         while (nr) {
             const uint32_t ch = __ffs(nr) - 1;
             nr &= nr - 1;
@@ -970,12 +979,50 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
         }
         *(uint64_t *)(E + 8 * j) = e8;
         mm[j] = (uint8_t)minus_m;
+      }
+      // append this warp's -axis children to the list: one atomic per warp
+      const uint32_t c = __popc(minus_m);
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t u = __shfl_up_sync(kFull, incl, d);
+          if (lane >= (uint32_t)d) incl += u;
+      }
+      uint32_t base = 0;
+      if (lane == 31 && incl) base = atomicAdd(&ms->pad[0], incl);
+      base = __shfl_sync(kFull, base, 31) + incl - c;
+      while (minus_m) {
+          const uint32_t ch = __ffs(minus_m) - 1;
+          minus_m &= minus_m - 1;
+          if (base < lst_cap) lst[base] = (uint16_t)((j << 3) | ch);
+          base++;
+      }
     }
     __syncthreads();
     if (bad) ms->bad = 1;
 
-    // pass C: resolve the -axis children in rounds (see sent_round); a neighbour under a constant L1 node is that
-    // node's index, any other E[8 rank + child]
+    // pass C: resolve the -axis children.  A neighbour under a constant L1 node is that node's index, any other
+    // E[8 rank + child].  When the list fits, one list entry per thread, each following its chain (at most 3 hops:
+    // each lands on a child index with one more bit set; a target another thread is resolving reads either its
+    // sentinel, which the chain then follows, or its final index); otherwise per listed node in rounds (see
+    // sent_round), where every read is final.
+    const uint32_t n_lst = ms->pad[0];
+    if (n_lst <= lst_cap) {
+        volatile IdxT *Ev = E;
+        for (uint32_t e = threadIdx.x; e < n_lst; e += kT) {
+            const uint32_t ent = lst[e], j = ent >> 3, ch = ent & 7u;
+            uint32_t q = 8 * (uint32_t)act[j] + ch, w = Ev[8 * j + ch];
+            for (int hop = 0; hop < 4 && w >= sent; hop++) {
+                q = mdec(q, kMX << (w - sent)) & cbits;
+                const uint32_t k2 = q >> 3, word = cw[k2 >> 5], bit = k2 & 31u;
+                w = ((word >> bit) & 1u) ? (uint32_t)P[k2]
+                                         : (uint32_t)Ev[8 * (rk[k2 >> 5] + __popc(~word & ((1u << bit) - 1u))) + (q & 7u)];
+            }
+            Ev[8 * j + ch] = (IdxT)(w < sent ? w : 0u);
+        }
+        __syncthreads();
+        return ms->bad == 0;
+    }
 #pragma unroll 1
     for (uint32_t r = 0; r < 3; r++) {
         for (uint32_t j = threadIdx.x; j < n_act; j += kT) {

@@ -255,6 +255,45 @@ def test_b32_bricks_with_many_non_constant_l1_nodes_take_the_full_layout():
     assert np.array_equal(out[:len(ref)], ref)
 
 
+def test_b32_leaf_minus_list_and_its_fallback():
+    """The compact leaf layout resolves the -axis children of the leaf level from a list kept in the unused
+    part of its children area, which holds 4 (1792 - listed nodes) entries; a brick with more -axis children
+    resolves them per listed node instead.  Two 32^3 bricks of x-stripes (every L1 node of the striped part
+    is non-constant, with three -axis children: R_y / R_z toward the previous node) over a constant
+    background: the first striped in 10 of its 32 z-layers (1280 listed nodes, more -axis children than the
+    list holds), the second in 4 (512 listed nodes, the list).  Every LOD against the oracle."""
+    shape = (32, 32, 64)
+    vol = np.full(shape, 7, np.uint32)
+    x = np.arange(64)
+    stripes = (1 + (x & 1)).astype(np.uint32)[None, None, :]
+    vol[:10, :, :32] = np.broadcast_to(stripes[:, :, :32], (10, 32, 32))
+    vol[:4, :, 32:] = np.broadcast_to(stripes[:, :, 32:], (4, 32, 32))
+    V = O.encode_volume(vol, 5, stride=1)
+    fits = []
+    for bid in range(2):
+        br = np.ascontiguousarray(vol[:, :, 32 * bid:32 * bid + 32])
+        blocks = br.reshape(16, 2, 16, 2, 16, 2).transpose(0, 2, 4, 1, 3, 5).reshape(4096, 8)
+        n_act = int((blocks != blocks[:, :1]).any(axis=1).sum())
+        nl = list(O.encode_brick(br)[2])
+        ops, i = [], 0
+        while i < len(nl):
+            ops.append(nl[i])
+            i += 2 if (nl[i] & 7) == 5 else 1
+        op = np.array(ops).reshape(-1, 8) & 7
+        c = np.arange(8)
+        minus = int((((op == 1) & ((c & 1) == 0)) | ((op == 2) & ((c & 2) == 0)) | ((op == 3) & ((c & 4) == 0))).sum())
+        assert n_act <= 1792 and len(op) == n_act
+        fits.append(minus <= 4 * (1792 - n_act))
+    assert fits == [False, True]
+    gv = import_oracle_volume(V)
+    ids = np.repeat(np.arange(2, dtype=np.uint32), 6)
+    lods = np.tile(np.arange(6, dtype=np.uint8), 2)
+    out, off, st = gpu_decode(gv, 5, ids, lods)
+    ref, roff, rst = O.decode_bricks(V, ids, lods)
+    assert (rst == 0).all() and (st == 0).all()
+    assert np.array_equal(out[:len(ref)], ref)
+
+
 def test_wide_palette_path():
     """Bricks with more than 253 palette entries use 16-bit indices in shared memory."""
     rng = np.random.default_rng(2)
