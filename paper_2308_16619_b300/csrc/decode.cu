@@ -135,7 +135,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
         t8n = (otail + 7) / 8;
     };
     // full steps: at least 2K symbols left, so every lane below K decodes an op
-    while (left >= 2 * K && otail < need) {
+    auto full_step = [&]() {
         if (pos > lim) refill();
         const uint32_t e = lut[x & (kM - 1u)];
         const uint32_t sym = e & 15u;
@@ -152,7 +152,14 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
             otail += K;
             left -= K;
         }
+    };
+    // two at a time while two full steps are sure (a step takes at most 2K symbols) and the first cannot
+    // reach `need`
+    while (left >= 4 * K && otail + K < need) {
+        full_step();
+        full_step();
     }
+    while (left >= 2 * K && otail < need) full_step();
     // the last steps: a lane decodes an op only if it and the deltas owed by the lanes before it fit
     while (left > 0 && otail < need) {
         if (pos > lim) refill();
