@@ -525,7 +525,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
                 w[c >> 2] |= (op | (stop << 3)) << (8 * (c & 3u));
                 if (op == kNeedPal) {  // gathered with its label for the palette pass (first 256)
                     const uint32_t at = atomicAdd(&sh_npc, 1u);
-                    if (at < 256) S.plist[at] = make_uint2(8 * r + c, v[c]);
+                    if (at < 256) S.plist[at] = make_uint2((8 * r + c) << 1 | stop, v[c]);  // op index, stop bit
                 }
             }
             *(uint2 *)(ops + 8 * r) = make_uint2(w[0], w[1]);
@@ -548,6 +548,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         uint32_t rank = 0;
         if (tid < n_need) {
             mine = S.plist[tid];
+#pragma unroll 8
             for (uint32_t k = 0; k < n_need; k++) rank += S.plist[k].x < mine.x ? 1u : 0u;
         }
         if (tid < 2 * (kT / 32)) sh_pd[tid] = 0;
@@ -565,9 +566,9 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
                 const uint2 mine2 = lane < kn ? S.plist[k0 + lane] : make_uint2(0u, 0u);
                 const uint32_t res = palette_chunk(mine2.y, kn, win, ip, np, pal, S.red);
                 if (lane < kn) {
-                    ops[mine2.x] = (uint8_t)((ops[mine2.x] & 8u) | res);
-                    if ((res & 7u) == OP_PD)
-                        atomicAdd(&sh_pd[(mine2.x >= n_int_ops ? (kT / 32) : 0u) + mine2.x / per], 1u);
+                    const uint32_t oi = mine2.x >> 1;  // the op's index; its stop bit came along from phase B
+                    ops[oi] = (uint8_t)(((mine2.x & 1u) << 3) | res);
+                    if ((res & 7u) == OP_PD) atomicAdd(&sh_pd[(oi >= n_int_ops ? (kT / 32) : 0u) + oi / per], 1u);
                 }
             }
             if (lane == 0) sh_np = np;
