@@ -223,6 +223,7 @@ Arena g_arena[kArenaDevices];
 std::mutex g_arena_mu;
 cudaEvent_t g_arena_done[kArenaDevices];  // recorded after the last kernel of an encode that read the arena
 void *g_readback[kArenaDevices];          // pinned host copy of an encode's per-batch results
+cudaEvent_t g_readback_done[kArenaDevices];  // recorded after the copy into g_readback
 
 cudaError_t arena_get(int dev, size_t bytes, void **out) {
     Arena &A = g_arena[dev];
@@ -458,6 +459,7 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
     SC.lvl = A + o_lvl;
     Readback *rb_d = (Readback *)(A + o_rb);
     if (!g_readback[dev]) CKE(cudaMallocHost(&g_readback[dev], sizeof(Readback)));
+    if (!g_readback_done[dev]) CKE(cudaEventCreateWithFlags(&g_readback_done[dev], cudaEventDisableTiming));
     Readback &rb = *(Readback *)g_readback[dev];
     if (g_arena_done[dev]) CKE(cudaStreamWaitEvent(st, g_arena_done[dev], 0));  // the previous encode is done with it
     else CKE(cudaEventCreateWithFlags(&g_arena_done[dev], cudaEventDisableTiming));
@@ -485,10 +487,12 @@ static int encode_run(EncRun &R, const csgv::EncVol &EV, uint64_t ev_first, uint
         CKE(csgv::launch_scan(SC.sizes, mm, gfirst, v->pal_off, v->int_off, v->leaf_off, (uint64_t *)rb_d->tot,
                               rb_d->maxes, rb_d->scan, st));
         const bool final_batch = j + mm >= m;
-        if (build_lut && final_batch && (rc = vol_lut(v, rb_d->freq, st))) return bail(rc);  // tables are final
         const uint64_t prev[3] = {R.tot[0], R.tot[1], R.tot[2]};
         CKE(cudaMemcpyAsync(&rb, rb_d, sizeof rb, cudaMemcpyDeviceToHost, st));
-        CKE(cudaStreamSynchronize(st));
+        CKE(cudaEventRecord(g_readback_done[dev], st));
+        // the decode table is built while the host reads the totals back (the tables are final)
+        if (build_lut && final_batch && (rc = vol_lut(v, rb_d->freq, st))) return bail(rc);
+        CKE(cudaEventSynchronize(g_readback_done[dev]));
         for (int a = 0; a < 3; a++) {
             R.tot[a] = rb.tot[a];
             R.maxes[a] = std::max(R.maxes[a], rb.maxes[a]);

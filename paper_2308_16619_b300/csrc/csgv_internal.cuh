@@ -37,7 +37,8 @@ struct RecJob {
     uint64_t stride, leaf_at, t8_at, t8_leaf_at;
     uint64_t lev_at, flag_at, list_at;  // b = 64 only
     uint32_t *info;
-    uint32_t *counter;  // work counter of the rANS kernel; counter[16..21]: list counts and work counters of the rebuild split
+    uint32_t *counter;  // 64 words: [0] work counter of the rANS kernel; [16..21] list counts and work counters of the
+                        // rebuild split; [24..25] oversized LOD 0 requests and their work counter
     uint32_t *lists;    // 4 x n request indices (the rebuild split's three lists, then oversized LOD 0 requests)
     uint32_t compact_nodes;  // 32^3 bricks: LOD 0 requests with more non-constant L1 nodes take the full layout
 };

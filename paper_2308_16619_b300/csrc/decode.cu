@@ -1716,7 +1716,9 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     if (e == cudaSuccess && !packed)  // the largest shared-memory carve-out: up to 6 CTAs per SM
         e = cudaFuncSetAttribute(rk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(J.counter, 0, 4, st);
+    // every counter of the slice at once: the rANS work counter, the split's list counts and work counters
+    // (counter[16..21]) and the oversized-request count and work counter (counter[24..25])
+    e = cudaMemsetAsync(J.counter, 0, 128, st);
     if (e != cudaSuccess) return e;
     const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
     const uint32_t rec_blocks = max(1u, min(S.rec_per_sm, 6u)) * g;
@@ -1746,8 +1748,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         if (V.N == 5 && J.lists && J.n >= kSplitMin) {  // large batch: fine and coarse requests apart
             uint32_t *counts = J.counter + 16, *lists = J.lists;
             const uint32_t smem_m = rb_layout_part<uint8_t>(V.N, 1).total, smem_c = rb_layout_part<uint8_t>(V.N, 2).total;
-            e = cudaMemsetAsync(counts, 0, 24, st);  // list counts, then the lists' work counters
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_coarse<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
             if (e != cudaSuccess) return e;
             const uint32_t mt = S.medium_threads == 64 || S.medium_threads == 256 ? S.medium_threads : 128u;
@@ -1763,8 +1764,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             const uint32_t lt = S.leafc_threads == 256 ? 256u : 128u;
             auto lk = lt == 256 ? rebuild_listed_leafc<256> : rebuild_listed_leafc<128>;
             uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
-            e = cudaMemsetAsync(n_full, 0, 8, st);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e != cudaSuccess) return e;
             int per_l = 0;
@@ -1801,8 +1801,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             const uint32_t lt = S.leafc_threads == 256 ? 256u : 128u;
             auto lk = lt == 256 ? rebuild_leafc<256> : rebuild_leafc<128>;
             uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
-            e = cudaMemsetAsync(n_full, 0, 8, st);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
             if (e == cudaSuccess)  // the largest shared-memory carve-out: 8 CTAs per SM at 128 threads
                 e = cudaFuncSetAttribute(lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e == cudaSuccess)

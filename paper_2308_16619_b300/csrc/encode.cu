@@ -709,10 +709,10 @@ __global__ void __launch_bounds__(kEncSmallThreads, 16)
 // One coding substep: lanes with `act` code `sym` into their state x (Sec. 3.3, R9); renormalisation words go
 // below `top`, in lane order.
 __device__ __forceinline__ void rans_code_substep(uint32_t &x, uint32_t &top, uint16_t *words, uint32_t sym, bool act,
-                                                  uint32_t f_reg, uint32_t c_reg, float rcp_reg, uint32_t smask,
+                                                  uint32_t f_reg, uint32_t c_reg, uint32_t m_reg, uint32_t smask,
                                                   uint32_t lt) {
     const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
-    const float rf = __shfl_sync(kFull, rcp_reg, sym);
+    const uint32_t mf = __shfl_sync(kFull, m_reg, sym);
     // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
     const bool emit = act && x >= (f << 20);
     const uint32_t m = __ballot_sync(kFull, emit) & smask;
@@ -722,14 +722,14 @@ __device__ __forceinline__ void rans_code_substep(uint32_t &x, uint32_t &top, ui
     }
     top -= __popc(m);
     if (act) {
-        // x / f through a float reciprocal: here x < f * 2^20, so the rounded estimate is within one of the
-        // quotient (three roundings of relative error 2^-24 each on a quotient below 2^20); the integer
-        // remainder check makes it exact
-        uint32_t qt = __float2uint_rz(__uint2float_rz(x) * rf);
-        int32_t r = (int32_t)(x - qt * f);
-        if (r < 0) { qt -= 1; r += (int32_t)f; }
-        if (r >= (int32_t)f) { qt += 1; r -= (int32_t)f; }
-        x = qt * kM + (uint32_t)r + c;
+        // x / f by multiplication with a reciprocal (division by an invariant integer, Granlund and
+        // Montgomery 1994): with m = floor((2^32 - 1) / f) = 2^32 / f - e, 0 < e <= 1, the high word of x m is
+        // x / f - x e / 2^32 rounded down, i.e. the quotient or one less for every x < 2^32; one remainder
+        // check makes it exact
+        uint32_t qt = __umulhi(x, mf);
+        uint32_t r = x - qt * f;
+        if (r >= f) { qt += 1; r -= f; }
+        x = qt * kM + r + c;
     }
 }
 
@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     uint8_t *wsm = smem_raw + warp * kRansEncWin;
     const uint32_t *F = freq + 16 * st;
     const uint32_t f_reg = lane < 16 ? F[lane] : 1u;
-    const float rcp_reg = 1.0f / (float)f_reg;
+    const uint32_t m_reg = 0xFFFFFFFFu / f_reg;  // reciprocal of f for the quotient x / f
     uint32_t c_reg = 0;
     for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < lane) ? F[s2] : 0u;
     const uint32_t K = lanes_for(n, G.K_max, G.S_min);
@@ -774,8 +774,8 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
                 const bool act = lane < K && i < n_ops;
                 const uint32_t o = act ? (uint32_t)wsm[first + i - lo16] : 0u;
                 const bool pd = act && (o & 7u) == OP_PD;
-                if (__any_sync(kFull, pd)) rans_code_substep(x, top, words, o >> 4, pd, f_reg, c_reg, rcp_reg, kFull, lt);
-                rans_code_substep(x, top, words, o & 15u, act, f_reg, c_reg, rcp_reg, kFull, lt);
+                if (__any_sync(kFull, pd)) rans_code_substep(x, top, words, o >> 4, pd, f_reg, c_reg, m_reg, kFull, lt);
+                rans_code_substep(x, top, words, o & 15u, act, f_reg, c_reg, m_reg, kFull, lt);
             }
             // this window's op bytes are read for the last time (the op array is dead after this kernel); the
             // lines shared with the next window down or with the brick's other stream are kept
@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     const uint32_t tab = lane >> 4, tsym = lane & 15u;  // this lane's table entry
     const uint32_t *F = freq + 16 * tab;
     const uint32_t f_reg = F[tsym];
-    const float rcp_reg = 1.0f / (float)(f_reg ? f_reg : 1u);
+    const uint32_t m_reg = 0xFFFFFFFFu / (f_reg ? f_reg : 1u);  // reciprocal of f for the quotient x / f
     uint32_t c_reg = 0;
     for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < tsym) ? F[s2] : 0u;
     uint8_t *wbase = smem_raw + warp * kRansEncWin;
@@ -888,8 +888,8 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
             const bool pd = act && (o & 7u) == OP_PD;
             // the deltas first, then the ops: the reverse of the decoder's order (entry 16 st + s of the tables)
             if (__any_sync(kFull, pd))
-                rans_code_substep(x, top, words, (o >> 4) + 16 * st, pd, f_reg, c_reg, rcp_reg, smask, lt);
-            rans_code_substep(x, top, words, (o & 15u) + 16 * st, act, f_reg, c_reg, rcp_reg, smask, lt);
+                rans_code_substep(x, top, words, (o >> 4) + 16 * st, pd, f_reg, c_reg, m_reg, smask, lt);
+            rans_code_substep(x, top, words, (o & 15u) + 16 * st, act, f_reg, c_reg, m_reg, smask, lt);
             if (run) s_hi--;
         }
         // final states ahead of the words, state 0 first, low half first
@@ -1140,27 +1140,41 @@ __global__ void __launch_bounds__(kScanBlock) scan_write_kernel(const uint32_t *
     }
 }
 
-// Copy each brick's palette and words from scratch to the packed arrays.
-__global__ void __launch_bounds__(256) compact_kernel(EncGeom G, EncScratch SC, uint64_t first, const uint64_t *pal_off,
-                                                      const uint64_t *int_off, const uint64_t *leaf_off, uint32_t *pal,
-                                                      uint16_t *int_words, uint16_t *leaf_words, uint32_t *n_int_sym,
-                                                      uint32_t *n_leaf_sym) {
-    const uint32_t slot = blockIdx.x;
+// Copy each brick's palette and words from scratch to the packed arrays: one warp per brick (its sizes read
+// once by eight lanes), the three runs copied with independent loads in flight (the copies are small, so the
+// kernel is bound by the latency of its dependent loads rather than by bandwidth).
+constexpr uint32_t kCompactWarps = 8;
+
+template <typename T>
+__device__ __forceinline__ void copy_run(T *__restrict__ d, const T *__restrict__ s, uint32_t n, uint32_t lane) {
+    uint32_t k = lane;
+    for (; k + 96 < n; k += 128) {
+        const T a = s[k], b = s[k + 32], c = s[k + 64], e = s[k + 96];
+        d[k] = a; d[k + 32] = b; d[k + 64] = c; d[k + 96] = e;
+    }
+    for (; k < n; k += 32) d[k] = s[k];
+}
+
+__global__ void __launch_bounds__(kCompactWarps * 32) compact_kernel(EncGeom G, EncScratch SC, uint64_t first, uint32_t n,
+                                                                     const uint64_t *pal_off, const uint64_t *int_off,
+                                                                     const uint64_t *leaf_off, uint32_t *pal,
+                                                                     uint16_t *int_words, uint16_t *leaf_words,
+                                                                     uint32_t *n_int_sym, uint32_t *n_leaf_sym) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t slot = blockIdx.x * kCompactWarps + (threadIdx.x >> 5);
+    if (slot >= n) return;
     const uint32_t *sz = SC.sizes + (size_t)slot * 8;
     const uint64_t id = first + slot;
-    const uint32_t np = sz[0], nwi = sz[3], nwl = sz[4], si = sz[5], sl = sz[6];
-    const uint32_t *ps = SC.pal + (size_t)slot * G.pal_cap;
-    const uint16_t *wi = SC.w_int + (size_t)slot * (G.int_cap + 64) + si;
-    const uint16_t *wl = SC.w_leaf + (size_t)slot * (G.leaf_cap + 64) + sl;
-    uint32_t *pd = pal + pal_off[id];
-    uint16_t *di = int_words + int_off[id], *dl = leaf_words + leaf_off[id];
-    for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) pd[k] = ps[k];
-    for (uint32_t k = threadIdx.x; k < nwi; k += blockDim.x) di[k] = wi[k];
-    for (uint32_t k = threadIdx.x; k < nwl; k += blockDim.x) dl[k] = wl[k];
-    if (threadIdx.x == 0) {
-        n_int_sym[id] = sz[1];
-        n_leaf_sym[id] = sz[2];
-    }
+    const uint32_t szl = lane < 7 ? sz[lane] : 0u;  // n_pal, n_int_sym, n_leaf_sym, words, word starts
+    const uint64_t offl = lane == 0 ? pal_off[id] : lane == 1 ? int_off[id] : lane == 2 ? leaf_off[id] : 0ull;
+    const uint32_t np = __shfl_sync(kFull, szl, 0), nwi = __shfl_sync(kFull, szl, 3), nwl = __shfl_sync(kFull, szl, 4);
+    const uint32_t si = __shfl_sync(kFull, szl, 5), sl = __shfl_sync(kFull, szl, 6);
+    const uint64_t op = __shfl_sync(kFull, offl, 0), oi = __shfl_sync(kFull, offl, 1), ol = __shfl_sync(kFull, offl, 2);
+    copy_run(pal + op, SC.pal + (size_t)slot * G.pal_cap, np, lane);
+    copy_run(int_words + oi, SC.w_int + (size_t)slot * (G.int_cap + 64) + si, nwi, lane);
+    copy_run(leaf_words + ol, SC.w_leaf + (size_t)slot * (G.leaf_cap + 64) + sl, nwl, lane);
+    if (lane == 1) n_int_sym[id] = szl;
+    if (lane == 2) n_leaf_sym[id] = szl;
 }
 
 }  // namespace
@@ -1277,8 +1291,8 @@ cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t firs
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps("compact", st);
-        compact_kernel<<<n, 256, 0, st>>>(G, SC, first, pal_off, int_off, leaf_off, pal, int_words, leaf_words, n_int_sym,
-                                          n_leaf_sym);
+        compact_kernel<<<(n + kCompactWarps - 1) / kCompactWarps, kCompactWarps * 32, 0, st>>>(
+            G, SC, first, n, pal_off, int_off, leaf_off, pal, int_words, leaf_words, n_int_sym, n_leaf_sym);
     }
     return cudaGetLastError();
 }
