@@ -28,6 +28,9 @@
 //     of the brick, L0 included, are held as palette indices in shared memory (uint8 when every palette
 //     has <= 253 entries, else uint16); level t is then written as x-fastest labels with 16-byte
 //     streaming stores.
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "csgv_internal.cuh"
@@ -1690,6 +1693,23 @@ __global__ void __launch_bounds__(kGwThreads) rebuild_global(VolDev V, RecJob J,
 
 // ---------------------------------------------------------------- launchers (host)
 
+// cudaFuncSetAttribute once per device, kernel, attribute and value: the attributes last for the process,
+// and setting them again on every decode only costs host time ahead of the launches
+static cudaError_t func_attr(const void *fn, cudaFuncAttribute a, int value) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, fn, (int)a);
+    const auto it = done.find(key);
+    if (it != done.end() && it->second == value) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, a, value);
+    if (e == cudaSuccess) done[key] = value;
+    return e;
+}
+
 uint32_t rans_records_smem_bytes(uint32_t ring_words) { return 2 * kM * 4 + kRecWarps * ring_words * 2; }
 uint32_t rans_records_packed_smem_bytes() { return 2 * kM * 4 + kRecWarps * kPkWarpWords * 2; }
 
@@ -1711,10 +1731,10 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     const uint32_t ring = S.ring_words == 128 || S.ring_words == 512 ? S.ring_words : 256u;
     auto rk = ring == 128 ? rans_records<128> : ring == 512 ? rans_records<512> : rans_records<256>;
     const uint32_t smem_a = packed ? rans_records_packed_smem_bytes() : rans_records_smem_bytes(ring);
-    cudaError_t e = cudaFuncSetAttribute(packed ? rans_records_packed : rk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = func_attr((const void *)(packed ? rans_records_packed : rk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_a);
     if (e == cudaSuccess && !packed)  // the largest shared-memory carve-out: up to 6 CTAs per SM
-        e = cudaFuncSetAttribute(rk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = func_attr((const void *)rk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     // every counter of the slice at once: the rANS work counter, the split's list counts and work counters
     // (counter[16..21]) and the oversized-request count and work counter (counter[24..25])
@@ -1740,7 +1760,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     const bool wide = max_pal > RbTraits<uint8_t>::kSent;  // uint16 palette indices
     const uint32_t smem_b = rebuild_smem_bytes(V.N, wide);
     if (wide) {
-        e = cudaFuncSetAttribute(rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+        e = func_attr((const void *)rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
         if (e != cudaSuccess) return e;
         ProfScope ps("rebuild", st);
         rebuild<uint16_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
@@ -1748,13 +1768,13 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         if (V.N == 5 && J.lists && J.n >= kSplitMin) {  // large batch: fine and coarse requests apart
             uint32_t *counts = J.counter + 16, *lists = J.lists;
             const uint32_t smem_m = rb_layout_part<uint8_t>(V.N, 1).total, smem_c = rb_layout_part<uint8_t>(V.N, 2).total;
-            e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_coarse<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
+            e = func_attr((const void *)rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            if (e == cudaSuccess) e = func_attr((const void *)rebuild_coarse<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
             if (e != cudaSuccess) return e;
             const uint32_t mt = S.medium_threads == 64 || S.medium_threads == 256 ? S.medium_threads : 128u;
             auto mk = mt == 64 ? rebuild_medium<uint8_t, 64> : mt == 256 ? rebuild_medium<uint8_t, 256>
                                                                          : rebuild_medium<uint8_t, 128>;
-            e = cudaFuncSetAttribute(mk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_m);
+            e = func_attr((const void *)mk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_m);
             if (e != cudaSuccess) return e;
             int per_m = 0;  // persistent grid: the CTAs that fit
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_m, mk, (int)mt, smem_m) != cudaSuccess || per_m < 1)
@@ -1764,8 +1784,8 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             const uint32_t lt = S.leafc_threads == 256 ? 256u : 128u;
             auto lk = lt == 256 ? rebuild_listed_leafc<256> : rebuild_listed_leafc<128>;
             uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
-            e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            e = func_attr((const void *)lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            if (e == cudaSuccess) e = func_attr((const void *)lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e != cudaSuccess) return e;
             int per_l = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, lk, (int)lt, smem_l) != cudaSuccess || per_l < 1)
@@ -1783,14 +1803,14 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             return cudaGetLastError();
         }
         if (V.N <= 3) {
-            e = cudaFuncSetAttribute(rebuild_tiny_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            e = func_attr((const void *)rebuild_tiny_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;
             ProfScope ps("rebuild", st);
             rebuild_tiny_brick<uint8_t><<<J.n, kRbTinyThreads, smem_b, st>>>(V, J, out, out_off, status);
             return cudaGetLastError();
         }
         if (V.N <= 4) {
-            e = cudaFuncSetAttribute(rebuild_small_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+            e = func_attr((const void *)rebuild_small_brick<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;
             ProfScope ps("rebuild", st);
             rebuild_small_brick<uint8_t><<<J.n, kRbSmallThreads, smem_b, st>>>(V, J, out, out_off, status);
@@ -1801,11 +1821,11 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             const uint32_t lt = S.leafc_threads == 256 ? 256u : 128u;
             auto lk = lt == 256 ? rebuild_leafc<256> : rebuild_leafc<128>;
             uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
-            e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
+            e = func_attr((const void *)lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
             if (e == cudaSuccess)  // the largest shared-memory carve-out: 8 CTAs per SM at 128 threads
-                e = cudaFuncSetAttribute(lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+                e = func_attr((const void *)lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+                e = func_attr((const void *)rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
             if (e != cudaSuccess) return e;
             ProfScope ps("rebuild", st);
             lk<<<J.n, lt, smem_l, st>>>(V, J, out, out_off, status, J.lists, n_full);
@@ -1813,7 +1833,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
                                                                              n_full, n_full + 1);
             return cudaGetLastError();
         }
-        e = cudaFuncSetAttribute(rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
+        e = func_attr((const void *)rebuild<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
         if (e != cudaSuccess) return e;
         ProfScope ps("rebuild", st);
         rebuild<uint8_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);

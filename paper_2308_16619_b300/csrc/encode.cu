@@ -709,9 +709,9 @@ __global__ void __launch_bounds__(kEncSmallThreads, 16)
 // One coding substep: lanes with `act` code `sym` into their state x (Sec. 3.3, R9); renormalisation words go
 // below `top`, in lane order.
 __device__ __forceinline__ void rans_code_substep(uint32_t &x, uint32_t &top, uint16_t *words, uint32_t sym, bool act,
-                                                  uint32_t f_reg, uint32_t c_reg, uint32_t m_reg, uint32_t smask,
-                                                  uint32_t lt) {
-    const uint32_t f = __shfl_sync(kFull, f_reg, sym), c = __shfl_sync(kFull, c_reg, sym);
+                                                  uint32_t fc_reg, uint32_t m_reg, uint32_t smask, uint32_t lt) {
+    // the lanes hold f | c << 16 (f <= 4096, c < 4096) and the reciprocal m of f for their symbol
+    const uint32_t fc = __shfl_sync(kFull, fc_reg, sym), f = fc & 0xFFFFu, c = fc >> 16;
     const uint32_t mf = __shfl_sync(kFull, m_reg, sym);
     // renormalise before coding: keep x below f * 2^20 (one 16-bit word at most)
     const bool emit = act && x >= (f << 20);
@@ -754,6 +754,7 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     const uint32_t m_reg = 0xFFFFFFFFu / f_reg;  // reciprocal of f for the quotient x / f
     uint32_t c_reg = 0;
     for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < lane) ? F[s2] : 0u;
+    const uint32_t fc_reg = f_reg | (c_reg << 16);
     const uint32_t K = lanes_for(n, G.K_max, G.S_min);
     const uint32_t lt = lanemask_lt();
     uint32_t top = cap;
@@ -774,8 +775,8 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
                 const bool act = lane < K && i < n_ops;
                 const uint32_t o = act ? (uint32_t)wsm[first + i - lo16] : 0u;
                 const bool pd = act && (o & 7u) == OP_PD;
-                if (__any_sync(kFull, pd)) rans_code_substep(x, top, words, o >> 4, pd, f_reg, c_reg, m_reg, kFull, lt);
-                rans_code_substep(x, top, words, o & 15u, act, f_reg, c_reg, m_reg, kFull, lt);
+                if (__any_sync(kFull, pd)) rans_code_substep(x, top, words, o >> 4, pd, fc_reg, m_reg, kFull, lt);
+                rans_code_substep(x, top, words, o & 15u, act, fc_reg, m_reg, kFull, lt);
             }
             // this window's op bytes are read for the last time (the op array is dead after this kernel); the
             // lines shared with the next window down or with the brick's other stream are kept
@@ -814,6 +815,7 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
     const uint32_t m_reg = 0xFFFFFFFFu / (f_reg ? f_reg : 1u);  // reciprocal of f for the quotient x / f
     uint32_t c_reg = 0;
     for (uint32_t s2 = 0; s2 < 16; s2++) c_reg += (s2 < tsym) ? F[s2] : 0u;
+    const uint32_t fc_reg = f_reg | (c_reg << 16);
     uint8_t *wbase = smem_raw + warp * kRansEncWin;
     const uint32_t g_end = min(kEpkSegs, n_q - q0);
     uint32_t g = 0;
@@ -888,8 +890,8 @@ __global__ void __launch_bounds__(kRansEncWarps * 32)
             const bool pd = act && (o & 7u) == OP_PD;
             // the deltas first, then the ops: the reverse of the decoder's order (entry 16 st + s of the tables)
             if (__any_sync(kFull, pd))
-                rans_code_substep(x, top, words, (o >> 4) + 16 * st, pd, f_reg, c_reg, m_reg, smask, lt);
-            rans_code_substep(x, top, words, (o & 15u) + 16 * st, act, f_reg, c_reg, m_reg, smask, lt);
+                rans_code_substep(x, top, words, (o >> 4) + 16 * st, pd, fc_reg, m_reg, smask, lt);
+            rans_code_substep(x, top, words, (o & 15u) + 16 * st, act, fc_reg, m_reg, smask, lt);
             if (run) s_hi--;
         }
         // final states ahead of the words, state 0 first, low half first
