@@ -230,10 +230,24 @@ __device__ __forceinline__ uint32_t palette_chunk(uint32_t lab, uint32_t kn, uin
 }
 
 // Encode (or, when count != nullptr, only count the nibbles of) one brick: phases A-D.
-template <uint32_t kT>  // threads per CTA: 64..256
+// kT: threads per CTA (64..256); kN: the brick's N when the kernel is launched for that brick size only
+// (at most 5: the level arrays in shared memory), else 0; with it the brick's geometry and every level offset
+// fold to constants (encode_kernel on voronoi512 b=32: 194 M -> 163 M warp instructions, 0.279 -> 0.247 ms)
+template <uint32_t kT, uint32_t kN = 0>
 __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride,
                                              uint32_t n_in_batch, EncScratch SC, unsigned long long *count) {
+    static_assert(kN <= 5, "bricks of 64^3 keep their level arrays in global memory");
     extern __shared__ __align__(16) uint8_t smem_raw[];
+    if constexpr (kN != 0) {
+        if (G.N != kN) return;  // launched for another brick size
+        G.N = kN;
+        G.b = 1u << kN;
+        uint32_t u = 0;
+#pragma unroll
+        for (uint32_t l = 1; l <= kN; l++) u += 1u << (3 * (kN - l));
+        G.up_nodes = u;
+        G.lvl_bytes = 0;
+    }
     EncSmem S(smem_raw, G, SC.lvl + (size_t)blockIdx.x * G.lvl_bytes);
     __shared__ uint32_t hist[32];
     __shared__ uint32_t sh_np;
@@ -329,6 +343,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         }
         __syncthreads();
         // levels of more than 64 nodes by the whole CTA, the smaller ones by warp 0 alone (no CTA barriers)
+#pragma unroll
         for (uint32_t l = 2; l <= N; l++) {
             const uint32_t nl = 1u << (3 * (N - l));
             const bool big = nl > 64;
@@ -682,20 +697,22 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
 
 // 4 CTAs per SM (64 registers): the compiler's own choice for this body, kept as a bound so that edits
 // elsewhere in it do not drop the kernel to 3 CTAs per SM
+template <uint32_t kN>  // 5 for bricks of 32^3, 0 (any size) for larger ones
 __global__ void __launch_bounds__(kEncThreads, 4)
     encode_kernel(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
                   EncScratch SC, unsigned long long *count) {
-    encode_brick<kEncThreads>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
+    encode_brick<kEncThreads, kN>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
 }
 
 // The same for bricks of 16^3 and smaller, which need little shared memory (6.4 KB at 16^3): 128-thread CTAs,
 // 16 per SM at 32 registers a thread.  For the 32768 bricks of a 512^3 volume at 16^3: 0.51 ms, against 0.53
 // (64 threads, 24 per SM), 0.60 (256 threads, 8 per SM) and 0.71 ms (256 threads, 4 per SM).
 constexpr uint32_t kEncSmallThreads = 128;
+template <uint32_t kN>  // 4 for bricks of 16^3, 0 (any size) for smaller ones
 __global__ void __launch_bounds__(kEncSmallThreads, 16)
     encode_kernel_small(EncVol EV, EncGeom G, uint64_t brick0, uint64_t brick_stride, uint32_t n_in_batch,
                         EncScratch SC, unsigned long long *count) {
-    encode_brick<kEncSmallThreads>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
+    encode_brick<kEncSmallThreads, kN>(EV, G, brick0, brick_stride, n_in_batch, SC, count);
 }
 
 // ---- E. rANS, one warp per stream (brick slot q / 2, stream q % 2), from the op bytes of the encode kernel
@@ -1216,14 +1233,15 @@ cudaError_t launch_encode(const EncVol &EV, const EncGeom &G, uint64_t brick0, u
                           const uint32_t *freq, const EncScratch &SC, unsigned long long *count, cudaStream_t st) {
     // bricks of 16^3 and smaller: more CTAs per SM (encode_kernel_small)
     const bool small = G.N <= 4;
-    cudaError_t e = cudaFuncSetAttribute(small ? encode_kernel_small : encode_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
+    // the brick sizes of the benchmarks (32^3, 16^3) take kernels specialised for them
+    auto k = small ? (G.N == 4 ? encode_kernel_small<4> : encode_kernel_small<0>)
+                   : (G.N == 5 ? encode_kernel<5> : encode_kernel<0>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps(count ? "encode_count" : "encode", st);
-        if (small) encode_kernel_small<<<n, kEncSmallThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
-        else encode_kernel<<<n, kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
+        k<<<n, small ? kEncSmallThreads : kEncThreads, G.smem, st>>>(EV, G, brick0, stride, n, SC, count);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || count || !freq) return e;  // no tables yet: the caller codes later
