@@ -472,6 +472,70 @@ __device__ __forceinline__ void rec_masks(uint64_t r8, uint32_t &nr, uint32_t &p
     st = gather4(lo << 4) | gather4(hi << 4) << 4;
 }
 
+// bytes of m with bit 7 set -> 0xFF, the others -> 0 (prmt replicating the sign bit of each byte)
+__device__ __forceinline__ uint32_t sext_bytes(uint32_t m) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(m));
+    return r;
+}
+// 0xFF in the bytes of o (each 0..7) equal to those of c, else 0
+__device__ __forceinline__ uint32_t bytes_eq(uint32_t o, uint32_t c) {
+    return sext_bytes(~((o ^ c) + 0x7F7F7F7Fu) & 0x80808080u);
+}
+__device__ __forceinline__ uint32_t bsel(uint32_t a, uint32_t b, uint32_t m) { return (a & ~m) | (b & m); }
+// bit 7 set in the bytes where a < b, for bytes b < 0x80
+__device__ __forceinline__ uint32_t bytes_lt(uint32_t a, uint32_t b) {
+    return ~(((a | 0x80808080u) - b) | a) & 0x80808080u;
+}
+
+// The 8 children of a non-constant node with uint8 indices, from its 8 op records at once (child c in byte
+// c % 4 of word c / 4, byte-wise SIMD in two registers; the same values as one child at a time, Alg. 1): R_p
+// the node's index pk; R_a toward +axis (the child's a-bit set) the index of the node's +a neighbour
+// (px, py, pz; R4); R_a toward -axis the sentinel kSent + a; P_0 / P_a / P_delta the palette index i_p, i_p + 1,
+// i_p - 1 - delta, i_p being ipl plus the node's P_a records before the child (R1, R3).  Sets `minus` (bit c:
+// an R_a child toward -axis) and the stop bits `st`; returns false if the records cannot belong to this node:
+// op 7, a stop bit on the leaf level, a step out of the brick (lo3 / hi3: the node on the low / high face of
+// axis a, bit a), a P_a past the palette or a P_delta before its first entry.
+__device__ __forceinline__ bool kids8_u8(uint64_t r8, uint32_t ipl, uint32_t pk, uint32_t px, uint32_t py, uint32_t pz,
+                                         uint32_t lo3, uint32_t hi3, uint32_t np, bool leaf, uint2 &v8,
+                                         uint32_t &minus, uint32_t &st) {
+    constexpr uint32_t B1 = 0x01010101u, BX = 0xFF00FF00u, BY = 0xFFFF0000u, S = RbTraits<uint8_t>::kSent;
+    const uint32_t w0 = (uint32_t)r8, w1 = (uint32_t)(r8 >> 32);
+    const uint32_t o0 = w0 & 0x07070707u, o1 = w1 & 0x07070707u;
+    const uint32_t x0 = bytes_eq(o0, B1), x1 = bytes_eq(o1, B1);
+    const uint32_t y0 = bytes_eq(o0, 2 * B1), y1 = bytes_eq(o1, 2 * B1);
+    const uint32_t z0 = bytes_eq(o0, 3 * B1), z1 = bytes_eq(o1, 3 * B1);
+    const uint32_t d0 = bytes_eq(o0, 5 * B1), d1 = bytes_eq(o1, 5 * B1);             // P_delta
+    const uint32_t a0 = bytes_eq(o0, 6 * B1) & B1, a1 = bytes_eq(o1, 6 * B1) & B1;   // P_a: 1 per byte
+    const uint32_t p0 = sext_bytes(o0 << 5), p1 = sext_bytes(o1 << 5);                // ops 4..7
+    // i_p before each child: byte sums of the P_a bytes before it (at most 7: no carries)
+    const uint32_t na0 = (a0 * B1) >> 24, na1 = (a1 * B1) >> 24;
+    const uint32_t i0 = ipl * B1 + a0 * 0x01010100u, i1 = (ipl + na0) * B1 + a1 * 0x01010100u;
+    const uint32_t e0 = B1 + ((w0 >> 4) & 0x0F0F0F0Fu), e1 = B1 + ((w1 >> 4) & 0x0F0F0F0Fu);  // 1 + delta
+    uint32_t v0 = pk * B1, v1 = pk * B1;
+    v0 = bsel(v0, px * B1, x0 & BX);
+    v0 = bsel(v0, S * B1, x0 & ~BX);
+    v1 = bsel(v1, px * B1, x1 & BX);
+    v1 = bsel(v1, S * B1, x1 & ~BX);
+    v0 = bsel(v0, py * B1, y0 & BY);
+    v0 = bsel(v0, (S + 1) * B1, y0 & ~BY);
+    v1 = bsel(v1, py * B1, y1 & BY);
+    v1 = bsel(v1, (S + 1) * B1, y1 & ~BY);
+    v0 = bsel(v0, (S + 2) * B1, z0);  // children 0..3 lie toward -z
+    v1 = bsel(v1, pz * B1, z1);        // children 4..7 toward +z
+    v0 = bsel(v0, i0 + a0 - (d0 & e0), p0);
+    v1 = bsel(v1, i1 + a1 - (d1 & e1), p1);
+    v8 = make_uint2(v0, v1);
+    minus = gather4((x0 & ~BX) | (y0 & ~BY) | z0) | gather4((x1 & ~BX) | (y1 & ~BY)) << 4;
+    st = gather4(w0 << 4) | gather4(w1 << 4) << 4;
+    const uint32_t xs = x0 | x1, ys = y0 | y1;
+    const bool bad = (((o0 + B1) | (o1 + B1)) & 0x08080808u) != 0 || (leaf && st != 0) ||
+                     ((hi3 & 1u) && (xs & BX)) || ((lo3 & 1u) && (xs & ~BX)) || ((hi3 & 2u) && (ys & BY)) ||
+                     ((lo3 & 2u) && (ys & ~BY)) || ((hi3 & 4u) && z1) || ((lo3 & 4u) && z0) ||
+                     ((a0 | a1) && ipl + na0 + na1 >= np) || ((bytes_lt(i0, e0) & d0) | (bytes_lt(i1, e1) & d1)) != 0;
+    return !bad;
+}
+
 // The -axis children of a level are resolved in three rounds.  A child c whose a-bit is 0 and whose op is R_a
 // reads the node before it along a, which is child c | (1 << a) of the neighbouring parent: a child index with
 // one more bit set.  Children with all three bits set are never -axis children, so resolving the -axis children
@@ -823,6 +887,21 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
         const uint32_t k = parent_of(j);
         const uint64_t r8 = kSmemRec ? *(const uint64_t *)(R + 8 * j) : __ldg((const unsigned long long *)(R + 8 * j));
         const uint32_t ipl = ip0 + (kSmemRec ? T8[j] : __ldg(T8 + j));
+        if constexpr (sizeof(IdxT) == 1) {  // the 8 children at once
+            const uint32_t lo3 = ((k & kMX & pbits) == 0 ? 1u : 0u) | ((k & kMY & pbits) == 0 ? 2u : 0u) |
+                                 ((k & kMZ & pbits) == 0 ? 4u : 0u);
+            const uint32_t hi3 = ((k & kMX & pbits) == (kMX & pbits) ? 1u : 0u) |
+                                 ((k & kMY & pbits) == (kMY & pbits) ? 2u : 0u) |
+                                 ((k & kMZ & pbits) == (kMZ & pbits) ? 4u : 0u);
+            const uint32_t px = P[minc(k, kMX) & pbits], py = P[minc(k, kMY) & pbits], pz = P[minc(k, kMZ) & pbits];
+            uint2 v8;
+            uint32_t minus_m, st;
+            bad |= !kids8_u8(r8, ipl, P[k], px, py, pz, lo3, hi3, np, !cmC, v8, minus_m, st);
+            if (cmC) cmC[k] = (uint8_t)st;
+            *(uint2 *)(C + 8 * k) = v8;
+            mm[j] = (uint8_t)minus_m;
+            continue;
+        }
         uint32_t nr, pm, st;
         rec_masks(r8, nr, pm, st);
         if (cmC) cmC[k] = (uint8_t)st;
@@ -945,7 +1024,7 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
     }
     __syncthreads();
 
-    // pass B: one thread per listed node decodes its 8 records (children of R_p keep the node's index).  Its
+    // pass B: one thread per listed node decodes its 8 records at once (kids8_u8) into E[8j .. 8j + 7].  Its
     // -axis children are also appended to a list (node << 3 | child) in the part of the E area past the listed
     // nodes, for pass C; the list's length is counted even when it does not fit.
     bool bad = false;
@@ -958,36 +1037,16 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
         const uint32_t k = act[j];
         const uint64_t r8 = __ldg((const unsigned long long *)(R + 8 * j));
         const uint32_t ipl = ip0 + __ldg(T8 + j);
-        uint32_t nr, pm, st;
-        rec_masks(r8, nr, pm, st);
-        const uint32_t lo = (uint32_t)r8, hi = (uint32_t)(r8 >> 32);
-        bad |= (((lo & 0x07070707u) + 0x01010101u) & 0x08080808u) != 0 ||
-               (((hi & 0x07070707u) + 0x01010101u) & 0x08080808u) != 0 || st != 0 ||
-               (pm != 0 && ipl + __popc(pm) >= np);
         const uint32_t lo3 = ((k & kMX & pbits) == 0 ? 1u : 0u) | ((k & kMY & pbits) == 0 ? 2u : 0u) |
                              ((k & kMZ & pbits) == 0 ? 4u : 0u);
         const uint32_t hi3 = ((k & kMX & pbits) == (kMX & pbits) ? 1u : 0u) |
                              ((k & kMY & pbits) == (kMY & pbits) ? 2u : 0u) |
                              ((k & kMZ & pbits) == (kMZ & pbits) ? 4u : 0u);
-        uint64_t e8 = 0x0101010101010101ull * (uint64_t)P[k];
-        while (nr) {
-            const uint32_t ch = __ffs(nr) - 1;
-            nr &= nr - 1;
-            const uint32_t o = ((ch & 4u ? hi : lo) >> (8 * (ch & 3u))) & 0xFFu;
-            const uint32_t op = o & 7u, delta = o >> 4;
-            const uint32_t ipc = ipl + __popc(pm & ((1u << ch) - 1u));
-            const bool rx = op <= OP_RZ;  // R_x, R_y, R_z (op != R_p here)
-            const uint32_t a = (op - OP_RX) & 3u;
-            const bool plus = rx && ((ch >> a) & 1u);
-            const bool minus = rx && !plus;
-            const uint32_t pv = P[minc(k, kMX << a) & pbits];  // +axis: the neighbour's parent (R4)
-            uint32_t v = ipc + (op == OP_PA ? 1u : 0u) - (op == OP_PD ? 1u + delta : 0u);  // R1, R3
-            v = plus ? pv : minus ? sent + a : v;
-            bad |= (plus && ((hi3 >> a) & 1u)) || (minus && ((lo3 >> a) & 1u)) || (op == OP_PD && ipc < 1 + delta);
-            e8 = (e8 & ~(0xFFull << (8 * ch))) | ((uint64_t)(v & 0xFFu) << (8 * ch));
-            minus_m |= (minus ? 1u : 0u) << ch;
-        }
-        *(uint64_t *)(E + 8 * j) = e8;
+        const uint32_t px = P[minc(k, kMX) & pbits], py = P[minc(k, kMY) & pbits], pz = P[minc(k, kMZ) & pbits];
+        uint2 v8;
+        uint32_t st;
+        bad |= !kids8_u8(r8, ipl, P[k], px, py, pz, lo3, hi3, np, true, v8, minus_m, st);
+        *(uint2 *)(E + 8 * j) = v8;
         mm[j] = (uint8_t)minus_m;
       }
       // append this warp's -axis children to the list: one atomic per warp
