@@ -749,7 +749,8 @@ __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t 
 
 // Levels with at most kSmallPar parents (the top of the tree): one thread per child in Morton order,
 // the whole CTA.  The j-th non-constant parent's records sit at 8j; j, i_p and the stop bits come from
-// the active-parent mask and warp ballots over a parent's 8 lanes.  Arguments as for rebuild_level.
+// the active-parent mask and warp ballots over a parent's 8 lanes.  With uint8 indices a thread takes a whole
+// parent instead (kids8_u8).  Arguments as for rebuild_level.
 template <typename IdxT, bool kSmemRec, uint32_t kT>
 __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t l,
                                                     const uint8_t *R, const uint16_t *T8, uint32_t n_left,
@@ -769,6 +770,47 @@ __device__ __forceinline__ bool rebuild_small_level(uint8_t *smem, const RbLayou
     const uint64_t amask = !cmP ? 1ull : npar == 8 ? (~(uint64_t)cmP[0] & 0xFFull) : ~*(const uint64_t *)cmP;
     n_act = __popcll(amask);
     if (8 * n_act > n_left) return false;  // uniform
+    if constexpr (sizeof(IdxT) == 1) {  // uint8 indices: a thread per parent, its 8 children at once (kids8_u8)
+        uint8_t *mb = reinterpret_cast<uint8_t *>(ms->msk);  // -axis children of parent k (bit c)
+        bool bad = false;
+        for (uint32_t k = threadIdx.x; k < npar; k += kT) {
+            uint2 v8;
+            uint32_t minus = 0, st = 0xFFu;
+            if ((amask >> k) & 1ull) {
+                const uint32_t j = __popcll(amask & ((1ull << k) - 1ull));
+                const uint64_t r8 = kSmemRec ? *(const uint64_t *)(R + 8 * j) : __ldg((const unsigned long long *)(R + 8 * j));
+                const uint32_t ipl = ip0 + (kSmemRec ? T8[j] : __ldg(T8 + j));
+                const uint32_t lo3 = ((k & kMX & pbits) == 0 ? 1u : 0u) | ((k & kMY & pbits) == 0 ? 2u : 0u) |
+                                     ((k & kMZ & pbits) == 0 ? 4u : 0u);
+                const uint32_t hi3 = ((k & kMX & pbits) == (kMX & pbits) ? 1u : 0u) |
+                                     ((k & kMY & pbits) == (kMY & pbits) ? 2u : 0u) |
+                                     ((k & kMZ & pbits) == (kMZ & pbits) ? 4u : 0u);
+                const uint32_t px = P[minc(k, kMX) & pbits], py = P[minc(k, kMY) & pbits], pz = P[minc(k, kMZ) & pbits];
+                bad |= !kids8_u8(r8, ipl, P[k], px, py, pz, lo3, hi3, np, !cmC, v8, minus, st);
+            } else {  // a constant parent: its children repeat it
+                const uint32_t r = 0x01010101u * (uint32_t)P[k];
+                v8 = make_uint2(r, r);
+            }
+            *(uint2 *)(C + 8 * k) = v8;
+            if (cmC) cmC[k] = (uint8_t)st;
+            mb[k] = (uint8_t)minus;
+        }
+        if (threadIdx.x == 0) ms->bad = 0;
+        __syncthreads();
+        if (bad) ms->bad = 1;
+        volatile IdxT *Cv = C;
+        for (uint32_t k = threadIdx.x; k < npar; k += kT) {
+            uint32_t m = mb[k];
+            while (m) {
+                const uint32_t c = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t q = 8 * k + c;
+                Cv[q] = (IdxT)chase<IdxT>(Cv, q, Cv[q], cbits);
+            }
+        }
+        __syncthreads();
+        return ms->bad == 0;
+    }
     const uint32_t nch = 8 * npar, steps = (nch + 31) / 32;
     const uint32_t grp = 0xFFu << (lane & 24u), lt = lanemask_lt();
     bool bad = false;
