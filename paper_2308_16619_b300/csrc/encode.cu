@@ -437,13 +437,8 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         n_act_total = n_act_all;
     }
     const uint32_t n_ops = 8 * n_act_total, n_int_ops = 8 * lvl_rank[1];
-    for (uint32_t r = tid; r < n_act_total; r += kT) {
-        uint32_t l = N;
-        for (uint32_t L = 1; L < N; L++)
-            if (r >= lvl_rank[L]) {
-                l = L;
-                break;
-            }
+    // the parent of rank r on level l
+    auto parent_ops = [&](uint32_t r, uint32_t l) {
         const uint32_t lc = l - 1;
         const uint32_t p = S.list[r];
         // one thread per active parent: its 8 children, the parents next to it toward +axis, and the nodes
@@ -524,7 +519,7 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             }
             uint2 st2 = make_uint2(0u, 0u);
             if (lc >= 1) st2 = *(const uint2 *)(S.cst + loff(G.N, lc) + 8 * p);  // flags 0 / 1, one byte each
-            uint32_t w[2] = {0u, 0u};
+            uint32_t w[2] = {0u, 0u}, need = 0;
 #pragma unroll
             for (uint32_t c = 0; c < 8; c++) {
                 const bool bx = c & 1u, by = c & 2u, bz = c & 4u;
@@ -538,14 +533,34 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
                                     : kNeedPal;
                 const uint32_t stop = ((c < 4 ? st2.x : st2.y) >> (8 * (c & 3u))) & 1u;
                 w[c >> 2] |= (op | (stop << 3)) << (8 * (c & 3u));
-                if (op == kNeedPal) {  // gathered with its label for the palette pass (first 256)
-                    const uint32_t at = atomicAdd(&sh_npc, 1u);
-                    if (at < 256) S.plist[at] = make_uint2((8 * r + c) << 1 | stop, v[c]);  // op index, stop bit
-                }
+                need |= (op == kNeedPal ? 1u : 0u) << c;
+            }
+            if (need) {  // the children no reuse fits, gathered with their labels for the palette pass (first 256)
+                uint32_t at = atomicAdd(&sh_npc, (uint32_t)__popc(need));
+#pragma unroll
+                for (uint32_t c = 0; c < 8; c++)
+                    if ((need >> c) & 1u) {
+                        const uint32_t stop = ((c < 4 ? st2.x : st2.y) >> (8 * (c & 3u))) & 1u;
+                        if (at < 256) S.plist[at] = make_uint2((8 * r + c) << 1 | stop, v[c]);  // op index, stop bit
+                        at++;
+                    }
             }
             *(uint2 *)(ops + 8 * r) = make_uint2(w[0], w[1]);
         }
+    };
+    // thread t takes the ranks r = t (mod kT): the parents above level 1 first (their level by rank), then
+    // those of level 1, whose children are voxels (a loop of its own, specialised on the level)
+    const uint32_t r_leaf = lvl_rank[1];
+    for (uint32_t r = tid; r < r_leaf; r += kT) {
+        uint32_t l = N;
+        for (uint32_t L = 2; L < N; L++)
+            if (r >= lvl_rank[L]) {
+                l = L;
+                break;
+            }
+        parent_ops(r, l);
     }
+    for (uint32_t r = r_leaf + (tid + kT - r_leaf % kT) % kT; r < n_act_total; r += kT) parent_ops(r, 1u);
     __syncthreads();
 
     // each warp takes a contiguous range of the op array in phases C and D
