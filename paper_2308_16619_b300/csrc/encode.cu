@@ -382,8 +382,19 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
             const uint32_t valid = 16 * q + 16 <= ne ? 0xFFFFu : (1u << (ne - 16 * q)) - 1u;
             return m & valid;
         };
+        // one brick size: a thread's chunk masks are computed once and kept in registers
+        constexpr uint32_t kCpt = kN ? ((((1u << (3 * kN)) - 1u) / 7u + 15u) / 16u + kT - 1u) / kT : 1u;
+        uint32_t mk[kCpt];
         uint32_t cnt = 0;
-        for (uint32_t q = q0; q < q1; q++) cnt += __popc(act_mask(q));
+        if constexpr (kN != 0) {
+#pragma unroll
+            for (uint32_t j = 0; j < kCpt; j++) {
+                mk[j] = q0 + j < q1 ? act_mask(q0 + j) : 0u;
+                cnt += __popc(mk[j]);
+            }
+        } else {
+            for (uint32_t q = q0; q < q1; q++) cnt += __popc(act_mask(q));
+        }
         uint32_t incl = cnt;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -399,8 +410,11 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         for (uint32_t l = 1; l <= (uint32_t)kMaxN; l++) bnd[l] = l <= N ? loff(G.N, l) : ne;
         {
             uint32_t run = base;
-            for (uint32_t q = q0; q < q1; q++) {
-                const uint32_t m = act_mask(q);
+#pragma unroll
+            for (uint32_t j = 0; j < (kN ? kCpt : q1 - q0); j++) {
+                const uint32_t q = q0 + j;
+                if (q >= q1) break;
+                const uint32_t m = kN ? mk[j] : act_mask(q);
 #pragma unroll
                 for (uint32_t l = 2; l <= (uint32_t)kMaxN; l++)
                     if (l <= N && bnd[l] >= 16 * q && bnd[l] < 16 * q + 16)
@@ -415,8 +429,33 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
         __syncthreads();
         // stream rank of each active parent: S.list[rank] = its index within its level
         uint32_t run = base;
-        for (uint32_t q = q0; q < q1; q++) {
-            uint32_t m = act_mask(q);
+#pragma unroll
+        for (uint32_t j = 0; j < (kN ? kCpt : q1 - q0); j++) {
+            const uint32_t q = q0 + j;
+            if (q >= q1) break;
+            uint32_t m = kN ? mk[j] : act_mask(q);
+            if (kN) {  // a chunk inside one level (all but the chunks where a level starts past their first node)
+                uint32_t lq = 1, lb = 0;
+                bool inside = false;
+#pragma unroll
+                for (uint32_t L = 2; L <= (uint32_t)kMaxN; L++) {
+                    if (L <= N && 16 * q >= bnd[L]) {
+                        lq = L;
+                        lb = bnd[L];
+                    }
+                    inside |= L <= N && bnd[L] > 16 * q && bnd[L] < 16 * q + 16;
+                }
+                if (!inside) {
+                    uint32_t r = n_act_all - lvl_sp[lq + 1] + run - lvl_sp[lq];
+                    const uint32_t e0 = 16 * q - lb;
+                    run += __popc(m);
+                    while (m) {
+                        S.list[r++] = (uint16_t)(e0 + __ffs(m) - 1);
+                        m &= m - 1;
+                    }
+                    continue;
+                }
+            }
             while (m) {
                 const uint32_t k = __ffs(m) - 1, e = 16 * q + k;
                 m &= m - 1;
