@@ -562,3 +562,51 @@ def test_b64_range_and_corrupt_status():
         out, off, st = gpu_decode(bad, 6, ids, lods)
         assert st[0] in (0, 4) and st[1] == 0
         assert np.array_equal(out[off[1]:], ref[off[1]:])
+
+
+@pytest.mark.parametrize("b", [32, 16, 8])
+def test_edited_op_streams_decode_like_the_oracle(b):
+    """Random edits of one brick's op streams (reuse ops exchanged, P_delta inserted, removed or given another
+    delta, P_a added or dropped, op 7, stop bits set or flipped; tests/stream_mutants.py), each edited pair
+    rANS-coded with the oracle's coder into a brick of its own: at every LOD the CUDA decoder either gives the
+    labels the oracle decodes from the edited nibbles (Alg. 1) or, exactly when the oracle rejects them,
+    status 4.  The edits reach op combinations the encoder never emits (R_a toward +axis next to P_delta, P_a
+    runs, deltas past the palette), so this pins the byte-wise 8-children decode of the rebuild against the
+    oracle's one child at a time."""
+    from tests import stream_mutants as SM
+    N = b.bit_length() - 1
+    base = synth.voronoi((b, b, b), 40 if b == 32 else 12, seed=11)
+    pal, ni, nl = O.encode_brick(base)
+    V = O.encode_volume(base, N, stride=1)
+    freq = np.asarray(V.freq, np.uint32)
+    rng = np.random.default_rng(100 + b)
+    edits = [(ni, nl)] + SM.mutants(rng, ni, nl, 63)
+    M = len(edits)
+    pal_off = np.arange(M + 1, dtype=np.uint64) * len(pal)
+    int_w, leaf_w, int_off, leaf_off, nis, nls = [], [], [0], [0], [], []
+    for e_i, e_l in edits:
+        wi = O.rans_encode(e_i, O.lanes(len(e_i), 32, 256), freq[:16]) if len(e_i) else np.zeros(0, np.uint16)
+        wl = O.rans_encode(e_l, O.lanes(len(e_l), 32, 256), freq[16:]) if len(e_l) else np.zeros(0, np.uint16)
+        int_w.append(wi)
+        leaf_w.append(wl)
+        int_off.append(int_off[-1] + len(wi))
+        leaf_off.append(leaf_off[-1] + len(wl))
+        nis.append(len(e_i))
+        nls.append(len(e_l))
+    csgv = _csgv()
+    gv = csgv.csgv_volume_import(N, (b * M, b, b), 32, 256, freq, pal_off, np.tile(pal, M),
+                                 np.asarray(int_off, np.uint64), np.concatenate(int_w).astype(np.uint16),
+                                 np.asarray(leaf_off, np.uint64), np.concatenate(leaf_w).astype(np.uint16),
+                                 np.asarray(nis, np.uint32), np.asarray(nls, np.uint32))
+    valid = 0
+    for t in range(N + 1):
+        out, off, st = gpu_decode(gv, N, np.arange(M, dtype=np.uint32), np.full(M, t, np.uint8))
+        for m, (e_i, e_l) in enumerate(edits):
+            ref, rc = O.decode_brick(pal, e_i, e_l, N, t)
+            if rc == O.ORC_OK:
+                valid += t == 0
+                assert st[m] == 0, (t, m, st[m])
+                assert np.array_equal(out[off[m]:off[m] + ref.size], ref.ravel()), (t, m)
+            else:
+                assert rc == O.ORC_ERR_CORRUPT and st[m] == 4, (t, m, rc, st[m])
+    assert 10 <= valid < M  # both outcomes are exercised

@@ -495,3 +495,23 @@ def test_decoded_bytes_are_multiples_of_lod_size():
     assert [(32 >> t) ** 3 for t in range(6)] == [32768, 4096, 512, 64, 8, 1]
     assert sum(8 ** k for k in range(6)) == O.pyramid_nodes(5)
     assert math.isclose(sum((32 >> t) ** 3 for t in range(6)) / 6, 6241.5)
+
+
+def test_stream_edits_keep_the_grammar_and_the_oracle_total():
+    """The stream editor of the GPU edit tests (tests/stream_mutants.py): parsing and flattening a real stream
+    is the identity, and on its edits the oracle's decoder always returns labels from the palette or a corrupt
+    status, never anything else (the edits reach both outcomes)."""
+    import synth
+    from tests import stream_mutants as SM
+    base = synth.voronoi((16, 16, 16), 12, seed=11)
+    pal, ni, nl = O.encode_brick(base)
+    assert np.array_equal(SM.flatten(SM.parse(ni)), ni) and np.array_equal(SM.flatten(SM.parse(nl)), nl)
+    seen = set()
+    for e_i, e_l in SM.mutants(np.random.default_rng(5), ni, nl, 60):
+        for t in range(5):
+            lab, rc = O.decode_brick(pal, e_i, e_l, 4, t)
+            assert rc in (O.ORC_OK, O.ORC_ERR_CORRUPT)
+            if rc == O.ORC_OK:
+                assert np.isin(lab, pal).all()
+            seen.add(rc)
+    assert seen == {O.ORC_OK, O.ORC_ERR_CORRUPT}
