@@ -509,7 +509,13 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
                 const uint32_t x0 = 2 * compact6(p), y0 = 2 * compact6(p >> 1), z0 = 2 * compact6(p >> 2);
                 if (B.interior && (B.X & 1u) == 0 && (reinterpret_cast<uintptr_t>(B.vol) & 7u) == 0) {
                     // rows of two voxels (x0 is even, rows 8-byte aligned): the 8 children in four 8-byte loads,
-                    // their -x neighbours from the 8 bytes before each row, -y and -z from the rows before
+                    // their -x neighbours from the 8 bytes before each row, -y and -z from the rows before; a -axis
+                    // neighbour node that is constant (81 % of the L1 nodes here) has its label in every voxel, so
+                    // its voxels are not loaded
+                    const uint8_t *Cp = S.cst + loff(G.N, l);
+                    const uint32_t qx = mdec(p, pmx), qy = mdec(p, pmy), qz = mdec(p, pmz);
+                    const bool kx = !lox && Cp[qx], ky = !loy && Cp[qy], kz = !loz && Cp[qz];
+                    const uint32_t lx = Lp[qx], ly = Lp[qy], lz = Lp[qz];
                     const uint32_t *r0 = B.base + B.sz * z0 + B.sy * y0 + x0;
 #pragma unroll
                     for (uint32_t k = 0; k < 4; k++) {  // k = dy + 2 dz, children 2k and 2k + 1
@@ -517,17 +523,21 @@ __device__ __forceinline__ void encode_brick(EncVol EV, EncGeom G, uint64_t bric
                         const uint2 a = __ldg(reinterpret_cast<const uint2 *>(rk));
                         v[2 * k] = a.x;
                         v[2 * k + 1] = a.y;
-                        nx[2 * k] = lox ? 0u : __ldg(reinterpret_cast<const uint2 *>(rk - 2)).y;
+                        nx[2 * k] = lox ? 0u : kx ? lx : __ldg(reinterpret_cast<const uint2 *>(rk - 2)).y;
                         nx[2 * k + 1] = 0u;
                         if ((k & 1u) == 0) {  // y-bit 0: the row before along y
-                            const uint2 m = loy ? make_uint2(0u, 0u) : __ldg(reinterpret_cast<const uint2 *>(rk - B.sy));
+                            const uint2 m = loy ? make_uint2(0u, 0u)
+                                            : ky  ? make_uint2(ly, ly)
+                                                  : __ldg(reinterpret_cast<const uint2 *>(rk - B.sy));
                             ny[2 * k] = m.x;
                             ny[2 * k + 1] = m.y;
                         } else {
                             ny[2 * k] = ny[2 * k + 1] = 0u;
                         }
                         if ((k & 2u) == 0) {  // z-bit 0: the row before along z
-                            const uint2 m = loz ? make_uint2(0u, 0u) : __ldg(reinterpret_cast<const uint2 *>(rk - B.sz));
+                            const uint2 m = loz ? make_uint2(0u, 0u)
+                                            : kz  ? make_uint2(lz, lz)
+                                                  : __ldg(reinterpret_cast<const uint2 *>(rk - B.sz));
                             nz[2 * k] = m.x;
                             nz[2 * k + 1] = m.y;
                         } else {
