@@ -472,16 +472,6 @@ __device__ __forceinline__ void rec_masks(uint64_t r8, uint32_t &nr, uint32_t &p
     st = gather4(lo << 4) | gather4(hi << 4) << 4;
 }
 
-// bytes of m with bit 7 set -> 0xFF, the others -> 0 (prmt replicating the sign bit of each byte)
-__device__ __forceinline__ uint32_t sext_bytes(uint32_t m) {
-    uint32_t r;
-    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(m));
-    return r;
-}
-// 0xFF in the bytes of o (each 0..7) equal to those of c, else 0
-__device__ __forceinline__ uint32_t bytes_eq(uint32_t o, uint32_t c) {
-    return sext_bytes(~((o ^ c) + 0x7F7F7F7Fu) & 0x80808080u);
-}
 __device__ __forceinline__ uint32_t bsel(uint32_t a, uint32_t b, uint32_t m) { return (a & ~m) | (b & m); }
 // bit 7 set in the bytes where a < b, for bytes b < 0x80
 __device__ __forceinline__ uint32_t bytes_lt(uint32_t a, uint32_t b) {
@@ -501,13 +491,16 @@ __device__ __forceinline__ bool kids8_u8(uint64_t r8, uint32_t ipl, uint32_t pk,
                                          uint32_t &minus, uint32_t &st) {
     constexpr uint32_t B1 = 0x01010101u, BX = 0xFF00FF00u, BY = 0xFFFF0000u, S = RbTraits<uint8_t>::kSent;
     const uint32_t w0 = (uint32_t)r8, w1 = (uint32_t)(r8 >> 32);
+    // the 4 ops of a word as the 4 selector nibbles of a byte permute, which then maps every op through an
+    // 8-entry byte table: 0xFF (or 1) for the ops of a class, 0 for the others
     const uint32_t o0 = w0 & 0x07070707u, o1 = w1 & 0x07070707u;
-    const uint32_t x0 = bytes_eq(o0, B1), x1 = bytes_eq(o1, B1);
-    const uint32_t y0 = bytes_eq(o0, 2 * B1), y1 = bytes_eq(o1, 2 * B1);
-    const uint32_t z0 = bytes_eq(o0, 3 * B1), z1 = bytes_eq(o1, 3 * B1);
-    const uint32_t d0 = bytes_eq(o0, 5 * B1), d1 = bytes_eq(o1, 5 * B1);             // P_delta
-    const uint32_t a0 = bytes_eq(o0, 6 * B1) & B1, a1 = bytes_eq(o1, 6 * B1) & B1;   // P_a: 1 per byte
-    const uint32_t p0 = sext_bytes(o0 << 5), p1 = sext_bytes(o1 << 5);                // ops 4..7
+    const uint32_t c0 = __byte_perm(o0 | (o0 >> 4), 0u, 0x4420u), c1 = __byte_perm(o1 | (o1 >> 4), 0u, 0x4420u);
+    const uint32_t x0 = __byte_perm(0x0000FF00u, 0u, c0), x1 = __byte_perm(0x0000FF00u, 0u, c1);  // R_x (op 1)
+    const uint32_t y0 = __byte_perm(0x00FF0000u, 0u, c0), y1 = __byte_perm(0x00FF0000u, 0u, c1);  // R_y (op 2)
+    const uint32_t z0 = __byte_perm(0xFF000000u, 0u, c0), z1 = __byte_perm(0xFF000000u, 0u, c1);  // R_z (op 3)
+    const uint32_t d0 = __byte_perm(0u, 0x0000FF00u, c0), d1 = __byte_perm(0u, 0x0000FF00u, c1);  // P_delta (5)
+    const uint32_t a0 = __byte_perm(0u, 0x00010000u, c0), a1 = __byte_perm(0u, 0x00010000u, c1);  // P_a (6): 1
+    const uint32_t p0 = __byte_perm(0u, 0xFFFFFFFFu, c0), p1 = __byte_perm(0u, 0xFFFFFFFFu, c1);  // ops 4..7
     // i_p before each child: byte sums of the P_a bytes before it (at most 7: no carries)
     const uint32_t na0 = (a0 * B1) >> 24, na1 = (a1 * B1) >> 24;
     const uint32_t i0 = ipl * B1 + a0 * 0x01010100u, i1 = (ipl + na0) * B1 + a1 * 0x01010100u;
@@ -529,7 +522,8 @@ __device__ __forceinline__ bool kids8_u8(uint64_t r8, uint32_t ipl, uint32_t pk,
     minus = gather4((x0 & ~BX) | (y0 & ~BY) | z0) | gather4((x1 & ~BX) | (y1 & ~BY)) << 4;
     st = gather4(w0 << 4) | gather4(w1 << 4) << 4;
     const uint32_t xs = x0 | x1, ys = y0 | y1;
-    const bool bad = (((o0 + B1) | (o1 + B1)) & 0x08080808u) != 0 || (leaf && st != 0) ||
+    const bool bad = (__byte_perm(0u, 0xFF000000u, c0) | __byte_perm(0u, 0xFF000000u, c1)) != 0 ||  // op 7
+                     (leaf && ((w0 | w1) & 0x08080808u) != 0) ||
                      ((hi3 & 1u) && (xs & BX)) || ((lo3 & 1u) && (xs & ~BX)) || ((hi3 & 2u) && (ys & BY)) ||
                      ((lo3 & 2u) && (ys & ~BY)) || ((hi3 & 4u) && z1) || ((lo3 & 4u) && z0) ||
                      ((a0 | a1) && ipl + na0 + na1 >= np) || ((bytes_lt(i0, e0) & d0) | (bytes_lt(i1, e1) & d1)) != 0;
