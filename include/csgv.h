@@ -388,7 +388,7 @@ CSGV_API int csgv_volume_leaves_to_device(csgv_volume *vol);
 /*
  * The launch shape of a volume's decodes (csgv_decode_autotune picks it; it
  * changes speed only, never the decoded labels).  Defaults: 192 MiB, 4, 512,
- * 128, 128, 1792 (the fastest point for 4096 LOD 0 requests of 32^3 bricks).
+ * 128, 128, 1280 (the fastest point for 4096 LOD 0 requests of 32^3 bricks).
  */
 typedef struct csgv_decode_tuning {
     uint64_t workspace_bytes;  /* op-record workspace per slice of requests (more: fewer, larger slices) */
@@ -400,7 +400,7 @@ typedef struct csgv_decode_tuning {
                                   requests: 64, 128 or 256 */
     uint32_t compact_nodes;    /* a LOD 0 request of a 32^3 brick with at most this many non-constant L1
                                   nodes is rebuilt in the compact layout (rebuild_threads threads), one with
-                                  more in the full layout (256 threads); 0 .. 1792 */
+                                  more in the full layout (256 threads); 0 .. 1280 */
     uint32_t pad;
     double ms;                 /* measured time of the batch with this configuration (autotune only) */
 } csgv_decode_tuning;
@@ -410,7 +410,7 @@ typedef struct csgv_decode_tuning {
  * keep the fastest in the volume for later csgv_decode_bricks calls; *best
  * receives it.  One knob at a time, each from the best point so far: rANS ring
  * depth x CTAs per SM, threads per LOD 0 request, the compact/full split of LOD
- * 0 requests (0, 256, 512, 1024, 1792 nodes), threads per LOD 1 request,
+ * 0 requests (0, 256, 512, 1024, 1280 nodes), threads per LOD 1 request,
  * workspace per slice (64 MiB .. 1 GiB); each point is timed as the median of
  * five runs after a warm-up run (CUDA events on the stream).  The batch's
  * outputs are written by every run.  Synchronises the stream.  The paper has

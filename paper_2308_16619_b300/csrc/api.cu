@@ -848,7 +848,7 @@ bool tuning_valid(const csgv_decode_tuning &t) {
     return t.workspace_bytes >= (1ull << 20) && t.rans_ctas_per_sm >= 4 && t.rans_ctas_per_sm <= 6 &&
            (t.ring_words == 128 || t.ring_words == 256 || t.ring_words == 512) &&
            (t.rebuild_threads == 128 || t.rebuild_threads == 256) &&
-           (t.medium_threads == 64 || t.medium_threads == 128 || t.medium_threads == 256) && t.compact_nodes <= 1792 &&
+           (t.medium_threads == 64 || t.medium_threads == 128 || t.medium_threads == 256) && t.compact_nodes <= csgv::kLeafCap &&
            !(t.ring_words == 512 && t.rans_ctas_per_sm == 6);  // 6 x 40 KB of shared memory do not fit an SM
 }
 void apply_tuning(csgv_volume *v, const csgv_decode_tuning &t) {
@@ -927,7 +927,7 @@ int csgv_decode_autotune(csgv_volume *vol, const uint32_t *brick_ids_dev, const 
     for (uint32_t ring : {128u, 256u, 512u})
         search([&](csgv_decode_tuning &c, uint32_t x) { c.ring_words = ring; c.rans_ctas_per_sm = x; }, {4u, 5u, 6u});
     search([](csgv_decode_tuning &c, uint32_t x) { c.rebuild_threads = x; }, {128u, 256u});
-    search([](csgv_decode_tuning &c, uint32_t x) { c.compact_nodes = x; }, {0u, 256u, 512u, 1024u, 1792u});
+    search([](csgv_decode_tuning &c, uint32_t x) { c.compact_nodes = x; }, {0u, 256u, 512u, 1024u, csgv::kLeafCap});
     search([](csgv_decode_tuning &c, uint32_t x) { c.medium_threads = x; }, {64u, 128u, 256u});
     search([](csgv_decode_tuning &c, uint32_t x) { c.workspace_bytes = (uint64_t)x << 20; }, {64u, 192u, 512u, 1024u});
     cudaEventDestroy(e0);

@@ -96,11 +96,15 @@ __host__ __device__ inline uint32_t lanes_for(uint32_t n, uint32_t K_max, uint32
 }
 
 // Launch shape of a decode (csgv_decode_autotune searches it; kept per volume)
+// The compact leaf layout of 32^3 LOD 0 requests holds the children of at most this many non-constant L1 nodes
+// (20.8 KB of shared memory with the levels above: 10 CTAs of 128 threads per SM)
+constexpr uint32_t kLeafCap = 1280;
+
 struct DecodeShape {
     uint32_t rec_per_sm = 4;        // rANS record kernel: CTAs of 8 warps per SM (4..6)
     uint32_t ring_words = 512;      // rANS record kernel: stream words staged per warp (128, 256, 512)
     uint32_t leafc_threads = 128;   // 32^3 bricks, compact leaf layout: threads per request (128, 256)
-    uint32_t compact_nodes = 1792;  // 32^3 bricks: LOD 0 requests with at most this many non-constant L1 nodes take
+    uint32_t compact_nodes = kLeafCap;  // 32^3 bricks: LOD 0 requests with at most this many non-constant L1 nodes take
                                     // the compact layout, the others the full one (256 threads, 8 warps)
     uint32_t medium_threads = 128;  // 32^3 bricks, LOD 1 requests of large mixed batches (64, 128, 256)
 };

@@ -620,8 +620,8 @@ __host__ __device__ constexpr RbLayout rb_layout_part(uint32_t N, uint32_t lmin)
 // only the 8 children of each non-constant ("listed") L1 node are held, in listed (Morton) order, at most
 // kLeafCap nodes.  They share one region with the staged interior records and the level-1 parent lists, which
 // are dead once level 1 is rebuilt.  A request with more listed L1 nodes (more than 8 kLeafCap leaf records)
-// goes to the full-layout kernel.
-constexpr uint32_t kLeafCap = 1792;
+// goes to the full-layout kernel.  kLeafCap (csgv_internal.cuh): 1280 nodes, 20.8 KB, 10 CTAs of 128 threads per SM
+// (on voronoi512 b=32 0.143 -> 0.138 ms against 1792 nodes, 26.4 KB and 8 CTAs; 1536 nodes and 9 CTAs 0.138).
 template <typename IdxT>
 __host__ __device__ constexpr RbLayout rb_layout_leafc(uint32_t N) {
     uint32_t nodes = 0;
@@ -1439,7 +1439,7 @@ __device__ __forceinline__ void rebuild_list(const VolDev &V, const RecJob &J, u
 
 // The LOD 0 list of a large mixed batch of 32^3 bricks in the compact leaf layout (as rebuild_leafc, persistent)
 template <uint32_t kT>
-__global__ void __launch_bounds__(kT, 1024 / kT) rebuild_listed_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kT, kT == 128 ? 10 : 1024 / kT) rebuild_listed_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                                     const uint64_t *__restrict__ out_off,
                                                                     int32_t *__restrict__ status, const uint32_t *list,
                                                                     const uint32_t *count, uint32_t *next,
@@ -1475,12 +1475,12 @@ __global__ void __launch_bounds__(kRbCoarseThreads, 32) rebuild_coarse(VolDev V,
     rebuild_list<IdxT, kRbCoarseThreads, 2, false, 5>(V, J, out, out_off, status, list, count, next, smem);
 }
 
-// Requests of 32^3 bricks with uint8 indices at any LOD, in the compact leaf layout (rb_layout_leafc, 25.8 KB):
-// 128-thread CTAs, 8 per SM, twice the bricks in flight of rebuild's 51 KB layout (or 256-thread CTAs, 4 per
+// Requests of 32^3 bricks with uint8 indices at any LOD, in the compact leaf layout (rb_layout_leafc, 20.8 KB):
+// 128-thread CTAs, 10 per SM, 2.5 times the bricks in flight of rebuild's 51 KB layout (or 256-thread CTAs, 4 per
 // SM: the autotuner's choice of warps per brick).  A LOD 0 request with more than kLeafCap non-constant L1
 // nodes is appended to `full` (count in *n_full) for rebuild_listed.
 template <uint32_t kT>
-__global__ void __launch_bounds__(kT, 1024 / kT) rebuild_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kT, kT == 128 ? 10 : 1024 / kT) rebuild_leafc(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                              const uint64_t *__restrict__ out_off,
                                                              int32_t *__restrict__ status, uint32_t *full,
                                                              uint32_t *n_full) {
@@ -1922,7 +1922,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             auto lk = lt == 256 ? rebuild_leafc<256> : rebuild_leafc<128>;
             uint32_t *n_full = J.counter + 24;  // count, then the work counter of rebuild_listed
             e = func_attr((const void *)lk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_l);
-            if (e == cudaSuccess)  // the largest shared-memory carve-out: 8 CTAs per SM at 128 threads
+            if (e == cudaSuccess)  // the largest shared-memory carve-out: 10 CTAs per SM at 128 threads
                 e = func_attr((const void *)lk, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e == cudaSuccess)
                 e = func_attr((const void *)rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);

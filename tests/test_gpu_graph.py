@@ -69,7 +69,7 @@ def test_autotune_keeps_decoding_exact(batch):
     assert best.workspace_bytes in (64 << 20, 192 << 20, 512 << 20, 1024 << 20)
     assert best.rans_ctas_per_sm in (4, 5, 6) and best.ring_words in (128, 256, 512)
     assert best.rebuild_threads in (128, 256) and best.medium_threads in (64, 128, 256) and 0 < best.ms < 1e3
-    assert best.compact_nodes in (0, 256, 512, 1024, 1792)
+    assert best.compact_nodes in (0, 256, 512, 1024, 1280)
     assert csgv.csgv_decode_get_tuning(v).as_dict() == dict(best.as_dict(), ms=0.0)  # kept in the volume
     out.fill_(-1)
     csgv.csgv_decode_bricks(v, t["ids"], t["lods"], out, t["offs"], st)
@@ -114,7 +114,7 @@ def test_every_decode_tuning_point_decodes_exactly():
     points = 0
     for ring, ctas, lt, mt, ws in itertools.product((128, 256, 512), (4, 5, 6), (128, 256), (64, 128, 256),
                                                     (64, 1024)):
-        cn = (0, 256, 512, 1024, 1792)[points % 5]  # the compact/full split, cycled over the points
+        cn = (0, 256, 512, 1024, 1280)[points % 5]  # the compact/full split, cycled over the points
         tu = csgv.DecodeTuning(workspace_bytes=ws << 20, rans_ctas_per_sm=ctas, ring_words=ring, rebuild_threads=lt,
                                medium_threads=mt, compact_nodes=cn)
         if ring == 512 and ctas == 6:  # 6 x 40 KB of shared memory: refused

@@ -223,7 +223,7 @@ def test_unaligned_output_offsets_use_scalar_stores():
 
 
 def test_b32_bricks_with_many_non_constant_l1_nodes_take_the_full_layout():
-    """32^3 bricks with uint8 palette indices decode in a compact leaf layout that holds at most 1792
+    """32^3 bricks with uint8 palette indices decode in a compact leaf layout that holds at most 1280
     non-constant L1 nodes; bricks with more go to the full-layout kernel in the same decode call.  Here half
     the bricks are 8-label noise (every L1 node non-constant, small palettes), half are Voronoi cells, and
     some are mixed; every LOD of every brick, requests in shuffled order, against the oracle."""
@@ -236,14 +236,14 @@ def test_b32_bricks_with_many_non_constant_l1_nodes_take_the_full_layout():
     V = O.encode_volume(vol, 5, stride=1)
     gv = import_oracle_volume(V)
     assert gv.info().max_palette <= 253
-    # non-constant L1 nodes per brick, from the volume: some bricks above the compact layout's 1792
+    # non-constant L1 nodes per brick, from the volume: some bricks above the compact layout's 1280
     n_nc = []
     for bid in range(V.n_bricks):
         bx, by, bz = bid % 4, (bid // 4) % 2, bid // 8
         br = vol[bz * 32:bz * 32 + 32, by * 32:by * 32 + 32, bx * 32:bx * 32 + 32]
         blocks = br.reshape(16, 2, 16, 2, 16, 2).transpose(0, 2, 4, 1, 3, 5).reshape(4096, 8)
         n_nc.append(int((blocks != blocks[:, :1]).any(axis=1).sum()))
-    assert max(n_nc) > 1792 and min(n_nc) <= 1792
+    assert max(n_nc) > 1280 and min(n_nc) <= 1280
     n = V.n_bricks
     ids = np.repeat(np.arange(n, dtype=np.uint32), 6)
     lods = np.tile(np.arange(6, dtype=np.uint8), n)
@@ -257,7 +257,7 @@ def test_b32_bricks_with_many_non_constant_l1_nodes_take_the_full_layout():
 
 def test_b32_leaf_minus_list_and_its_fallback():
     """The compact leaf layout resolves the -axis children of the leaf level from a list kept in the unused
-    part of its children area, which holds 4 (1792 - listed nodes) entries; a brick with more -axis children
+    part of its children area, which holds 4 (1280 - listed nodes) entries; a brick with more -axis children
     resolves them per listed node instead.  Two 32^3 bricks of x-stripes (every L1 node of the striped part
     is non-constant, with three -axis children: R_y / R_z toward the previous node) over a constant
     background: the first striped in 10 of its 32 z-layers (1280 listed nodes, more -axis children than the
@@ -282,8 +282,8 @@ def test_b32_leaf_minus_list_and_its_fallback():
         op = np.array(ops).reshape(-1, 8) & 7
         c = np.arange(8)
         minus = int((((op == 1) & ((c & 1) == 0)) | ((op == 2) & ((c & 2) == 0)) | ((op == 3) & ((c & 4) == 0))).sum())
-        assert n_act <= 1792 and len(op) == n_act
-        fits.append(minus <= 4 * (1792 - n_act))
+        assert n_act <= 1280 and len(op) == n_act
+        fits.append(minus <= 4 * (1280 - n_act))
     assert fits == [False, True]
     gv = import_oracle_volume(V)
     ids = np.repeat(np.arange(2, dtype=np.uint32), 6)
