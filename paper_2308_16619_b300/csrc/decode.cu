@@ -13,21 +13,23 @@
 //     every 8th record (the palette position i_p there, reading R3), and checks the stream's end (every
 //     state back at L, every word read).
 //
-//   rebuild (one CTA of 256 threads per request).  Alg. 1 level by level, in parallel over the nodes of
-//     a level.  With one record per child, the 8 records of the j-th non-constant parent of a level
-//     sit at 8j, and i_p at them is known, so a level takes two barrier-separated passes:
-//       1. every child takes its parent's palette index (the stop-bit semantics: a constant parent's
-//          block keeps its label), and each warp lists the non-constant parents of its range of the
-//          level in Morton (= stream) order;
-//       2. one thread per listed parent decodes its records whose op is not R_p: R_a toward +axis
-//          reads the neighbour's parent (reading R4), palette ops index the palette (R1, R3), and R_a
-//          toward -axis is written as a sentinel naming the axis (and noted per listed parent);
-//       3. the sentinels are resolved by following them: a chain has at most 3 hops, since each hop
-//          lands on a child index with one more bit set.
-//     Levels with at most 64 parents are rebuilt one thread per child instead.  All levels
-//     of the brick, L0 included, are held as palette indices in shared memory (uint8 when every palette
-//     has <= 253 entries, else uint16); level t is then written as x-fastest labels with 16-byte
-//     streaming stores.
+//   rebuild (one CTA per request).  Alg. 1 level by level, in parallel over the nodes of a level.  With one
+//     record per child, the 8 records of the j-th non-constant parent of a level sit at 8j, and i_p at them
+//     is known, so a level takes barrier-separated passes:
+//       1. the children of constant parents take their parent's palette index (the stop-bit semantics), and
+//          the non-constant parents of the level are listed in Morton (= stream) order;
+//       2. one thread per listed parent decodes its 8 records at once, byte-wise in two registers
+//          (kids8_u8): R_p keeps the parent's index, R_a toward +axis reads the neighbour's parent
+//          (reading R4), palette ops index the palette (R1, R3), and R_a toward -axis is written as a
+//          sentinel naming the axis (and noted per listed parent);
+//       3. the sentinels are resolved, in rounds by the child index's bit count or by following a list of
+//          them: a chain has at most 3 hops, since each hop lands on a child index with one more bit set.
+//     Levels with at most 64 parents take a thread per parent (uint16 indices: a thread per child).  The
+//     levels are held as palette indices in shared memory (uint8 when every palette has <= 253 entries,
+//     else uint16): all of them, L0 included, in the full layout (rebuild, 256 threads); for LOD 0 of 32^3
+//     bricks the compact layout (rebuild_leafc, 128 threads) holds L0 only under the non-constant L1 nodes.
+//     Level t is then written as x-fastest labels with 16-byte streaming stores.  The kernels launched for
+//     one brick size take N as a template argument, so level offsets and layouts are constants.
 #include <map>
 #include <mutex>
 #include <tuple>

@@ -1,26 +1,28 @@
 // encode.cu -- brick encoder (Alg. 2 of the paper), frequency prepass and
 // packing for sm_103a.
 //
-// encode_kernel: one CTA of 256 threads per brick:
+// encode_kernel: one CTA of 256 threads per brick (128 for bricks of 16^3 and smaller), specialised on the
+// brick size for 32^3 and 16^3:
 //   A. pyramid (Sec. 3.1): L1 from the volume (16-byte row loads for bricks
 //      inside an aligned volume), L2..LN in shared memory; each node is the
 //      most frequent of its 8 children, ties to the first occurrence in the
 //      child array (Sec. 3.4), plus a constant-subtree flag.
-//   B. per level, the list of active (non-constant) parents in Morton order
-//      and, for each of their children in parallel, the first applicable
-//      reuse operation R_p, R_x, R_y, R_z (Sec. 3.2, reading R4); children
-//      no reuse fits are marked for the palette pass.
-//   C. palette pass: the marked children are gathered in stream order, then
-//      one warp walks them with the last 17 palette entries in registers
-//      (lane i holds palette[i_p-i]): a ballot finds P_0 (lane 0) or the
-//      smallest P_delta (lanes 1..16); otherwise P_a appends the label (Sec.
-//      3.2, bestOperation order).
-//   D. nibble positions (one extra nibble after each P_delta, reading R18):
-//      a nibble's position is its op's index in its stream plus the P_delta
-//      ops before it; interior and leaf nibbles go to scratch, or are only
-//      counted in the prepass (Sec. 3.4).
+//   B. the active (non-constant) parents of every level ranked in stream
+//      order (level by level from the root, Morton order within a level);
+//      one thread per active parent picks, for each of its 8 children, the
+//      first applicable reuse operation R_p, R_x, R_y, R_z (Sec. 3.2, reading
+//      R4) and writes the 8 op bytes (op | stop << 3) at 8 x its rank;
+//      children no reuse fits are gathered for the palette pass.
+//   C. palette pass: the gathered children in stream order, walked by one
+//      warp with the last 17 palette entries in registers (lane i holds
+//      palette[i_p-i]): a ballot finds P_0 (lane 0) or the smallest P_delta
+//      (lanes 1..16); otherwise P_a appends the label (Sec. 3.2,
+//      bestOperation order); the op byte gets the delta (delta << 4).
+//   D. each stream's symbol count (its ops plus a delta nibble per P_delta,
+//      reading R18); in the prepass the nibbles are counted (Sec. 3.4).
 // rans_encode_kernel: one warp per stream, K interleaved states in lanes,
-//   symbols in reverse; renormalisation words are pushed downward from the
+//   the op bytes coded from the last step down (a P_delta's delta on its op's
+//   state, reading R10); renormalisation words are pushed downward from the
 //   top of the scratch area so that the decoder reads them forward in lane
 //   order (Sec. 3.3, readings R9/R10).
 // A scan kernel turns per-brick sizes into offsets and a compaction kernel
