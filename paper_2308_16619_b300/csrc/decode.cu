@@ -1894,10 +1894,15 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
                 per_l = 1;
             split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, lists, counts);
             ProfScope ps("rebuild", st);
-            lk<<<min(J.n, (uint32_t)per_l * g), lt, smem_l, st>>>(V, J, out, out_off, status, lists, counts, counts + 3,
-                                                                   lists + 3 * J.n, n_full);
-            rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status,
-                                                                             lists + 3 * J.n, n_full, n_full + 1);
+            if (S.compact_nodes == 0) {  // every LOD 0 request in the full layout: its list goes there directly
+                rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists,
+                                                                                 counts, counts + 3);
+            } else {
+                lk<<<min(J.n, (uint32_t)per_l * g), lt, smem_l, st>>>(V, J, out, out_off, status, lists, counts,
+                                                                       counts + 3, lists + 3 * J.n, n_full);
+                rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status,
+                                                                                 lists + 3 * J.n, n_full, n_full + 1);
+            }
             mk<<<min(J.n, (uint32_t)per_m * g), mt, smem_m, st>>>(V, J, out, out_off, status, lists + J.n, counts + 1,
                                                                   counts + 4);
             rebuild_coarse<uint8_t><<<min(J.n, 32 * g), kRbCoarseThreads, smem_c, st>>>(
