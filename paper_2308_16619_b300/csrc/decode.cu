@@ -889,8 +889,11 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
         const uint32_t cw = *(const uint32_t *)(cmP + 4 * b);  // const bits of parents 32b .. 32b+31
         const bool pc = (cw >> lane) & 1u;
         const uint32_t r = T::kRep * (uint32_t)P[k];
-        if (sizeof(IdxT) == 1) *(uint2 *)(C + 8 * k) = make_uint2(r, r);
-        else *(uint4 *)(C + 8 * k) = make_uint4(r, r, r, r);
+        if (sizeof(IdxT) == 1) {
+            if (pc) *(uint2 *)(C + 8 * k) = make_uint2(r, r);  // a listed parent's 8 children come from pass 2
+        } else {
+            *(uint4 *)(C + 8 * k) = make_uint4(r, r, r, r);
+        }
         if (cmC && pc) cmC[k] = 0xFF;
         if (!pc) mylist[cnt + __popc(~cw & lt_of(lane))] = (uint16_t)k;
         cnt += __popc(~cw);
@@ -899,25 +902,23 @@ __device__ __forceinline__ bool rebuild_level(uint8_t *smem, const RbLayout &Ly,
     __syncthreads();
 
     // pass 2: one thread per listed parent decodes its records whose op is not R_p
-    uint32_t wbase[nw];  // first listed index of each warp's list
+    uint32_t wbase[nw], wofs[nw];  // first listed index of each warp's list; act index - listed index there
     n_act = 0;
 #pragma unroll
     for (uint32_t v = 0; v < nw; v++) {
         wbase[v] = n_act;
+        wofs[v] = 32 * bpw * v - n_act;
         n_act += ms->wcnt[v];
     }
     if (8 * n_act > n_left) return false;  // uniform: every thread sees the same counts
     const uint32_t nlb = (n_act + 31) / 32;
     uint8_t *mm = smem + Ly.mls;  // children toward -axis of listed parent j (bit c = child c)
     bool bad = false;
-    auto parent_of = [&](uint32_t j) -> uint32_t {
-        uint32_t w = 0;
+    auto parent_of = [&](uint32_t j) -> uint32_t {  // listed parent j lies in the list of the last warp starting at or before j
+        uint32_t o = wofs[0];
 #pragma unroll
-        for (uint32_t v = 1; v < nw; v++) w += j >= wbase[v] ? 1u : 0u;
-        uint32_t wb = 0;
-#pragma unroll
-        for (uint32_t v = 0; v < nw; v++) wb = v == w ? wbase[v] : wb;
-        return act[32 * bpw * w + (j - wb)];
+        for (uint32_t v = 1; v < nw; v++) o = j >= wbase[v] ? wofs[v] : o;
+        return act[j + o];
     };
     for (uint32_t b = warp; b < nlb; b += nw) {
         const uint32_t j = 32 * b + lane;
@@ -1348,7 +1349,7 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
 }
 
 template <typename IdxT>
-__global__ void __launch_bounds__(kRbThreads) rebuild(VolDev V, RecJob J, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kRbThreads, 4) rebuild(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                       const uint64_t *__restrict__ out_off,
                                                       int32_t *__restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -1451,7 +1452,7 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 10 : 1024 / kT) rebuild_listed
 }
 
 template <typename IdxT>
-__global__ void __launch_bounds__(kRbThreads) rebuild_listed(VolDev V, RecJob J, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kRbThreads, 4) rebuild_listed(VolDev V, RecJob J, uint32_t *__restrict__ out,
                                                              const uint64_t *__restrict__ out_off,
                                                              int32_t *__restrict__ status, const uint32_t *list,
                                                              const uint32_t *count, uint32_t *next) {
