@@ -660,16 +660,36 @@ __device__ __forceinline__ uint32_t lev_off(uint32_t N, uint32_t l) {
     return u;
 }
 
-// every voxel of a side^3 block gets one label (kT threads)
-template <uint32_t kT>
-__device__ __forceinline__ void store_const(uint32_t label, uint32_t side, uint32_t *out, bool vec) {
-    const uint32_t n = side * side * side;
-    if (vec && side >= 4) {
-        const uint4 o = make_uint4(label, label, label, label);
-        for (uint32_t i = threadIdx.x; i < n / 4; i += kT) __stcs((uint4 *)out + i, o);
+// Four consecutive labels out, streaming: one 16-byte store where the output is 16-byte aligned (al, the
+// output's address mod 16, is 0), two 8-byte stores where it is 8-byte aligned, else four 4-byte stores.  The
+// sectors written are the same; only the number of store instructions differs.
+__device__ __forceinline__ void store4(uint32_t *p, uint32_t al, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    if (al == 0) {
+        __stcs((uint4 *)p, make_uint4(a, b, c, d));
+    } else if (al == 8) {
+        __stcs((uint2 *)p, make_uint2(a, b));
+        __stcs((uint2 *)p + 1, make_uint2(c, d));
     } else {
-        for (uint32_t i = threadIdx.x; i < n; i += kT) out[i] = label;
+        __stcs(p, a);
+        __stcs(p + 1, b);
+        __stcs(p + 2, c);
+        __stcs(p + 3, d);
     }
+}
+
+// every voxel of a side^3 block gets one label (kT threads); al = the output's address mod 16 (a multiple of 4):
+// the labels before the first 16-byte boundary and after the last one are written one by one
+template <uint32_t kT>
+__device__ __forceinline__ void store_const(uint32_t label, uint32_t side, uint32_t *out, uint32_t al) {
+    const uint32_t n = side * side * side;
+    const uint32_t head = min(n, ((16u - al) & 15u) >> 2);
+    const uint32_t body = (n - head) / 4;
+    const uint4 o = make_uint4(label, label, label, label);
+    uint4 *ov = (uint4 *)(out + head);
+    for (uint32_t i = threadIdx.x; i < body; i += kT) __stcs(ov + i, o);
+    const uint32_t tail = head + 4 * body;
+    if (threadIdx.x < head) out[threadIdx.x] = label;
+    else if (threadIdx.x - head < n - tail) out[tail + threadIdx.x - head] = label;
 }
 
 template <typename IdxT, int kPal>  // kPal: 0 palette in lanes (<= 32 entries), 1 in shared memory, 2 global
@@ -685,10 +705,10 @@ __device__ __forceinline__ uint32_t lab(uint32_t v, uint32_t pal_reg, const uint
 // indices) and four 16-byte rows out.  Units go to threads x-fastest, so that the threads of a warp
 // complete whole 128-byte rows; their loads are at most 2-way bank conflicts.
 template <typename IdxT, int kPal, uint32_t kT>
-__device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t *out, bool vec, uint32_t pal_reg,
+__device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t *out, uint32_t al, uint32_t pal_reg,
                                             const uint32_t *pal_s, const uint32_t *pal, uint32_t np) {
     const uint32_t side = 1u << s;
-    if (vec && side >= 4) {
+    if (side >= 4) {
         const uint32_t units = 1u << (3 * s - 4);
         const uint32_t xb = s - 2, yb = s - 1;  // bits of the unit's x and y index
         for (uint32_t u0 = 0; u0 < units; u0 += kT) {
@@ -726,8 +746,8 @@ __device__ __forceinline__ void store_level(const IdxT *C, uint32_t s, uint32_t 
                 uint32_t *o = out + ((size_t)z0 * side + y0) * side + x0;
 #pragma unroll
                 for (uint32_t k = 0; k < 4; k++)
-                    __stcs((uint4 *)(o + (size_t)(k >> 1) * side * side + (k & 1u) * side),
-                           make_uint4(r[k][0], r[k][1], r[k][2], r[k][3]));
+                    store4(o + (size_t)(k >> 1) * side * side + (k & 1u) * side, al, r[k][0], r[k][1], r[k][2],
+                           r[k][3]);
             }
         }
     } else {
@@ -1159,7 +1179,7 @@ __device__ __forceinline__ bool rebuild_leaf_compact(uint8_t *smem, const RbLayo
 // rank) or repeat its L1 index; both are loaded and one is selected (the rank of a constant node points
 // inside the E area, or at its end), so that the lanes of a warp take one path.
 template <int kPal, uint32_t kT>
-__device__ __forceinline__ void store_leaf_compact(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t *out, bool vec,
+__device__ __forceinline__ void store_leaf_compact(uint8_t *smem, const RbLayout &Ly, uint32_t N, uint32_t *out, uint32_t al,
                                                    uint32_t pal_reg, const uint32_t *pal_s, const uint32_t *pal,
                                                    uint32_t np) {
     typedef uint8_t IdxT;
@@ -1183,21 +1203,6 @@ __device__ __forceinline__ void store_leaf_compact(uint8_t *smem, const RbLayout
         w[2] = c1 ? rep1 : e1.x;
         w[3] = c1 ? rep1 : e1.y;
     };
-    if (!vec) {
-        const uint32_t n = side * side * side;
-        for (uint32_t i0 = 0; i0 < n; i0 += kT) {
-            const uint32_t i = i0 + threadIdx.x;
-            const uint32_t ii = i < n ? i : 0u;
-            const uint32_t x = ii & (side - 1), y = (ii >> s) & (side - 1), z = ii >> (2 * s);
-            const uint32_t mq = spread5(x) | (spread5(y) << 1) | (spread5(z) << 2);
-            uint32_t w[4];
-            kids2((mq >> 3) & ~1u, w);
-            const uint32_t v = (w[(mq >> 2) & 3u] >> (8 * (mq & 3u))) & 0xFFu;
-            const uint32_t l = lab<IdxT, kPal>(v, pal_reg, pal_s, pal, np);
-            if (i < n) out[i] = l;
-        }
-        return;
-    }
     const uint32_t units = 1u << (3 * s - 4);
     const uint32_t xb = s - 2, yb = s - 1;
     // kT is a multiple of the units of one z-layer pair (2^(xb + yb) = 128 for N = 5): x0 and y0 per thread
@@ -1222,8 +1227,7 @@ __device__ __forceinline__ void store_leaf_compact(uint8_t *smem, const RbLayout
         uint32_t *o = out + ((size_t)z0 * side + y0) * side + x0;
 #pragma unroll
         for (uint32_t k = 0; k < 4; k++)
-            __stcs((uint4 *)(o + (size_t)(k >> 1) * side * side + (k & 1u) * side),
-                   make_uint4(r[k][0], r[k][1], r[k][2], r[k][3]));
+            store4(o + (size_t)(k >> 1) * side * side + (k & 1u) * side, al, r[k][0], r[k][1], r[k][2], r[k][3]);
     }
 }
 
@@ -1251,13 +1255,13 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
     const uint32_t *pal = V.pal + p0;
     const uint32_t n_int = V.n_int_sym[id], n_leaf = V.n_leaf_sym[id];
     if (np == 0 || np > RbTraits<IdxT>::kSent) return kStCorrupt;
-    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    const uint32_t al = (uint32_t)(reinterpret_cast<uintptr_t>(out) & 15u);  // a multiple of 4
     const uint32_t side = 1u << (N - t);
 
     // homogeneous brick: no symbols, every LOD is palette[0] (reading R2)
     if (n_int == 0 && n_leaf == 0) {
         if (V.int_off[id + 1] != V.int_off[id] || V.leaf_off[id + 1] != V.leaf_off[id]) return kStCorrupt;
-        store_const<kT>(__ldg(pal), side, out, vec);
+        store_const<kT>(__ldg(pal), side, out, al);
         return kStOk;
     }
     if (t == N) {  // the root: palette index 0 (Alg. 1 initialisation)
@@ -1335,16 +1339,16 @@ __device__ int32_t rebuild_request(const VolDev &V, const RecJob &J, uint8_t *sm
 
     if constexpr (kLeafC) {
         if (t == 0) {
-            if (np <= 32) store_leaf_compact<0, kT>(smem, Ly, N, out, vec, pal_reg, pal_s, pal, np);
-            else store_leaf_compact<1, kT>(smem, Ly, N, out, vec, pal_reg, pal_s, pal, np);
+            if (np <= 32) store_leaf_compact<0, kT>(smem, Ly, N, out, al, pal_reg, pal_s, pal, np);
+            else store_leaf_compact<1, kT>(smem, Ly, N, out, al, pal_reg, pal_s, pal, np);
             return kStOk;
         }
     }
     const IdxT *C = lev + lev_off(N, t);
     const uint32_t s = N - t;
-    if (np <= 32) store_level<IdxT, 0, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
-    else if (sizeof(IdxT) == 1) store_level<IdxT, 1, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
-    else store_level<IdxT, 2, kT>(C, s, out, vec, pal_reg, pal_s, pal, np);
+    if (np <= 32) store_level<IdxT, 0, kT>(C, s, out, al, pal_reg, pal_s, pal, np);
+    else if (sizeof(IdxT) == 1) store_level<IdxT, 1, kT>(C, s, out, al, pal_reg, pal_s, pal, np);
+    else store_level<IdxT, 2, kT>(C, s, out, al, pal_reg, pal_s, pal, np);
     return kStOk;
 }
 
@@ -1746,8 +1750,8 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
     if ((t == 1 && used != info_int) || (t == 0 && used != info_leaf)) return kStCorrupt;
     const IdxT *Ct = lev + lev_off(N, t);
     auto lab = [&](uint32_t v) { return pal_in_smem ? pal_s[min(v, np - 1)] : __ldg(pal + min(v, np - 1)); };
-    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
-    if (vec && side >= 4) {
+    const uint32_t al = (uint32_t)(reinterpret_cast<uintptr_t>(out) & 15u);
+    if (side >= 4) {
         // a unit is 16 Morton-consecutive nodes, a 4 x 2 x 2 block (Morton bits x0 y0 z0 x1); row (dy, dz)
         // holds Morton offsets o, o+1, o+8, o+9 with o = 2 dy + 4 dz
         const uint32_t units = nvox / 16, xb = s - 2, yb = s - 1;
@@ -1767,8 +1771,8 @@ __device__ int32_t rebuild_global_request(const VolDev &V, const RecJob &J, uint
 #pragma unroll
             for (uint32_t k = 0; k < 4; k++) {  // k = dy + 2 dz
                 const uint32_t b0 = 2 * k;
-                __stcs((uint4 *)(o + (size_t)(k >> 1) * side * side + (k & 1u) * side),
-                       make_uint4(lab(n16[b0]), lab(n16[b0 + 1]), lab(n16[b0 + 8]), lab(n16[b0 + 9])));
+                store4(o + (size_t)(k >> 1) * side * side + (k & 1u) * side, al, lab(n16[b0]), lab(n16[b0 + 1]),
+                       lab(n16[b0 + 8]), lab(n16[b0 + 9]));
             }
         }
     } else {

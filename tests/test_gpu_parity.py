@@ -207,19 +207,39 @@ def test_plain_equals_batched_and_mixed_batch_equals_alone():
         assert np.array_equal(outq[offq[k]:offq[k] + B3], out[off[r]:off[r] + B3])
 
 
-def test_unaligned_output_offsets_use_scalar_stores():
-    vol = structured_volume(9, (32, 32, 64), 40)
-    V = O.encode_volume(vol, 4, stride=1)
+@pytest.mark.parametrize("b", [64, 32, 16])
+def test_output_offsets_of_every_alignment(b):
+    """Requests whose output starts 0, 4, 8 or 12 bytes past a 16-byte boundary (rows of four labels go out as
+    one 16-byte, two 8-byte or four 4-byte stores; a constant brick's labels before the first and after the
+    last 16-byte boundary one by one) decode to the oracle's labels at every LOD and leave the labels between
+    requests untouched.  The volume has a homogeneous brick and a noise brick (many non-constant L1 nodes)."""
+    N = b.bit_length() - 1
+    vol = synth.voronoi((2 * b, 2 * b, 2 * b), 30, seed=71, warp_amp=2, bg_permille=300)
+    vol[:b, :b, :b] = 17
+    rng = np.random.default_rng(72)
+    vol[b:, :b, :b] = rng.integers(0, 200, size=(b, b, b)).astype(np.uint32) + 3
+    V = O.encode_volume(vol, N, stride=1)
     gv = import_oracle_volume(V)
     n = V.n_bricks
-    ids = np.arange(n, dtype=np.uint32)
-    lods = np.zeros(n, np.uint8)
-    offsets = 3 + np.arange(n, dtype=np.int64) * (4096 + 1)  # not multiples of 4 elements
-    out, _, st = gpu_decode(gv, 4, ids, lods, offsets=offsets, total=int(offsets[-1]) + 4096 + 1)
-    ref, roff, _ = O.decode_bricks(V, ids, lods)
-    assert (st == 0).all()
-    for i in range(n):
-        assert np.array_equal(out[offsets[i]:offsets[i] + 4096], ref[roff[i]:roff[i] + 4096])
+    ids = np.repeat(np.arange(n, dtype=np.uint32), N + 1)
+    lods = np.tile(np.arange(N + 1, dtype=np.uint8), n)
+    sizes = (b >> lods.astype(np.int64)) ** 3
+    shift = (ids.astype(np.int64) + lods) % 4  # labels past the boundary: every residue at every LOD
+    offsets = np.empty(len(ids), np.int64)
+    end = 0
+    for i in range(len(ids)):
+        offsets[i] = -(-(end + 1) // 4) * 4 + shift[i]  # at least one untouched label before each request
+        end = offsets[i] + sizes[i]
+    total = int(end) + 1
+    out, _, st = gpu_decode(gv, N, ids, lods, offsets=offsets, total=total)
+    ref, roff, rst = O.decode_bricks(V, ids, lods)
+    assert (st == 0).all() and (rst == 0).all()
+    written = np.zeros(total, bool)
+    for i in range(len(ids)):
+        o, m, r = int(offsets[i]), int(sizes[i]), int(roff[i])
+        assert np.array_equal(out[o:o + m], ref[r:r + m]), (i, int(ids[i]), int(lods[i]), int(shift[i]))
+        written[o:o + m] = True
+    assert (out[~written] == 0xFFFFFFFF).all()
 
 
 def test_b32_bricks_with_many_non_constant_l1_nodes_take_the_full_layout():
