@@ -71,10 +71,15 @@ __device__ __forceinline__ uint32_t minc(uint32_t m, uint32_t ma) { return (((m 
 __device__ __forceinline__ uint32_t mode8(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t w4, uint32_t w5,
                                          uint32_t w6, uint32_t w7, bool &all_equal) {
     const uint32_t w[8] = {w0, w1, w2, w3, w4, w5, w6, w7};
-    uint32_t rem = 0xFFu, best = w0, bestc = 0;
+    uint32_t m0 = 1u;  // the positions holding w0
 #pragma unroll
-    for (uint32_t c = 0; c < 8; c++) {
-        if (((rem >> c) & 1u) && __popc(rem) > bestc) {
+    for (uint32_t j = 1; j < 8; j++) m0 |= (w[j] == w0 ? 1u : 0u) << j;
+    all_equal = m0 == 0xFFu;
+    uint32_t rem = 0xFFu & ~m0, best = w0, bestc = __popc(m0);
+#pragma unroll
+    for (uint32_t c = 1; c < 8; c++) {
+        if (__popc(rem) <= bestc) break;  // rem only shrinks and bestc only grows
+        if ((rem >> c) & 1u) {
             const uint32_t v = w[c];
             uint32_t m = 0;
 #pragma unroll
@@ -87,7 +92,6 @@ __device__ __forceinline__ uint32_t mode8(uint32_t w0, uint32_t w1, uint32_t w2,
             rem &= ~m;
         }
     }
-    all_equal = bestc == 8;
     return best;
 }
 
