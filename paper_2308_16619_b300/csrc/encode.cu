@@ -1231,17 +1231,21 @@ __global__ void __launch_bounds__(kScanBlock) scan_write_kernel(const uint32_t *
     }
 }
 
-// Copy each brick's palette and words from scratch to the packed arrays: one warp per brick (its sizes read
-// once by eight lanes), the three runs copied with independent loads in flight (the copies are small, so the
-// kernel is bound by the latency of its dependent loads rather than by bandwidth).
+// Copy each brick's palette and words from scratch to the packed arrays: one warp per run (a brick's palette,
+// interior words or leaf words), eight loads in flight per lane.  The runs are short (about 2 KB a brick on
+// the benchmark volumes), so the kernel is bound by the latency of its dependent loads rather than by
+// bandwidth, and a brick's three runs go to three warps instead of one after another.
 constexpr uint32_t kCompactWarps = 8;
 
 template <typename T>
 __device__ __forceinline__ void copy_run(T *__restrict__ d, const T *__restrict__ s, uint32_t n, uint32_t lane) {
     uint32_t k = lane;
-    for (; k + 96 < n; k += 128) {
-        const T a = s[k], b = s[k + 32], c = s[k + 64], e = s[k + 96];
-        d[k] = a; d[k + 32] = b; d[k + 64] = c; d[k + 96] = e;
+    for (; k + 224 < n; k += 256) {
+        T a[8];
+#pragma unroll
+        for (uint32_t j = 0; j < 8; j++) a[j] = s[k + 32 * j];
+#pragma unroll
+        for (uint32_t j = 0; j < 8; j++) d[k + 32 * j] = a[j];
     }
     for (; k < n; k += 32) d[k] = s[k];
 }
@@ -1252,20 +1256,20 @@ __global__ void __launch_bounds__(kCompactWarps * 32) compact_kernel(EncGeom G, 
                                                                      uint16_t *int_words, uint16_t *leaf_words,
                                                                      uint32_t *n_int_sym, uint32_t *n_leaf_sym) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t slot = blockIdx.x * kCompactWarps + (threadIdx.x >> 5);
-    if (slot >= n) return;
-    const uint32_t *sz = SC.sizes + (size_t)slot * 8;
+    const uint64_t task = (uint64_t)blockIdx.x * kCompactWarps + (threadIdx.x >> 5);
+    if (task >= 3ull * n) return;
+    const uint32_t slot = (uint32_t)(task / 3), run = (uint32_t)(task % 3);
+    const uint32_t *sz = SC.sizes + (size_t)slot * 8;  // n_pal, n_int_sym, n_leaf_sym, words, word starts
     const uint64_t id = first + slot;
-    const uint32_t szl = lane < 7 ? sz[lane] : 0u;  // n_pal, n_int_sym, n_leaf_sym, words, word starts
-    const uint64_t offl = lane == 0 ? pal_off[id] : lane == 1 ? int_off[id] : lane == 2 ? leaf_off[id] : 0ull;
-    const uint32_t np = __shfl_sync(kFull, szl, 0), nwi = __shfl_sync(kFull, szl, 3), nwl = __shfl_sync(kFull, szl, 4);
-    const uint32_t si = __shfl_sync(kFull, szl, 5), sl = __shfl_sync(kFull, szl, 6);
-    const uint64_t op = __shfl_sync(kFull, offl, 0), oi = __shfl_sync(kFull, offl, 1), ol = __shfl_sync(kFull, offl, 2);
-    copy_run(pal + op, SC.pal + (size_t)slot * G.pal_cap, np, lane);
-    copy_run(int_words + oi, SC.w_int + (size_t)slot * (G.int_cap + 64) + si, nwi, lane);
-    copy_run(leaf_words + ol, SC.w_leaf + (size_t)slot * (G.leaf_cap + 64) + sl, nwl, lane);
-    if (lane == 1) n_int_sym[id] = szl;
-    if (lane == 2) n_leaf_sym[id] = szl;
+    if (run == 0) {
+        copy_run(pal + pal_off[id], SC.pal + (size_t)slot * G.pal_cap, sz[0], lane);
+    } else if (run == 1) {
+        copy_run(int_words + int_off[id], SC.w_int + (size_t)slot * (G.int_cap + 64) + sz[5], sz[3], lane);
+        if (lane == 0) n_int_sym[id] = sz[1];
+    } else {
+        copy_run(leaf_words + leaf_off[id], SC.w_leaf + (size_t)slot * (G.leaf_cap + 64) + sz[6], sz[4], lane);
+        if (lane == 0) n_leaf_sym[id] = sz[2];
+    }
 }
 
 }  // namespace
@@ -1383,7 +1387,7 @@ cudaError_t launch_compact(const EncGeom &G, const EncScratch &SC, uint64_t firs
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps("compact", st);
-        compact_kernel<<<(n + kCompactWarps - 1) / kCompactWarps, kCompactWarps * 32, 0, st>>>(
+        compact_kernel<<<(unsigned)((3ull * n + kCompactWarps - 1) / kCompactWarps), kCompactWarps * 32, 0, st>>>(
             G, SC, first, n, pal_off, int_off, leaf_off, pal, int_words, leaf_words, n_int_sym, n_leaf_sym);
     }
     return cudaGetLastError();
