@@ -438,8 +438,17 @@ CSGV_API int csgv_decode_set_tuning(csgv_volume *vol, const csgv_decode_tuning *
  * *n_kernels, and clears the records.  Enabling costs two event records per
  * launch; disabled (the default) it costs nothing.  Returns CSGV_ERR_INVALID_ARG
  * for NULL outputs, CSGV_ERR_CUDA if an event fails.
+ *
+ * The events come from a per-device pool that csgv_profile_read refills with the
+ * events it has read; a launch timed while the pool is empty creates its events,
+ * which costs host time between launches.  csgv_profile_reserve adds n_events
+ * new events for the current device to the pool, so that a timed run of known
+ * length (two events per launch) creates none.  The library owns them until the
+ * process ends.  Returns CSGV_ERR_CUDA if an event cannot be created (the events
+ * made before it stay in the pool).
  */
 CSGV_API int csgv_profile_enable(int on);
+CSGV_API int csgv_profile_reserve(uint32_t n_events);
 CSGV_API int csgv_profile_read(uint32_t max_kernels, char *names, double *total_ms, uint32_t *launches,
                                uint32_t *n_kernels);
 

@@ -20,8 +20,8 @@ SYMBOLS = ("csgv_last_error", "csgv_build_freq_table", "csgv_encode_bricks", "cs
            "csgv_decode_bricks_plain", "csgv_volume_info_get", "csgv_volume_export", "csgv_volume_import",
            "csgv_volume_destroy", "csgv_encode_bricks_noalloc", "csgv_serve_create", "csgv_serve_submit",
            "csgv_serve_poll", "csgv_serve_release", "csgv_serve_stats_get", "csgv_serve_destroy",
-           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_read", "csgv_decode_autotune",
-           "csgv_decode_get_tuning", "csgv_decode_set_tuning",
+           "csgv_freq_table_from_counts", "csgv_profile_enable", "csgv_profile_reserve", "csgv_profile_read",
+           "csgv_decode_autotune", "csgv_decode_get_tuning", "csgv_decode_set_tuning",
            "csgv_volume_leaves_to_host", "csgv_volume_leaves_to_device",
            "csgv_encode_bricks_sampled", "csgv_volume_destroy_async", "csgv_stream_encoder_create",
            "csgv_stream_encoder_add", "csgv_stream_encoder_finish", "csgv_stream_encoder_destroy",
@@ -98,6 +98,7 @@ def lib():
                                                  C.POINTER(vp), vp]
         L.csgv_volume_leaves_to_device.argtypes = [vp]
         L.csgv_profile_enable.argtypes = [C.c_int]
+        L.csgv_profile_reserve.argtypes = [u32]
         L.csgv_profile_read.argtypes = [u32, vp, vp, vp, vp]
         L.csgv_last_error.restype = C.c_char_p
         L.csgv_build_freq_table.argtypes = [vp, vp, u32, u32, C.POINTER(FreqTable), vp]
@@ -459,6 +460,11 @@ class Server:
 def profile_enable(on=True):
     """Record CUDA events around every kernel launch of the library (csgv_profile_enable)."""
     _check(lib().csgv_profile_enable(1 if on else 0))
+
+
+def profile_reserve(n_events):
+    """Pre-create n_events timing events for the current device (csgv_profile_reserve): two per timed launch."""
+    _check(lib().csgv_profile_reserve(int(n_events)))
 
 
 def profile_read(max_kernels=32):

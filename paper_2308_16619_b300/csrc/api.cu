@@ -1056,6 +1056,25 @@ int csgv_profile_enable(int on) {
     return CSGV_OK;
 }
 
+int csgv_profile_reserve(uint32_t n_events) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::vector<cudaEvent_t> made;
+    made.reserve(n_events);
+    cudaError_t err = cudaSuccess;
+    for (uint32_t i = 0; i < n_events && err == cudaSuccess; i++) {
+        cudaEvent_t e = nullptr;
+        err = cudaEventCreate(&e);
+        if (err == cudaSuccess) made.push_back(e);
+    }
+    {
+        std::lock_guard<std::mutex> lk(csgv::g_prof_mu);
+        for (cudaEvent_t e : made) csgv::g_prof_free.push_back({dev, e});
+    }
+    if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate");
+    return CSGV_OK;
+}
+
 int csgv_profile_read(uint32_t max_kernels, char *names, double *total_ms, uint32_t *launches, uint32_t *n_kernels) {
     if (!names || !total_ms || !launches || !n_kernels) return fail(CSGV_ERR_INVALID_ARG, "NULL output");
     CK(cudaDeviceSynchronize());
