@@ -137,7 +137,9 @@ CSGV_API int csgv_encode_bricks_sampled(const uint32_t *vol_dev, const uint64_t 
  * its own level of detail, decoded on the GPU at once).  Request r decodes
  * brick brick_ids_dev[r] to level of detail lods_dev[r] (0 = full
  * resolution, N = the single root label) into out_dev + out_offsets_dev[r]:
- * (b >> lod)^3 labels, x fastest.  Per slice of requests (sized by the
+ * (b >> lod)^3 labels, x fastest.  An offset may be any label index; outputs
+ * that start on a 16-byte boundary take 16-byte stores, the others 8- or 4-byte
+ * ones (the same bytes, more store instructions).  Per slice of requests (sized by the
  * workspace): a persistent rANS kernel whose warps take streams from a work
  * counter, then the reconstruction, one CTA per request (large mixed-LOD
  * slices: one persistent kernel per LOD class).  status_dev[r] receives CSGV_OK,
