@@ -145,3 +145,27 @@ def test_large_batch_split_with_empty_classes(mix):
     torch.cuda.synchronize()
     assert (status.cpu().numpy() == 0).all() and (rst == 0).all()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
+
+
+def test_empty_batch_is_a_no_op():
+    """No requests: the decode, the plain decode and the autotuner return at once, write nothing and leave
+    the volume's launch shape as it was."""
+    import torch
+    import paper_2308_16619_b300 as csgv
+    vol = synth.voronoi((64, 64, 64), 30, seed=25, warp_amp=2, bg_permille=200)
+    d = torch.from_numpy(vol.view(np.int32)).cuda()
+    v = csgv.csgv_encode_bricks(d, 32, csgv.csgv_build_freq_table(d, 32, 1))
+    before = csgv.csgv_decode_get_tuning(v).as_dict()
+    ids = torch.empty(0, dtype=torch.int32, device="cuda")
+    lods = torch.empty(0, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(0, dtype=torch.int64, device="cuda")
+    st = torch.empty(0, dtype=torch.int32, device="cuda")
+    out = torch.full((16,), -7, dtype=torch.int32, device="cuda")
+    csgv.csgv_decode_bricks(v, ids, lods, out, offs, st)
+    csgv.csgv_decode_bricks_plain(v, ids, lods, out, offs, st)
+    best = csgv.csgv_decode_autotune(v, ids, lods, out, offs, st)
+    torch.cuda.synchronize()
+    assert bool((out == -7).all())
+    assert csgv.csgv_decode_get_tuning(v).as_dict() == before
+    assert dict(best.as_dict(), ms=0.0) == dict(before, ms=0.0)
+    v.close()
