@@ -750,7 +750,7 @@ static int decode_range(const csgv_volume *v, const uint32_t *ids, const uint8_t
     if (v->ready && cap == cudaStreamCaptureStatusNone) CK(cudaStreamWaitEvent(st, v->ready, 0));
     void *ws = nullptr;
     CK(cudaMallocFromPoolAsync(&ws, bytes, pool, st));
-    csgv::RecJob J;
+    csgv::RecJob J{};
     J.counter = (uint32_t *)ws;
     J.info = (uint32_t *)((uint8_t *)ws + 256);
     J.recs = (uint8_t *)ws + 256 + info_bytes;

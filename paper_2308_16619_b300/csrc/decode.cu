@@ -206,12 +206,31 @@ __global__ void __launch_bounds__(kRecWarps * 32, 6) rans_records(VolDev V, RecJ
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint16_t *win = (uint16_t *)(smem + 2 * kM * 4) + warp * kWin;
+    // listed queue (large mixed-LOD slices): the two streams of every LOD 0 request, then the interior streams
+    // of the LOD 1 requests, then those of the coarser ones, so that the long streams go first and no warp
+    // draws the leaf stream of a request that has none to decode
+    uint32_t c0 = J.n, c1 = 0, c2 = 0;
+    if (J.listed_q) {
+        c0 = J.counter[16];
+        c1 = J.counter[17];
+        c2 = J.counter[18];
+    }
+    const uint32_t q_end = J.listed_q ? 2 * c0 + c1 + c2 : 2 * J.n;
     for (;;) {
         uint32_t q = 0;
         if (lane == 0) q = atomicAdd(J.counter, 1u);
         q = __shfl_sync(kFull, q, 0);
-        if (q >= 2 * J.n) break;
-        const uint32_t i = q >> 1, s = q & 1u;
+        if (q >= q_end) break;
+        uint32_t i = q >> 1, s = q & 1u;
+        if (J.listed_q) {
+            if (q < 2 * c0) {
+                i = J.lists[q >> 1];
+            } else {
+                const uint32_t k = q - 2 * c0;
+                i = k < c1 ? J.lists[J.n + k] : J.lists[2 * J.n + (k - c1)];
+                s = 0;
+            }
+        }
         const uint32_t id = J.ids[i], t = J.lods[i];
         // interior stream: needed below the root (t < N); leaf stream: needed for t == 0
         if (id >= V.n_bricks || t > V.N || (s == 0 ? t >= V.N : t != 0)) continue;
@@ -1390,8 +1409,9 @@ __global__ void __launch_bounds__(kRbTinyThreads, 32) rebuild_tiny_brick(VolDev 
     if (threadIdx.x == 0) status[i] = st;
 }
 
-// Large mixed-LOD batches of 32^3 bricks: split_lods lists the requests by class (LOD 0, LOD 1, LOD >= 2),
-// and one kernel per class rebuilds its list: rebuild_listed_leafc in the compact leaf layout (its few
+// Large mixed-LOD batches of 32^3 bricks: split_lods lists the requests by class (LOD 0, LOD 1, LOD >= 2)
+// before the rANS kernel, which then takes its streams class by class (the longest first), and one kernel per
+// class rebuilds its list: rebuild_listed_leafc in the compact leaf layout (its few
 // oversized requests then by rebuild_listed, as rebuild does); rebuild_medium (LOD 1) with
 // 128-thread CTAs in a layout without L0 (14 KB), 14 per SM; rebuild_coarse (LOD >= 2) with 64-thread CTAs
 // in a layout of levels 2..N (3.4 KB), 32 per SM, since such a request has at most 64 parents per level,
@@ -1847,12 +1867,23 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     // (counter[16..21]) and the oversized-request count and work counter (counter[24..25])
     e = cudaMemsetAsync(J.counter, 0, 128, st);
     if (e != cudaSuccess) return e;
+    const bool wide = max_pal > RbTraits<uint8_t>::kSent;  // uint16 palette indices
+    // large mixed-LOD slices of 32^3 bricks: the requests listed by LOD class first, for the rANS kernel's queue
+    // and for the rebuild kernels of the classes
+    const bool split = !packed && V.N == 5 && !wide && J.lists && J.n >= kSplitMin;
+    RecJob Jq = J;
+    if (split) {
+        split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, J.lists, J.counter + 16);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        Jq.listed_q = 1;
+    }
     const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
     const uint32_t rec_blocks = max(1u, min(S.rec_per_sm, 6u)) * g;
     {
         ProfScope ps("rans_records", st);
         if (packed) rans_records_packed<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
-        else rk<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
+        else rk<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, Jq);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1864,7 +1895,6 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         else rebuild_global<uint32_t><<<J.n, kGwThreads, 0, st>>>(V, J, out, out_off, status);
         return cudaGetLastError();
     }
-    const bool wide = max_pal > RbTraits<uint8_t>::kSent;  // uint16 palette indices
     const uint32_t smem_b = rebuild_smem_bytes(V.N, wide);
     if (wide) {
         e = func_attr((const void *)rebuild<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
@@ -1872,7 +1902,7 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
         ProfScope ps("rebuild", st);
         rebuild<uint16_t><<<J.n, kRbThreads, smem_b, st>>>(V, J, out, out_off, status);
     } else {
-        if (V.N == 5 && J.lists && J.n >= kSplitMin) {  // large batch: fine and coarse requests apart
+        if (split) {  // large batch: fine and coarse requests apart (listed above)
             uint32_t *counts = J.counter + 16, *lists = J.lists;
             const uint32_t smem_m = rb_layout_part<uint8_t>(V.N, 1).total, smem_c = rb_layout_part<uint8_t>(V.N, 2).total;
             e = func_attr((const void *)rebuild_listed<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b);
@@ -1897,7 +1927,6 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
             int per_l = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, lk, (int)lt, smem_l) != cudaSuccess || per_l < 1)
                 per_l = 1;
-            split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, lists, counts);
             ProfScope ps("rebuild", st);
             if (S.compact_nodes == 0) {  // every LOD 0 request in the full layout: its list goes there directly
                 rebuild_listed<uint8_t><<<min(J.n, 4 * g), kRbThreads, smem_b, st>>>(V, J, out, out_off, status, lists,
