@@ -41,7 +41,6 @@ struct RecJob {
                         // rebuild split; [24..25] oversized LOD 0 requests and their work counter
     uint32_t *lists;    // 4 x n request indices (the rebuild split's three lists, then oversized LOD 0 requests)
     uint32_t compact_nodes;  // 32^3 bricks: LOD 0 requests with more non-constant L1 nodes take the full layout
-    uint32_t listed_q;       // 1: the rANS kernel takes its streams from the split's lists (filled before it)
 };
 
 // Device view of a compressed volume (passed to kernels by value).

@@ -197,7 +197,7 @@ __device__ uint32_t decode_stream(const uint16_t *w, uint32_t n_words, uint32_t 
     return ok ? otail : (otail | kRecBad);
 }
 
-template <uint32_t kWin>
+template <uint32_t kWin, bool kListed = false>  // kListed: a large mixed-LOD slice, its streams taken from the class lists
 __global__ void __launch_bounds__(kRecWarps * 32, 6) rans_records(VolDev V, RecJob J) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *lut_s = (uint32_t *)smem;
@@ -210,19 +210,19 @@ __global__ void __launch_bounds__(kRecWarps * 32, 6) rans_records(VolDev V, RecJ
     // of the LOD 1 requests, then those of the coarser ones, so that the long streams go first and no warp
     // draws the leaf stream of a request that has none to decode
     uint32_t c0 = J.n, c1 = 0, c2 = 0;
-    if (J.listed_q) {
+    if (kListed) {
         c0 = J.counter[16];
         c1 = J.counter[17];
         c2 = J.counter[18];
     }
-    const uint32_t q_end = J.listed_q ? 2 * c0 + c1 + c2 : 2 * J.n;
+    const uint32_t q_end = kListed ? 2 * c0 + c1 + c2 : 2 * J.n;
     for (;;) {
         uint32_t q = 0;
         if (lane == 0) q = atomicAdd(J.counter, 1u);
         q = __shfl_sync(kFull, q, 0);
         if (q >= q_end) break;
         uint32_t i = q >> 1, s = q & 1u;
-        if (J.listed_q) {
+        if (kListed) {
             if (q < 2 * c0) {
                 i = J.lists[q >> 1];
             } else {
@@ -1856,7 +1856,11 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     // bricks of 16^3 and smaller: streams of a few states, decoded several to a warp
     const bool packed = V.N <= 4;
     const uint32_t ring = S.ring_words == 128 || S.ring_words == 512 ? S.ring_words : 256u;
-    auto rk = ring == 128 ? rans_records<128> : ring == 512 ? rans_records<512> : rans_records<256>;
+    const bool split = !packed && V.N == 5 && max_pal <= RbTraits<uint8_t>::kSent && J.lists && J.n >= kSplitMin;
+    auto rk = split ? (ring == 128   ? rans_records<128, true>
+                       : ring == 512 ? rans_records<512, true>
+                                     : rans_records<256, true>)
+                    : (ring == 128 ? rans_records<128> : ring == 512 ? rans_records<512> : rans_records<256>);
     const uint32_t smem_a = packed ? rans_records_packed_smem_bytes() : rans_records_smem_bytes(ring);
     cudaError_t e = func_attr((const void *)(packed ? rans_records_packed : rk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_a);
@@ -1868,22 +1872,19 @@ cudaError_t launch_decode_slice(const VolDev &V, uint32_t max_pal, const RecJob 
     e = cudaMemsetAsync(J.counter, 0, 128, st);
     if (e != cudaSuccess) return e;
     const bool wide = max_pal > RbTraits<uint8_t>::kSent;  // uint16 palette indices
-    // large mixed-LOD slices of 32^3 bricks: the requests listed by LOD class first, for the rANS kernel's queue
-    // and for the rebuild kernels of the classes
-    const bool split = !packed && V.N == 5 && !wide && J.lists && J.n >= kSplitMin;
-    RecJob Jq = J;
+    // large mixed-LOD slices of 32^3 bricks (split): the requests listed by LOD class first, for the rANS
+    // kernel's queue and for the rebuild kernels of the classes
     if (split) {
         split_lods<<<(J.n + 255) / 256, 256, 0, st>>>(J, V.N, J.lists, J.counter + 16);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        Jq.listed_q = 1;
     }
     const uint32_t need = (2 * J.n + kRecWarps - 1) / kRecWarps;
     const uint32_t rec_blocks = max(1u, min(S.rec_per_sm, 6u)) * g;
     {
         ProfScope ps("rans_records", st);
         if (packed) rans_records_packed<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
-        else rk<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, Jq);
+        else rk<<<min(rec_blocks, need), kRecWarps * 32, smem_a, st>>>(V, J);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
