@@ -80,3 +80,14 @@ def test_noalloc_encoder_rejects_a_brick_count_that_would_wrap_without_gpu():
     assert rc == csgv.CSGV_ERR_INVALID_ARG
     msg = L.csgv_last_error()
     assert b"bricks of 2^3" in msg and b"at most" in msg, msg
+
+
+def test_request_layout_packs_requests_back_to_back():
+    import numpy as np
+    lods = np.array([0, 5, 1, 5, 2, 0], np.uint8)
+    off, total = csgv.request_layout(32, lods)
+    sizes = [32768, 1, 4096, 1, 512, 32768]
+    assert off.dtype == np.int64 and off.tolist() == [0, 32768, 32769, 36865, 36866, 37378]
+    assert total == sum(sizes)
+    off0, total0 = csgv.request_layout(16, np.zeros(0, np.uint8))
+    assert len(off0) == 0 and total0 == 0
